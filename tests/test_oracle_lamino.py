@@ -1,0 +1,135 @@
+"""Pins for the oracle's laminographic operator L (and L-hat, adjoints).
+
+* P1: L-hat against the direct-sum definition sum_r u(r) exp(-2 pi i xi.r)
+  on small volumes; error falls with m and reaches rounding at m = 12.
+* P2: adjoint identities for L and for every stage.
+* P3: a Gaussian blob, whose projection has a closed form (Fourier slice
+  theorem), pins phi, theta, signs and the 1/(h w) normalisation.
+* P4: phi = 0 reduces to tomography about z (sums along y at theta = 0 and
+  along x at theta = pi/2).
+"""
+import numpy as np
+import pytest
+
+from oracle import lamino
+from oracle.lamino import Geometry, centred
+
+
+def _rel(a, b):
+    return np.linalg.norm((a - b).ravel()) / np.linalg.norm(np.ravel(b))
+
+
+def _geom(n1=16, n0=16, n2=16, h=16, w=16, T=16, phi=0.5, m=4, seed=0):
+    rng = np.random.default_rng(seed)
+    return Geometry(n1=n1, n0=n0, n2=n2, h=h, w=w, theta=rng.uniform(0, 2 * np.pi, T), phi=phi, m=m)
+
+
+@pytest.mark.parametrize("dims", [(16, 16, 16, 16, 16, 16), (12, 8, 12, 10, 14, 5)])
+def test_lhat_matches_direct_nudft(dims):
+    n1, n0, n2, h, w, T = dims
+    rng = np.random.default_rng(10)
+    u = rng.standard_normal((n1, n0, n2))
+    errs = []
+    for m in (2, 4, 6, 8, 12):
+        g = _geom(n1, n0, n2, h, w, T, phi=0.61, m=m)
+        errs.append(_rel(lamino.lhat(u, g), lamino.lhat_exact(u, g)))
+    assert all(a > b for a, b in zip(errs, errs[1:]))
+    assert errs[1] < 2e-4
+    assert errs[-1] < 1e-10
+
+
+def test_lhat_direct_sum_rotation_and_tilt_conventions():
+    # at phi = 0 the exact slice at theta = 0 is the DFT of the sum over y in
+    # (x, z): independent of the operator code
+    rng = np.random.default_rng(11)
+    n = 8
+    u = rng.standard_normal((n, n, n))
+    g = Geometry(n1=n, n0=n, n2=n, h=n, w=n, theta=np.array([0.0]), phi=0.0)
+    s = u.sum(axis=2)                                     # [x, z]
+    k = np.arange(n)
+    ph = np.exp(2j * np.pi * k * (n // 2) / n)            # centring phase
+    ref = (np.fft.fft2(s) * ph[:, None] * ph[None, :]).T   # [kz, kx]
+    ref = np.roll(np.roll(ref, n // 2, 0), n // 2, 1)      # frequency order -n/2..n/2-1
+    assert _rel(lamino.lhat_exact(u, g)[0], ref) < 1e-12
+
+
+def test_adjoint_identity_full_operator():
+    g = _geom(n1=12, n0=8, n2=12, h=10, w=14, T=7, phi=0.4)
+    rng = np.random.default_rng(12)
+    u = rng.standard_normal((12, 8, 12))
+    v = rng.standard_normal((7, 10, 14)) + 1j * rng.standard_normal((7, 10, 14))
+    Lu = lamino.lam_forward(u, g)
+    lhs = np.vdot(Lu, v).real
+    rhs = np.vdot(u, lamino.lam_adjoint(v, g))
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(Lu) * np.linalg.norm(v)
+    Lh = lamino.lhat(u, g)
+    lhs = np.vdot(Lh, v).real
+    rhs = np.vdot(u, lamino.lhat_adj(v, g))
+    assert abs(lhs - rhs) <= 1e-12 * np.linalg.norm(Lh) * np.linalg.norm(v)
+
+
+def test_adjoint_identity_per_stage():
+    g = _geom(n1=12, n0=8, n2=12, h=10, w=14, T=7, phi=0.4)
+    rng = np.random.default_rng(13)
+    c = lambda *s: rng.standard_normal(s) + 1j * rng.standard_normal(s)
+    a, b = c(12, 8, 12), c(12, 10, 12)
+    assert abs(np.vdot(lamino.f_u1d(a, g), b) - np.vdot(a, lamino.f_u1d_adj(b, g))) < 1e-12 * 1e3
+    a, b = c(12, 10, 12), c(7, 10, 14)
+    assert abs(np.vdot(lamino.f_u2d(a, g), b) - np.vdot(a, lamino.f_u2d_adj(b, g))) < 1e-12 * 1e4
+    a, b = c(7, 10, 14), c(7, 10, 14)
+    assert abs(np.vdot(lamino.f_2d_inv(a), b) - np.vdot(a, lamino.f_2d_inv_adj(b))) < 1e-12 * 1e2
+
+
+def test_f2d_cancels_f2d_inverse():
+    rng = np.random.default_rng(14)
+    x = rng.standard_normal((3, 10, 14)) + 1j * rng.standard_normal((3, 10, 14))
+    assert _rel(lamino.f_2d(lamino.f_2d_inv(x)), x) < 1e-13
+    assert _rel(lamino.f_2d_inv(lamino.f_2d(x)), x) < 1e-13
+
+
+def _blob_case(m):
+    n, nz, h, w, T = 48, 48, 48, 48, 6
+    phi = np.deg2rad(30.0)
+    th = np.linspace(0, 2 * np.pi, T, endpoint=False) + 0.3
+    c = np.array([3.3, -2.1, 1.7])
+    s = 2.5
+    rx = centred(n)[:, None, None]
+    rz = centred(nz)[None, :, None]
+    ry = centred(n)[None, None, :]
+    u = np.exp(-((rx - c[0]) ** 2 + (ry - c[1]) ** 2 + (rz - c[2]) ** 2) / (2 * s * s))
+    g = Geometry(n1=n, n0=nz, n2=n, h=h, w=w, theta=th, phi=phi, m=m)
+    # closed form: the line integral of the blob along the beam b = e_u x e_v
+    # is sqrt(2 pi) s exp(-((s_det - c.e_u)^2 + (t_det - c.e_v)^2) / (2 s^2))
+    thc = th[:, None, None]
+    cu = c[0] * np.cos(thc) + c[1] * np.sin(thc)
+    cv = c[0] * np.sin(phi) * np.sin(thc) - c[1] * np.sin(phi) * np.cos(thc) + c[2] * np.cos(phi)
+    S = centred(w)[None, None, :]
+    Tt = centred(h)[None, :, None]
+    proj = np.sqrt(2 * np.pi) * s * np.exp(-((S - cu) ** 2 + (Tt - cv) ** 2) / (2 * s * s))
+    return lamino.lam_forward(u, g), proj
+
+
+def test_gaussian_blob_projection_closed_form():
+    d4, proj = _blob_case(4)
+    assert _rel(d4, proj) < 1e-4
+    d10, proj = _blob_case(10)
+    assert _rel(d10, proj) < 1e-10
+
+
+def test_phi_zero_is_tomography():
+    n = 16
+    u = np.zeros((n, n, n))
+    u[3:9, 5:12, 2:13] = 1.0                      # axis-aligned box [x, z, y]
+    u[10:14, 2:6, 4:7] = 0.5
+    th = np.array([0.0, np.pi / 2])
+    g = Geometry(n1=n, n0=n, n2=n, h=n, w=n, theta=th, phi=0.0, m=12)
+    d = lamino.lam_forward(u, g)
+    # theta = 0: beam along -y, detector u <-> x, v <-> z
+    assert _rel(d[0], u.sum(axis=2).T) < 1e-10
+    # theta = pi/2: beam along +x, detector u <-> y, v <-> z
+    assert _rel(d[1], u.sum(axis=0)) < 1e-10
+
+
+def test_accuracy_metric():
+    a = np.array([3.0, 4.0])
+    assert lamino.accuracy_error(a, a * 0.9) == pytest.approx(0.1)
