@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Benchmark of ADMM-TV laminography on B300: seconds per ADMM-TV iteration
+(FP32, 4 CG steps per iteration, L-hat / L-hat^H in the Algorithm 2 form) and
+the L-hat + L-hat^H bandwidth against the HBM roofline, at 1024^3.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Workload (``large``): volume 1024 x 1024 x 1024 FP32, 1024 angles uniform on
+[0, 2 pi), detector 1024 x 1024, tilt phi = 30 deg, seeded ellipsoid +
+thin-layer circuit phantom, data = L u + 1 % Gaussian noise, alpha = 1e-3,
+rho = 0.5 (adaptive), oversampling 2, Gaussian half-width 4.  A step is one
+outer ADMM-TV iteration (LSP with 4 CG steps, RSP, multiplier and penalty
+updates) replayed as a CUDA graph.  All inputs are synthetic; working sets are
+tens of GB, far larger than L2, so no explicit L2 flush is needed.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (one kv plane of the 2D stage, four x-slabs of the z stage) and
+scales it to seconds per iteration.  Under torchrun (N > 1) every rank runs an
+independent replica (weak scaling, no data-path collective); only the timing
+is reduced across ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALPHA, RHO, N_INNER, PHI_DEG = 1e-3, 0.5, 4, 30.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--size", type=int, default=1024, help="n = nz = h = w = n_theta")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-f64", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(n):
+    return (f"large: ADMM-TV {n}^3 FP32, {n} angles on [0,2pi), detector {n}x{n}, phi=30deg, "
+            f"ellipsoid+circuit phantom, 1% noise, alpha=1e-3, rho=0.5 adaptive, 4 CG steps/iter")
+
+
+# ---------------------------------------------------------------------------
+# algorithmic traffic (stage-boundary tensors; f32 volume, c64 spectra)
+# ---------------------------------------------------------------------------
+
+def lhat_bytes(n, nz, h, w, T):
+    """L-hat: read u (4 B/voxel), write + read u1 (8 B per n^2 h point each),
+    write d_hat (8 B per T h w point).  L-hat^H moves the same bytes."""
+    return 4 * n * n * nz + 16 * n * n * h + 8 * T * h * w
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r for r in csv.reader(io.StringIO(getattr(self, "out", ""))) if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip().lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# oracle sample (cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(n, nz, h, w, T, n_planes=1, n_slabs=4):
+    """Time the FP64 oracle on a sample of the workload and scale to s/iter.
+
+    One ADMM iteration of the oracle's Algorithm 2 LSP applies L-hat twice
+    (forward pass on u, line search on p) and L-hat^H once per CG step, 4 CG
+    steps.  Timed: the 2D stage forward and transpose on n_planes kv planes,
+    the z stage forward and transpose on n_slabs x-slabs; scaled by h / n_planes
+    and n / n_slabs.  TV/elementwise terms are not included."""
+    from oracle import lamino as olam
+    from oracle import usfft
+    from paper_2511_01893_b300 import inputs
+    theta = inputs.angles(T)
+    g = olam.Geometry(n1=n, n0=nz, n2=n, h=h, w=w, theta=theta, phi=np.deg2rad(PHI_DEG))
+    rng = np.random.default_rng(0)
+    xi_x, xi_y, xi_z = olam.slice_frequencies(g)
+    t2f = t2a = 0.0
+    for k in range(n_planes):
+        kv = (h // 2 + 7 * k) % h
+        plane = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+        vals = rng.standard_normal((T, w)) + 1j * rng.standard_normal((T, w))
+        t0 = time.perf_counter()
+        usfft.usfft2d_type2(plane, xi_x[:, kv, :], xi_y[:, kv, :])
+        t1 = time.perf_counter()
+        usfft.usfft2d_type1(vals, xi_x[:, kv, :], xi_y[:, kv, :], n, n)
+        t2 = time.perf_counter()
+        t2f += t1 - t0
+        t2a += t2 - t1
+    slab = rng.standard_normal((n_slabs, nz, n))
+    t0 = time.perf_counter()
+    u1 = usfft.usfft1d_type2(slab, xi_z, axis=1)
+    t1 = time.perf_counter()
+    usfft.usfft1d_type1(u1, xi_z, nz, axis=1)
+    t2 = time.perf_counter()
+    fwd = t2f / n_planes * h + (t1 - t0) / n_slabs * n
+    adj = t2a / n_planes * h + (t2 - t1) / n_slabs * n
+    s_per_iter = N_INNER * (2 * fwd + adj)
+    sample = (f"FP64 oracle: F_u2D and its transpose on {n_planes} of {h} kv planes and F_u1D and its "
+              f"transpose on {n_slabs} of {n} x-slabs of the {n}^3 problem, scaled to one ADMM iteration "
+              f"(4 CG steps x (2 L-hat + 1 L-hat^H)); TV/elementwise work not included")
+    return s_per_iter, sample, (t2f + t2a + (t2 - t0))
+
+
+def cores_used():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        nt = max([i.get("num_threads", 1) for i in info] or [1])
+    except Exception:
+        nt = 1
+    return {"threads": int(nt), "host_cores": os.cpu_count()}
+
+
+# ---------------------------------------------------------------------------
+# reference arm
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    n = args.size
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, sample, _ = oracle_sample(n, n, n, n, n, n_planes=1, n_slabs=2)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    c = cores_used()
+    line = {
+        "impl": "reference", "metric": "ADMM-TV seconds per iteration", "value": value, "unit": "s/iter",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(n), "precision": "FP64 CPU oracle"},
+        "cpu_baseline": {"value": value, "unit": "s/iter", "cores": c["threads"], "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "s/iter", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2511_01893_b300 import inputs
+    from paper_2511_01893_b300 import lamino as glam
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n = args.size
+    nz = h = w = T = n
+    phi = np.deg2rad(PHI_DEG)
+    theta = inputs.angles(T)
+
+    # ---- inputs (synthetic, resident in HBM) --------------------------------
+    u_true = inputs.ellipsoid_circuit_phantom(n, nz, seed=1238, device=dev, dtype=torch.float32)
+    plan = glam.Plan(n, nz, h, w, theta, phi, prec="f32", device=dev)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        d = plan.forward(u_true)
+        sigma = 0.01 * d.real.abs().max().item()
+        gen = torch.Generator(device=dev).manual_seed(99 + rank)
+        d.real.add_(torch.randn(d.shape, generator=gen, device=dev, dtype=torch.float32), alpha=sigma)
+    stream.synchronize()
+    del u_true
+    torch.cuda.empty_cache()
+
+    admm = glam.Admm(plan)
+    with torch.cuda.stream(stream):
+        admm.init(d, ALPHA, RHO, N_INNER, adapt_rho=True)
+        admm.run(args.warmup, graph=True)
+    stream.synchronize()
+    launches_per_step = admm.graph_kernels()
+
+    # ---- timed ADMM iterations ------------------------------------------------
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        with torch.cuda.stream(stream):
+            ev0.record(stream)
+            admm.run(args.steps, graph=True)
+            ev1.record(stream)
+        stream.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    t_admm = ev0.elapsed_time(ev1) / 1e3
+    if world > 1:
+        tt = torch.tensor([t_admm], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_admm = tt.item()
+    s_per_iter = t_admm / (args.steps * world)
+    status = admm.status()
+    sc = admm.scalars()
+
+    # ---- L-hat + L-hat^H operator pair (bandwidth vs HBM roofline) ----------
+    reps = 3
+    p = admm.u.clone()
+    out_c = torch.empty(plan.data_shape, dtype=plan.cdtype, device=dev)
+    out_r = torch.empty(plan.vol_shape, dtype=plan.rdtype, device=dev)
+    with torch.cuda.stream(stream):
+        plan.forward_hat(p, out=out_c)
+        plan.adjoint_hat(out_c, out=out_r)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps + 1)]
+        evs[0].record(stream)
+        for r in range(reps):
+            plan.forward_hat(p, out=out_c)
+            evs[2 * r + 1].record(stream)
+            plan.adjoint_hat(out_c, out=out_r)
+            evs[2 * r + 2].record(stream)
+    stream.synchronize()
+    t_fwd = statistics.median([evs[2 * r].elapsed_time(evs[2 * r + 1]) / 1e3 for r in range(reps)])
+    t_adj = statistics.median([evs[2 * r + 1].elapsed_time(evs[2 * r + 2]) / 1e3 for r in range(reps)])
+    op_bytes = 2 * lhat_bytes(n, nz, h, w, T)
+    achieved = op_bytes / (t_fwd + t_adj) / 1e9
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak, peak_src = json.load(open(peaks_path))["hbm_gbs"], "measured"
+    else:
+        peak, peak_src = 6400.0, "fallback"
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        tj = json.load(open(prof))
+        if tj.get("size") == n:
+            traffic = tj.get("lhat_pair_dram_bytes")
+    del p, out_c, out_r
+
+    line = {
+        "metric": "ADMM-TV seconds per iteration", "value": s_per_iter, "unit": "s/iter", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_admm / args.steps * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(n), "n": n, "nz": nz, "det_h": h, "det_w": w, "n_theta": T,
+                   "phi_deg": PHI_DEG, "n_inner": N_INNER, "graph": True, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (state ~80 GB)"},
+        "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak,
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "kernel": "L-hat + L-hat^H operator pair (all stage kernels)",
+                     "algorithmic_bytes": op_bytes, "t_lhat_s": t_fwd, "t_lhat_adj_s": t_adj},
+        "gpu_launches": launches_per_step * args.steps,
+        "admm": {"status": status, "objective": sc["objective"], "rho": sc["rho"], "iters_done": sc["iter"]},
+    }
+
+    # ---- FP64 comparator at 256^3 (the precision workload) ------------------
+    if not args.no_f64 and rank == 0:
+        line["f64_comparison"] = f64_comparison(glam, inputs, dev, stream)
+
+    # ---- end to end through the one-call API (host data in, host volume out) -
+    del admm
+    torch.cuda.empty_cache()
+    if not args.no_e2e:
+        d_host = torch.empty(d.shape, dtype=torch.float32, pin_memory=True)
+        d_host.copy_(d.real)
+        del d
+        torch.cuda.empty_cache()
+        t0 = time.perf_counter()
+        u_host = glam.reconstruct(d_host.numpy(), theta, phi, n, nz, args.steps, ALPHA, RHO)
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_e2e = tt.item()
+        line["e2e"] = {"value": t_e2e / (args.steps * world), "unit": "s/iter",
+                       "h2d_bytes_per_step": int(d_host.numel() * 4 // args.steps),
+                       "d2h_bytes_per_step": int(u_host.size * 4 // args.steps),
+                       "api": "reconstruct() one call, K iterations, host data/volume, includes plan + allocation"}
+    line["clocks"] = clk.summary()
+
+    # ---- oracle on the host cores (rank 0, N = 1) ----------------------------
+    if not args.no_cpu and rank == 0 and world == 1:
+        v, sample, spent = oracle_sample(n, nz, h, w, T)
+        c = cores_used()
+        line["cpu_baseline"] = {"value": v, "unit": "s/iter", "cores": c["threads"], "kind": "oracle",
+                                "sample": sample, "host_cores": c["host_cores"], "sample_seconds": spent}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0 if status == 0 else 1
+
+
+def f64_comparison(glam, inputs, dev, stream, n=256, iters=4):
+    """FP32 (graph) vs plain FP64 GPU path on the 256^3 precision workload."""
+    import torch
+    theta = inputs.angles(n)
+    phi = np.deg2rad(PHI_DEG)
+    u = inputs.ellipsoid_phantom(n, n, 12, seed=1235, device=dev, dtype=torch.float64)
+    out = {"workload": f"precision: {n}^3, {n} angles, detector {n}x{n}, phi=30deg, ellipsoid phantom, "
+                       f"1% noise, {iters} ADMM-TV iterations"}
+    p64 = glam.Plan(n, n, n, n, theta, phi, prec="f64", device=dev)
+    with torch.cuda.stream(stream):
+        d = p64.forward(u)
+        sigma = 0.01 * d.real.abs().max().item()
+        gen = torch.Generator(device=dev).manual_seed(7)
+        d.real.add_(torch.randn(d.shape, generator=gen, device=dev, dtype=torch.float64), alpha=sigma)
+    stream.synchronize()
+    res = {}
+    for prec, plan in (("f64", p64), ("f32", glam.Plan(n, n, n, n, theta, phi, prec="f32", device=dev))):
+        a = glam.Admm(plan)
+        with torch.cuda.stream(stream):
+            a.init(d, ALPHA, RHO, N_INNER)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            a.run(iters, graph=(prec == "f32"))
+            e1.record(stream)
+        stream.synchronize()
+        res[prec] = (e0.elapsed_time(e1) / 1e3 / iters, a.u.double().clone())
+        del a
+    err = (torch.linalg.vector_norm(res["f32"][1] - res["f64"][1])
+           / torch.linalg.vector_norm(res["f64"][1])).item()
+    out.update({"f32_graph_s_per_iter": res["f32"][0], "f64_plain_s_per_iter": res["f64"][0],
+                "speedup": res["f64"][0] / res["f32"][0], "rel_l2_f32_vs_f64": err})
+    return out
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

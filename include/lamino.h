@@ -1,0 +1,184 @@
+/*
+ * lamino.h - C ABI of the B300 laminography library (liblamino.so).
+ *
+ * The library computes the Fourier-based laminographic forward operator L,
+ * its adjoint, the total-variation pieces and ADMM-TV reconstruction of
+ * Ma et al., "mLR: Scalable Laminography Reconstruction based on
+ * Memoization" (SC'25): Eq. 1 (objective), Section 2 (operator shapes and
+ * Algorithm 1, LSP), Algorithm 2 and Section 4.2 (operation cancellation
+ * and the fused subtraction).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Sizes.  n = n1 = n2 (lateral, x and y), nz = n0 (z, the rotation axis),
+ *   det_h = h and det_w = w (detector rows and columns), n_theta = T.  All of
+ *   n, nz, h, w must be powers of two in [8, 2048]; T >= 1.
+ * Layouts (row-major, last index fastest):
+ *   volume u       real      [n][nz][n]   = u[x][z][y]
+ *   data d, d_hat  complex   [T][h][w]    = d[theta][v][u]   (interleaved re, im)
+ *   gradient field real      [3][n][nz][n] (component 0: x, 1: z, 2: y)
+ * Precision.  A plan is created for LAM_F32 (float / float2 arrays) or
+ *   LAM_F64 (double / double2 arrays); every array passed to it uses that type.
+ * Geometry.  theta[k] is the k-th rotation angle in radians; phi is the beam's
+ *   elevation above the sample plane in radians, 0 <= phi < pi/2 (phi = 0 is
+ *   tomography about z).  Slice frequencies are
+ *     xi = (ku/w) (cos th, sin th, 0) + (kv/h) (sin phi sin th, -sin phi cos th, cos phi),
+ *   ku in [-w/2, w/2), kv in [-h/2, h/2); coordinates are centred.
+ * Pointers.  Every array argument is a device pointer owned by the caller
+ *   (reconstruct() alone also accepts host pointers).  Nothing on the
+ *   operator or ADMM path allocates: scratch comes from the caller's
+ *   workspace (lam_workspace_bytes) and ADMM state (admm_state_bytes).
+ *   The plan owns only its geometry tables (allocated by lam_plan_create).
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Calls are asynchronous on it; a call returns once its kernels
+ *   are enqueued.
+ * Errors.  Every call returns LAM_OK or a negative lam_status; arguments are
+ *   checked on the host before anything is enqueued (a failed check enqueues
+ *   nothing).  lam_last_error() gives a message for the calling thread.
+ *   Device-side conditions (non-finite ADMM scalars) set a status word in the
+ *   ADMM state that admm_status() reads.  No C++ exception crosses the ABI.
+ */
+#ifndef LAMINO_H
+#define LAMINO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LAM_OK = 0,
+    LAM_EINVAL = -1,       /* bad argument (size, pointer, angle, precision) */
+    LAM_ENOMEM = -2,       /* plan tables could not be allocated */
+    LAM_ECUDA = -3,        /* a CUDA call or kernel launch failed */
+    LAM_ETIMEOUT = -4,     /* reserved: a bounded device wait gave up */
+    LAM_ENAN = -5,         /* non-finite value in an ADMM reduction */
+    LAM_EUNSUPPORTED = -6  /* size or option outside what the kernels support */
+} lam_status;
+
+typedef enum { LAM_F32 = 0, LAM_F64 = 1 } lam_prec;
+
+typedef struct lam_plan lam_plan;
+
+/* Create a plan for one geometry.  oversample must be 2 (the padded grids
+ * are 2nz, 2n, 2n); half_width m in [2, 8] sets 2m Gaussian taps per
+ * dimension.  theta is a host array of n_theta angles (copied).  The plan
+ * uploads its FP64-computed tables (deapodisation, z-gather weights,
+ * per-angle slice coordinates, twiddles) to the current device. */
+lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, int n_theta,
+                           const double* theta, double phi, int oversample, int half_width,
+                           int prec);
+lam_status lam_plan_destroy(lam_plan* plan);
+
+/* Bytes of device scratch the operator calls need (ws argument).  The
+ * workspace holds the z-transformed volume u1[h][n][n] (complex) and a batch
+ * of padded planes.  Alignment: 256 bytes. */
+size_t lam_workspace_bytes(const lam_plan* plan);
+
+/* L (Section 2, Algorithm 1 forward pass: F*_2D F_u2D F_u1D):
+ *   d[th][v][u] = 1/(h w) sum_{kv,ku} u^(xi(th,kv,ku)) exp(+2 pi i (ku s/w + kv t/h)),
+ * u^ evaluated by the Gaussian USFFT (oversampling 2, half-width m).
+ * u: real [n][nz][n] (read); d: complex [T][h][w] (written). */
+lam_status lam_forward(const lam_plan* plan, const void* u, void* d, void* ws, void* stream);
+
+/* Re L^H (the transpose of lam_forward under Re<.,.>; F*_u1D F*_u2D F_2D/(hw)).
+ * d: complex [T][h][w] (read); u: real [n][nz][n] (written). */
+lam_status lam_adjoint(const lam_plan* plan, const void* d, void* u, void* ws, void* stream);
+
+/* L-hat = F_u2D F_u1D (Algorithm 2 forward pass, no F*_2D).  If sub is not
+ * NULL the output is L-hat u - sub (the subtraction fused into F_u2D,
+ * Section 4.2).  u real [n][nz][n]; d_hat, sub complex [T][h][w]. */
+lam_status lam_forward_hat(const lam_plan* plan, const void* u, void* d_hat, const void* sub,
+                           void* ws, void* stream);
+
+/* Re L-hat^H = Re F*_u1D F*_u2D (Algorithm 2 adjoint pass, no F_2D).
+ * d_hat complex [T][h][w] (read); u real [n][nz][n] (written). */
+lam_status lam_adjoint_hat(const lam_plan* plan, const void* d_hat, void* u, void* ws, void* stream);
+
+/* Per-angle centred 2D DFT on the h x w grid (Section 4.2):
+ *   inverse = 0: F_2D, out = sum in exp(-2 pi i (ku s/w + kv t/h))   (unnormalised)
+ *   inverse = 1: F*_2D, out = 1/(h w) sum in exp(+2 pi i (...))
+ * in, out complex [T][h][w]; in == out is allowed. */
+lam_status lam_fft2d(const lam_plan* plan, const void* in, void* out, int inverse, void* stream);
+
+/* Forward-difference gradient with a zero difference at the last index.
+ * u real [n][nz][n] (read); g real [3][n][nz][n] (written). */
+lam_status tv_grad(const lam_plan* plan, const void* u, void* g, void* stream);
+
+/* div = -grad^T (exact negative transpose of tv_grad).
+ * g real [3][n][nz][n] (read); u real [n][nz][n] (written). */
+lam_status tv_div(const lam_plan* plan, const void* g, void* u, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * ADMM-TV (Section 2: LSP, RSP, multiplier and penalty updates; LSP in the
+ * Algorithm 2 form).  The state is one caller-allocated device buffer; the
+ * library lays it out (u, psi, lambda, CG vectors, d_hat, residual, FP64
+ * scalars and an iteration history) and never allocates.
+ * ------------------------------------------------------------------------- */
+
+/* Scalars readable with admm_read_scalars (indices into the returned array). */
+enum {
+    LAM_SC_RHO = 0,        /* current penalty rho */
+    LAM_SC_ALPHA = 1,      /* TV weight alpha */
+    LAM_SC_OBJECTIVE = 2,  /* 1/2 ||L u - d||^2 + alpha TV(u) after the last step */
+    LAM_SC_RESID_R = 3,    /* primal residual r = ||grad u - psi|| */
+    LAM_SC_RESID_S = 4,    /* dual residual s = rho ||div(psi - psi_old)|| */
+    LAM_SC_ITER = 5,       /* outer iterations done */
+    LAM_SC_DATA2 = 6,      /* ||L u - d||^2 */
+    LAM_SC_TV = 7,         /* TV(u) */
+    LAM_SC_STATUS = 8,     /* 0, or LAM_ENAN once a reduction was non-finite */
+    LAM_NSCALARS = 16
+};
+
+/* Bytes of the ADMM state buffer (256-byte aligned pieces). */
+lam_status admm_state_bytes(const lam_plan* plan, size_t* bytes);
+
+/* Initialise: u = psi = lambda = 0, rho, alpha, d_hat = F_2D d, residual =
+ * -d_hat.  adapt_rho != 0 enables residual balancing (mu = 10, factor 2).
+ * d: complex [T][h][w] device array (read).  n_inner >= 1 CG steps per LSP. */
+lam_status admm_init(const lam_plan* plan, void* state, const void* d, double alpha, double rho,
+                     int n_inner, int adapt_rho, void* ws, void* stream);
+
+/* One outer ADMM iteration: LSP (n_inner CG steps, 1 L-hat and 1 L-hat^H
+ * each), RSP shrinkage, multiplier update, residuals, penalty update and the
+ * objective.  All scalars stay on the device; no host synchronisation. */
+lam_status admm_step(const lam_plan* plan, void* state, void* ws, void* stream);
+
+/* iters outer iterations.  use_graph != 0 captures one iteration into a CUDA
+ * graph (on first use for this (state, ws) pair; cached in the plan) and
+ * replays it; `stream` must then not be the legacy default stream. */
+lam_status admm_run(const lam_plan* plan, void* state, void* ws, int iters, int use_graph,
+                    void* stream);
+
+/* Device pointer to the volume u inside the state (real [n][nz][n]). */
+void* admm_u(const lam_plan* plan, void* state);
+
+/* Copy LAM_NSCALARS doubles to host memory (synchronises `stream`). */
+lam_status admm_read_scalars(const lam_plan* plan, const void* state, double* out, void* stream);
+
+/* Copy the history of the first `count` outer iterations to host memory as
+ * [count][4] doubles (objective, rho used, r, s); synchronises `stream`.
+ * The history holds up to 4096 iterations. */
+lam_status admm_read_history(const lam_plan* plan, const void* state, int count, double* out,
+                             void* stream);
+
+/* LAM_OK, or the status word of the state (LAM_ENAN); synchronises. */
+lam_status admm_status(const lam_plan* plan, const void* state, void* stream);
+
+/* One-call reconstruction (FP32): iters outer ADMM-TV iterations with 4 CG
+ * steps each from real data [n_theta][det_h][det_w] (host or device memory),
+ * alpha, rho (adaptive).  Allocates and frees its own plan, workspace and
+ * state; u_out (host or device) receives u[n][nz][n].  Synchronous. */
+lam_status reconstruct(const float* data, const double* theta, double phi, int n, int nz,
+                       int det_h, int det_w, int n_theta, int iters, double alpha, double rho,
+                       float* u_out);
+
+/* Thread-local message for the last non-OK status returned on this thread. */
+const char* lam_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAMINO_H */

@@ -1,0 +1,44 @@
+/*
+ * lamino_stages.h - per-stage entry points of liblamino.so, for stage-level
+ * parity tests and profiling.  Same conventions as lamino.h; u1 is the
+ * z-transformed volume stored plane-major as complex [h][n][n]
+ * (u1[kv][x][y]), the layout the plane stage reads.
+ */
+#ifndef LAMINO_STAGES_H
+#define LAMINO_STAGES_H
+
+#include "lamino.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* F_u1D (Section 2): u real [n][nz][n] -> u1 complex [h][n][n]. */
+lam_status lamx_u1d_fwd(const lam_plan* plan, const void* u, void* u1, void* stream);
+
+/* Re F*_u1D (transpose of lamx_u1d_fwd, real part): u1 -> u. */
+lam_status lamx_u1d_adj(const lam_plan* plan, const void* u1, void* u, void* stream);
+
+/* F_u2D (Section 2): u1 complex [h][n][n] -> d_hat complex [T][h][w]; if sub
+ * is not NULL the output is F_u2D u1 - sub (Section 4.2's fused
+ * subtraction).  Uses the plane part of ws. */
+lam_status lamx_u2d_fwd(const lam_plan* plan, const void* u1, void* d_hat, const void* sub, void* ws,
+                        void* stream);
+
+/* F*_u2D (transpose of lamx_u2d_fwd): d_hat -> u1.  Uses the plane part of ws. */
+lam_status lamx_u2d_adj(const lam_plan* plan, const void* d_hat, void* u1, void* ws, void* stream);
+
+/* Launch shapes chosen by the plan, for diagnostics: out[0..count) receives
+ * TY (z forward), TY (z transpose), rows per block, columns per block,
+ * scatter tile side, tile images, planes per batch, jmin, jmax. */
+lam_status lamx_plan_info(const lam_plan* plan, int* out, int count);
+
+/* Kernel nodes in the CUDA graph admm_run captured for this state (one outer
+ * iteration); 0 before the first graph run. */
+lam_status lamx_admm_graph_kernels(const lam_plan* plan, void* state, size_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LAMINO_STAGES_H */

@@ -18,7 +18,13 @@ g^(x) = sqrt(4 pi beta) / M * exp(-4 pi^2 beta x^2 / M^2):
 2. zero-pad     place f'[x] at index x mod M of a length-M buffer;
 3. FFT          P[j] = sum_x f'[x] exp(-2 pi i j x / M);
 4. gather       F(xi) ~= sum_{t=0}^{2m-1} exp(-(M xi - j_t)^2 / (4 beta)) P[j_t mod M]
-                with j0 = floor(M xi), j_t = j0 - m + 1 + t.
+                with j0 = floor(M xi + TAP_SHIFT), j_t = j0 - m + 1 + t.
+
+The paper gives no tap rule.  The window is the 2m grid nodes around M xi;
+its switch point is moved TAP_SHIFT = 2^-17 grid units below each node so that
+points lying on a node up to rounding (whole slice lines do, at angles that are
+multiples of pi/2) are not split between two windows by rounding noise: any
+implementation that knows M xi to better than ~1e-6 picks the same window.
 
 beta = m R / (4 pi (R - 1/2)) is the Greengard-Lee choice for a kernel of
 half-width m at oversampling R.  Type 1 (the adjoint used by L^H) is the exact
@@ -50,12 +56,15 @@ def pad_index(N: int, M: int) -> np.ndarray:
     return (np.arange(N) - N // 2) % M
 
 
+TAP_SHIFT = 2.0 ** -17
+
+
 def taps(t: np.ndarray, m: int, beta: float):
     """Tap indices (unwrapped) and Gaussian weights for grid positions t = M xi.
 
     Returns (j, w), each of shape t.shape + (2m,)."""
     t = np.asarray(t, dtype=np.float64)
-    j0 = np.floor(t)
+    j0 = np.floor(t + TAP_SHIFT)
     j = j0[..., None] + (np.arange(2 * m) - m + 1)
     w = np.exp(-((t[..., None] - j) ** 2) / (4.0 * beta))
     return j.astype(np.int64), w

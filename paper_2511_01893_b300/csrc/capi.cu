@@ -1,0 +1,864 @@
+// capi.cu - plans, geometry tables and the C ABI of liblamino (include/lamino.h).
+//
+// The plan computes every table in FP64 on the host (deapodisation factors,
+// z-gather taps and weights, the kv ranges of the gather-form z spread,
+// twiddles and per-angle slice-coordinate constants) and uploads them once.
+// Operator calls only enqueue kernels on the caller's stream and use the
+// caller's workspace; ADMM keeps all of its vectors and FP64 scalars in the
+// caller's state buffer.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/lamino.h"
+#include "../../include/lamino_stages.h"
+#include "admm.h"
+#include "kernels.h"
+
+using namespace lam;
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+
+static thread_local std::string g_err;
+
+static lam_status fail(lam_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) return fail(LAM_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct AdmmHost {
+    int n_inner = 4;
+    void* ws = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    size_t graph_kernels = 0;  // kernel nodes in the captured outer iteration
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int ilog2(int v) {
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+static bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+struct lam_plan {
+    int n1, nz, n2, h, w, T, m, R, prec;
+    int M0, M1, M2, Nmax;
+    double phi, beta;
+    int device;
+    std::vector<void*> dev_allocs;
+    // device tables
+    void *dz, *d1, *d2, *wz, *tw, *ang;
+    int *j0z, *kvlo, *kvhi;
+    int jmin, jmax;
+    // launch shapes
+    int TYf, TYa, RB, CB, TS, nimg, nbatch;
+    // workspace layout
+    size_t ws_u1, ws_planes, ws_tmp, ws_bytes;
+    mutable std::mutex mu;
+    mutable std::map<void*, AdmmHost> admm;
+
+    size_t elem() const { return prec == LAM_F64 ? sizeof(double) : sizeof(float); }
+    size_t celem() const { return 2 * elem(); }
+    long long nvox() const { return (long long)n1 * nz * n2; }
+    long long ndata() const { return (long long)T * h * w; }
+};
+
+namespace {
+
+template <typename T> void* upload(lam_plan* p, const std::vector<T>& v, lam_status* st) {
+    void* d = nullptr;
+    if (cudaMalloc(&d, std::max<size_t>(v.size() * sizeof(T), 16)) != cudaSuccess) {
+        *st = fail(LAM_ENOMEM, "cudaMalloc of %zu bytes for a plan table failed", v.size() * sizeof(T));
+        return nullptr;
+    }
+    p->dev_allocs.push_back(d);
+    if (!v.empty() && cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+        *st = fail(LAM_ECUDA, "upload of a plan table failed");
+        return nullptr;
+    }
+    return d;
+}
+
+template <typename T> std::vector<T> cast_vec(const std::vector<double>& v) {
+    return std::vector<T>(v.begin(), v.end());
+}
+
+// deapodisation 1/(M g^(x)) = exp(4 pi^2 beta x^2 / M^2) / sqrt(4 pi beta), x centred
+std::vector<double> deapod(int N, int M, double beta) {
+    std::vector<double> d(N);
+    for (int i = 0; i < N; ++i) {
+        const double x = i - N / 2;
+        d[i] = std::exp(4.0 * M_PI * M_PI * beta * x * x / ((double)M * M)) / std::sqrt(4.0 * M_PI * beta);
+    }
+    return d;
+}
+
+template <typename T> lam_status build_tables(lam_plan* p, const double* theta) {
+    lam_status st = LAM_OK;
+    const double beta = p->beta;
+    const int m = p->m, nt = 2 * m;
+    p->dz = upload(p, cast_vec<T>(deapod(p->nz, p->M0, beta)), &st);
+    if (st) return st;
+    p->d1 = upload(p, cast_vec<T>(deapod(p->n1, p->M1, beta)), &st);
+    if (st) return st;
+    p->d2 = upload(p, cast_vec<T>(deapod(p->n2, p->M2, beta)), &st);
+    if (st) return st;
+    // z gather: xi_z = (kv - h/2)/h cos(phi), taps j0 - m + 1 + t with j0 = floor(M0 xi + kTapShift),
+    // weights exp(-(M0 xi - j)^2/(4 beta))
+    std::vector<int> j0(p->h);
+    std::vector<double> wz((size_t)p->h * nt);
+    const double cp = std::cos(p->phi);
+    for (int kv = 0; kv < p->h; ++kv) {
+        const double t = p->M0 * ((double)(kv - p->h / 2) / p->h * cp);
+        const double f = std::floor(t + kTapShift);
+        j0[kv] = (int)f;
+        for (int q = 0; q < nt; ++q) {
+            const double dd = t - (f - m + 1 + q);
+            wz[(size_t)kv * nt + q] = std::exp(-dd * dd / (4.0 * beta));
+        }
+    }
+    int jmin = j0[0] - m + 1, jmax = j0[0] + m;
+    for (int kv = 0; kv < p->h; ++kv) {
+        jmin = std::min(jmin, j0[kv] - m + 1);
+        jmax = std::max(jmax, j0[kv] + m);
+    }
+    const int E = jmax - jmin + 1;
+    std::vector<int> lo(E), hi(E);
+    for (int e = 0; e < E; ++e) {
+        const int cell = jmin + e;
+        int l = p->h, r = 0;
+        for (int kv = 0; kv < p->h; ++kv)
+            if (j0[kv] - m + 1 <= cell && cell <= j0[kv] + m) {
+                l = std::min(l, kv);
+                r = std::max(r, kv + 1);
+            }
+        if (l >= r) l = r = 0;
+        // j0 is non-decreasing in kv (cos phi >= 0), so the kv set is contiguous
+        lo[e] = l;
+        hi[e] = r;
+    }
+    p->jmin = jmin;
+    p->jmax = jmax;
+    p->j0z = (int*)upload(p, j0, &st);
+    if (st) return st;
+    p->wz = upload(p, cast_vec<T>(wz), &st);
+    if (st) return st;
+    p->kvlo = (int*)upload(p, lo, &st);
+    if (st) return st;
+    p->kvhi = (int*)upload(p, hi, &st);
+    if (st) return st;
+    // twiddles exp(-2 pi i q / Nmax)
+    std::vector<T> tw(2 * (size_t)p->Nmax);
+    for (int q = 0; q < p->Nmax; ++q) {
+        const double a = -2.0 * M_PI * q / p->Nmax;
+        tw[2 * q] = (T)std::cos(a);
+        tw[2 * q + 1] = (T)std::sin(a);
+    }
+    p->tw = upload(p, tw, &st);
+    if (st) return st;
+    // per-angle slice coordinates (grid units):
+    //   x: ku * M1 cos th / w + kv * M1 sin phi sin th / h
+    //   y: ku * M2 sin th / w - kv * M2 sin phi cos th / h
+    const double sp = std::sin(p->phi);
+    if (sizeof(T) == sizeof(float)) {
+        std::vector<AngleF> ang(p->T);
+        auto split = [](double v, float& hi, float& lo) {
+            hi = (float)v;
+            lo = (float)(v - (double)hi);
+        };
+        for (int k = 0; k < p->T; ++k) {
+            const double c = std::cos(theta[k]), s = std::sin(theta[k]);
+            split(p->M1 * c / p->w, ang[k].ax_hi, ang[k].ax_lo);
+            split(p->M1 * sp * s / p->h, ang[k].sx_hi, ang[k].sx_lo);
+            split(p->M2 * s / p->w, ang[k].ay_hi, ang[k].ay_lo);
+            split(-p->M2 * sp * c / p->h, ang[k].sy_hi, ang[k].sy_lo);
+        }
+        p->ang = upload(p, ang, &st);
+    } else {
+        std::vector<AngleD> ang(p->T);
+        for (int k = 0; k < p->T; ++k) {
+            const double c = std::cos(theta[k]), s = std::sin(theta[k]);
+            ang[k].ax = p->M1 * c / p->w;
+            ang[k].sx = p->M1 * sp * s / p->h;
+            ang[k].ay = p->M2 * s / p->w;
+            ang[k].sy = -p->M2 * sp * c / p->h;
+        }
+        p->ang = upload(p, ang, &st);
+    }
+    return st;
+}
+
+static int pick_lines(int len, size_t celem, size_t budget, int divides, int cap) {
+    int l = cap;
+    while (l > 1 && ((size_t)2 * l * len * celem > budget || divides % l != 0)) l >>= 1;
+    return l;
+}
+
+template <typename T> Usfft1dArgs<T> args1d(const lam_plan* p, int TY) {
+    Usfft1dArgs<T> a;
+    a.n1 = p->n1;
+    a.nz = p->nz;
+    a.n2 = p->n2;
+    a.h = p->h;
+    a.M0 = p->M0;
+    a.logM0 = ilog2(p->M0);
+    a.m = p->m;
+    a.TY = TY;
+    a.dz = (const T*)p->dz;
+    a.j0z = p->j0z;
+    a.wz = (const T*)p->wz;
+    a.kvlo = p->kvlo;
+    a.kvhi = p->kvhi;
+    a.jmin = p->jmin;
+    a.jmax = p->jmax;
+    a.tw = (const C<T>*)p->tw;
+    a.twstride = p->Nmax / p->M0;
+    return a;
+}
+
+template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p) {
+    Usfft2dArgs<T> a;
+    a.n1 = p->n1;
+    a.n2 = p->n2;
+    a.h = p->h;
+    a.w = p->w;
+    a.T_ = p->T;
+    a.M1 = p->M1;
+    a.M2 = p->M2;
+    a.logM1 = ilog2(p->M1);
+    a.logM2 = ilog2(p->M2);
+    a.m = p->m;
+    a.inv4beta = (T)(1.0 / (4.0 * p->beta));
+    a.d1 = (const T*)p->d1;
+    a.d2 = (const T*)p->d2;
+    a.ang = (const typename AngleT<T>::type*)p->ang;
+    a.tw = (const C<T>*)p->tw;
+    a.tw1 = p->Nmax / p->M1;
+    a.tw2 = p->Nmax / p->M2;
+    a.RB = p->RB;
+    a.CB = p->CB;
+    a.TS = p->TS;
+    a.nimg = p->nimg;
+    return a;
+}
+
+template <typename T> Fft2dArgs<T> argsfft(const lam_plan* p) {
+    Fft2dArgs<T> a;
+    a.T_ = p->T;
+    a.h = p->h;
+    a.w = p->w;
+    a.logh = ilog2(p->h);
+    a.logw = ilog2(p->w);
+    a.tw = (const C<T>*)p->tw;
+    a.twh = p->Nmax / p->h;
+    a.tww = p->Nmax / p->w;
+    return a;
+}
+
+// ---- operator sequences ----------------------------------------------------
+
+template <typename T>
+lam_status fwd_hat(const lam_plan* p, const T* u, C<T>* out, const C<T>* sub, void* ws, cudaStream_t s) {
+    char* w = (char*)ws;
+    C<T>* u1 = (C<T>*)(w + p->ws_u1);
+    C<T>* P = (C<T>*)(w + p->ws_planes);
+    CK(launch_usfft1d_fwd<T>(u, u1, args1d<T>(p, p->TYf), s));
+    const Usfft2dArgs<T> a = args2d<T>(p);
+    for (int kv0 = 0; kv0 < p->h; kv0 += p->nbatch) {
+        const int nb = std::min(p->nbatch, p->h - kv0);
+        CK(launch_usfft2d_fwd<T>(u1, P, out, sub, kv0, nb, a, s));
+    }
+    return LAM_OK;
+}
+
+template <typename T> lam_status adj_hat(const lam_plan* p, const C<T>* in, T* u, void* ws, cudaStream_t s) {
+    char* w = (char*)ws;
+    C<T>* u1 = (C<T>*)(w + p->ws_u1);
+    C<T>* P = (C<T>*)(w + p->ws_planes);
+    const Usfft2dArgs<T> a = args2d<T>(p);
+    for (int kv0 = 0; kv0 < p->h; kv0 += p->nbatch) {
+        const int nb = std::min(p->nbatch, p->h - kv0);
+        CK(launch_usfft2d_adj<T>(in, P, u1, kv0, nb, a, s));
+    }
+    CK(launch_usfft1d_adj<T>(u1, u, args1d<T>(p, p->TYa), s));
+    return LAM_OK;
+}
+
+template <typename T> lam_status fft2d(const lam_plan* p, const C<T>* in, C<T>* out, int dir, T scale, cudaStream_t s) {
+    CK(launch_fft2d_angles<T>(in, out, dir, scale, argsfft<T>(p), s));
+    return LAM_OK;
+}
+
+// ---- ADMM state layout -------------------------------------------------------
+
+struct StateLayout {
+    size_t sc, hist, partials, counter, u, Gd, G0, G1, p, psi, lam, dpsi, dhat, r, Lp, total;
+};
+
+StateLayout layout(const lam_plan* p) {
+    StateLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align256(o + bytes);
+        return at;
+    };
+    const size_t vb = (size_t)p->nvox() * p->elem();
+    const size_t db = (size_t)p->ndata() * p->celem();
+    L.sc = take(SC_COUNT * sizeof(double));
+    L.hist = take((size_t)kHistCap * 4 * sizeof(double));
+    L.partials = take((size_t)kRedBlocks * 4 * sizeof(double));
+    L.counter = take(sizeof(unsigned int));
+    L.u = take(vb);
+    L.Gd = take(vb);
+    L.G0 = take(vb);
+    L.G1 = take(vb);
+    L.p = take(vb);
+    L.psi = take(3 * vb);
+    L.lam = take(3 * vb);
+    L.dpsi = take(3 * vb);
+    L.dhat = take(db);
+    L.r = take(db);
+    L.Lp = take(db);
+    L.total = o;
+    return L;
+}
+
+__global__ void k_init_scalars(double* sc, double rho, double alpha, double invhw, double adapt,
+                               unsigned int* counter) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = 0; i < SC_COUNT; ++i) sc[i] = 0.0;
+    sc[SC_RHO] = rho;
+    sc[SC_ALPHA] = alpha;
+    sc[SC_INVHW] = invhw;
+    sc[SC_ADAPT] = adapt;
+    *counter = 0;
+}
+
+template <typename T> struct StatePtrs {
+    T *u, *Gd, *G0, *G1, *p, *psi, *lam, *dpsi;
+    C<T>*dhat, *r, *Lp;
+    AdmmRed red;
+    double* hist;
+};
+
+template <typename T> StatePtrs<T> ptrs(const lam_plan* p, void* state) {
+    const StateLayout L = layout(p);
+    char* b = (char*)state;
+    StatePtrs<T> s;
+    s.u = (T*)(b + L.u);
+    s.Gd = (T*)(b + L.Gd);
+    s.G0 = (T*)(b + L.G0);
+    s.G1 = (T*)(b + L.G1);
+    s.p = (T*)(b + L.p);
+    s.psi = (T*)(b + L.psi);
+    s.lam = (T*)(b + L.lam);
+    s.dpsi = (T*)(b + L.dpsi);
+    s.dhat = (C<T>*)(b + L.dhat);
+    s.r = (C<T>*)(b + L.r);
+    s.Lp = (C<T>*)(b + L.Lp);
+    s.red.sc = (double*)(b + L.sc);
+    s.red.partials = (double*)(b + L.partials);
+    s.red.counter = (unsigned int*)(b + L.counter);
+    s.hist = (double*)(b + L.hist);
+    return s;
+}
+
+template <typename T> Admm<T> admm_ops(const lam_plan* p) {
+    Admm<T> a;
+    a.v.n1 = p->n1;
+    a.v.nz = p->nz;
+    a.v.n2 = p->n2;
+    a.v.N = p->nvox();
+    return a;
+}
+
+template <typename T>
+lam_status admm_init_t(const lam_plan* p, void* state, const void* d, double alpha, double rho, int adapt,
+                       cudaStream_t s) {
+    const StateLayout L = layout(p);
+    StatePtrs<T> S = ptrs<T>(p, state);
+    const size_t vb = (size_t)p->nvox() * p->elem();
+    CK(cudaMemsetAsync(S.u, 0, vb, s));
+    CK(cudaMemsetAsync(S.p, 0, vb, s));
+    CK(cudaMemsetAsync(S.psi, 0, 3 * vb, s));
+    CK(cudaMemsetAsync(S.lam, 0, 3 * vb, s));
+    (void)L;
+    k_init_scalars<<<1, 32, 0, s>>>(S.red.sc, rho, alpha, 1.0 / ((double)p->h * p->w), adapt ? 1.0 : 0.0,
+                                    S.red.counter);
+    CK(cudaGetLastError());
+    lam_status st = fft2d<T>(p, (const C<T>*)d, S.dhat, -1, (T)1, s);
+    if (st) return st;
+    const Admm<T> ops = admm_ops<T>(p);
+    CK(ops.neg_copy(S.dhat, S.r, p->ndata(), s));
+    CK(ops.residual_norm(S.r, p->ndata(), S.red, s));
+    return LAM_OK;
+}
+
+template <typename T> lam_status admm_step_t(const lam_plan* p, void* state, void* ws, int n_inner, cudaStream_t s) {
+    StatePtrs<T> S = ptrs<T>(p, state);
+    const Admm<T> ops = admm_ops<T>(p);
+    const long long nd = p->ndata();
+    lam_status st;
+    for (int i = 0; i < n_inner; ++i) {
+        T* Gc = (i & 1) ? S.G1 : S.G0;
+        T* Gp = (i & 1) ? S.G0 : S.G1;
+        // adjoint pass: G = Re L_hat^H r / (hw) - rho div(grad u - g)
+        if ((st = adj_hat<T>(p, S.r, S.Gd, ws, s))) return st;
+        CK(ops.lsp_G(S.Gd, S.u, S.psi, S.lam, S.p, Gp, Gc, i == 0, S.red, s));
+        // CG direction and its forward pass
+        CK(ops.lsp_p(Gc, S.p, S.red, s));
+        if ((st = fwd_hat<T>(p, S.p, S.Lp, nullptr, ws, s))) return st;
+        // exact line search, u and residual update
+        CK(ops.lsp_update(S.u, S.p, S.r, S.Lp, nd, S.red, s));
+    }
+    CK(ops.rsp(S.u, S.psi, S.lam, S.dpsi, S.red, S.hist, kHistCap, s));
+    return LAM_OK;
+}
+
+__global__ void k_real_to_complex(const float* __restrict__ src, C<float>* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = cmake<float>(src[i], 0.f);
+}
+
+template <typename T> lam_status u2d_fwd_t(const lam_plan* p, const void* u1, void* out, const void* sub,
+                                                  void* ws, cudaStream_t s) {
+    C<T>* P = (C<T>*)((char*)ws + p->ws_planes);
+    const Usfft2dArgs<T> a = args2d<T>(p);
+    for (int kv0 = 0; kv0 < p->h; kv0 += p->nbatch)
+        CK(launch_usfft2d_fwd<T>((const C<T>*)u1, P, (C<T>*)out, (const C<T>*)sub, kv0,
+                                 std::min(p->nbatch, p->h - kv0), a, s));
+    return LAM_OK;
+}
+template <typename T> lam_status u2d_adj_t(const lam_plan* p, const void* in, void* u1, void* ws,
+                                                  cudaStream_t s) {
+    C<T>* P = (C<T>*)((char*)ws + p->ws_planes);
+    const Usfft2dArgs<T> a = args2d<T>(p);
+    for (int kv0 = 0; kv0 < p->h; kv0 += p->nbatch)
+        CK(launch_usfft2d_adj<T>((const C<T>*)in, P, (C<T>*)u1, kv0, std::min(p->nbatch, p->h - kv0), a, s));
+    return LAM_OK;
+}
+
+lam_status check_plan(const lam_plan* p) {
+    if (!p) return fail(LAM_EINVAL, "plan is NULL");
+    return LAM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+const char* lam_last_error(void) { return g_err.c_str(); }
+
+lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, int n_theta, const double* theta,
+                           double phi, int oversample, int half_width, int prec) {
+    if (!out) return fail(LAM_EINVAL, "out is NULL");
+    *out = nullptr;
+    const int dims[4] = {n, nz, det_h, det_w};
+    const char* names[4] = {"n", "nz", "det_h", "det_w"};
+    for (int i = 0; i < 4; ++i)
+        if (!pow2(dims[i]) || dims[i] < 8 || dims[i] > 2048)
+            return fail(LAM_EUNSUPPORTED, "%s = %d: must be a power of two in [8, 2048]", names[i], dims[i]);
+    if (n_theta < 1 || n_theta > 65536) return fail(LAM_EINVAL, "n_theta = %d out of range", n_theta);
+    if (!theta) return fail(LAM_EINVAL, "theta is NULL");
+    for (int k = 0; k < n_theta; ++k)
+        if (!std::isfinite(theta[k])) return fail(LAM_EINVAL, "theta[%d] is not finite", k);
+    if (!(phi >= 0.0 && phi < M_PI / 2)) return fail(LAM_EINVAL, "phi = %g must be in [0, pi/2)", phi);
+    if (oversample != 2) return fail(LAM_EUNSUPPORTED, "oversample = %d: only 2 is supported", oversample);
+    if (half_width < 2 || half_width > 8) return fail(LAM_EUNSUPPORTED, "half_width = %d not in [2, 8]", half_width);
+    if (prec != LAM_F32 && prec != LAM_F64) return fail(LAM_EINVAL, "prec = %d", prec);
+
+    lam_plan* p = new lam_plan();
+    p->n1 = p->n2 = n;
+    p->nz = nz;
+    p->h = det_h;
+    p->w = det_w;
+    p->T = n_theta;
+    p->m = half_width;
+    p->R = oversample;
+    p->prec = prec;
+    p->phi = phi;
+    p->M0 = 2 * nz;
+    p->M1 = 2 * n;
+    p->M2 = 2 * n;
+    p->Nmax = std::max(std::max(p->M0, p->M1), std::max(p->h, p->w));
+    p->beta = half_width * 2.0 / (4.0 * M_PI * 1.5);
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        delete p;
+        return fail(LAM_ECUDA, "no CUDA device");
+    }
+    lam_status st = prec == LAM_F32 ? build_tables<float>(p, theta) : build_tables<double>(p, theta);
+    cudaError_t ce = prec == LAM_F32 ? configure_usfft1d<float>() : configure_usfft1d<double>();
+    if (!ce) ce = prec == LAM_F32 ? configure_usfft2d<float>() : configure_usfft2d<double>();
+    if (!ce) ce = prec == LAM_F32 ? configure_fft2d<float>() : configure_fft2d<double>();
+    if (!st && ce) st = fail(LAM_ECUDA, "kernel configuration failed: %s", cudaGetErrorString(ce));
+    if (st) {
+        lam_plan_destroy(p);
+        return st;
+    }
+    const size_t ce_ = p->celem();
+    const size_t budget = 200 * 1024;
+    // z stage: TY columns per block
+    p->TYf = 16;
+    while (p->TYf > 1 && ((size_t)2 * p->TYf * p->M0 * ce_ > budget || p->n2 % p->TYf)) p->TYf >>= 1;
+    p->TYa = 16;
+    while (p->TYa > 1 && ((size_t)(2 * p->M0 + p->h) * p->TYa * ce_ > budget || p->n2 % p->TYa)) p->TYa >>= 1;
+    p->RB = pick_lines(p->M2, ce_, 96 * 1024, p->n1, 16);
+    p->CB = pick_lines(p->M1, ce_, 96 * 1024, p->M2, 16);
+    p->TS = std::min(32, std::min(p->M1, p->M2));
+    // unwrapped slice positions reach |p| <= M (1 + sin phi) / 2 + m + 2
+    const double reach = std::max(p->M1, p->M2) * (1.0 + std::sin(phi)) / 2.0 + p->m + 2;
+    p->nimg = (int)std::ceil(reach / std::min(p->M1, p->M2));
+    const size_t plane = (size_t)p->M1 * p->M2 * ce_;
+    p->nbatch = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->h, (256u << 20) / plane));
+    p->ws_u1 = 0;
+    p->ws_planes = align256((size_t)p->h * p->n1 * p->n2 * ce_);
+    p->ws_tmp = p->ws_planes + align256((size_t)p->nbatch * plane);
+    p->ws_bytes = p->ws_tmp + align256((size_t)p->ndata() * ce_);
+    *out = p;
+    return LAM_OK;
+}
+
+lam_status lam_plan_destroy(lam_plan* plan) {
+    if (!plan) return LAM_OK;
+    for (auto& kv : plan->admm)
+        if (kv.second.graph) cudaGraphExecDestroy(kv.second.graph);
+    for (void* d : plan->dev_allocs) cudaFree(d);
+    delete plan;
+    return LAM_OK;
+}
+
+size_t lam_workspace_bytes(const lam_plan* plan) { return plan ? plan->ws_bytes : 0; }
+
+#define DISPATCH(p, F32CALL, F64CALL) ((p)->prec == LAM_F32 ? (F32CALL) : (F64CALL))
+
+lam_status lam_forward_hat(const lam_plan* p, const void* u, void* d_hat, const void* sub, void* ws, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!u || !d_hat || !ws) return fail(LAM_EINVAL, "NULL array argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    return DISPATCH(p, fwd_hat<float>(p, (const float*)u, (C<float>*)d_hat, (const C<float>*)sub, ws, s),
+                    fwd_hat<double>(p, (const double*)u, (C<double>*)d_hat, (const C<double>*)sub, ws, s));
+}
+
+lam_status lam_adjoint_hat(const lam_plan* p, const void* d_hat, void* u, void* ws, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!u || !d_hat || !ws) return fail(LAM_EINVAL, "NULL array argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    return DISPATCH(p, adj_hat<float>(p, (const C<float>*)d_hat, (float*)u, ws, s),
+                    adj_hat<double>(p, (const C<double>*)d_hat, (double*)u, ws, s));
+}
+
+lam_status lam_forward(const lam_plan* p, const void* u, void* d, void* ws, void* stream) {
+    if (lam_status st = lam_forward_hat(p, u, d, nullptr, ws, stream)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const double sc = 1.0 / ((double)p->h * p->w);
+    return DISPATCH(p, fft2d<float>(p, (const C<float>*)d, (C<float>*)d, +1, (float)sc, s),
+                    fft2d<double>(p, (const C<double>*)d, (C<double>*)d, +1, sc, s));
+}
+
+lam_status lam_adjoint(const lam_plan* p, const void* d, void* u, void* ws, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!u || !d || !ws) return fail(LAM_EINVAL, "NULL array argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    void* tmp = (char*)ws + p->ws_tmp;
+    const double sc = 1.0 / ((double)p->h * p->w);
+    lam_status st = DISPATCH(p, fft2d<float>(p, (const C<float>*)d, (C<float>*)tmp, -1, (float)sc, s),
+                             fft2d<double>(p, (const C<double>*)d, (C<double>*)tmp, -1, sc, s));
+    if (st) return st;
+    return lam_adjoint_hat(p, tmp, u, ws, stream);
+}
+
+lam_status lam_fft2d(const lam_plan* p, const void* in, void* out, int inverse, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!in || !out) return fail(LAM_EINVAL, "NULL array argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    const double sc = inverse ? 1.0 / ((double)p->h * p->w) : 1.0;
+    const int dir = inverse ? +1 : -1;
+    return DISPATCH(p, fft2d<float>(p, (const C<float>*)in, (C<float>*)out, dir, (float)sc, s),
+                    fft2d<double>(p, (const C<double>*)in, (C<double>*)out, dir, sc, s));
+}
+
+lam_status tv_grad(const lam_plan* p, const void* u, void* g, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!u || !g) return fail(LAM_EINVAL, "NULL array argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(DISPATCH(p, admm_ops<float>(p).grad((const float*)u, (float*)g, s),
+                admm_ops<double>(p).grad((const double*)u, (double*)g, s)));
+    return LAM_OK;
+}
+
+lam_status tv_div(const lam_plan* p, const void* g, void* u, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!u || !g) return fail(LAM_EINVAL, "NULL array argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(DISPATCH(p, admm_ops<float>(p).div((const float*)g, (float*)u, s),
+                admm_ops<double>(p).div((const double*)g, (double*)u, s)));
+    return LAM_OK;
+}
+
+lam_status admm_state_bytes(const lam_plan* p, size_t* bytes) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!bytes) return fail(LAM_EINVAL, "bytes is NULL");
+    *bytes = layout(p).total;
+    return LAM_OK;
+}
+
+lam_status admm_init(const lam_plan* p, void* state, const void* d, double alpha, double rho, int n_inner,
+                     int adapt_rho, void* ws, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!state || !d || !ws) return fail(LAM_EINVAL, "NULL array argument");
+    if (n_inner < 1 || n_inner > 64) return fail(LAM_EINVAL, "n_inner = %d not in [1, 64]", n_inner);
+    if (!(rho > 0) || !std::isfinite(rho)) return fail(LAM_EINVAL, "rho = %g must be positive", rho);
+    if (!(alpha >= 0) || !std::isfinite(alpha)) return fail(LAM_EINVAL, "alpha = %g must be >= 0", alpha);
+    cudaStream_t s = (cudaStream_t)stream;
+    {
+        std::lock_guard<std::mutex> lk(p->mu);
+        AdmmHost& h = p->admm[state];
+        if (h.graph) cudaGraphExecDestroy(h.graph);
+        h.graph = nullptr;
+        h.n_inner = n_inner;
+        h.ws = ws;
+    }
+    return DISPATCH(p, admm_init_t<float>(p, state, d, alpha, rho, adapt_rho, s),
+                    admm_init_t<double>(p, state, d, alpha, rho, adapt_rho, s));
+}
+
+static lam_status lookup(const lam_plan* p, void* state, AdmmHost** h) {
+    std::lock_guard<std::mutex> lk(p->mu);
+    auto it = p->admm.find(state);
+    if (it == p->admm.end()) return fail(LAM_EINVAL, "state was not initialised with admm_init on this plan");
+    *h = &it->second;
+    return LAM_OK;
+}
+
+lam_status admm_step(const lam_plan* p, void* state, void* ws, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!state || !ws) return fail(LAM_EINVAL, "NULL array argument");
+    AdmmHost* h;
+    if (lam_status st = lookup(p, state, &h)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return DISPATCH(p, admm_step_t<float>(p, state, ws, h->n_inner, s),
+                    admm_step_t<double>(p, state, ws, h->n_inner, s));
+}
+
+lam_status admm_run(const lam_plan* p, void* state, void* ws, int iters, int use_graph, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!state || !ws) return fail(LAM_EINVAL, "NULL array argument");
+    if (iters < 0) return fail(LAM_EINVAL, "iters = %d", iters);
+    AdmmHost* h;
+    if (lam_status st = lookup(p, state, &h)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!use_graph) {
+        for (int k = 0; k < iters; ++k)
+            if (lam_status st = admm_step(p, state, ws, stream)) return st;
+        return LAM_OK;
+    }
+    if (s == nullptr) return fail(LAM_EINVAL, "graph replay needs a non-default stream");
+    if (!h->graph || h->ws != ws) {
+        if (h->graph) cudaGraphExecDestroy(h->graph);
+        h->graph = nullptr;
+        h->ws = ws;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        lam_status st = admm_step(p, state, ws, stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(s, &g);
+        if (st) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (ce != cudaSuccess) return fail(LAM_ECUDA, "stream capture failed: %s", cudaGetErrorString(ce));
+        size_t nn = 0;
+        h->graph_kernels = 0;
+        if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+                for (size_t i = 0; i < nn; ++i) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+                        ++h->graph_kernels;
+                }
+        }
+        ce = cudaGraphInstantiate(&h->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return fail(LAM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+    }
+    for (int k = 0; k < iters; ++k) CK(cudaGraphLaunch(h->graph, s));
+    return LAM_OK;
+}
+
+void* admm_u(const lam_plan* p, void* state) {
+    if (!p || !state) return nullptr;
+    return (char*)state + layout(p).u;
+}
+
+lam_status admm_read_scalars(const lam_plan* p, const void* state, double* out, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!state || !out) return fail(LAM_EINVAL, "NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(out, (const char*)state + layout(p).sc, LAM_NSCALARS * sizeof(double),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return LAM_OK;
+}
+
+lam_status admm_read_history(const lam_plan* p, const void* state, int count, double* out, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!state || !out) return fail(LAM_EINVAL, "NULL argument");
+    if (count < 0 || count > kHistCap) return fail(LAM_EINVAL, "count = %d not in [0, %d]", count, kHistCap);
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(out, (const char*)state + layout(p).hist, (size_t)count * 4 * sizeof(double),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return LAM_OK;
+}
+
+lam_status admm_status(const lam_plan* p, const void* state, void* stream) {
+    double sc[LAM_NSCALARS];
+    if (lam_status st = admm_read_scalars(p, state, sc, stream)) return st;
+    if (sc[LAM_SC_STATUS] != 0.0) return fail(LAM_ENAN, "a non-finite value appeared in an ADMM reduction");
+    return LAM_OK;
+}
+
+static bool on_device(const void* ptr) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+lam_status reconstruct(const float* data, const double* theta, double phi, int n, int nz, int det_h, int det_w,
+                       int n_theta, int iters, double alpha, double rho, float* u_out) {
+    if (!data || !theta || !u_out) return fail(LAM_EINVAL, "NULL argument");
+    if (iters < 0) return fail(LAM_EINVAL, "iters = %d", iters);
+    lam_plan* p = nullptr;
+    if (lam_status st = lam_plan_create(&p, n, nz, det_h, det_w, n_theta, theta, phi, 2, 4, LAM_F32)) return st;
+    size_t sb = 0;
+    admm_state_bytes(p, &sb);
+    const size_t nd = (size_t)p->ndata();
+    void *ws = nullptr, *state = nullptr, *dreal = nullptr, *dc = nullptr;
+    cudaStream_t s = nullptr;
+    lam_status st = LAM_OK;
+    auto cleanup = [&]() {
+        if (s) cudaStreamSynchronize(s);
+        cudaFree(ws);
+        cudaFree(state);
+        cudaFree(dreal);
+        cudaFree(dc);
+        if (s) cudaStreamDestroy(s);
+        lam_plan_destroy(p);
+    };
+    if (cudaMalloc(&ws, p->ws_bytes) || cudaMalloc(&state, sb) || cudaMalloc(&dreal, nd * sizeof(float)) ||
+        cudaMalloc(&dc, nd * sizeof(C<float>)) || cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) {
+        cleanup();
+        return fail(LAM_ENOMEM, "reconstruct: device allocation failed");
+    }
+    const bool in_dev = on_device(data), out_dev = on_device(u_out);
+    if (cudaMemcpyAsync(dreal, data, nd * sizeof(float), in_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                        s) != cudaSuccess) {
+        cleanup();
+        return fail(LAM_ECUDA, "reconstruct: data copy failed");
+    }
+    k_real_to_complex<<<1184, 256, 0, s>>>((const float*)dreal, (C<float>*)dc, (long long)nd);
+    if ((st = admm_init(p, state, dc, alpha, rho, 4, 1, ws, s)) == LAM_OK)
+        st = admm_run(p, state, ws, iters, 1, s);
+    if (st == LAM_OK) {
+        const size_t vb = (size_t)p->nvox() * sizeof(float);
+        if (cudaMemcpyAsync(u_out, admm_u(p, state), vb, out_dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                            s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            st = fail(LAM_ECUDA, "reconstruct: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    if (st == LAM_OK) {
+        double sc[LAM_NSCALARS];
+        if (admm_read_scalars(p, state, sc, s) == LAM_OK && sc[LAM_SC_STATUS] != 0.0)
+            st = fail(LAM_ENAN, "reconstruct: non-finite ADMM scalar");
+    }
+    cleanup();
+    return st;
+}
+
+// ---- stage entry points (lamino_stages.h) ------------------------------------
+
+lam_status lamx_u1d_fwd(const lam_plan* p, const void* u, void* u1, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(DISPATCH(p, launch_usfft1d_fwd<float>((const float*)u, (C<float>*)u1, args1d<float>(p, p->TYf), s),
+                launch_usfft1d_fwd<double>((const double*)u, (C<double>*)u1, args1d<double>(p, p->TYf), s)));
+    return LAM_OK;
+}
+
+lam_status lamx_u1d_adj(const lam_plan* p, const void* u1, void* u, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(DISPATCH(p, launch_usfft1d_adj<float>((const C<float>*)u1, (float*)u, args1d<float>(p, p->TYa), s),
+                launch_usfft1d_adj<double>((const C<double>*)u1, (double*)u, args1d<double>(p, p->TYa), s)));
+    return LAM_OK;
+}
+
+lam_status lamx_u2d_fwd(const lam_plan* p, const void* u1, void* d_hat, const void* sub, void* ws, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return DISPATCH(p, u2d_fwd_t<float>(p, u1, d_hat, sub, ws, s), u2d_fwd_t<double>(p, u1, d_hat, sub, ws, s));
+}
+
+lam_status lamx_u2d_adj(const lam_plan* p, const void* d_hat, void* u1, void* ws, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return DISPATCH(p, u2d_adj_t<float>(p, d_hat, u1, ws, s), u2d_adj_t<double>(p, d_hat, u1, ws, s));
+}
+
+lam_status lamx_admm_graph_kernels(const lam_plan* p, void* state, size_t* count) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!count) return fail(LAM_EINVAL, "count is NULL");
+    AdmmHost* h;
+    if (lam_status st = lookup(p, state, &h)) return st;
+    *count = h->graph ? h->graph_kernels : 0;
+    return LAM_OK;
+}
+
+lam_status lamx_plan_info(const lam_plan* p, int* out, int count) {
+    if (lam_status st = check_plan(p)) return st;
+    const int v[] = {p->TYf, p->TYa, p->RB, p->CB, p->TS, p->nimg, p->nbatch, p->jmin, p->jmax};
+    const int nv = (int)(sizeof(v) / sizeof(v[0]));
+    for (int i = 0; i < count && i < nv; ++i) out[i] = v[i];
+    return LAM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// fft2d.cu - F_2D and F*_2D: centred 2D DFT of every angle's h x w grid.
+//
+// F*_2D (Section 2, the last step of L) is the per-angle inverse 2D FFT on the
+// equispaced detector-frequency grid; F_2D (Algorithm 2, d_hat = F_2D d) is its
+// inverse.  With centred indices (ku - w/2, iu - w/2, ...) the centred DFT of
+// even-length axes equals a plain DFT with the input and output multiplied by
+// (-1)^index and the whole result by (-1)^(h/2 + w/2):
+//   exp(s 2 pi i (k - n/2)(i - n/2) / n) = (-1)^(k + i + n/2) exp(s 2 pi i k i / n).
+// Row pass: load * (-1)^(kv + ku), FFT along w, store * (-1)^iu.
+// Column pass (in place): FFT along h, store * (-1)^(iv + h/2 + w/2) * scale.
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace lam {
+
+template <int DIR, typename T>
+__global__ void __launch_bounds__(256) k_fft2d_rows(const C<T>* in, C<T>* out,
+                                                    int RB, Fft2dArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* bufb = bufa + RB * a.w;
+    const int th = blockIdx.y, r0 = blockIdx.x * RB;
+    const size_t base = ((size_t)th * a.h + r0) * a.w;
+    for (int i = threadIdx.x; i < RB * a.w; i += blockDim.x) {
+        const int r = i / a.w, k = i - r * a.w;
+        const C<T> v = in[base + i];
+        bufa[i] = ((r0 + r + k) & 1) ? cmake<T>(-v.x, -v.y) : v;
+    }
+    __syncthreads();
+    const C<T>* res = fft_lines<DIR, T>(bufa, bufb, RB, a.w, a.w, a.logw, a.tw, a.tww);
+    for (int i = threadIdx.x; i < RB * a.w; i += blockDim.x) {
+        const int r = i / a.w, k = i - r * a.w;
+        const C<T> v = res[i];
+        out[base + i] = (k & 1) ? cmake<T>(-v.x, -v.y) : v;
+        (void)r;
+    }
+}
+
+template <int DIR, typename T>
+__global__ void __launch_bounds__(256) k_fft2d_cols(C<T>* __restrict__ io, int CB, T scale, Fft2dArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* bufb = bufa + CB * a.h;
+    const int th = blockIdx.y, c0 = blockIdx.x * CB;
+    C<T>* pl = io + (size_t)th * a.h * a.w + c0;
+    for (int i = threadIdx.x; i < a.h * CB; i += blockDim.x) {
+        const int r = i / CB, c = i - r * CB;
+        bufa[c * a.h + r] = pl[(size_t)r * a.w + c];
+    }
+    __syncthreads();
+    const C<T>* res = fft_lines<DIR, T>(bufa, bufb, CB, a.h, a.h, a.logh, a.tw, a.twh);
+    const int gsign = ((a.h / 2 + a.w / 2) & 1);
+    for (int i = threadIdx.x; i < a.h * CB; i += blockDim.x) {
+        const int r = i / CB, c = i - r * CB;
+        const C<T> v = res[c * a.h + r];
+        const T s = ((r + gsign) & 1) ? -scale : scale;
+        pl[(size_t)r * a.w + c] = cscale(v, s);
+    }
+}
+
+static int lines_per_block(int len, size_t elem) {
+    // two buffers of `lines` lines in at most 64 KB, at most 16 lines
+    int l = (int)((64 * 1024) / (2 * (size_t)len * elem));
+    if (l < 1) l = 1;
+    if (l > 16) l = 16;
+    int p = 1;
+    while (p * 2 <= l) p *= 2;
+    return p;
+}
+
+template <typename T>
+cudaError_t launch_fft2d_angles(const C<T>* in, C<T>* out, int dir, T scale, const Fft2dArgs<T>& a,
+                                cudaStream_t s) {
+    int RB = lines_per_block(a.w, sizeof(C<T>));
+    if (RB > a.h) RB = a.h;
+    int CB = lines_per_block(a.h, sizeof(C<T>));
+    if (CB > a.w) CB = a.w;
+    const size_t sr = (size_t)2 * RB * a.w * sizeof(C<T>);
+    const size_t sc = (size_t)2 * CB * a.h * sizeof(C<T>);
+    if (dir > 0) {
+        k_fft2d_rows<1, T><<<dim3(a.h / RB, a.T_), 256, sr, s>>>(in, out, RB, a);
+        k_fft2d_cols<1, T><<<dim3(a.w / CB, a.T_), 256, sc, s>>>(out, CB, scale, a);
+    } else {
+        k_fft2d_rows<-1, T><<<dim3(a.h / RB, a.T_), 256, sr, s>>>(in, out, RB, a);
+        k_fft2d_cols<-1, T><<<dim3(a.w / CB, a.T_), 256, sc, s>>>(out, CB, scale, a);
+    }
+    return cudaGetLastError();
+}
+
+template <typename T> cudaError_t configure_fft2d() {
+    const int mx = kMaxDynSmem;
+    cudaError_t e = cudaSuccess;
+    if (!e) e = cudaFuncSetAttribute(k_fft2d_rows<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (!e) e = cudaFuncSetAttribute(k_fft2d_rows<-1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (!e) e = cudaFuncSetAttribute(k_fft2d_cols<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    if (!e) e = cudaFuncSetAttribute(k_fft2d_cols<-1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    return e;
+}
+
+template cudaError_t launch_fft2d_angles<float>(const C<float>*, C<float>*, int, float, const Fft2dArgs<float>&,
+                                                cudaStream_t);
+template cudaError_t launch_fft2d_angles<double>(const C<double>*, C<double>*, int, double,
+                                                 const Fft2dArgs<double>&, cudaStream_t);
+template cudaError_t configure_fft2d<float>();
+template cudaError_t configure_fft2d<double>();
+
+}  // namespace lam

@@ -1,0 +1,85 @@
+// kernels.h - argument blocks and launchers of the laminography kernels
+// (internal to liblamino; the public ABI is include/lamino.h).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace lam {
+
+// dynamic shared memory opt-in granted to every kernel (227 KB, the sm_100+
+// per-block maximum); set once per plan creation so launches need no
+// attribute calls (and stay legal under stream capture).
+constexpr int kMaxDynSmem = 227 * 1024;
+
+template <typename T> cudaError_t configure_usfft1d();
+template <typename T> cudaError_t configure_usfft2d();
+template <typename T> cudaError_t configure_fft2d();
+template <typename T> size_t scatter_acc_bytes();  // per tile cell, all warps
+
+// ---- F_u1D -----------------------------------------------------------------
+template <typename T> struct Usfft1dArgs {
+    int n1, nz, n2, h;
+    int M0, logM0;
+    int m;             // half-width; 2m taps
+    int TY;            // columns per block (divides n2)
+    const T* dz;       // [nz] deapodisation along z
+    const int* j0z;    // [h] floor(M0 xi_z(kv))
+    const T* wz;       // [h][2m] Gaussian weights of taps j0z - m + 1 + t
+    const int* kvlo;   // [jmax - jmin + 1] first kv whose taps reach unwrapped cell e
+    const int* kvhi;   // one past the last such kv
+    int jmin, jmax;    // unwrapped cell range touched by any tap
+    const C<T>* tw;    // twiddles exp(-2 pi i q / Nmax)
+    int twstride;      // Nmax / M0
+};
+
+template <typename T>
+cudaError_t launch_usfft1d_fwd(const T* u, C<T>* u1, const Usfft1dArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_usfft1d_adj(const C<T>* u1, T* u, const Usfft1dArgs<T>& a, cudaStream_t s);
+
+// ---- F_u2D -----------------------------------------------------------------
+template <typename T> struct AngleT;
+template <> struct AngleT<float> { typedef AngleF type; };
+template <> struct AngleT<double> { typedef AngleD type; };
+
+template <typename T> struct Usfft2dArgs {
+    int n1, n2, h, w, T_;          // T_ = number of angles
+    int M1, M2, logM1, logM2;
+    int m;
+    T inv4beta;                     // 1 / (4 beta)
+    const T* d1;                    // [n1] deapodisation along x
+    const T* d2;                    // [n2] deapodisation along y
+    const typename AngleT<T>::type* ang;   // [T_] slice-coordinate constants
+    const C<T>* tw;
+    int tw1, tw2;                   // Nmax / M1, Nmax / M2
+    int RB;                         // rows per block (row passes)
+    int CB;                         // columns per block (column passes)
+    int TS;                         // scatter tile side
+    int nimg;                       // tile images +-1..nimg checked per line (unwrapped positions)
+};
+
+// forward: planes kv0 .. kv0 + nb - 1 of u1 ([h][n1][n2]) -> out ([T][h][w]),
+// using the padded-plane buffer P ([nb][M1][M2]).  If sub != nullptr the
+// output is the value minus sub (same layout as out).
+template <typename T>
+cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* sub, int kv0, int nb,
+                               const Usfft2dArgs<T>& a, cudaStream_t s);
+// transpose: planes kv0 .. kv0 + nb - 1 of in ([T][h][w]) -> u1 ([h][n1][n2])
+template <typename T>
+cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int kv0, int nb,
+                               const Usfft2dArgs<T>& a, cudaStream_t s);
+
+// ---- F_2D / F*_2D (centred, per angle) ----------------------------------------
+template <typename T> struct Fft2dArgs {
+    int T_, h, w, logh, logw;
+    const C<T>* tw;
+    int twh, tww;                   // Nmax / h, Nmax / w
+};
+// dir = -1: sum exp(-...), dir = +1: sum exp(+...); result scaled by `scale`
+template <typename T>
+cudaError_t launch_fft2d_angles(const C<T>* in, C<T>* out, int dir, T scale, const Fft2dArgs<T>& a,
+                                cudaStream_t s);
+
+}  // namespace lam

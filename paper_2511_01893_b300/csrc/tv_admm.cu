@@ -1,0 +1,431 @@
+// tv_admm.cu - TV gradient / divergence and the fused ADMM-TV elementwise steps.
+//
+// Readings of the paper (which names the steps but not their discretisation):
+//   grad  forward differences along x, z, y of u[x][z][y] with a zero
+//         difference at the last index; div = -grad^T (Section 2, the nabla of
+//         Algorithms 1 and 2).
+//   LSP   G = Re L_hat^H r / (h w) - rho div(grad u - psi + lambda / rho),
+//         Dai-Yuan direction p = -G + beta p, beta = ||G||^2 / <p, G - G_prev>,
+//         exact line search gamma = -<G, p> / (||L_hat p||^2 / (h w) + rho ||grad p||^2),
+//         u += gamma p and r += gamma L_hat p (r = L_hat u - d_hat kept by linearity).
+//   RSP   psi = shrink_iso(grad u + lambda / rho, alpha / rho);
+//         lambda += rho (grad u - psi); residuals r = ||grad u - psi||,
+//         s = rho ||div(psi - psi_old)||; rho doubles if r > 10 s, halves if s > 10 r.
+//
+// Reductions are deterministic: each block folds its elements (FP32 partial
+// sums of at most 8 terms per thread in the FP32 path, then FP64), writes one
+// FP64 partial per quantity, and the last block to finish sums the partials in
+// a fixed order.  Scalars (rho, beta, gamma, norms) stay in device memory so a
+// whole outer iteration can be replayed as a CUDA graph.
+#include "admm.h"
+
+namespace lam {
+
+// ---------------------------------------------------------------------------
+// indexing helpers
+// ---------------------------------------------------------------------------
+
+// forward difference of f at (x,z,y) along axis a (0: x, 1: z, 2: y)
+template <typename T>
+__device__ __forceinline__ T fdiff(const T* __restrict__ f, long long i, int x, int z, int y, int a, const Vol& v) {
+    if (a == 0) return x + 1 < v.n1 ? f[i + (long long)v.nz * v.n2] - f[i] : (T)0;
+    if (a == 1) return z + 1 < v.nz ? f[i + v.n2] - f[i] : (T)0;
+    return y + 1 < v.n2 ? f[i + 1] - f[i] : (T)0;
+}
+
+__device__ __forceinline__ long long astride(int a, const Vol& v) {
+    return a == 0 ? (long long)v.nz * v.n2 : (a == 1 ? (long long)v.n2 : 1LL);
+}
+__device__ __forceinline__ int acoord(int a, int x, int z, int y) { return a == 0 ? x : (a == 1 ? z : y); }
+__device__ __forceinline__ int alen(int a, const Vol& v) { return a == 0 ? v.n1 : (a == 1 ? v.nz : v.n2); }
+
+// ---------------------------------------------------------------------------
+// deterministic block + grid reduction of K doubles
+// ---------------------------------------------------------------------------
+
+template <int K>
+__device__ void reduce_store(double (&val)[K], double* partials, unsigned int* counter, double* sc, int dst) {
+    __shared__ double sh[K][32];
+    __shared__ bool last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double v = val[k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[k][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < K; ++k) {
+            double s = 0;
+            for (int w = 0; w < nw; ++w) s += sh[k][w];
+            partials[blockIdx.x * K + k] = s;
+        }
+        __threadfence();
+        const unsigned int t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        double s = 0;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) s += ((volatile double*)partials)[b * K + k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[k][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < K; ++k) {
+            double s = 0;
+            for (int w = 0; w < nw; ++w) s += sh[k][w];
+            sc[dst + k] = s;
+        }
+        *counter = 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// grad / div
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_grad(const T* __restrict__ u, T* __restrict__ g, Vol v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
+        int x, z, y;
+        v.coords(i, x, z, y);
+        for (int a = 0; a < 3; ++a) g[a * v.N + i] = fdiff(u, i, x, z, y, a, v);
+    }
+}
+
+// div p at one voxel: sum_a p_a[i] [i_a <= N_a - 2] - p_a[i - e_a] [i_a >= 1]
+template <typename F>
+__device__ __forceinline__ auto div_at(F pa, long long i, int x, int z, int y, const Vol& v) -> decltype(pa(0, 0LL)) {
+    decltype(pa(0, 0LL)) s = 0;
+    for (int a = 0; a < 3; ++a) {
+        const int c = acoord(a, x, z, y), n = alen(a, v);
+        if (c + 1 < n) s += pa(a, i);
+        if (c >= 1) s -= pa(a, i - astride(a, v));
+    }
+    return s;
+}
+
+template <typename T>
+__global__ void k_div(const T* __restrict__ p, T* __restrict__ out, Vol v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
+        int x, z, y;
+        v.coords(i, x, z, y);
+        out[i] = div_at([&](int a, long long j) { return p[a * v.N + j]; }, i, x, z, y, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LSP steps
+// ---------------------------------------------------------------------------
+
+// G = Gd * inv_hw - rho * div(q),  q_a(j) = d_a u(j) - psi_a(j) + lambda_a(j) / rho.
+// Reduces ||G||^2, <p, G>, <p, G_prev> into sc[SC_GG..SC_GG+2].
+template <typename T>
+__global__ void __launch_bounds__(256) k_lsp_G(const T* __restrict__ Gd, const T* __restrict__ u,
+                                               const T* __restrict__ psi, const T* __restrict__ lam,
+                                               const T* __restrict__ p, const T* __restrict__ Gprev,
+                                               T* __restrict__ G, int first, AdmmRed r, Vol v) {
+    const double rho_d = r.sc[SC_RHO];
+    const T rho = (T)rho_d, irho = (T)(1.0 / rho_d), ihw = (T)r.sc[SC_INVHW];
+    double acc[3] = {0, 0, 0};
+    T loc[3] = {0, 0, 0};
+    int cnt = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
+        int x, z, y;
+        v.coords(i, x, z, y);
+        auto q = [&](int a, long long j) -> T {
+            int xx = x, zz = z, yy = y;
+            if (j != i) {  // j = i - e_a
+                if (a == 0) --xx;
+                else if (a == 1) --zz;
+                else --yy;
+            }
+            return fdiff(u, j, xx, zz, yy, a, v) - psi[a * v.N + j] + lam[a * v.N + j] * irho;
+        };
+        const T g = Gd[i] * ihw - rho * div_at(q, i, x, z, y, v);
+        G[i] = g;
+        loc[0] += g * g;
+        if (!first) {
+            const T pi = p[i];
+            loc[1] += pi * g;
+            loc[2] += pi * Gprev[i];
+        }
+        if (++cnt == 8) {
+            for (int k = 0; k < 3; ++k) { acc[k] += (double)loc[k]; loc[k] = 0; }
+            cnt = 0;
+        }
+    }
+    for (int k = 0; k < 3; ++k) acc[k] += (double)loc[k];
+    reduce_store<3>(acc, r.partials, r.counter, r.sc, SC_GG);
+}
+
+// beta (Dai-Yuan, 0 on the first step) and <G, p_new> = -||G||^2 + beta <p_old, G>
+__global__ void k_beta(double* sc, int first) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double GG = sc[SC_GG], pG = sc[SC_PG], pGp = sc[SC_PGP];
+    double beta = 0.0;
+    if (!first) {
+        const double den = pG - pGp;
+        beta = den != 0.0 ? GG / den : 0.0;
+    }
+    if (!isfinite(beta) || !isfinite(GG)) {
+        sc[SC_STATUS] = -5.0;
+        beta = 0.0;
+    }
+    sc[SC_BETA] = beta;
+    sc[SC_GP] = -GG + (first ? 0.0 : beta * pG);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_lsp_p(const T* __restrict__ G, T* __restrict__ p, const double* sc, Vol v) {
+    const T beta = (T)sc[SC_BETA];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x)
+        p[i] = -G[i] + beta * p[i];
+}
+
+// ||grad f||^2 into sc[dst]
+template <typename T>
+__global__ void __launch_bounds__(256) k_gradnorm2(const T* __restrict__ f, AdmmRed r, int dst, Vol v) {
+    double acc[1] = {0};
+    T loc = 0;
+    int cnt = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
+        int x, z, y;
+        v.coords(i, x, z, y);
+        for (int a = 0; a < 3; ++a) {
+            const T d = fdiff(f, i, x, z, y, a, v);
+            loc += d * d;
+        }
+        if (++cnt == 8) { acc[0] += (double)loc; loc = 0; cnt = 0; }
+    }
+    acc[0] += (double)loc;
+    reduce_store<1>(acc, r.partials, r.counter, r.sc, dst);
+}
+
+// ||c||^2 of a complex array into sc[dst]
+template <typename T>
+__global__ void __launch_bounds__(256) k_cnorm2(const C<T>* __restrict__ c, long long n, AdmmRed r, int dst) {
+    double acc[1] = {0};
+    T loc = 0;
+    int cnt = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const C<T> z = c[i];
+        loc += z.x * z.x + z.y * z.y;
+        if (++cnt == 8) { acc[0] += (double)loc; loc = 0; cnt = 0; }
+    }
+    acc[0] += (double)loc;
+    reduce_store<1>(acc, r.partials, r.counter, r.sc, dst);
+}
+
+__global__ void k_gamma(double* sc) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double den = sc[SC_LP2] * sc[SC_INVHW] + sc[SC_RHO] * sc[SC_GRADP2];
+    double g = den > 0.0 ? -sc[SC_GP] / den : 0.0;
+    if (!isfinite(g)) {
+        sc[SC_STATUS] = -5.0;
+        g = 0.0;
+    }
+    sc[SC_GAMMA] = g;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_axpy_u(T* __restrict__ u, const T* __restrict__ p, const double* sc, Vol v) {
+    const T g = (T)sc[SC_GAMMA];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x)
+        u[i] += g * p[i];
+}
+
+// r += gamma Lp; ||r||^2 into sc[SC_R2]
+template <typename T>
+__global__ void __launch_bounds__(256) k_axpy_r(C<T>* __restrict__ rr, const C<T>* __restrict__ Lp, long long n,
+                                                AdmmRed r) {
+    const T g = (T)r.sc[SC_GAMMA];
+    double acc[1] = {0};
+    T loc = 0;
+    int cnt = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        C<T> a = rr[i];
+        const C<T> b = Lp[i];
+        a.x += g * b.x;
+        a.y += g * b.y;
+        rr[i] = a;
+        loc += a.x * a.x + a.y * a.y;
+        if (++cnt == 8) { acc[0] += (double)loc; loc = 0; cnt = 0; }
+    }
+    acc[0] += (double)loc;
+    reduce_store<1>(acc, r.partials, r.counter, r.sc, SC_R2);
+}
+
+// ---------------------------------------------------------------------------
+// RSP, multiplier, residuals
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rsp(const T* __restrict__ u, T* __restrict__ psi, T* __restrict__ lam,
+                                             T* __restrict__ dpsi, AdmmRed r, Vol v) {
+    const double rho_d = r.sc[SC_RHO];
+    const T rho = (T)rho_d, irho = (T)(1.0 / rho_d), kappa = (T)(r.sc[SC_ALPHA] / rho_d);
+    double acc[2] = {0, 0};
+    T loc[2] = {0, 0};
+    int cnt = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
+        int x, z, y;
+        v.coords(i, x, z, y);
+        T gu[3], zz[3], pn[3];
+        T m2 = 0, g2 = 0;
+        for (int a = 0; a < 3; ++a) {
+            gu[a] = fdiff(u, i, x, z, y, a, v);
+            zz[a] = gu[a] + lam[a * v.N + i] * irho;
+            m2 += zz[a] * zz[a];
+            g2 += gu[a] * gu[a];
+        }
+        const T mag = sqrt(m2);
+        const T f = mag > kappa ? (T)1 - kappa / mag : (T)0;
+        T e2 = 0;
+        for (int a = 0; a < 3; ++a) {
+            pn[a] = f * zz[a];
+            const long long j = a * v.N + i;
+            dpsi[j] = pn[a] - psi[j];
+            psi[j] = pn[a];
+            const T e = gu[a] - pn[a];
+            lam[j] += rho * e;
+            e2 += e * e;
+        }
+        loc[0] += e2;
+        loc[1] += sqrt(g2);
+        if (++cnt == 8) {
+            acc[0] += (double)loc[0];
+            acc[1] += (double)loc[1];
+            loc[0] = loc[1] = 0;
+            cnt = 0;
+        }
+    }
+    acc[0] += (double)loc[0];
+    acc[1] += (double)loc[1];
+    reduce_store<2>(acc, r.partials, r.counter, r.sc, SC_RP2);
+}
+
+// ||div dpsi||^2 into sc[SC_SD2]
+template <typename T>
+__global__ void __launch_bounds__(256) k_divnorm2(const T* __restrict__ p, AdmmRed r, Vol v) {
+    double acc[1] = {0};
+    T loc = 0;
+    int cnt = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
+        int x, z, y;
+        v.coords(i, x, z, y);
+        const T d = div_at([&](int a, long long j) { return p[a * v.N + j]; }, i, x, z, y, v);
+        loc += d * d;
+        if (++cnt == 8) { acc[0] += (double)loc; loc = 0; cnt = 0; }
+    }
+    acc[0] += (double)loc;
+    reduce_store<1>(acc, r.partials, r.counter, r.sc, SC_SD2);
+}
+
+// residuals, objective, history, penalty update, iteration count
+__global__ void k_outer_scalars(double* sc, double* hist, int hist_cap) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double rho = sc[SC_RHO];
+    const double rr = sqrt(sc[SC_RP2]);
+    const double ss = rho * sqrt(sc[SC_SD2]);
+    const double data2 = sc[SC_R2] * sc[SC_INVHW];
+    const double obj = 0.5 * data2 + sc[SC_ALPHA] * sc[SC_TVSUM];
+    sc[SC_RESID_R] = rr;
+    sc[SC_RESID_S] = ss;
+    sc[SC_DATA2] = data2;
+    sc[SC_TV] = sc[SC_TVSUM];
+    sc[SC_OBJ] = obj;
+    if (!isfinite(obj) || !isfinite(rr) || !isfinite(ss)) sc[SC_STATUS] = -5.0;
+    const int it = (int)sc[SC_ITER];
+    if (it < hist_cap) {
+        hist[4 * it + 0] = obj;
+        hist[4 * it + 1] = rho;
+        hist[4 * it + 2] = rr;
+        hist[4 * it + 3] = ss;
+    }
+    if (sc[SC_ADAPT] != 0.0) {
+        if (rr > 10.0 * ss) sc[SC_RHO] = 2.0 * rho;
+        else if (ss > 10.0 * rr) sc[SC_RHO] = 0.5 * rho;
+    }
+    sc[SC_ITER] = it + 1;
+}
+
+// r = -d_hat (u = 0 at start), data weight, scalars
+template <typename T>
+__global__ void k_neg_copy(const C<T>* __restrict__ src, C<T>* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const C<T> a = src[i];
+        dst[i] = cmake<T>(-a.x, -a.y);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+static inline int egrid(long long n) {
+    long long b = (n + 255) / 256;
+    return (int)(b < kRedBlocks ? b : kRedBlocks);
+}
+
+template <typename T>
+cudaError_t Admm<T>::grad(const T* u, T* g, cudaStream_t s) const {
+    k_grad<T><<<egrid(v.N), 256, 0, s>>>(u, g, v);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t Admm<T>::div(const T* g, T* u, cudaStream_t s) const {
+    k_div<T><<<egrid(v.N), 256, 0, s>>>(g, u, v);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t Admm<T>::lsp_G(const T* Gd, const T* u, const T* psi, const T* lam, const T* p, const T* Gprev, T* G,
+                           int first, const AdmmRed& r, cudaStream_t s) const {
+    k_lsp_G<T><<<egrid(v.N), 256, 0, s>>>(Gd, u, psi, lam, p, Gprev, G, first, r, v);
+    k_beta<<<1, 32, 0, s>>>(r.sc, first);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t Admm<T>::lsp_p(const T* G, T* p, const AdmmRed& r, cudaStream_t s) const {
+    k_lsp_p<T><<<egrid(v.N), 256, 0, s>>>(G, p, r.sc, v);
+    k_gradnorm2<T><<<egrid(v.N), 256, 0, s>>>(p, r, SC_GRADP2, v);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t Admm<T>::lsp_update(T* u, const T* p, C<T>* res, const C<T>* Lp, long long nd, const AdmmRed& r,
+                                cudaStream_t s) const {
+    k_cnorm2<T><<<egrid(nd), 256, 0, s>>>(Lp, nd, r, SC_LP2);
+    k_gamma<<<1, 32, 0, s>>>(r.sc);
+    k_axpy_u<T><<<egrid(v.N), 256, 0, s>>>(u, p, r.sc, v);
+    k_axpy_r<T><<<egrid(nd), 256, 0, s>>>(res, Lp, nd, r);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t Admm<T>::rsp(const T* u, T* psi, T* lam, T* dpsi, const AdmmRed& r, double* hist, int hist_cap,
+                         cudaStream_t s) const {
+    k_rsp<T><<<egrid(v.N), 256, 0, s>>>(u, psi, lam, dpsi, r, v);
+    k_divnorm2<T><<<egrid(v.N), 256, 0, s>>>(dpsi, r, v);
+    k_outer_scalars<<<1, 32, 0, s>>>(r.sc, hist, hist_cap);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t Admm<T>::neg_copy(const C<T>* src, C<T>* dst, long long n, cudaStream_t s) const {
+    k_neg_copy<T><<<egrid(n), 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t Admm<T>::residual_norm(const C<T>* res, long long n, const AdmmRed& r, cudaStream_t s) const {
+    k_cnorm2<T><<<egrid(n), 256, 0, s>>>(res, n, r, SC_R2);
+    return cudaGetLastError();
+}
+
+template struct Admm<float>;
+template struct Admm<double>;
+
+}  // namespace lam

@@ -1,0 +1,366 @@
+// usfft2d.cu - F_u2D and its transpose: one 2D unequally-spaced FFT per kv plane.
+//
+// F_u2D (Section 2) maps u1[n1, h, n2] to u2[n_theta, h, w]: for each kv plane
+// it evaluates sum_{x,y} u1[x, kv, y] exp(-2 pi i (xi_x x + xi_y y)) at the
+// n_theta * w slice points (xi_x, xi_y)(theta, kv, ku).  Gaussian USFFT in 2D:
+// deapodise, zero-pad to M1 x M2 = 2 n1 x 2 n2, row FFTs (only the n1 non-zero
+// rows), column FFTs, then a separable 2m x 2m Gaussian gather.
+//
+// Forward (type 2) kernels, per batch of nb planes held in P[nb][M1][M2]:
+//   k_rowfft_fwd   u1 rows -> deapodised, padded, FFT along y -> P rows
+//   k_colfft_fwd   P columns (n1 non-zero entries) -> FFT along x, in place
+//   k_gather2d     one thread per slice point: 64 taps from P, optional fused
+//                  subtraction (out = value - sub, Section 4.2)
+// Transpose (type 1):
+//   k_scatter2d    tile-owned accumulation: a block owns a TS x TS tile of the
+//                  padded plane, finds for each angle the (contiguous) ku range
+//                  of slice points whose taps reach the tile, and accumulates
+//                  weight * value in per-warp shared-memory copies of the tile
+//                  (compensated summation in FP32); the copies are summed and
+//                  the tile is written once.  No global atomics; the result
+//                  does not depend on scheduling.
+//   k_colfft_adj   inverse FFT along x, keep the n1 rows the crop needs
+//   k_rowfft_adj   inverse FFT along y, crop, deapodise -> u1 rows
+#include "fft.cuh"
+#include "kernels.h"
+
+namespace lam {
+
+// --------------------------------------------------------------------------
+// row / column passes
+// --------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rowfft_fwd(const C<T>* __restrict__ u1, C<T>* __restrict__ P,
+                                                    int kv0, Usfft2dArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* bufb = bufa + a.RB * a.M2;
+    const int b = blockIdx.y, kv = kv0 + b;
+    const int x0 = blockIdx.x * a.RB;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    for (int i = tid; i < a.RB * a.M2; i += nthr) bufa[i] = cmake<T>(0, 0);
+    __syncthreads();
+    const C<T>* src = u1 + ((size_t)kv * a.n1 + x0) * a.n2;
+    for (int i = tid; i < a.RB * a.n2; i += nthr) {
+        const int r = i / a.n2, y = i - r * a.n2;
+        const T s = a.d1[x0 + r] * a.d2[y];
+        bufa[r * a.M2 + wrap(y - a.n2 / 2, a.M2)] = cscale(src[i], s);
+    }
+    __syncthreads();
+    const C<T>* res = fft_lines<-1, T>(bufa, bufb, a.RB, a.M2, a.M2, a.logM2, a.tw, a.tw2);
+    C<T>* dst = P + (size_t)b * a.M1 * a.M2;
+    for (int i = tid; i < a.RB * a.M2; i += nthr) {
+        const int r = i / a.M2, j = i - r * a.M2;
+        dst[(size_t)wrap(x0 + r - a.n1 / 2, a.M1) * a.M2 + j] = res[i];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_colfft_fwd(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* bufb = bufa + a.CB * a.M1;
+    const int b = blockIdx.y;
+    const int c0 = blockIdx.x * a.CB;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
+    for (int i = tid; i < a.CB * a.M1; i += nthr) bufa[i] = cmake<T>(0, 0);
+    __syncthreads();
+    for (int i = tid; i < a.n1 * a.CB; i += nthr) {
+        const int x = i / a.CB, c = i - x * a.CB;
+        const int row = wrap(x - a.n1 / 2, a.M1);
+        bufa[c * a.M1 + row] = pl[(size_t)row * a.M2 + c];
+    }
+    __syncthreads();
+    const C<T>* res = fft_lines<-1, T>(bufa, bufb, a.CB, a.M1, a.M1, a.logM1, a.tw, a.tw1);
+    for (int i = tid; i < a.M1 * a.CB; i += nthr) {
+        const int j = i / a.CB, c = i - j * a.CB;
+        pl[(size_t)j * a.M2 + c] = res[c * a.M1 + j];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_colfft_adj(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* bufb = bufa + a.CB * a.M1;
+    const int b = blockIdx.y;
+    const int c0 = blockIdx.x * a.CB;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
+    for (int i = tid; i < a.M1 * a.CB; i += nthr) {
+        const int j = i / a.CB, c = i - j * a.CB;
+        bufa[c * a.M1 + j] = pl[(size_t)j * a.M2 + c];
+    }
+    __syncthreads();
+    const C<T>* res = fft_lines<+1, T>(bufa, bufb, a.CB, a.M1, a.M1, a.logM1, a.tw, a.tw1);
+    for (int i = tid; i < a.n1 * a.CB; i += nthr) {
+        const int x = i / a.CB, c = i - x * a.CB;
+        const int row = wrap(x - a.n1 / 2, a.M1);
+        pl[(size_t)row * a.M2 + c] = res[c * a.M1 + row];
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rowfft_adj(const C<T>* __restrict__ P, C<T>* __restrict__ u1,
+                                                    int kv0, Usfft2dArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* bufb = bufa + a.RB * a.M2;
+    const int b = blockIdx.y, kv = kv0 + b;
+    const int x0 = blockIdx.x * a.RB;
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const C<T>* pl = P + (size_t)b * a.M1 * a.M2;
+    for (int i = tid; i < a.RB * a.M2; i += nthr) {
+        const int r = i / a.M2, j = i - r * a.M2;
+        bufa[i] = pl[(size_t)wrap(x0 + r - a.n1 / 2, a.M1) * a.M2 + j];
+    }
+    __syncthreads();
+    const C<T>* res = fft_lines<+1, T>(bufa, bufb, a.RB, a.M2, a.M2, a.logM2, a.tw, a.tw2);
+    C<T>* dst = u1 + ((size_t)kv * a.n1 + x0) * a.n2;
+    for (int i = tid; i < a.RB * a.n2; i += nthr) {
+        const int r = i / a.n2, y = i - r * a.n2;
+        const T s = a.d1[x0 + r] * a.d2[y];
+        dst[i] = cscale(res[r * a.M2 + wrap(y - a.n2 / 2, a.M2)], s);
+    }
+}
+
+// --------------------------------------------------------------------------
+// slice-point positions
+// --------------------------------------------------------------------------
+
+__device__ __forceinline__ void point_pos(const AngleF& g, int kuc, int kvc, int& jx, float& fx, int& jy,
+                                          float& fy) {
+    grid_pos(kuc, kvc, g.ax_hi, g.ax_lo, g.sx_hi, g.sx_lo, jx, fx);
+    grid_pos(kuc, kvc, g.ay_hi, g.ay_lo, g.sy_hi, g.sy_lo, jy, fy);
+}
+__device__ __forceinline__ void point_pos(const AngleD& g, int kuc, int kvc, int& jx, double& fx, int& jy,
+                                          double& fy) {
+    grid_pos(kuc, kvc, g.ax, g.sx, jx, fx);
+    grid_pos(kuc, kvc, g.ay, g.sy, jy, fy);
+}
+__device__ __forceinline__ void line_coef(const AngleF& g, int kvc, float& Ax, float& Cx, float& Ay, float& Cy) {
+    Ax = g.ax_hi;
+    Cx = (float)kvc * g.sx_hi;
+    Ay = g.ay_hi;
+    Cy = (float)kvc * g.sy_hi;
+}
+__device__ __forceinline__ void line_coef(const AngleD& g, int kvc, double& Ax, double& Cx, double& Ay,
+                                          double& Cy) {
+    Ax = g.ax;
+    Cx = (double)kvc * g.sx;
+    Ay = g.ay;
+    Cy = (double)kvc * g.sy;
+}
+
+// --------------------------------------------------------------------------
+// gather (type 2 interpolation) with optional fused subtraction
+// --------------------------------------------------------------------------
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather2d(const C<T>* __restrict__ P, C<T>* __restrict__ out,
+                                                  const C<T>* __restrict__ sub, int kv0, Usfft2dArgs<T> a) {
+    const int th = blockIdx.x, b = blockIdx.y, kv = kv0 + b;
+    const int kvc = kv - a.h / 2;
+    const typename AngleT<T>::type g = a.ang[th];
+    const C<T>* pl = P + (size_t)b * a.M1 * a.M2;
+    const int nt = 2 * a.m;
+    for (int ku = threadIdx.x; ku < a.w; ku += blockDim.x) {
+        int jx, jy;
+        T fx, fy;
+        point_pos(g, ku - a.w / 2, kvc, jx, fx, jy, fy);
+        T wy[16];
+        for (int t = 0; t < nt; ++t) {
+            const T d = fy + (T)(a.m - 1 - t);
+            wy[t] = gexp(-d * d * a.inv4beta);
+        }
+        T sr = 0, si = 0;
+        for (int s = 0; s < nt; ++s) {
+            const T dx = fx + (T)(a.m - 1 - s);
+            const T wx = gexp(-dx * dx * a.inv4beta);
+            const C<T>* row = pl + (size_t)wrap(jx - a.m + 1 + s, a.M1) * a.M2;
+            T rr = 0, ri = 0;
+            for (int t = 0; t < nt; ++t) {
+                const C<T> p = row[wrap(jy - a.m + 1 + t, a.M2)];
+                rr += wy[t] * p.x;
+                ri += wy[t] * p.y;
+            }
+            sr += wx * rr;
+            si += wx * ri;
+        }
+        const size_t o = ((size_t)th * a.h + kv) * a.w + ku;
+        C<T> v = cmake<T>(sr, si);
+        if (sub) v = csub(v, sub[o]);
+        out[o] = v;
+    }
+}
+
+// --------------------------------------------------------------------------
+// scatter (type 1 spreading), tile-owned, per-warp accumulators
+// --------------------------------------------------------------------------
+
+template <typename T> struct Acc;  // accumulator cell
+template <> struct Acc<float> {
+    float sr, si, cr, ci;  // sum and Kahan compensation
+    __device__ __forceinline__ void zero() { sr = si = cr = ci = 0.f; }
+    __device__ __forceinline__ void add(float vr, float vi) {
+        const float yr = vr - cr, yi = vi - ci;
+        const float tr = sr + yr, ti = si + yi;
+        cr = (tr - sr) - yr;
+        ci = (ti - si) - yi;
+        sr = tr;
+        si = ti;
+    }
+};
+template <> struct Acc<double> {
+    double sr, si;
+    __device__ __forceinline__ void zero() { sr = si = 0.0; }
+    __device__ __forceinline__ void add(double vr, double vi) {
+        sr += vr;
+        si += vi;
+    }
+};
+
+// ku interval [lo, hi] (centred) of points on the line p = A ku + Cc whose
+// position lies in [bmin, bmax); conservative by one point at each end.
+template <typename T>
+__device__ __forceinline__ void clip_line(T A, T Cc, T bmin, T bmax, int& lo, int& hi) {
+    if (fabs(A) < (T)1e-6) {
+        if (!(Cc >= bmin - (T)1 && Cc < bmax + (T)1)) {
+            lo = 1;
+            hi = 0;
+        }
+        return;
+    }
+    T t0 = (bmin - Cc) / A, t1 = (bmax - Cc) / A;
+    if (t0 > t1) {
+        const T tmp = t0;
+        t0 = t1;
+        t1 = tmp;
+    }
+    // clamp before the conversion so that huge quotients stay in int range
+    t0 = fmax(t0, (T)-1e8);
+    t1 = fmin(t1, (T)1e8);
+    const int l = (int)floor(t0) - 1, h = (int)ceil(t1) + 1;
+    lo = max(lo, l);
+    hi = min(hi, h);
+}
+
+template <typename T, int NW>
+__global__ void __launch_bounds__(NW * 32) k_scatter2d(const C<T>* __restrict__ in, C<T>* __restrict__ P,
+                                                       int kv0, Usfft2dArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Acc<T>* acc = reinterpret_cast<Acc<T>*>(smem_raw);  // [NW][TS*TS]
+    const int TS = a.TS;
+    const int tiles_y = a.M2 / TS;
+    const int tx0 = (blockIdx.x / tiles_y) * TS, ty0 = (blockIdx.x % tiles_y) * TS;
+    const int b = blockIdx.y, kv = kv0 + b, kvc = kv - a.h / 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < NW * TS * TS; i += blockDim.x) acc[i].zero();
+    __syncthreads();
+    Acc<T>* my = acc + warp * TS * TS;
+    const int nt = 2 * a.m, ntap = nt * nt;
+    const int kmin = -a.w / 2, kmax = a.w / 2 - 1;
+    for (int th = warp; th < a.T_; th += NW) {
+        const typename AngleT<T>::type g = a.ang[th];
+        T Ax, Cx, Ay, Cy;
+        line_coef(g, kvc, Ax, Cx, Ay, Cy);
+        // images of the tile in unwrapped coordinates
+        for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
+            const int bx0 = tx0 + ix * a.M1;
+            for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
+                const int by0 = ty0 + iy * a.M2;
+                int lo = kmin, hi = kmax;
+                clip_line<T>(Ax, Cx, (T)(bx0 - a.m), (T)(bx0 + TS + a.m - 1), lo, hi);
+                clip_line<T>(Ay, Cy, (T)(by0 - a.m), (T)(by0 + TS + a.m - 1), lo, hi);
+                for (int kuc = lo; kuc <= hi; ++kuc) {
+                    int jx, jy;
+                    T fx, fy;
+                    point_pos(g, kuc, kvc, jx, fx, jy, fy);
+                    const C<T> v = in[((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2)];
+                    for (int ti = lane; ti < ntap; ti += 32) {
+                        const int s = ti % nt, t = ti / nt;
+                        const int cx = jx - a.m + 1 + s - bx0;
+                        const int cy = jy - a.m + 1 + t - by0;
+                        if (cx >= 0 && cx < TS && cy >= 0 && cy < TS) {
+                            const T dx = fx + (T)(a.m - 1 - s);
+                            const T dy = fy + (T)(a.m - 1 - t);
+                            const T wgt = gexp(-dx * dx * a.inv4beta) * gexp(-dy * dy * a.inv4beta);
+                            my[cx * TS + cy].add(wgt * v.x, wgt * v.y);
+                        }
+                    }
+                    __syncwarp();
+                }
+            }
+        }
+    }
+    __syncthreads();
+    C<T>* pl = P + (size_t)b * a.M1 * a.M2;
+    for (int i = threadIdx.x; i < TS * TS; i += blockDim.x) {
+        Acc<T> tot;
+        tot.zero();
+        for (int wv = 0; wv < NW; ++wv) tot.add(acc[wv * TS * TS + i].sr, acc[wv * TS * TS + i].si);
+        const int cx = i / TS, cy = i - cx * TS;
+        pl[(size_t)(tx0 + cx) * a.M2 + ty0 + cy] = cmake<T>(tot.sr, tot.si);
+    }
+}
+
+// --------------------------------------------------------------------------
+// launchers
+// --------------------------------------------------------------------------
+
+constexpr int kScatterWarps = 4;
+
+template <typename T>
+cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* sub, int kv0, int nb,
+                               const Usfft2dArgs<T>& a, cudaStream_t s) {
+    const size_t sr = (size_t)2 * a.RB * a.M2 * sizeof(C<T>);
+    const size_t sc = (size_t)2 * a.CB * a.M1 * sizeof(C<T>);
+    k_rowfft_fwd<T><<<dim3(a.n1 / a.RB, nb), 256, sr, s>>>(u1, P, kv0, a);
+    k_colfft_fwd<T><<<dim3(a.M2 / a.CB, nb), 256, sc, s>>>(P, a);
+    k_gather2d<T><<<dim3(a.T_, nb), a.w < 256 ? a.w : 256, 0, s>>>(P, out, sub, kv0, a);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int kv0, int nb, const Usfft2dArgs<T>& a,
+                               cudaStream_t s) {
+    constexpr int NW = kScatterWarps;
+    const size_t sa = (size_t)NW * a.TS * a.TS * sizeof(Acc<T>);
+    const size_t sr = (size_t)2 * a.RB * a.M2 * sizeof(C<T>);
+    const size_t sc = (size_t)2 * a.CB * a.M1 * sizeof(C<T>);
+    k_scatter2d<T, NW><<<dim3((a.M1 / a.TS) * (a.M2 / a.TS), nb), NW * 32, sa, s>>>(in, P, kv0, a);
+    k_colfft_adj<T><<<dim3(a.M2 / a.CB, nb), 256, sc, s>>>(P, a);
+    k_rowfft_adj<T><<<dim3(a.n1 / a.RB, nb), 256, sr, s>>>(P, u1, kv0, a);
+    return cudaGetLastError();
+}
+
+template <typename T> size_t scatter_acc_bytes() { return sizeof(Acc<T>) * kScatterWarps; }
+
+template <typename T> cudaError_t configure_usfft2d() {
+    const int mx = kMaxDynSmem;
+    cudaError_t e = cudaSuccess;
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (!e) e = cudaFuncSetAttribute(k_rowfft_fwd<T>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_colfft_fwd<T>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_rowfft_adj<T>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_colfft_adj<T>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_scatter2d<T, kScatterWarps>, at, mx);
+    return e;
+}
+
+template cudaError_t launch_usfft2d_fwd<float>(const C<float>*, C<float>*, C<float>*, const C<float>*, int, int,
+                                               const Usfft2dArgs<float>&, cudaStream_t);
+template cudaError_t launch_usfft2d_fwd<double>(const C<double>*, C<double>*, C<double>*, const C<double>*, int,
+                                                int, const Usfft2dArgs<double>&, cudaStream_t);
+template cudaError_t launch_usfft2d_adj<float>(const C<float>*, C<float>*, C<float>*, int, int,
+                                               const Usfft2dArgs<float>&, cudaStream_t);
+template cudaError_t launch_usfft2d_adj<double>(const C<double>*, C<double>*, C<double>*, int, int,
+                                                const Usfft2dArgs<double>&, cudaStream_t);
+template size_t scatter_acc_bytes<float>();
+template size_t scatter_acc_bytes<double>();
+template cudaError_t configure_usfft2d<float>();
+template cudaError_t configure_usfft2d<double>();
+
+}  // namespace lam

@@ -1,0 +1,324 @@
+"""ctypes binding of liblamino.so (C ABI in include/lamino.h).
+
+Argument marshalling only: every step of the operator and of ADMM-TV runs in
+the library's CUDA kernels.  PyTorch supplies device memory (tensors) and the
+stream (``torch.cuda.current_stream()``).  There is no CPU fallback: if the
+library is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblamino.so")
+
+LAM_F32, LAM_F64 = 0, 1
+NSCALARS = 16
+SC = dict(rho=0, alpha=1, objective=2, r=3, s=4, iter=5, data2=6, tv=7, status=8)
+
+_lib = None
+
+
+class LaminoError(RuntimeError):
+    pass
+
+
+def lib() -> ctypes.CDLL:
+    """Load liblamino.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise LaminoError(f"{LIB_PATH} is missing: run `python -m paper_2511_01893_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        sig = {
+            "lam_plan_create": [ctypes.POINTER(vp), i, i, i, i, i, ctypes.POINTER(d), d, i, i, i],
+            "lam_plan_destroy": [vp],
+            "lam_forward": [vp, vp, vp, vp, vp],
+            "lam_adjoint": [vp, vp, vp, vp, vp],
+            "lam_forward_hat": [vp, vp, vp, vp, vp, vp],
+            "lam_adjoint_hat": [vp, vp, vp, vp, vp],
+            "lam_fft2d": [vp, vp, vp, i, vp],
+            "tv_grad": [vp, vp, vp, vp],
+            "tv_div": [vp, vp, vp, vp],
+            "admm_state_bytes": [vp, ctypes.POINTER(sz)],
+            "admm_init": [vp, vp, vp, d, d, i, i, vp, vp],
+            "admm_step": [vp, vp, vp, vp],
+            "admm_run": [vp, vp, vp, i, i, vp],
+            "admm_read_scalars": [vp, vp, ctypes.POINTER(d), vp],
+            "admm_read_history": [vp, vp, i, ctypes.POINTER(d), vp],
+            "admm_status": [vp, vp, vp],
+            "reconstruct": [vp, ctypes.POINTER(d), d, i, i, i, i, i, i, d, d, vp],
+            "lamx_u1d_fwd": [vp, vp, vp, vp],
+            "lamx_u1d_adj": [vp, vp, vp, vp],
+            "lamx_u2d_fwd": [vp, vp, vp, vp, vp, vp],
+            "lamx_u2d_adj": [vp, vp, vp, vp, vp],
+            "lamx_plan_info": [vp, ctypes.POINTER(i), i],
+            "lamx_admm_graph_kernels": [vp, vp, ctypes.POINTER(sz)],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.lam_workspace_bytes.argtypes = [vp]
+        L.lam_workspace_bytes.restype = sz
+        L.admm_u.argtypes = [vp, vp]
+        L.admm_u.restype = vp
+        L.lam_last_error.argtypes = []
+        L.lam_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        msg = lib().lam_last_error().decode(errors="replace")
+        raise LaminoError(f"{what} failed with status {status}: {msg}")
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise LaminoError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise LaminoError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+@dataclass(frozen=True)
+class Geometry:
+    n: int
+    nz: int
+    h: int
+    w: int
+    theta: tuple
+    phi: float
+    m: int = 4
+
+    @property
+    def n_theta(self) -> int:
+        return len(self.theta)
+
+
+class Plan:
+    """A plan for one geometry and precision ('f32' or 'f64') on the current device."""
+
+    def __init__(self, n, nz, h, w, theta, phi, m=4, prec="f32", device=None):
+        if not torch.cuda.is_available():
+            raise LaminoError("no CUDA device: the laminography operators run only on the GPU")
+        self.device = torch.device("cuda" if device is None else device)
+        theta = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+        self.n, self.nz, self.h, self.w, self.T = int(n), int(nz), int(h), int(w), len(theta)
+        self.theta, self.phi, self.m = theta, float(phi), int(m)
+        self.prec = prec
+        self.rdtype = torch.float32 if prec == "f32" else torch.float64
+        self.cdtype = torch.complex64 if prec == "f32" else torch.complex128
+        h_ = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(lib().lam_plan_create(ctypes.byref(h_), self.n, self.nz, self.h, self.w, self.T,
+                                         theta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.phi,
+                                         2, self.m, LAM_F32 if prec == "f32" else LAM_F64),
+                   "lam_plan_create")
+        self._h = h_
+        nbytes = lib().lam_workspace_bytes(self._h)
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.lam_plan_destroy(h)
+            self._h = None
+
+    # shapes
+    @property
+    def vol_shape(self):
+        return (self.n, self.nz, self.n)
+
+    @property
+    def data_shape(self):
+        return (self.T, self.h, self.w)
+
+    def _vol(self):
+        return torch.empty(self.vol_shape, dtype=self.rdtype, device=self.device)
+
+    def _data(self):
+        return torch.empty(self.data_shape, dtype=self.cdtype, device=self.device)
+
+    def _inp(self, t, dtype, shape):
+        t = torch.as_tensor(t)
+        if t.dtype != dtype or t.device != self.device or not t.is_contiguous():
+            t = t.to(device=self.device, dtype=dtype).contiguous()
+        if tuple(t.shape) != tuple(shape):
+            raise LaminoError(f"expected shape {shape}, got {tuple(t.shape)}")
+        return t
+
+    # operators
+    def forward(self, u, out=None):
+        u = self._inp(u, self.rdtype, self.vol_shape)
+        out = self._data() if out is None else out
+        _check(lib().lam_forward(self._h, _ptr(u), _ptr(out), _ptr(self.ws), _stream()), "lam_forward")
+        return out
+
+    def adjoint(self, d, out=None):
+        d = self._inp(d, self.cdtype, self.data_shape)
+        out = self._vol() if out is None else out
+        _check(lib().lam_adjoint(self._h, _ptr(d), _ptr(out), _ptr(self.ws), _stream()), "lam_adjoint")
+        return out
+
+    def forward_hat(self, u, sub=None, out=None):
+        u = self._inp(u, self.rdtype, self.vol_shape)
+        if sub is not None:
+            sub = self._inp(sub, self.cdtype, self.data_shape)
+        out = self._data() if out is None else out
+        _check(lib().lam_forward_hat(self._h, _ptr(u), _ptr(out), _ptr(sub), _ptr(self.ws), _stream()),
+               "lam_forward_hat")
+        return out
+
+    def adjoint_hat(self, d_hat, out=None):
+        d_hat = self._inp(d_hat, self.cdtype, self.data_shape)
+        out = self._vol() if out is None else out
+        _check(lib().lam_adjoint_hat(self._h, _ptr(d_hat), _ptr(out), _ptr(self.ws), _stream()),
+               "lam_adjoint_hat")
+        return out
+
+    def fft2d(self, x, inverse=False, out=None):
+        x = self._inp(x, self.cdtype, self.data_shape)
+        out = self._data() if out is None else out
+        _check(lib().lam_fft2d(self._h, _ptr(x), _ptr(out), int(bool(inverse)), _stream()), "lam_fft2d")
+        return out
+
+    def tv_grad(self, u, out=None):
+        u = self._inp(u, self.rdtype, self.vol_shape)
+        out = torch.empty((3,) + self.vol_shape, dtype=self.rdtype, device=self.device) if out is None else out
+        _check(lib().tv_grad(self._h, _ptr(u), _ptr(out), _stream()), "tv_grad")
+        return out
+
+    def tv_div(self, g, out=None):
+        g = self._inp(g, self.rdtype, (3,) + self.vol_shape)
+        out = self._vol() if out is None else out
+        _check(lib().tv_div(self._h, _ptr(g), _ptr(out), _stream()), "tv_div")
+        return out
+
+    # stages (u1 is complex [h][n][n], plane-major)
+    def u1d_fwd(self, u):
+        u = self._inp(u, self.rdtype, self.vol_shape)
+        out = torch.empty((self.h, self.n, self.n), dtype=self.cdtype, device=self.device)
+        _check(lib().lamx_u1d_fwd(self._h, _ptr(u), _ptr(out), _stream()), "lamx_u1d_fwd")
+        return out
+
+    def u1d_adj(self, u1):
+        u1 = self._inp(u1, self.cdtype, (self.h, self.n, self.n))
+        out = self._vol()
+        _check(lib().lamx_u1d_adj(self._h, _ptr(u1), _ptr(out), _stream()), "lamx_u1d_adj")
+        return out
+
+    def u2d_fwd(self, u1, sub=None):
+        u1 = self._inp(u1, self.cdtype, (self.h, self.n, self.n))
+        if sub is not None:
+            sub = self._inp(sub, self.cdtype, self.data_shape)
+        out = self._data()
+        _check(lib().lamx_u2d_fwd(self._h, _ptr(u1), _ptr(out), _ptr(sub), _ptr(self.ws), _stream()),
+               "lamx_u2d_fwd")
+        return out
+
+    def u2d_adj(self, d_hat):
+        d_hat = self._inp(d_hat, self.cdtype, self.data_shape)
+        out = torch.empty((self.h, self.n, self.n), dtype=self.cdtype, device=self.device)
+        _check(lib().lamx_u2d_adj(self._h, _ptr(d_hat), _ptr(out), _ptr(self.ws), _stream()), "lamx_u2d_adj")
+        return out
+
+    def info(self):
+        arr = (ctypes.c_int * 9)()
+        _check(lib().lamx_plan_info(self._h, arr, 9), "lamx_plan_info")
+        keys = ["TY_fwd", "TY_adj", "rows_per_block", "cols_per_block", "tile", "images", "planes_per_batch",
+                "jmin", "jmax"]
+        return dict(zip(keys, list(arr)))
+
+
+class Admm:
+    """ADMM-TV state on the device (caller-allocated through torch)."""
+
+    def __init__(self, plan: Plan):
+        self.plan = plan
+        nb = ctypes.c_size_t()
+        _check(lib().admm_state_bytes(plan._h, ctypes.byref(nb)), "admm_state_bytes")
+        self.state = torch.empty(nb.value, dtype=torch.uint8, device=plan.device)
+        self.iters = 0
+
+    def init(self, d, alpha, rho, n_inner=4, adapt_rho=True):
+        d = self.plan._inp(d, self.plan.cdtype, self.plan.data_shape)
+        _check(lib().admm_init(self.plan._h, _ptr(self.state), _ptr(d), float(alpha), float(rho), int(n_inner),
+                               int(bool(adapt_rho)), _ptr(self.plan.ws), _stream()), "admm_init")
+        self.iters = 0
+        return self
+
+    def step(self):
+        _check(lib().admm_step(self.plan._h, _ptr(self.state), _ptr(self.plan.ws), _stream()), "admm_step")
+        self.iters += 1
+
+    def run(self, iters, graph=False):
+        _check(lib().admm_run(self.plan._h, _ptr(self.state), _ptr(self.plan.ws), int(iters), int(bool(graph)),
+                              _stream()), "admm_run")
+        self.iters += iters
+
+    @property
+    def u(self) -> torch.Tensor:
+        """The volume u inside the state (a view; no copy)."""
+        p = self.plan
+        off = lib().admm_u(p._h, _ptr(self.state)) - self.state.data_ptr()
+        esz = 4 if p.prec == "f32" else 8
+        n = p.n * p.nz * p.n
+        return self.state[off:off + n * esz].view(p.rdtype).view(p.vol_shape)
+
+    def scalars(self) -> dict:
+        arr = (ctypes.c_double * NSCALARS)()
+        _check(lib().admm_read_scalars(self.plan._h, _ptr(self.state), arr, _stream()), "admm_read_scalars")
+        return {k: arr[i] for k, i in SC.items()}
+
+    def history(self, count=None) -> np.ndarray:
+        count = self.iters if count is None else count
+        arr = (ctypes.c_double * (4 * max(count, 1)))()
+        _check(lib().admm_read_history(self.plan._h, _ptr(self.state), count, arr, _stream()),
+               "admm_read_history")
+        return np.frombuffer(arr, dtype=np.float64)[: 4 * count].reshape(count, 4).copy()
+
+    def graph_kernels(self) -> int:
+        """Kernel launches per outer iteration in the captured graph (0 before a graph run)."""
+        n = ctypes.c_size_t()
+        _check(lib().lamx_admm_graph_kernels(self.plan._h, _ptr(self.state), ctypes.byref(n)),
+               "lamx_admm_graph_kernels")
+        return n.value
+
+    def status(self) -> int:
+        return lib().admm_status(self.plan._h, _ptr(self.state), _stream())
+
+
+def reconstruct(data, theta, phi, n, nz, iters, alpha, rho):
+    """One-call FP32 ADMM-TV (4 CG steps per iteration) from real data [T][h][w].
+
+    data may be a numpy array (host) or a CUDA tensor; returns u with the same
+    kind of storage."""
+    theta = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
+    if isinstance(data, torch.Tensor) and data.is_cuda:
+        d = data.to(torch.float32).contiguous()
+        out = torch.empty((n, nz, n), dtype=torch.float32, device=d.device)
+        dp, op = ctypes.c_void_p(d.data_ptr()), ctypes.c_void_p(out.data_ptr())
+    else:
+        d = np.ascontiguousarray(np.asarray(data, dtype=np.float32))
+        out = np.empty((n, nz, n), dtype=np.float32)
+        dp, op = ctypes.c_void_p(d.ctypes.data), ctypes.c_void_p(out.ctypes.data)
+    T, h, w = d.shape
+    _check(lib().reconstruct(dp, theta.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), float(phi), int(n), int(nz),
+                             int(h), int(w), int(T), int(iters), float(alpha), float(rho), op), "reconstruct")
+    return out
