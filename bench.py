@@ -22,12 +22,9 @@ is reduced across ranks.
 from __future__ import annotations
 
 import argparse
-import csv
-import io
 import json
 import os
 import statistics
-import subprocess
 import sys
 import time
 
@@ -72,43 +69,99 @@ def lhat_bytes(n, nz, h, w, T):
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    """Samples SM clock, power and clock-event reasons every 200 ms through
+    NVML (read-only queries) while the timed region runs."""
 
-    def __init__(self, gpu_index):
-        self.gpu = gpu_index
-        self.proc = None
+    REASONS = {"hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40,
+               "sw_power_cap": 0x4}
+
+    def __init__(self, gpu_index, period=0.2):
+        self.gpu, self.period = gpu_index, period
+        self.samples = []
+        self.errors = []
+        self._stop = None
+
+    def _run(self):
+        import pynvml
+        h = pynvml.nvmlDeviceGetHandleByIndex(self.gpu)
+        mx = pynvml.nvmlDeviceGetMaxClockInfo(h, pynvml.NVML_CLOCK_SM)
+        while not self._stop.is_set():
+            try:
+                sm = pynvml.nvmlDeviceGetClockInfo(h, pynvml.NVML_CLOCK_SM)
+                try:
+                    rs = pynvml.nvmlDeviceGetCurrentClocksEventReasons(h)
+                except AttributeError:
+                    rs = pynvml.nvmlDeviceGetCurrentClocksThrottleReasons(h)
+                pw = pynvml.nvmlDeviceGetPowerUsage(h) / 1000.0
+                self.samples.append((sm, mx, rs, pw))
+            except Exception as ex:
+                self.errors.append(repr(ex))
+            self._stop.wait(self.period)
 
     def __enter__(self):
+        import threading
+        self._smi = None
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
-                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-        except OSError:
-            self.proc = None
+            import pynvml
+            pynvml.nvmlInit()
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+            if vis and vis.split(",")[0].strip().isdigit():
+                self.gpu = int(vis.split(",")[self.gpu].strip())
+            self._stop = threading.Event()
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+        except Exception:
+            # no NVML bindings: nvidia-smi writes samples to a file
+            import subprocess
+            import tempfile
+            self._stop = None
+            self._file = tempfile.NamedTemporaryFile(prefix="clocks_", suffix=".csv", delete=False).name
+            q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap")
+            try:
+                self._smi = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                              "--format=csv,noheader,nounits", "-lms", str(int(self.period * 1000)),
+                                              "-f", self._file], stdout=subprocess.DEVNULL,
+                                             stderr=subprocess.DEVNULL)
+            except OSError as ex:
+                self.errors.append(repr(ex))
         return self
 
     def __exit__(self, *exc):
-        self.out = ""
-        if self.proc is not None:
-            self.proc.terminate()
+        if self._stop is not None:
+            self._stop.set()
+            self._t.join(timeout=2)
+        if self._smi is not None:
+            self._smi.terminate()
             try:
-                self.out, _ = self.proc.communicate(timeout=5)
-            except subprocess.TimeoutExpired:
-                self.proc.kill()
-                self.out, _ = self.proc.communicate()
+                self._smi.wait(timeout=5)
+            except Exception:
+                self._smi.kill()
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            bits = [self.REASONS[k] for k in names]
+            try:
+                for line in open(self._file):
+                    f = [x.strip() for x in line.split(",")]
+                    if len(f) < 7:
+                        continue
+                    try:
+                        sm, mx, pw = float(f[0]), float(f[1]), float(f[2])
+                    except ValueError:
+                        continue
+                    rs = sum(b for b, v in zip(bits, f[3:7]) if v.lower() == "active")
+                    self.samples.append((sm, mx, rs, pw))
+                os.unlink(self._file)
+            except OSError as ex:
+                self.errors.append(repr(ex))
 
     def summary(self):
-        rows = [r for r in csv.reader(io.StringIO(getattr(self, "out", ""))) if len(r) >= 9]
-        if not rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].strip().lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0,
+                    "errors": self.errors[:3]}
+        reasons = sorted({k for s in self.samples for k, bit in self.REASONS.items() if s[2] & bit})
+        return {"sm_mhz": statistics.median(s[0] for s in self.samples), "sm_max_mhz": max(s[1] for s in self.samples),
+                "power_w_max": max(s[3] for s in self.samples), "reasons": reasons, "samples": len(self.samples)}
 
 
 # ---------------------------------------------------------------------------

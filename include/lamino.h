@@ -110,6 +110,16 @@ lam_status tv_grad(const lam_plan* plan, const void* u, void* g, void* stream);
  * g real [3][n][nz][n] (read); u real [n][nz][n] (written). */
 lam_status tv_div(const lam_plan* plan, const void* g, void* u, void* stream);
 
+/* Smoothed isotropic TV (the alpha ||u||_TV term of Eq. 1 with |.| replaced
+ * by sqrt(|.|^2 + eps^2)), for gradient-based use and autograd:
+ *   value = sum_voxels sqrt(|grad u|^2 + eps^2)            (written to *value,
+ *           host memory, if value != NULL; synchronises `stream`)
+ *   grad  = -div(grad u / sqrt(|grad u|^2 + eps^2))       (if grad != NULL)
+ * u real [n][nz][n] (read); grad real [n][nz][n] (written); eps > 0.  Uses
+ * the reduction scratch at the end of ws. */
+lam_status tv_smooth(const lam_plan* plan, const void* u, double eps, void* grad, double* value, void* ws,
+                     void* stream);
+
 /* ---------------------------------------------------------------------------
  * ADMM-TV (Section 2: LSP, RSP, multiplier and penalty updates; LSP in the
  * Algorithm 2 form).  The state is one caller-allocated device buffer; the

@@ -61,14 +61,15 @@ template <typename T> struct Admm {
     Vol v;
     cudaError_t grad(const T* u, T* g, cudaStream_t s) const;
     cudaError_t div(const T* g, T* u, cudaStream_t s) const;
-    cudaError_t lsp_G(const T* Gd, const T* u, const T* psi, const T* lam, const T* p, const T* Gprev, T* G,
+    cudaError_t lsp_G(const T* Gd, const T* du, const T* e, const T* lam, const T* p, const T* Gprev, T* G,
                       int first, const AdmmRed& r, cudaStream_t s) const;
     cudaError_t lsp_p(const T* G, T* p, const AdmmRed& r, cudaStream_t s) const;
-    cudaError_t lsp_update(T* u, const T* p, C<T>* res, const C<T>* Lp, long long nd, const AdmmRed& r,
-                           cudaStream_t s) const;
-    cudaError_t rsp(const T* u, T* psi, T* lam, T* dpsi, const AdmmRed& r, double* hist, int hist_cap,
+    cudaError_t lsp_update(T* du, T* u, const T* p, int first, int last, C<T>* res, const C<T>* Lp, long long nd,
+                           const AdmmRed& r, cudaStream_t s) const;
+    cudaError_t rsp(const T* u, const T* du, T* e, T* lam, T* dpsi, const AdmmRed& r, double* hist, int hist_cap,
                     cudaStream_t s) const;
     cudaError_t neg_copy(const C<T>* src, C<T>* dst, long long n, cudaStream_t s) const;
+    cudaError_t tv_smooth(const T* u, T* g, double eps, const AdmmRed& r, int dst, cudaStream_t s) const;
     cudaError_t residual_norm(const C<T>* res, long long n, const AdmmRed& r, cudaStream_t s) const;
 };
 

@@ -83,8 +83,9 @@ struct lam_plan {
     int jmin, jmax;
     // launch shapes
     int TYf, TYa, RB, CB, TS, nimg, nbatch;
+    double rmax;
     // workspace layout
-    size_t ws_u1, ws_planes, ws_tmp, ws_bytes;
+    size_t ws_u1, ws_planes, ws_tmp, ws_red, ws_bytes;
     mutable std::mutex mu;
     mutable std::map<void*, AdmmHost> admm;
 
@@ -219,9 +220,14 @@ template <typename T> lam_status build_tables(lam_plan* p, const double* theta) 
     return st;
 }
 
-static int pick_lines(int len, size_t celem, size_t budget, int divides, int cap) {
+// lines per block for the in-place FFT kernels: shared memory (extra + lines *
+// len elements) within `budget`, lines * len within the register budget
+// 8 * MAXB * threads, `divides` a multiple of lines, at most `cap`
+static int pick_lines(int len, size_t celem, size_t budget, int divides, int cap, int maxb, size_t extra_per_line = 0) {
     int l = cap;
-    while (l > 1 && ((size_t)2 * l * len * celem > budget || divides % l != 0)) l >>= 1;
+    while (l > 1 && ((size_t)l * (len * celem + extra_per_line) > budget || (long long)l * len > 8LL * maxb * 512 ||
+                     divides % l != 0))
+        l >>= 1;
     return l;
 }
 
@@ -270,6 +276,7 @@ template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p) {
     a.CB = p->CB;
     a.TS = p->TS;
     a.nimg = p->nimg;
+    a.rmax = (T)p->rmax;
     return a;
 }
 
@@ -323,7 +330,7 @@ template <typename T> lam_status fft2d(const lam_plan* p, const C<T>* in, C<T>* 
 // ---- ADMM state layout -------------------------------------------------------
 
 struct StateLayout {
-    size_t sc, hist, partials, counter, u, Gd, G0, G1, p, psi, lam, dpsi, dhat, r, Lp, total;
+    size_t sc, hist, partials, counter, u, du, Gd, G0, G1, p, e, lam, dpsi, dhat, r, Lp, total;
 };
 
 StateLayout layout(const lam_plan* p) {
@@ -341,11 +348,12 @@ StateLayout layout(const lam_plan* p) {
     L.partials = take((size_t)kRedBlocks * 4 * sizeof(double));
     L.counter = take(sizeof(unsigned int));
     L.u = take(vb);
+    L.du = take(vb);
     L.Gd = take(vb);
     L.G0 = take(vb);
     L.G1 = take(vb);
     L.p = take(vb);
-    L.psi = take(3 * vb);
+    L.e = take(3 * vb);
     L.lam = take(3 * vb);
     L.dpsi = take(3 * vb);
     L.dhat = take(db);
@@ -367,7 +375,7 @@ __global__ void k_init_scalars(double* sc, double rho, double alpha, double invh
 }
 
 template <typename T> struct StatePtrs {
-    T *u, *Gd, *G0, *G1, *p, *psi, *lam, *dpsi;
+    T *u, *du, *Gd, *G0, *G1, *p, *e, *lam, *dpsi;
     C<T>*dhat, *r, *Lp;
     AdmmRed red;
     double* hist;
@@ -378,11 +386,12 @@ template <typename T> StatePtrs<T> ptrs(const lam_plan* p, void* state) {
     char* b = (char*)state;
     StatePtrs<T> s;
     s.u = (T*)(b + L.u);
+    s.du = (T*)(b + L.du);
     s.Gd = (T*)(b + L.Gd);
     s.G0 = (T*)(b + L.G0);
     s.G1 = (T*)(b + L.G1);
     s.p = (T*)(b + L.p);
-    s.psi = (T*)(b + L.psi);
+    s.e = (T*)(b + L.e);
     s.lam = (T*)(b + L.lam);
     s.dpsi = (T*)(b + L.dpsi);
     s.dhat = (C<T>*)(b + L.dhat);
@@ -412,7 +421,7 @@ lam_status admm_init_t(const lam_plan* p, void* state, const void* d, double alp
     const size_t vb = (size_t)p->nvox() * p->elem();
     CK(cudaMemsetAsync(S.u, 0, vb, s));
     CK(cudaMemsetAsync(S.p, 0, vb, s));
-    CK(cudaMemsetAsync(S.psi, 0, 3 * vb, s));
+    CK(cudaMemsetAsync(S.e, 0, 3 * vb, s));
     CK(cudaMemsetAsync(S.lam, 0, 3 * vb, s));
     (void)L;
     k_init_scalars<<<1, 32, 0, s>>>(S.red.sc, rho, alpha, 1.0 / ((double)p->h * p->w), adapt ? 1.0 : 0.0,
@@ -436,14 +445,14 @@ template <typename T> lam_status admm_step_t(const lam_plan* p, void* state, voi
         T* Gp = (i & 1) ? S.G0 : S.G1;
         // adjoint pass: G = Re L_hat^H r / (hw) - rho div(grad u - g)
         if ((st = adj_hat<T>(p, S.r, S.Gd, ws, s))) return st;
-        CK(ops.lsp_G(S.Gd, S.u, S.psi, S.lam, S.p, Gp, Gc, i == 0, S.red, s));
+        CK(ops.lsp_G(S.Gd, S.du, S.e, S.lam, S.p, Gp, Gc, i == 0, S.red, s));
         // CG direction and its forward pass
         CK(ops.lsp_p(Gc, S.p, S.red, s));
         if ((st = fwd_hat<T>(p, S.p, S.Lp, nullptr, ws, s))) return st;
-        // exact line search, u and residual update
-        CK(ops.lsp_update(S.u, S.p, S.r, S.Lp, nd, S.red, s));
+        // exact line search, increment and residual update (u += du on the last step)
+        CK(ops.lsp_update(S.du, S.u, S.p, i == 0, i == n_inner - 1, S.r, S.Lp, nd, S.red, s));
     }
-    CK(ops.rsp(S.u, S.psi, S.lam, S.dpsi, S.red, S.hist, kHistCap, s));
+    CK(ops.rsp(S.u, S.du, S.e, S.lam, S.dpsi, S.red, S.hist, kHistCap, s));
     return LAM_OK;
 }
 
@@ -533,23 +542,27 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     }
     const size_t ce_ = p->celem();
     const size_t budget = 200 * 1024;
+    const int maxb = prec == LAM_F32 ? 2 : 1;
     // z stage: TY columns per block
-    p->TYf = 16;
-    while (p->TYf > 1 && ((size_t)2 * p->TYf * p->M0 * ce_ > budget || p->n2 % p->TYf)) p->TYf >>= 1;
-    p->TYa = 16;
-    while (p->TYa > 1 && ((size_t)(2 * p->M0 + p->h) * p->TYa * ce_ > budget || p->n2 % p->TYa)) p->TYa >>= 1;
-    p->RB = pick_lines(p->M2, ce_, 96 * 1024, p->n1, 16);
-    p->CB = pick_lines(p->M1, ce_, 96 * 1024, p->M2, 16);
+    p->TYf = pick_lines(p->M0, ce_, budget, p->n2, 16, maxb);
+    p->TYa = pick_lines(p->M0, ce_, budget, p->n2, 16, maxb, (size_t)p->h * ce_);
+    p->RB = pick_lines(p->M2, ce_, 128 * 1024, p->n1, 16, maxb);
+    p->CB = pick_lines(p->M1, ce_, 128 * 1024, p->M2, 16, maxb);
     p->TS = std::min(32, std::min(p->M1, p->M2));
     // unwrapped slice positions reach |p| <= M (1 + sin phi) / 2 + m + 2
     const double reach = std::max(p->M1, p->M2) * (1.0 + std::sin(phi)) / 2.0 + p->m + 2;
     p->nimg = (int)std::ceil(reach / std::min(p->M1, p->M2));
+    // |position| <= (w/2) M / w + (h/2) M sin(phi) / h (+ 1 for the grid offset)
+    p->rmax = std::hypot(p->M1 * 0.5, p->M1 * 0.5 * std::sin(phi)) + 1.0;
     const size_t plane = (size_t)p->M1 * p->M2 * ce_;
     p->nbatch = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->h, (256u << 20) / plane));
     p->ws_u1 = 0;
     p->ws_planes = align256((size_t)p->h * p->n1 * p->n2 * ce_);
     p->ws_tmp = p->ws_planes + align256((size_t)p->nbatch * plane);
-    p->ws_bytes = p->ws_tmp + align256((size_t)p->ndata() * ce_);
+    p->ws_red = p->ws_tmp + align256((size_t)p->ndata() * ce_);
+    // reduction scratch: scalars, per-block partials, completion counter
+    p->ws_bytes = p->ws_red + align256(SC_COUNT * sizeof(double)) + align256((size_t)kRedBlocks * 4 * sizeof(double)) +
+                  256;
     *out = p;
     return LAM_OK;
 }
@@ -628,6 +641,28 @@ lam_status tv_div(const lam_plan* p, const void* g, void* u, void* stream) {
     cudaStream_t s = (cudaStream_t)stream;
     CK(DISPATCH(p, admm_ops<float>(p).div((const float*)g, (float*)u, s),
                 admm_ops<double>(p).div((const double*)g, (double*)u, s)));
+    return LAM_OK;
+}
+
+lam_status tv_smooth(const lam_plan* p, const void* u, double eps, void* grad, double* value, void* ws,
+                     void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!u || !ws) return fail(LAM_EINVAL, "NULL array argument");
+    if (!(eps > 0) || !std::isfinite(eps)) return fail(LAM_EINVAL, "eps = %g must be positive", eps);
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)ws + p->ws_red;
+    AdmmRed r;
+    r.sc = (double*)base;
+    r.partials = (double*)(base + align256(SC_COUNT * sizeof(double)));
+    r.counter = (unsigned int*)(base + align256(SC_COUNT * sizeof(double)) +
+                                align256((size_t)kRedBlocks * 4 * sizeof(double)));
+    CK(cudaMemsetAsync(r.counter, 0, sizeof(unsigned int), s));
+    CK(DISPATCH(p, admm_ops<float>(p).tv_smooth((const float*)u, (float*)grad, eps, r, 0, s),
+                admm_ops<double>(p).tv_smooth((const double*)u, (double*)grad, eps, r, 0, s)));
+    if (value) {
+        CK(cudaMemcpyAsync(value, r.sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+    }
     return LAM_OK;
 }
 

@@ -121,4 +121,93 @@ __device__ C<T>* fft_lines(C<T>* a, C<T>* b, int nlines, int lstride, int N, int
     return src;
 }
 
+// ---------------------------------------------------------------------------
+// In-place variant: one shared buffer.  Each stage first loads every
+// butterfly input the thread owns into registers (at most MAXB butterflies of
+// radix <= 8 per thread: nlines * N <= 8 * MAXB * blockDim.x), synchronises,
+// then writes the outputs.  Half the shared memory of the ping-pong form, so
+// blocks can hold twice the lines.
+// ---------------------------------------------------------------------------
+
+template <int R, int DIR, int MAXB, typename T>
+__device__ __forceinline__ void fft_stage_ip(C<T>* buf, int nlines, int lstride, int N, int Ns,
+                                             const C<T>* __restrict__ tw, int twstride, int tid, int nthr) {
+    const int nb = N / R;
+    const int total = nlines * nb;
+    const int twstep = (N / (Ns * R)) * twstride;
+    C<T> v[MAXB][R];
+#pragma unroll
+    for (int bb = 0; bb < MAXB; ++bb) {
+        const int q = tid + bb * nthr;
+        if (q < total) {
+            const int line = q / nb;
+            const int j = q - line * nb;
+            const C<T>* s = buf + line * lstride;
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[bb][r] = s[j + r * nb];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int bb = 0; bb < MAXB; ++bb) {
+        const int q = tid + bb * nthr;
+        if (q < total) {
+            const int line = q / nb;
+            const int j = q - line * nb;
+            const int k = j & (Ns - 1);
+            if (Ns > 1) {
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    C<T> wv = tw[r * k * twstep];
+                    if (DIR > 0) wv.y = -wv.y;
+                    v[bb][r] = cmul(v[bb][r], wv);
+                }
+            }
+            if (R == 8) dft8<DIR>(v[bb]);
+            else if (R == 4) dft4<DIR>(v[bb]);
+            else dft2<DIR>(v[bb]);
+            C<T>* d = buf + line * lstride;
+            const int base = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) d[base + r * Ns] = v[bb][r];
+        }
+    }
+    __syncthreads();
+}
+
+// In-place FFT of nlines lines in buf (same conventions as fft_lines).  The
+// caller must __syncthreads() before; the call ends with a __syncthreads().
+// Requires nlines * N <= 8 * MAXB * blockDim.x (radix-8 stages); radix-4 and
+// radix-2 stages need at most 2x / 4x that many butterflies, which the
+// register arrays hold as well because they are sized for radix 8.
+// Butterflies per thread per radix-8 stage the in-place kernels are built for
+// (register budget at 512 threads: 2 x 8 complex floats, 1 x 8 complex doubles).
+template <typename T> struct FftMaxB;
+template <> struct FftMaxB<float> { static constexpr int value = 2; };
+template <> struct FftMaxB<double> { static constexpr int value = 1; };
+constexpr int kFftThreads = 512;
+
+template <int DIR, int MAXB, typename T>
+__device__ __forceinline__ void fft_lines_ip(C<T>* buf, int nlines, int lstride, int N, int logN, const C<T>* __restrict__ tw,
+                             int twstride) {
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    int Ns = 1;
+    int bits = logN;
+    while (bits > 0) {
+        if (bits >= 3 && bits != 4) {
+            fft_stage_ip<8, DIR, MAXB, T>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
+            Ns *= 8;
+            bits -= 3;
+        } else if (bits >= 2) {
+            fft_stage_ip<4, DIR, 2 * MAXB, T>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
+            Ns *= 4;
+            bits -= 2;
+        } else {
+            fft_stage_ip<2, DIR, 4 * MAXB, T>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
+            Ns *= 2;
+            bits -= 1;
+        }
+    }
+}
+
 }  // namespace lam

@@ -14,11 +14,10 @@
 namespace lam {
 
 template <int DIR, typename T>
-__global__ void __launch_bounds__(256) k_fft2d_rows(const C<T>* in, C<T>* out,
+__global__ void __launch_bounds__(kFftThreads) k_fft2d_rows(const C<T>* in, C<T>* out,
                                                     int RB, Fft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    C<T>* bufb = bufa + RB * a.w;
     const int th = blockIdx.y, r0 = blockIdx.x * RB;
     const size_t base = ((size_t)th * a.h + r0) * a.w;
     for (int i = threadIdx.x; i < RB * a.w; i += blockDim.x) {
@@ -27,7 +26,8 @@ __global__ void __launch_bounds__(256) k_fft2d_rows(const C<T>* in, C<T>* out,
         bufa[i] = ((r0 + r + k) & 1) ? cmake<T>(-v.x, -v.y) : v;
     }
     __syncthreads();
-    const C<T>* res = fft_lines<DIR, T>(bufa, bufb, RB, a.w, a.w, a.logw, a.tw, a.tww);
+    fft_lines_ip<DIR, FftMaxB<T>::value, T>(bufa, RB, a.w, a.w, a.logw, a.tw, a.tww);
+    const C<T>* res = bufa;
     for (int i = threadIdx.x; i < RB * a.w; i += blockDim.x) {
         const int r = i / a.w, k = i - r * a.w;
         const C<T> v = res[i];
@@ -37,10 +37,9 @@ __global__ void __launch_bounds__(256) k_fft2d_rows(const C<T>* in, C<T>* out,
 }
 
 template <int DIR, typename T>
-__global__ void __launch_bounds__(256) k_fft2d_cols(C<T>* __restrict__ io, int CB, T scale, Fft2dArgs<T> a) {
+__global__ void __launch_bounds__(kFftThreads) k_fft2d_cols(C<T>* __restrict__ io, int CB, T scale, Fft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    C<T>* bufb = bufa + CB * a.h;
     const int th = blockIdx.y, c0 = blockIdx.x * CB;
     C<T>* pl = io + (size_t)th * a.h * a.w + c0;
     for (int i = threadIdx.x; i < a.h * CB; i += blockDim.x) {
@@ -48,7 +47,8 @@ __global__ void __launch_bounds__(256) k_fft2d_cols(C<T>* __restrict__ io, int C
         bufa[c * a.h + r] = pl[(size_t)r * a.w + c];
     }
     __syncthreads();
-    const C<T>* res = fft_lines<DIR, T>(bufa, bufb, CB, a.h, a.h, a.logh, a.tw, a.twh);
+    fft_lines_ip<DIR, FftMaxB<T>::value, T>(bufa, CB, a.h, a.h, a.logh, a.tw, a.twh);
+    const C<T>* res = bufa;
     const int gsign = ((a.h / 2 + a.w / 2) & 1);
     for (int i = threadIdx.x; i < a.h * CB; i += blockDim.x) {
         const int r = i / CB, c = i - r * CB;
@@ -58,31 +58,30 @@ __global__ void __launch_bounds__(256) k_fft2d_cols(C<T>* __restrict__ io, int C
     }
 }
 
-static int lines_per_block(int len, size_t elem) {
-    // two buffers of `lines` lines in at most 64 KB, at most 16 lines
-    int l = (int)((64 * 1024) / (2 * (size_t)len * elem));
-    if (l < 1) l = 1;
-    if (l > 16) l = 16;
-    int p = 1;
-    while (p * 2 <= l) p *= 2;
-    return p;
+// lines per block: at most 128 KB of shared memory, within the in-place FFT's
+// register budget (lines * len <= 8 * MAXB * threads), at most 32 lines
+template <typename T> static int lines_per_block(int len) {
+    const size_t elem = sizeof(C<T>);
+    int l = 32;
+    while (l > 1 && ((size_t)l * len * elem > 128 * 1024 || l * len > 8 * FftMaxB<T>::value * kFftThreads)) l >>= 1;
+    return l;
 }
 
 template <typename T>
 cudaError_t launch_fft2d_angles(const C<T>* in, C<T>* out, int dir, T scale, const Fft2dArgs<T>& a,
                                 cudaStream_t s) {
-    int RB = lines_per_block(a.w, sizeof(C<T>));
+    int RB = lines_per_block<T>(a.w);
     if (RB > a.h) RB = a.h;
-    int CB = lines_per_block(a.h, sizeof(C<T>));
+    int CB = lines_per_block<T>(a.h);
     if (CB > a.w) CB = a.w;
-    const size_t sr = (size_t)2 * RB * a.w * sizeof(C<T>);
-    const size_t sc = (size_t)2 * CB * a.h * sizeof(C<T>);
+    const size_t sr = (size_t)RB * a.w * sizeof(C<T>);
+    const size_t sc = (size_t)CB * a.h * sizeof(C<T>);
     if (dir > 0) {
-        k_fft2d_rows<1, T><<<dim3(a.h / RB, a.T_), 256, sr, s>>>(in, out, RB, a);
-        k_fft2d_cols<1, T><<<dim3(a.w / CB, a.T_), 256, sc, s>>>(out, CB, scale, a);
+        k_fft2d_rows<1, T><<<dim3(a.h / RB, a.T_), kFftThreads, sr, s>>>(in, out, RB, a);
+        k_fft2d_cols<1, T><<<dim3(a.w / CB, a.T_), kFftThreads, sc, s>>>(out, CB, scale, a);
     } else {
-        k_fft2d_rows<-1, T><<<dim3(a.h / RB, a.T_), 256, sr, s>>>(in, out, RB, a);
-        k_fft2d_cols<-1, T><<<dim3(a.w / CB, a.T_), 256, sc, s>>>(out, CB, scale, a);
+        k_fft2d_rows<-1, T><<<dim3(a.h / RB, a.T_), kFftThreads, sr, s>>>(in, out, RB, a);
+        k_fft2d_cols<-1, T><<<dim3(a.w / CB, a.T_), kFftThreads, sc, s>>>(out, CB, scale, a);
     }
     return cudaGetLastError();
 }

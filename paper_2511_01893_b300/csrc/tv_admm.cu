@@ -12,6 +12,17 @@
 //         lambda += rho (grad u - psi); residuals r = ||grad u - psi||,
 //         s = rho ||div(psi - psi_old)||; rho doubles if r > 10 s, halves if s > 10 r.
 //
+// Conditioning.  psi is close to grad u wherever the shrinkage is active, so
+// grad u - psi (which enters both the LSP gradient and the multiplier update)
+// is a small difference of two large numbers: formed from FP32 arrays it
+// carries an absolute error of ~1e-7 |grad u|, i.e. ~1e-4 relative.  The state
+// therefore stores the shrinkage residual e = grad u - psi itself, computed
+// from its closed form (e = kappa z/|z| - lambda/rho where the shrinkage is
+// active, e = grad u elsewhere, z = grad u + lambda/rho, kappa = alpha/rho),
+// and each LSP accumulates its increment du = u - u_start separately, so that
+// grad u - psi = grad du + e and psi - psi_old = grad du - (e - e_old) are
+// formed without cancellation.  psi itself is never stored.
+//
 // Reductions are deterministic: each block folds its elements (FP32 partial
 // sums of at most 8 terms per thread in the FP32 path, then FP64), writes one
 // FP64 partial per quantity, and the last block to finish sums the partials in
@@ -124,11 +135,12 @@ __global__ void k_div(const T* __restrict__ p, T* __restrict__ out, Vol v) {
 // LSP steps
 // ---------------------------------------------------------------------------
 
-// G = Gd * inv_hw - rho * div(q),  q_a(j) = d_a u(j) - psi_a(j) + lambda_a(j) / rho.
+// G = Gd * inv_hw - rho * div(q),  q_a(j) = d_a du(j) + e_a(j) + lambda_a(j) / rho
+// (= d_a u - psi_a + lambda_a / rho; du = 0 on the first CG step).
 // Reduces ||G||^2, <p, G>, <p, G_prev> into sc[SC_GG..SC_GG+2].
 template <typename T>
-__global__ void __launch_bounds__(256) k_lsp_G(const T* __restrict__ Gd, const T* __restrict__ u,
-                                               const T* __restrict__ psi, const T* __restrict__ lam,
+__global__ void __launch_bounds__(256) k_lsp_G(const T* __restrict__ Gd, const T* __restrict__ du,
+                                               const T* __restrict__ e, const T* __restrict__ lam,
                                                const T* __restrict__ p, const T* __restrict__ Gprev,
                                                T* __restrict__ G, int first, AdmmRed r, Vol v) {
     const double rho_d = r.sc[SC_RHO];
@@ -140,13 +152,17 @@ __global__ void __launch_bounds__(256) k_lsp_G(const T* __restrict__ Gd, const T
         int x, z, y;
         v.coords(i, x, z, y);
         auto q = [&](int a, long long j) -> T {
-            int xx = x, zz = z, yy = y;
-            if (j != i) {  // j = i - e_a
-                if (a == 0) --xx;
-                else if (a == 1) --zz;
-                else --yy;
+            T d = 0;
+            if (!first) {
+                int xx = x, zz = z, yy = y;
+                if (j != i) {  // j = i - e_a
+                    if (a == 0) --xx;
+                    else if (a == 1) --zz;
+                    else --yy;
+                }
+                d = fdiff(du, j, xx, zz, yy, a, v);
             }
-            return fdiff(u, j, xx, zz, yy, a, v) - psi[a * v.N + j] + lam[a * v.N + j] * irho;
+            return d + e[a * v.N + j] + lam[a * v.N + j] * irho;
         };
         const T g = Gd[i] * ihw - rho * div_at(q, i, x, z, y, v);
         G[i] = g;
@@ -234,11 +250,16 @@ __global__ void k_gamma(double* sc) {
     sc[SC_GAMMA] = g;
 }
 
+// du = gamma p (first CG step) or du += gamma p; on the last step also u += du
 template <typename T>
-__global__ void __launch_bounds__(256) k_axpy_u(T* __restrict__ u, const T* __restrict__ p, const double* sc, Vol v) {
+__global__ void __launch_bounds__(256) k_axpy_u(T* __restrict__ du, T* __restrict__ u, const T* __restrict__ p,
+                                                int first, int last, const double* sc, Vol v) {
     const T g = (T)sc[SC_GAMMA];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x)
-        u[i] += g * p[i];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
+        const T d = first ? g * p[i] : du[i] + g * p[i];
+        du[i] = d;
+        if (last) u[i] += d;
+    }
 }
 
 // r += gamma Lp; ||r||^2 into sc[SC_R2]
@@ -266,9 +287,12 @@ __global__ void __launch_bounds__(256) k_axpy_r(C<T>* __restrict__ rr, const C<T
 // RSP, multiplier, residuals
 // ---------------------------------------------------------------------------
 
+// psi = shrink(z, kappa), z = grad u + lambda / rho, kappa = alpha / rho, held as
+// e = grad u - psi; lambda += rho e; dpsi = psi - psi_old = grad du - (e - e_old).
+// Reduces ||e||^2 (the primal residual r^2) and TV(u) into sc[SC_RP2], sc[SC_TVSUM].
 template <typename T>
-__global__ void __launch_bounds__(256) k_rsp(const T* __restrict__ u, T* __restrict__ psi, T* __restrict__ lam,
-                                             T* __restrict__ dpsi, AdmmRed r, Vol v) {
+__global__ void __launch_bounds__(256) k_rsp(const T* __restrict__ u, const T* __restrict__ du, T* __restrict__ e,
+                                             T* __restrict__ lam, T* __restrict__ dpsi, AdmmRed r, Vol v) {
     const double rho_d = r.sc[SC_RHO];
     const T rho = (T)rho_d, irho = (T)(1.0 / rho_d), kappa = (T)(r.sc[SC_ALPHA] / rho_d);
     double acc[2] = {0, 0};
@@ -277,25 +301,27 @@ __global__ void __launch_bounds__(256) k_rsp(const T* __restrict__ u, T* __restr
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
         int x, z, y;
         v.coords(i, x, z, y);
-        T gu[3], zz[3], pn[3];
+        T gu[3], zz[3], lm[3];
         T m2 = 0, g2 = 0;
         for (int a = 0; a < 3; ++a) {
             gu[a] = fdiff(u, i, x, z, y, a, v);
-            zz[a] = gu[a] + lam[a * v.N + i] * irho;
+            lm[a] = lam[a * v.N + i];
+            zz[a] = gu[a] + lm[a] * irho;
             m2 += zz[a] * zz[a];
             g2 += gu[a] * gu[a];
         }
         const T mag = sqrt(m2);
-        const T f = mag > kappa ? (T)1 - kappa / mag : (T)0;
+        const bool active = mag > kappa;
+        const T kz = active ? kappa / mag : (T)0;
         T e2 = 0;
         for (int a = 0; a < 3; ++a) {
-            pn[a] = f * zz[a];
             const long long j = a * v.N + i;
-            dpsi[j] = pn[a] - psi[j];
-            psi[j] = pn[a];
-            const T e = gu[a] - pn[a];
-            lam[j] += rho * e;
-            e2 += e * e;
+            const T en = active ? kz * zz[a] - lm[a] * irho : gu[a];
+            const T ln = active ? rho * kz * zz[a] : lm[a] + rho * gu[a];
+            dpsi[j] = fdiff(du, i, x, z, y, a, v) - (en - e[j]);
+            e[j] = en;
+            lam[j] = ln;
+            e2 += en * en;
         }
         loc[0] += e2;
         loc[1] += sqrt(g2);
@@ -326,6 +352,46 @@ __global__ void __launch_bounds__(256) k_divnorm2(const T* __restrict__ p, AdmmR
     }
     acc[0] += (double)loc;
     reduce_store<1>(acc, r.partials, r.counter, r.sc, SC_SD2);
+}
+
+// Smoothed isotropic TV: value sum_i sqrt(|grad u|_i^2 + eps^2) into sc[dst] and,
+// if g != nullptr, its gradient g = -div(grad u / sqrt(|grad u|^2 + eps^2)).
+template <typename T>
+__device__ __forceinline__ T tv_unit(const T* __restrict__ u, long long j, int x, int z, int y, int a, T eps2,
+                                     const Vol& v) {
+    const T g0 = fdiff(u, j, x, z, y, 0, v), g1 = fdiff(u, j, x, z, y, 1, v), g2 = fdiff(u, j, x, z, y, 2, v);
+    const T ga = a == 0 ? g0 : (a == 1 ? g1 : g2);
+    return ga / sqrt(g0 * g0 + g1 * g1 + g2 * g2 + eps2);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_tv_smooth(const T* __restrict__ u, T* __restrict__ g, T eps, AdmmRed r,
+                                                   int dst, Vol v) {
+    const T eps2 = eps * eps;
+    double acc[1] = {0};
+    T loc = 0;
+    int cnt = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
+        int x, z, y;
+        v.coords(i, x, z, y);
+        const T g0 = fdiff(u, i, x, z, y, 0, v), g1 = fdiff(u, i, x, z, y, 1, v), g2 = fdiff(u, i, x, z, y, 2, v);
+        loc += sqrt(g0 * g0 + g1 * g1 + g2 * g2 + eps2);
+        if (g) {
+            auto nrm = [&](int a, long long j) -> T {
+                int xx = x, zz = z, yy = y;
+                if (j != i) {
+                    if (a == 0) --xx;
+                    else if (a == 1) --zz;
+                    else --yy;
+                }
+                return tv_unit(u, j, xx, zz, yy, a, eps2, v);
+            };
+            g[i] = -div_at(nrm, i, x, z, y, v);
+        }
+        if (++cnt == 8) { acc[0] += (double)loc; loc = 0; cnt = 0; }
+    }
+    acc[0] += (double)loc;
+    reduce_store<1>(acc, r.partials, r.counter, r.sc, dst);
 }
 
 // residuals, objective, history, penalty update, iteration count
@@ -385,9 +451,9 @@ cudaError_t Admm<T>::div(const T* g, T* u, cudaStream_t s) const {
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t Admm<T>::lsp_G(const T* Gd, const T* u, const T* psi, const T* lam, const T* p, const T* Gprev, T* G,
+cudaError_t Admm<T>::lsp_G(const T* Gd, const T* du, const T* e, const T* lam, const T* p, const T* Gprev, T* G,
                            int first, const AdmmRed& r, cudaStream_t s) const {
-    k_lsp_G<T><<<egrid(v.N), 256, 0, s>>>(Gd, u, psi, lam, p, Gprev, G, first, r, v);
+    k_lsp_G<T><<<egrid(v.N), 256, 0, s>>>(Gd, du, e, lam, p, Gprev, G, first, r, v);
     k_beta<<<1, 32, 0, s>>>(r.sc, first);
     return cudaGetLastError();
 }
@@ -398,18 +464,18 @@ cudaError_t Admm<T>::lsp_p(const T* G, T* p, const AdmmRed& r, cudaStream_t s) c
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t Admm<T>::lsp_update(T* u, const T* p, C<T>* res, const C<T>* Lp, long long nd, const AdmmRed& r,
-                                cudaStream_t s) const {
+cudaError_t Admm<T>::lsp_update(T* du, T* u, const T* p, int first, int last, C<T>* res, const C<T>* Lp, long long nd,
+                                const AdmmRed& r, cudaStream_t s) const {
     k_cnorm2<T><<<egrid(nd), 256, 0, s>>>(Lp, nd, r, SC_LP2);
     k_gamma<<<1, 32, 0, s>>>(r.sc);
-    k_axpy_u<T><<<egrid(v.N), 256, 0, s>>>(u, p, r.sc, v);
+    k_axpy_u<T><<<egrid(v.N), 256, 0, s>>>(du, u, p, first, last, r.sc, v);
     k_axpy_r<T><<<egrid(nd), 256, 0, s>>>(res, Lp, nd, r);
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t Admm<T>::rsp(const T* u, T* psi, T* lam, T* dpsi, const AdmmRed& r, double* hist, int hist_cap,
-                         cudaStream_t s) const {
-    k_rsp<T><<<egrid(v.N), 256, 0, s>>>(u, psi, lam, dpsi, r, v);
+cudaError_t Admm<T>::rsp(const T* u, const T* du, T* e, T* lam, T* dpsi, const AdmmRed& r, double* hist,
+                         int hist_cap, cudaStream_t s) const {
+    k_rsp<T><<<egrid(v.N), 256, 0, s>>>(u, du, e, lam, dpsi, r, v);
     k_divnorm2<T><<<egrid(v.N), 256, 0, s>>>(dpsi, r, v);
     k_outer_scalars<<<1, 32, 0, s>>>(r.sc, hist, hist_cap);
     return cudaGetLastError();
@@ -422,6 +488,12 @@ cudaError_t Admm<T>::neg_copy(const C<T>* src, C<T>* dst, long long n, cudaStrea
 template <typename T>
 cudaError_t Admm<T>::residual_norm(const C<T>* res, long long n, const AdmmRed& r, cudaStream_t s) const {
     k_cnorm2<T><<<egrid(n), 256, 0, s>>>(res, n, r, SC_R2);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t Admm<T>::tv_smooth(const T* u, T* g, double eps, const AdmmRed& r, int dst, cudaStream_t s) const {
+    k_tv_smooth<T><<<egrid(v.N), 256, 0, s>>>(u, g, (T)eps, r, dst, v);
     return cudaGetLastError();
 }
 

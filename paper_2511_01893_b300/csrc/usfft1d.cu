@@ -22,11 +22,10 @@
 namespace lam {
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_usfft1d_fwd(const T* __restrict__ u, C<T>* __restrict__ u1,
+__global__ void __launch_bounds__(kFftThreads) k_usfft1d_fwd(const T* __restrict__ u, C<T>* __restrict__ u1,
                                                      Usfft1dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    C<T>* bufb = bufa + a.TY * a.M0;
     const int tiles = a.n2 / a.TY;
     const int x = blockIdx.x / tiles;
     const int y0 = (blockIdx.x - x * tiles) * a.TY;
@@ -40,7 +39,8 @@ __global__ void __launch_bounds__(256) k_usfft1d_fwd(const T* __restrict__ u, C<
         bufa[c * a.M0 + wrap(z - a.nz / 2, a.M0)] = cmake<T>(v, 0);
     }
     __syncthreads();
-    const C<T>* P = fft_lines<-1, T>(bufa, bufb, a.TY, a.M0, a.M0, a.logM0, a.tw, a.twstride);
+    fft_lines_ip<-1, FftMaxB<T>::value, T>(bufa, a.TY, a.M0, a.M0, a.logM0, a.tw, a.twstride);
+    const C<T>* P = bufa;
     const int nt = 2 * a.m;
     C<T>* dst = u1 + (size_t)x * a.n2 + y0;
     const size_t plane = (size_t)a.n1 * a.n2;
@@ -60,12 +60,11 @@ __global__ void __launch_bounds__(256) k_usfft1d_fwd(const T* __restrict__ u, C<
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_usfft1d_adj(const C<T>* __restrict__ u1, T* __restrict__ u,
+__global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restrict__ u1, T* __restrict__ u,
                                                      Usfft1dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    C<T>* bufb = bufa + a.TY * a.M0;
-    C<T>* vals = bufb + a.TY * a.M0;  // [TY][h]
+    C<T>* vals = bufa + a.TY * a.M0;  // [TY][h]
     const int tiles = a.n2 / a.TY;
     const int x = blockIdx.x / tiles;
     const int y0 = (blockIdx.x - x * tiles) * a.TY;
@@ -96,7 +95,8 @@ __global__ void __launch_bounds__(256) k_usfft1d_adj(const C<T>* __restrict__ u1
         bufa[i] = cmake<T>(sr, si);
     }
     __syncthreads();
-    const C<T>* q = fft_lines<+1, T>(bufa, bufb, a.TY, a.M0, a.M0, a.logM0, a.tw, a.twstride);
+    fft_lines_ip<+1, FftMaxB<T>::value, T>(bufa, a.TY, a.M0, a.M0, a.logM0, a.tw, a.twstride);
+    const C<T>* q = bufa;
     T* dst = u + (size_t)x * a.nz * a.n2 + y0;
     for (int i = tid; i < a.nz * a.TY; i += nthr) {
         const int z = i / a.TY, c = i - z * a.TY;
@@ -106,15 +106,15 @@ __global__ void __launch_bounds__(256) k_usfft1d_adj(const C<T>* __restrict__ u1
 
 template <typename T>
 cudaError_t launch_usfft1d_fwd(const T* u, C<T>* u1, const Usfft1dArgs<T>& a, cudaStream_t s) {
-    const size_t smem = (size_t)2 * a.TY * a.M0 * sizeof(C<T>);
-    k_usfft1d_fwd<T><<<a.n1 * (a.n2 / a.TY), 256, smem, s>>>(u, u1, a);
+    const size_t smem = (size_t)a.TY * a.M0 * sizeof(C<T>);
+    k_usfft1d_fwd<T><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u, u1, a);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_usfft1d_adj(const C<T>* u1, T* u, const Usfft1dArgs<T>& a, cudaStream_t s) {
-    const size_t smem = (size_t)(2 * a.M0 + a.h) * a.TY * sizeof(C<T>);
-    k_usfft1d_adj<T><<<a.n1 * (a.n2 / a.TY), 256, smem, s>>>(u1, u, a);
+    const size_t smem = (size_t)(a.M0 + a.h) * a.TY * sizeof(C<T>);
+    k_usfft1d_adj<T><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u1, u, a);
     return cudaGetLastError();
 }
 

@@ -31,11 +31,10 @@ namespace lam {
 // --------------------------------------------------------------------------
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_rowfft_fwd(const C<T>* __restrict__ u1, C<T>* __restrict__ P,
+__global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(const C<T>* __restrict__ u1, C<T>* __restrict__ P,
                                                     int kv0, Usfft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    C<T>* bufb = bufa + a.RB * a.M2;
     const int b = blockIdx.y, kv = kv0 + b;
     const int x0 = blockIdx.x * a.RB;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -48,7 +47,8 @@ __global__ void __launch_bounds__(256) k_rowfft_fwd(const C<T>* __restrict__ u1,
         bufa[r * a.M2 + wrap(y - a.n2 / 2, a.M2)] = cscale(src[i], s);
     }
     __syncthreads();
-    const C<T>* res = fft_lines<-1, T>(bufa, bufb, a.RB, a.M2, a.M2, a.logM2, a.tw, a.tw2);
+    fft_lines_ip<-1, FftMaxB<T>::value, T>(bufa, a.RB, a.M2, a.M2, a.logM2, a.tw, a.tw2);
+    const C<T>* res = bufa;
     C<T>* dst = P + (size_t)b * a.M1 * a.M2;
     for (int i = tid; i < a.RB * a.M2; i += nthr) {
         const int r = i / a.M2, j = i - r * a.M2;
@@ -57,10 +57,9 @@ __global__ void __launch_bounds__(256) k_rowfft_fwd(const C<T>* __restrict__ u1,
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_colfft_fwd(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
+__global__ void __launch_bounds__(kFftThreads) k_colfft_fwd(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    C<T>* bufb = bufa + a.CB * a.M1;
     const int b = blockIdx.y;
     const int c0 = blockIdx.x * a.CB;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -73,7 +72,8 @@ __global__ void __launch_bounds__(256) k_colfft_fwd(C<T>* __restrict__ P, Usfft2
         bufa[c * a.M1 + row] = pl[(size_t)row * a.M2 + c];
     }
     __syncthreads();
-    const C<T>* res = fft_lines<-1, T>(bufa, bufb, a.CB, a.M1, a.M1, a.logM1, a.tw, a.tw1);
+    fft_lines_ip<-1, FftMaxB<T>::value, T>(bufa, a.CB, a.M1, a.M1, a.logM1, a.tw, a.tw1);
+    const C<T>* res = bufa;
     for (int i = tid; i < a.M1 * a.CB; i += nthr) {
         const int j = i / a.CB, c = i - j * a.CB;
         pl[(size_t)j * a.M2 + c] = res[c * a.M1 + j];
@@ -81,10 +81,9 @@ __global__ void __launch_bounds__(256) k_colfft_fwd(C<T>* __restrict__ P, Usfft2
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_colfft_adj(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
+__global__ void __launch_bounds__(kFftThreads) k_colfft_adj(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    C<T>* bufb = bufa + a.CB * a.M1;
     const int b = blockIdx.y;
     const int c0 = blockIdx.x * a.CB;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -94,7 +93,8 @@ __global__ void __launch_bounds__(256) k_colfft_adj(C<T>* __restrict__ P, Usfft2
         bufa[c * a.M1 + j] = pl[(size_t)j * a.M2 + c];
     }
     __syncthreads();
-    const C<T>* res = fft_lines<+1, T>(bufa, bufb, a.CB, a.M1, a.M1, a.logM1, a.tw, a.tw1);
+    fft_lines_ip<+1, FftMaxB<T>::value, T>(bufa, a.CB, a.M1, a.M1, a.logM1, a.tw, a.tw1);
+    const C<T>* res = bufa;
     for (int i = tid; i < a.n1 * a.CB; i += nthr) {
         const int x = i / a.CB, c = i - x * a.CB;
         const int row = wrap(x - a.n1 / 2, a.M1);
@@ -103,11 +103,10 @@ __global__ void __launch_bounds__(256) k_colfft_adj(C<T>* __restrict__ P, Usfft2
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_rowfft_adj(const C<T>* __restrict__ P, C<T>* __restrict__ u1,
+__global__ void __launch_bounds__(kFftThreads) k_rowfft_adj(const C<T>* __restrict__ P, C<T>* __restrict__ u1,
                                                     int kv0, Usfft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    C<T>* bufb = bufa + a.RB * a.M2;
     const int b = blockIdx.y, kv = kv0 + b;
     const int x0 = blockIdx.x * a.RB;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -117,7 +116,8 @@ __global__ void __launch_bounds__(256) k_rowfft_adj(const C<T>* __restrict__ P, 
         bufa[i] = pl[(size_t)wrap(x0 + r - a.n1 / 2, a.M1) * a.M2 + j];
     }
     __syncthreads();
-    const C<T>* res = fft_lines<+1, T>(bufa, bufb, a.RB, a.M2, a.M2, a.logM2, a.tw, a.tw2);
+    fft_lines_ip<+1, FftMaxB<T>::value, T>(bufa, a.RB, a.M2, a.M2, a.logM2, a.tw, a.tw2);
+    const C<T>* res = bufa;
     C<T>* dst = u1 + ((size_t)kv * a.n1 + x0) * a.n2;
     for (int i = tid; i < a.RB * a.n2; i += nthr) {
         const int r = i / a.n2, y = i - r * a.n2;
@@ -247,12 +247,20 @@ __device__ __forceinline__ void clip_line(T A, T Cc, T bmin, T bmax, int& lo, in
     hi = min(hi, h);
 }
 
+// Per-warp staging of up to 32 slice points: tap origin, weights, value.
+template <typename T> struct PointStage {
+    int jx[32], jy[32];
+    T wx[32][17], wy[32][17];  // padded: lane-strided writes stay conflict-free
+    C<T> v[32];
+};
+
 template <typename T, int NW>
 __global__ void __launch_bounds__(NW * 32) k_scatter2d(const C<T>* __restrict__ in, C<T>* __restrict__ P,
                                                        int kv0, Usfft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Acc<T>* acc = reinterpret_cast<Acc<T>*>(smem_raw);  // [NW][TS*TS]
     const int TS = a.TS;
+    Acc<T>* acc = reinterpret_cast<Acc<T>*>(smem_raw);  // [NW][TS*TS]
+    PointStage<T>* stage = reinterpret_cast<PointStage<T>*>(smem_raw + (size_t)NW * TS * TS * sizeof(Acc<T>));
     const int tiles_y = a.M2 / TS;
     const int tx0 = (blockIdx.x / tiles_y) * TS, ty0 = (blockIdx.x % tiles_y) * TS;
     const int b = blockIdx.y, kv = kv0 + b, kvc = kv - a.h / 2;
@@ -260,37 +268,79 @@ __global__ void __launch_bounds__(NW * 32) k_scatter2d(const C<T>* __restrict__ 
     for (int i = threadIdx.x; i < NW * TS * TS; i += blockDim.x) acc[i].zero();
     __syncthreads();
     Acc<T>* my = acc + warp * TS * TS;
+    PointStage<T>& st = stage[warp];
     const int nt = 2 * a.m, ntap = nt * nt;
     const int kmin = -a.w / 2, kmax = a.w / 2 - 1;
-    for (int th = warp; th < a.T_; th += NW) {
-        const typename AngleT<T>::type g = a.ang[th];
-        T Ax, Cx, Ay, Cy;
-        line_coef(g, kvc, Ax, Cx, Ay, Cy);
-        // images of the tile in unwrapped coordinates
-        for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
-            const int bx0 = tx0 + ix * a.M1;
-            for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
-                const int by0 = ty0 + iy * a.M2;
-                int lo = kmin, hi = kmax;
-                clip_line<T>(Ax, Cx, (T)(bx0 - a.m), (T)(bx0 + TS + a.m - 1), lo, hi);
-                clip_line<T>(Ay, Cy, (T)(by0 - a.m), (T)(by0 + TS + a.m - 1), lo, hi);
-                for (int kuc = lo; kuc <= hi; ++kuc) {
-                    int jx, jy;
-                    T fx, fy;
-                    point_pos(g, kuc, kvc, jx, fx, jy, fy);
-                    const C<T> v = in[((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2)];
-                    for (int ti = lane; ti < ntap; ti += 32) {
-                        const int s = ti % nt, t = ti / nt;
-                        const int cx = jx - a.m + 1 + s - bx0;
-                        const int cy = jy - a.m + 1 + t - by0;
-                        if (cx >= 0 && cx < TS && cy >= 0 && cy < TS) {
-                            const T dx = fx + (T)(a.m - 1 - s);
-                            const T dy = fy + (T)(a.m - 1 - t);
-                            const T wgt = gexp(-dx * dx * a.inv4beta) * gexp(-dy * dy * a.inv4beta);
-                            my[cx * TS + cy].add(wgt * v.x, wgt * v.y);
+    // half-extent of the box of point positions whose taps reach the tile
+    const T hx = (T)(TS + 2 * a.m) * (T)0.5, hy = hx;
+    for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
+        const int bx0 = tx0 + ix * a.M1;
+        for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
+            const int by0 = ty0 + iy * a.M2;
+            // centre of the position box (positions p with taps in [b0, b0 + TS))
+            const T cx = (T)bx0 + (T)(TS - 1) * (T)0.5, cy = (T)by0 + (T)(TS - 1) * (T)0.5;
+            if (sqrt(cx * cx + cy * cy) > a.rmax + hx * (T)1.5) continue;
+            int seen = 0;  // crossing lines found so far (all warps see the same sequence)
+            for (int base = 0; base < a.T_; base += 32) {
+                const int th = base + lane;
+                bool hit = false;
+                if (th < a.T_) {
+                    // the line p(ku) = ku A + kvc S has direction A / |A| and passes at
+                    // signed distance kvc |S| from the origin; test the distance from the
+                    // box centre against the box's support in the normal direction
+                    const typename AngleT<T>::type g = a.ang[th];
+                    T Ax, Cx, Ay, Cy;
+                    line_coef(g, kvc, Ax, Cx, Ay, Cy);
+                    const T nrm = sqrt(Ax * Ax + Ay * Ay);
+                    const T nx = -Ay / nrm, ny = Ax / nrm;
+                    const T dist = fabs((cx - Cx) * nx + (cy - Cy) * ny);
+                    hit = dist <= hx * fabs(nx) + hy * fabs(ny) + (T)1;
+                }
+                unsigned mask = __ballot_sync(0xffffffffu, hit);
+                while (mask) {
+                    const int bit = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const int my_turn = (seen++ % NW) == warp;
+                    if (!my_turn) continue;
+                    const int th2 = base + bit;
+                    const typename AngleT<T>::type g = a.ang[th2];
+                    T Ax, Cx, Ay, Cy;
+                    line_coef(g, kvc, Ax, Cx, Ay, Cy);
+                    int lo = kmin, hi = kmax;
+                    clip_line<T>(Ax, Cx, (T)(bx0 - a.m), (T)(bx0 + TS + a.m - 1), lo, hi);
+                    clip_line<T>(Ay, Cy, (T)(by0 - a.m), (T)(by0 + TS + a.m - 1), lo, hi);
+                    const C<T>* row = in + ((size_t)th2 * a.h + kv) * a.w + a.w / 2;
+                    for (int k0 = lo; k0 <= hi; k0 += 32) {
+                        const int cnt = min(32, hi - k0 + 1);
+                        if (lane < cnt) {
+                            const int kuc = k0 + lane;
+                            int jx, jy;
+                            T fx, fy;
+                            point_pos(g, kuc, kvc, jx, fx, jy, fy);
+                            st.jx[lane] = jx - a.m + 1 - bx0;
+                            st.jy[lane] = jy - a.m + 1 - by0;
+                            for (int t = 0; t < nt; ++t) {
+                                const T dx = fx + (T)(a.m - 1 - t), dy = fy + (T)(a.m - 1 - t);
+                                st.wx[lane][t] = gexp(-dx * dx * a.inv4beta);
+                                st.wy[lane][t] = gexp(-dy * dy * a.inv4beta);
+                            }
+                            st.v[lane] = row[kuc];
+                        }
+                        __syncwarp();
+                        for (int q = 0; q < cnt; ++q) {
+                            const int ox = st.jx[q], oy = st.jy[q];
+                            const C<T> v = st.v[q];
+                            for (int ti = lane; ti < ntap; ti += 32) {
+                                const int sx = ti % nt, sy = ti / nt;
+                                const int cx2 = ox + sx, cy2 = oy + sy;
+                                if (cx2 >= 0 && cx2 < TS && cy2 >= 0 && cy2 < TS) {
+                                    const T wgt = st.wx[q][sx] * st.wy[q][sy];
+                                    my[cx2 * TS + cy2].add(wgt * v.x, wgt * v.y);
+                                }
+                            }
+                            __syncwarp();
                         }
                     }
-                    __syncwarp();
                 }
             }
         }
@@ -315,10 +365,10 @@ constexpr int kScatterWarps = 4;
 template <typename T>
 cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* sub, int kv0, int nb,
                                const Usfft2dArgs<T>& a, cudaStream_t s) {
-    const size_t sr = (size_t)2 * a.RB * a.M2 * sizeof(C<T>);
-    const size_t sc = (size_t)2 * a.CB * a.M1 * sizeof(C<T>);
-    k_rowfft_fwd<T><<<dim3(a.n1 / a.RB, nb), 256, sr, s>>>(u1, P, kv0, a);
-    k_colfft_fwd<T><<<dim3(a.M2 / a.CB, nb), 256, sc, s>>>(P, a);
+    const size_t sr = (size_t)a.RB * a.M2 * sizeof(C<T>);
+    const size_t sc = (size_t)a.CB * a.M1 * sizeof(C<T>);
+    k_rowfft_fwd<T><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, kv0, a);
+    k_colfft_fwd<T><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
     k_gather2d<T><<<dim3(a.T_, nb), a.w < 256 ? a.w : 256, 0, s>>>(P, out, sub, kv0, a);
     return cudaGetLastError();
 }
@@ -327,12 +377,12 @@ template <typename T>
 cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int kv0, int nb, const Usfft2dArgs<T>& a,
                                cudaStream_t s) {
     constexpr int NW = kScatterWarps;
-    const size_t sa = (size_t)NW * a.TS * a.TS * sizeof(Acc<T>);
-    const size_t sr = (size_t)2 * a.RB * a.M2 * sizeof(C<T>);
-    const size_t sc = (size_t)2 * a.CB * a.M1 * sizeof(C<T>);
+    const size_t sa = (size_t)NW * a.TS * a.TS * sizeof(Acc<T>) + (size_t)NW * sizeof(PointStage<T>);
+    const size_t sr = (size_t)a.RB * a.M2 * sizeof(C<T>);
+    const size_t sc = (size_t)a.CB * a.M1 * sizeof(C<T>);
     k_scatter2d<T, NW><<<dim3((a.M1 / a.TS) * (a.M2 / a.TS), nb), NW * 32, sa, s>>>(in, P, kv0, a);
-    k_colfft_adj<T><<<dim3(a.M2 / a.CB, nb), 256, sc, s>>>(P, a);
-    k_rowfft_adj<T><<<dim3(a.n1 / a.RB, nb), 256, sr, s>>>(P, u1, kv0, a);
+    k_colfft_adj<T><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+    k_rowfft_adj<T><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(P, u1, kv0, a);
     return cudaGetLastError();
 }
 

@@ -46,6 +46,7 @@ def lib() -> ctypes.CDLL:
             "lam_fft2d": [vp, vp, vp, i, vp],
             "tv_grad": [vp, vp, vp, vp],
             "tv_div": [vp, vp, vp, vp],
+            "tv_smooth": [vp, vp, d, vp, ctypes.POINTER(d), vp, vp],
             "admm_state_bytes": [vp, ctypes.POINTER(sz)],
             "admm_init": [vp, vp, vp, d, d, i, i, vp, vp],
             "admm_step": [vp, vp, vp, vp],
@@ -210,6 +211,15 @@ class Plan:
         _check(lib().tv_div(self._h, _ptr(g), _ptr(out), _stream()), "tv_div")
         return out
 
+    def tv_smooth(self, u, eps, grad=True):
+        """(sum sqrt(|grad u|^2 + eps^2), -div(grad u / sqrt(|grad u|^2 + eps^2)) or None)."""
+        u = self._inp(u, self.rdtype, self.vol_shape)
+        g = self._vol() if grad else None
+        val = ctypes.c_double()
+        _check(lib().tv_smooth(self._h, _ptr(u), float(eps), _ptr(g), ctypes.byref(val), _ptr(self.ws), _stream()),
+               "tv_smooth")
+        return val.value, g
+
     # stages (u1 is complex [h][n][n], plane-major)
     def u1d_fwd(self, u):
         u = self._inp(u, self.rdtype, self.vol_shape)
@@ -244,6 +254,50 @@ class Plan:
         keys = ["TY_fwd", "TY_adj", "rows_per_block", "cols_per_block", "tile", "images", "planes_per_batch",
                 "jmin", "jmax"]
         return dict(zip(keys, list(arr)))
+
+
+class LamOp(torch.autograd.Function):
+    """d = L u as an autograd function; the backward is the hand-written
+    adjoint kernel (Re L^H g, PyTorch's convention for a real input and a
+    complex output).  Nothing is saved for the backward: the padded Fourier
+    grids are recomputed inside the adjoint."""
+
+    @staticmethod
+    def forward(ctx, u, plan):
+        ctx.plan = plan
+        return plan.forward(u.detach())
+
+    @staticmethod
+    def backward(ctx, g):
+        return ctx.plan.adjoint(g.contiguous()), None
+
+
+class TVOp(torch.autograd.Function):
+    """Smoothed isotropic TV(u) = sum sqrt(|grad u|^2 + eps^2); the backward is
+    -div(grad u / sqrt(|grad u|^2 + eps^2)) from the TV kernel."""
+
+    @staticmethod
+    def forward(ctx, u, plan, eps):
+        ctx.plan, ctx.eps = plan, eps
+        ctx.save_for_backward(u)
+        val, _ = plan.tv_smooth(u.detach(), eps, grad=False)
+        return torch.tensor(val, dtype=torch.float64, device=u.device)
+
+    @staticmethod
+    def backward(ctx, g):
+        (u,) = ctx.saved_tensors
+        _, grad = ctx.plan.tv_smooth(u.detach(), ctx.eps, grad=True)
+        return grad * g.to(grad.dtype), None, None
+
+
+def lam(u, plan):
+    """Differentiable L u."""
+    return LamOp.apply(u, plan)
+
+
+def tv(u, plan, eps=1e-3):
+    """Differentiable smoothed TV(u) (float64 scalar tensor)."""
+    return TVOp.apply(u, plan, eps)
 
 
 class Admm:

@@ -116,3 +116,29 @@ def test_penalty_rule_balances_residuals(tiny):
     for k in range(5):
         r, s, rho, nxt = info["r"][k], info["s"][k], info["rho"][k], info["rho"][k + 1]
         assert nxt == (2 * rho if r > 10 * s else 0.5 * rho if s > 10 * r else rho)
+
+
+def test_objective_gradient_matches_finite_differences():
+    # P7: the gradient Re L^H (L u - d) + alpha * (-div(grad u / |grad u|_eps)) of
+    # 1/2 ||L u - d||^2 + alpha TV_eps(u) against central differences (also a
+    # check of L^H against L)
+    from paper_2511_01893_b300 import inputs
+    n = 16
+    g = Geometry(n1=n, n0=n, n2=n, h=n, w=n, theta=inputs.angles(12), phi=np.deg2rad(20.0))
+    u0 = inputs.ellipsoid_phantom(n, n, 12, seed=1236).numpy()
+    d = lamino.lam_forward(u0, g)
+    u = 0.5 * u0 + 0.1 * np.random.default_rng(1).standard_normal(u0.shape)
+    alpha, eps = 1e-2, 0.1
+
+    def f(x):
+        r = lamino.lam_forward(x, g) - d
+        gg = tv.grad(x)
+        return 0.5 * np.vdot(r, r).real + alpha * np.sum(np.sqrt((gg * gg).sum(0) + eps * eps))
+
+    r = lamino.lam_forward(u, g) - d
+    gg = tv.grad(u)
+    G = lamino.lam_adjoint(r, g) + alpha * (-tv.div(gg / np.sqrt((gg * gg).sum(0) + eps * eps)))
+    v = np.random.default_rng(2).standard_normal(u.shape)
+    h = 1e-4
+    fd = (f(u + h * v) - f(u - h * v)) / (2 * h)
+    assert abs(fd - np.vdot(G, v)) <= 1e-9 * np.linalg.norm(G) * np.linalg.norm(v)
