@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
+    ap.add_argument("--op", choices=["admm", "lhat_pair"], default="admm",
+                    help="lhat_pair: time only L-hat + L-hat^H on the workload (no ADMM state); "
+                         "a small footprint for profiling")
     return ap.parse_args()
 
 
@@ -253,6 +256,43 @@ def run_reference(args):
 # our arm
 # ---------------------------------------------------------------------------
 
+def run_op_pair(args):
+    """Time L-hat + L-hat^H (steps pairs after warmup pairs) on the workload's
+    geometry with a random volume; prints one JSON line."""
+    import torch
+
+    from paper_2511_01893_b300 import inputs
+    from paper_2511_01893_b300 import lamino as glam
+    n = args.size
+    dev = torch.device("cuda", 0)
+    plan = glam.Plan(n, n, n, n, inputs.angles(n), np.deg2rad(PHI_DEG), prec="f32", device=dev)
+    u = torch.rand((n, n, n), device=dev, dtype=torch.float32)
+    d = torch.empty(plan.data_shape, dtype=plan.cdtype, device=dev)
+    v = torch.empty_like(u)
+    s = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(s):
+        for _ in range(args.warmup):
+            plan.forward_hat(u, out=d)
+            plan.adjoint_hat(d, out=v)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        tf = ta = 0.0
+        for _ in range(args.steps):
+            e[0].record(s)
+            plan.forward_hat(u, out=d)
+            e[1].record(s)
+            plan.adjoint_hat(d, out=v)
+            e[2].record(s)
+            s.synchronize()
+            tf += e[0].elapsed_time(e[1]) / 1e3
+            ta += e[1].elapsed_time(e[2]) / 1e3
+    tf /= max(args.steps, 1)
+    ta /= max(args.steps, 1)
+    byt = 2 * lhat_bytes(n, n, n, n, n)
+    print(json.dumps({"op": "lhat_pair", "size": n, "t_lhat_s": tf, "t_lhat_adj_s": ta,
+                      "gbs": byt / (tf + ta) / 1e9, "plan": plan.info()}), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -442,6 +482,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.op == "lhat_pair":
+        return run_op_pair(args)
     return run_ours(args)
 
 

@@ -45,15 +45,17 @@ struct AdmmRed {
     unsigned int* counter;  // zero between reductions
 };
 
-// volume [n1][nz][n2], N = n1 * nz * n2
+// volume [n1][nz][n2], N = n1 * nz * n2; nz and n2 are powers of two
+// (ln2 = log2 n2, lnz = log2 nz), so coordinates come from shifts and masks
 struct Vol {
     int n1, nz, n2;
+    int ln2, lnz;
     long long N;
     __device__ __forceinline__ void coords(long long i, int& x, int& z, int& y) const {
-        y = (int)(i % n2);
-        const long long t = i / n2;
-        z = (int)(t % nz);
-        x = (int)(t / nz);
+        y = (int)(i & (n2 - 1));
+        const long long t = i >> ln2;
+        z = (int)(t & (nz - 1));
+        x = (int)(t >> lnz);
     }
 };
 

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -84,6 +85,7 @@ struct lam_plan {
     // launch shapes
     int TYf, TYa, RB, CB, TS, nimg, nbatch;
     double rmax;
+    int pstride;
     // workspace layout
     size_t ws_u1, ws_planes, ws_tmp, ws_red, ws_bytes;
     mutable std::mutex mu;
@@ -277,6 +279,7 @@ template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p) {
     a.TS = p->TS;
     a.nimg = p->nimg;
     a.rmax = (T)p->rmax;
+    a.pstride = p->pstride;
     return a;
 }
 
@@ -409,6 +412,8 @@ template <typename T> Admm<T> admm_ops(const lam_plan* p) {
     a.v.n1 = p->n1;
     a.v.nz = p->nz;
     a.v.n2 = p->n2;
+    a.v.ln2 = ilog2(p->n2);
+    a.v.lnz = ilog2(p->nz);
     a.v.N = p->nvox();
     return a;
 }
@@ -544,8 +549,9 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     const size_t budget = 200 * 1024;
     const int maxb = prec == LAM_F32 ? 2 : 1;
     // z stage: TY columns per block
-    p->TYf = pick_lines(p->M0, ce_, budget, p->n2, 16, maxb);
-    p->TYa = pick_lines(p->M0, ce_, budget, p->n2, 16, maxb, (size_t)p->h * ce_);
+    // (column pairs share one complex line; E and O halves are nz long each)
+    p->TYf = std::max(2, pick_lines(p->nz, ce_, budget, p->n2, 16, maxb));
+    p->TYa = std::max(2, pick_lines(p->nz, ce_, budget, p->n2, 16, maxb, (size_t)p->h * ce_));
     p->RB = pick_lines(p->M2, ce_, 128 * 1024, p->n1, 16, maxb);
     p->CB = pick_lines(p->M1, ce_, 128 * 1024, p->M2, 16, maxb);
     p->TS = std::min(32, std::min(p->M1, p->M2));
@@ -554,8 +560,18 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     p->nimg = (int)std::ceil(reach / std::min(p->M1, p->M2));
     // |position| <= (w/2) M / w + (h/2) M sin(phi) / h (+ 1 for the grid offset)
     p->rmax = std::hypot(p->M1 * 0.5, p->M1 * 0.5 * std::sin(phi)) + 1.0;
+    // consecutive slice points are M1 / w cells apart; points at least sqrt 2
+    // cells apart have distinct tap-window origins
+    p->pstride = (int)std::ceil(std::sqrt(2.0) * p->w / (double)p->M1 - 1e-9);
+    if (p->pstride < 1) p->pstride = 1;
     const size_t plane = (size_t)p->M1 * p->M2 * ce_;
     p->nbatch = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->h, (256u << 20) / plane));
+    // LAMINO_PLANES_PER_BATCH overrides the number of padded planes processed per
+    // batch (workspace size follows); for tuning
+    if (const char* env = std::getenv("LAMINO_PLANES_PER_BATCH")) {
+        const int v = std::atoi(env);
+        if (v >= 1 && v <= p->h) p->nbatch = v;
+    }
     p->ws_u1 = 0;
     p->ws_planes = align256((size_t)p->h * p->n1 * p->n2 * ce_);
     p->ws_tmp = p->ws_planes + align256((size_t)p->nbatch * plane);

@@ -59,6 +59,7 @@ template <typename T> struct Usfft2dArgs {
     int TS;                         // scatter tile side
     int nimg;                       // tile images +-1..nimg checked per line (unwrapped positions)
     T rmax;                         // bound on |slice position| in grid units
+    int pstride;                    // scatter: lanes take points this far apart along a line
 };
 
 // forward: planes kv0 .. kv0 + nb - 1 of u1 ([h][n1][n2]) -> out ([T][h][w]),

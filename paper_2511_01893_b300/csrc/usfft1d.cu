@@ -7,8 +7,8 @@
 // with per-kv taps and weights from the plan's FP64-built tables.
 //
 // One block owns TY adjacent y-columns of one x-slab: it reads u[x][:][y0:y0+TY]
-// (TY contiguous values per z row), holds the TY padded lines in shared
-// memory, transforms them and writes u1[kv][x][y0:y0+TY] for every kv.  u1 is
+// (TY contiguous values per z row), transforms them in shared memory and
+// writes u1[kv][x][y0:y0+TY] for every kv.  u1 is
 // stored plane-major ([h][n1][n2]) so the per-plane 2D stage reads contiguous
 // planes.
 //
@@ -21,50 +21,99 @@
 
 namespace lam {
 
+// Two real columns a, b travel as one complex line z = a + i b.  The padded
+// transform of length M0 = 2 nz splits into even and odd outputs:
+//   P[2k]   = sum_x f[x] e^{-2 pi i k x / nz}                 (E = DFT_nz f)
+//   P[2k+1] = sum_x f[x] w^x e^{-2 pi i k x / nz}, w = e^{-2 pi i / M0}   (O)
+// with f placed at x mod nz, and the two real spectra separate as
+//   P_a[j] = (P_z[j] + conj P_z[-j]) / 2,  P_b[j] = (P_z[j] - conj P_z[-j]) / (2i).
+// So TY columns need TY FFTs of length nz instead of TY of length 2 nz.
+
+template <typename T> __device__ __forceinline__ C<T> pz_at(const C<T>* E, const C<T>* O, int j, int M0) {
+    const int jj = wrap(j, M0);
+    return (jj & 1) ? O[jj >> 1] : E[jj >> 1];
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads) k_usfft1d_fwd(const T* __restrict__ u, C<T>* __restrict__ u1,
-                                                     Usfft1dArgs<T> a) {
+                                                             Usfft1dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
+    C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);  // lines 2p (E) and 2p+1 (O), length nz
+    const int nz = a.nz, npair = a.TY / 2;
     const int tiles = a.n2 / a.TY;
     const int x = blockIdx.x / tiles;
     const int y0 = (blockIdx.x - x * tiles) * a.TY;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    for (int i = tid; i < a.TY * a.M0; i += nthr) bufa[i] = cmake<T>(0, 0);
-    __syncthreads();
-    const T* src = u + (size_t)x * a.nz * a.n2 + y0;
-    for (int i = tid; i < a.nz * a.TY; i += nthr) {
-        const int z = i / a.TY, c = i - z * a.TY;
-        const T v = src[(size_t)z * a.n2 + c] * a.dz[z];
-        bufa[c * a.M0 + wrap(z - a.nz / 2, a.M0)] = cmake<T>(v, 0);
+    const int twM0 = a.twstride;  // Nmax / M0
+    const T* src = u + (size_t)x * nz * a.n2 + y0;
+    for (int i = tid; i < nz * npair; i += nthr) {
+        const int z = i / npair, p = i - z * npair;
+        const int xc = z - nz / 2;
+        const T d = a.dz[z];
+        const T va = src[(size_t)z * a.n2 + 2 * p] * d, vb = src[(size_t)z * a.n2 + 2 * p + 1] * d;
+        const C<T> w = a.tw[wrap(xc, a.M0) * twM0];  // e^{-2 pi i xc / M0}
+        const int q = wrap(xc, nz);
+        buf[(2 * p) * nz + q] = cmake<T>(va, vb);
+        buf[(2 * p + 1) * nz + q] = cmake<T>(va * w.x - vb * w.y, va * w.y + vb * w.x);
     }
     __syncthreads();
-    fft_lines_ip<-1, FftMaxB<T>::value, T>(bufa, a.TY, a.M0, a.M0, a.logM0, a.tw, a.twstride);
-    const C<T>* P = bufa;
+    fft_lines_ip<-1, FftMaxB<T>::value, T>(buf, a.TY, nz, nz, a.logM0 - 1, a.tw, 2 * twM0);
     const int nt = 2 * a.m;
     C<T>* dst = u1 + (size_t)x * a.n2 + y0;
     const size_t plane = (size_t)a.n1 * a.n2;
-    for (int i = tid; i < a.h * a.TY; i += nthr) {
-        const int kv = i / a.TY, c = i - kv * a.TY;
+    for (int i = tid; i < a.h * npair; i += nthr) {
+        const int kv = i / npair, p = i - kv * npair;
+        const C<T>* E = buf + (2 * p) * nz;
+        const C<T>* O = E + nz;
         const int jb = a.j0z[kv] - a.m + 1;
         const T* wz = a.wz + kv * nt;
-        const C<T>* line = P + c * a.M0;
-        T sr = 0, si = 0;
+        T sar = 0, sai = 0, sbr = 0, sbi = 0;
         for (int t = 0; t < nt; ++t) {
-            const C<T> p = line[wrap(jb + t, a.M0)];
-            sr += wz[t] * p.x;
-            si += wz[t] * p.y;
+            const C<T> pp = pz_at(E, O, jb + t, a.M0);
+            const C<T> pm = pz_at(E, O, -(jb + t), a.M0);
+            const T wt = wz[t];
+            sar += wt * (pp.x + pm.x);
+            sai += wt * (pp.y - pm.y);
+            sbr += wt * (pp.x - pm.x);
+            sbi += wt * (pp.y + pm.y);
         }
-        dst[kv * plane + c] = cmake<T>(sr, si);
+        // a = (sa) / 2, b = (sb) / (2i) = (sb.im, -sb.re) / 2
+        C<T>* o = dst + kv * plane + 2 * p;
+        o[0] = cmake<T>((T)0.5 * sar, (T)0.5 * sai);
+        o[1] = cmake<T>((T)0.5 * sbi, (T)-0.5 * sbr);
     }
+}
+
+// Transpose.  For real outputs only the Hermitian part of each spread column
+// matters, Re IDFT(Q) = IDFT((Q[j] + conj Q[-j]) / 2), so two columns pack as
+//   Q_c[j] = (Q_a[j] + conj Q_a[-j]) / 2 + i (Q_b[j] + conj Q_b[-j]) / 2,
+// whose inverse transform is Re f_a + i Re f_b.  One thread builds Q_c at the
+// mirror pair j, M0 - j from four gather-form spreads, then the even / odd
+// halves go through two inverse FFTs of length nz and recombine as
+//   f[x] = E'[x mod nz] + e^{+2 pi i x / M0} O'[x mod nz].
+template <typename T>
+__device__ __forceinline__ C<T> spread_at(const C<T>* vals, int j, const Usfft1dArgs<T>& a, int nt) {
+    T sr = 0, si = 0;
+    int e = j + ((a.jmin - j + a.M0 - 1 + 64 * a.M0) / a.M0 - 64) * a.M0;  // smallest e >= jmin, e == j
+    for (; e <= a.jmax; e += a.M0) {
+        const int lo = a.kvlo[e - a.jmin], hi = a.kvhi[e - a.jmin];
+        for (int kv = lo; kv < hi; ++kv) {
+            const T wt = a.wz[kv * nt + (e - (a.j0z[kv] - a.m + 1))];
+            const C<T> v = vals[kv];
+            sr += wt * v.x;
+            si += wt * v.y;
+        }
+    }
+    return cmake<T>(sr, si);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restrict__ u1, T* __restrict__ u,
-                                                     Usfft1dArgs<T> a) {
+                                                             Usfft1dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    C<T>* vals = bufa + a.TY * a.M0;  // [TY][h]
+    const int nz = a.nz, npair = a.TY / 2, M0 = a.M0;
+    C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);  // TY lines of length nz (E, O per pair)
+    C<T>* vals = buf + a.TY * nz;                  // [TY][h]
     const int tiles = a.n2 / a.TY;
     const int x = blockIdx.x / tiles;
     const int y0 = (blockIdx.x - x * tiles) * a.TY;
@@ -77,43 +126,50 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restr
     }
     __syncthreads();
     const int nt = 2 * a.m;
-    // spread in gather form: cell j collects every unwrapped cell e == j (mod M0)
-    for (int i = tid; i < a.TY * a.M0; i += nthr) {
-        const int c = i / a.M0, j = i - c * a.M0;
-        T sr = 0, si = 0;
-        // smallest e >= jmin with e == j (mod M0)
-        int e = j + ((a.jmin - j + a.M0 - 1 + 64 * a.M0) / a.M0 - 64) * a.M0;
-        for (; e <= a.jmax; e += a.M0) {
-            const int lo = a.kvlo[e - a.jmin], hi = a.kvhi[e - a.jmin];
-            for (int kv = lo; kv < hi; ++kv) {
-                const T wt = a.wz[kv * nt + (e - (a.j0z[kv] - a.m + 1))];
-                const C<T> v = vals[c * a.h + kv];
-                sr += wt * v.x;
-                si += wt * v.y;
-            }
-        }
-        bufa[i] = cmake<T>(sr, si);
+    const int half = M0 / 2;
+    for (int i = tid; i < npair * (half + 1); i += nthr) {
+        const int p = i / (half + 1), j = i - p * (half + 1);
+        const int jm = wrap(-j, M0);
+        const C<T>* va = vals + (2 * p) * a.h;
+        const C<T>* vb = va + a.h;
+        const C<T> ap = spread_at(va, j, a, nt), am = spread_at(va, jm, a, nt);
+        const C<T> bp = spread_at(vb, j, a, nt), bm = spread_at(vb, jm, a, nt);
+        // Q_c[j] = (ap + conj am)/2 + i (bp + conj bm)/2
+        const C<T> qj = cmake<T>((T)0.5 * ((ap.x + am.x) - (bp.y - bm.y)), (T)0.5 * ((ap.y - am.y) + (bp.x + bm.x)));
+        // Q_c[-j] = (am + conj ap)/2 + i (bm + conj bp)/2
+        const C<T> qm = cmake<T>((T)0.5 * ((am.x + ap.x) - (bm.y - bp.y)), (T)0.5 * ((am.y - ap.y) + (bm.x + bp.x)));
+        C<T>* E = buf + (2 * p) * nz;
+        C<T>* O = E + nz;
+        ((j & 1) ? O : E)[j >> 1] = qj;
+        if (jm != j) ((jm & 1) ? O : E)[jm >> 1] = qm;
     }
     __syncthreads();
-    fft_lines_ip<+1, FftMaxB<T>::value, T>(bufa, a.TY, a.M0, a.M0, a.logM0, a.tw, a.twstride);
-    const C<T>* q = bufa;
-    T* dst = u + (size_t)x * a.nz * a.n2 + y0;
-    for (int i = tid; i < a.nz * a.TY; i += nthr) {
-        const int z = i / a.TY, c = i - z * a.TY;
-        dst[(size_t)z * a.n2 + c] = q[c * a.M0 + wrap(z - a.nz / 2, a.M0)].x * a.dz[z];
+    fft_lines_ip<+1, FftMaxB<T>::value, T>(buf, a.TY, nz, nz, a.logM0 - 1, a.tw, 2 * a.twstride);
+    T* dst = u + (size_t)x * nz * a.n2 + y0;
+    for (int i = tid; i < nz * npair; i += nthr) {
+        const int z = i / npair, p = i - z * npair;
+        const int xc = z - nz / 2;
+        const int q = wrap(xc, nz);
+        const C<T> e = buf[(2 * p) * nz + q], o = buf[(2 * p + 1) * nz + q];
+        C<T> w = a.tw[wrap(xc, M0) * a.twstride];  // e^{-2 pi i xc / M0}; use its conjugate
+        const T fr = e.x + (o.x * w.x + o.y * w.y);
+        const T fi = e.y + (o.y * w.x - o.x * w.y);
+        const T d = a.dz[z];
+        dst[(size_t)z * a.n2 + 2 * p] = fr * d;
+        dst[(size_t)z * a.n2 + 2 * p + 1] = fi * d;
     }
 }
 
 template <typename T>
 cudaError_t launch_usfft1d_fwd(const T* u, C<T>* u1, const Usfft1dArgs<T>& a, cudaStream_t s) {
-    const size_t smem = (size_t)a.TY * a.M0 * sizeof(C<T>);
+    const size_t smem = (size_t)a.TY * a.nz * sizeof(C<T>);
     k_usfft1d_fwd<T><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u, u1, a);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_usfft1d_adj(const C<T>* u1, T* u, const Usfft1dArgs<T>& a, cudaStream_t s) {
-    const size_t smem = (size_t)(a.M0 + a.h) * a.TY * sizeof(C<T>);
+    const size_t smem = (size_t)(a.nz + a.h) * a.TY * sizeof(C<T>);
     k_usfft1d_adj<T><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u1, u, a);
     return cudaGetLastError();
 }

@@ -12,13 +12,13 @@
 //   k_gather2d     one thread per slice point: 64 taps from P, optional fused
 //                  subtraction (out = value - sub, Section 4.2)
 // Transpose (type 1):
-//   k_scatter2d    tile-owned accumulation: a block owns a TS x TS tile of the
-//                  padded plane, finds for each angle the (contiguous) ku range
-//                  of slice points whose taps reach the tile, and accumulates
-//                  weight * value in per-warp shared-memory copies of the tile
-//                  (compensated summation in FP32); the copies are summed and
-//                  the tile is written once.  No global atomics; the result
-//                  does not depend on scheduling.
+//   k_scatter2d    tile-owned accumulation: a warp owns a TS x TS tile of the
+//                  padded plane, finds the slice lines that cross it and, per
+//                  line, the (contiguous) ku range of points whose taps reach
+//                  the tile, and accumulates weight * value in a shared-memory
+//                  copy of the tile (compensated summation in FP32); the tile
+//                  is written once.  No atomics; the result does not depend on
+//                  scheduling.
 //   k_colfft_adj   inverse FFT along x, keep the n1 rows the crop needs
 //   k_rowfft_adj   inverse FFT along y, crop, deapodise -> u1 rows
 #include "fft.cuh"
@@ -196,6 +196,133 @@ __global__ void __launch_bounds__(256) k_gather2d(const C<T>* __restrict__ P, C<
     }
 }
 
+// ku interval [lo, hi] (centred) of points on the line p = A ku + Cc whose
+// position lies in [bmin, bmax); conservative by one point at each end.
+template <typename T>
+__device__ __forceinline__ void clip_line(T A, T Cc, T bmin, T bmax, int& lo, int& hi) {
+    if (fabs(A) < (T)1e-6) {
+        if (!(Cc >= bmin - (T)1 && Cc < bmax + (T)1)) {
+            lo = 1;
+            hi = 0;
+        }
+        return;
+    }
+    T t0 = (bmin - Cc) / A, t1 = (bmax - Cc) / A;
+    if (t0 > t1) {
+        const T tmp = t0;
+        t0 = t1;
+        t1 = tmp;
+    }
+    // clamp before the conversion so that huge quotients stay in int range
+    t0 = fmax(t0, (T)-1e8);
+    t1 = fmin(t1, (T)1e8);
+    const int l = (int)floor(t0) - 1, h = (int)ceil(t1) + 1;
+    lo = max(lo, l);
+    hi = min(hi, h);
+}
+
+// Tiled gather: one warp per TS x TS tile of tap-window origins.  The warp
+// stages its tile plus a (2m - 1) halo of the padded plane in shared memory,
+// culls the slice lines against the tile, and evaluates exactly the points
+// whose window origin (j0 - m + 1 in both axes, unwrapped) falls in the tile
+// (or one of its periodic images), one point per lane.  Each point is owned
+// by exactly one (tile, image), so every output is written once.
+template <typename T, int TPB>
+__global__ void __launch_bounds__(TPB * 32) k_gather2d_tiled(const C<T>* __restrict__ P, C<T>* __restrict__ out,
+                                                             const C<T>* __restrict__ sub, int kv0, Usfft2dArgs<T> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TS = a.TS, nt = 2 * a.m;
+    const int SH = TS + nt - 1;  // staged rows
+    const int SW = TS + nt;      // staged row stride
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_x = a.M1 / TS, tiles_y = a.M2 / TS;
+    const int tile = blockIdx.x * TPB + warp;
+    if (tile >= tiles_x * tiles_y) return;
+    C<T>* st = reinterpret_cast<C<T>*>(smem_raw) + (size_t)warp * SH * SW;
+    const int tx0 = (tile / tiles_y) * TS, ty0 = (tile % tiles_y) * TS;
+    const int b = blockIdx.y, kv = kv0 + b, kvc = kv - a.h / 2;
+    const C<T>* pl = P + (size_t)b * a.M1 * a.M2;
+    for (int i = lane; i < SH * SH; i += 32) {
+        const int r = i / SH, c = i - r * SH;
+        st[r * SW + c] = pl[(size_t)wrap(tx0 + r, a.M1) * a.M2 + wrap(ty0 + c, a.M2)];
+    }
+    __syncwarp();
+    const int kmin = -a.w / 2, kmax = a.w / 2 - 1;
+    const T hx = (T)TS * (T)0.5 + (T)1;
+    for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
+        const int bx0 = tx0 + ix * a.M1;
+        for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
+            const int by0 = ty0 + iy * a.M2;
+            // positions whose window origin is in [b0, b0 + TS): p in [b0 + m - 1, b0 + TS + m - 1)
+            const T cx = (T)(bx0 + a.m - 1) + (T)TS * (T)0.5, cy = (T)(by0 + a.m - 1) + (T)TS * (T)0.5;
+            if (sqrt(cx * cx + cy * cy) > a.rmax + hx * (T)1.5) continue;
+            for (int base = 0; base < a.T_; base += 32) {
+                const int th = base + lane;
+                bool hit = false;
+                if (th < a.T_) {
+                    const typename AngleT<T>::type g = a.ang[th];
+                    T Ax, Cx, Ay, Cy;
+                    line_coef(g, kvc, Ax, Cx, Ay, Cy);
+                    const T nrm = sqrt(Ax * Ax + Ay * Ay);
+                    const T nx = -Ay / nrm, ny = Ax / nrm;
+                    const T dist = fabs((cx - Cx) * nx + (cy - Cy) * ny);
+                    hit = dist <= hx * (fabs(nx) + fabs(ny)) + (T)1;
+                }
+                unsigned mask = __ballot_sync(0xffffffffu, hit);
+                while (mask) {
+                    const int th2 = base + __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    const typename AngleT<T>::type g = a.ang[th2];
+                    T Ax, Cx, Ay, Cy;
+                    line_coef(g, kvc, Ax, Cx, Ay, Cy);
+                    int lo = kmin, hi = kmax;
+                    clip_line<T>(Ax, Cx, (T)(bx0 + a.m - 1), (T)(bx0 + TS + a.m - 1), lo, hi);
+                    clip_line<T>(Ay, Cy, (T)(by0 + a.m - 1), (T)(by0 + TS + a.m - 1), lo, hi);
+                    const size_t orow = ((size_t)th2 * a.h + kv) * a.w + a.w / 2;
+                    for (int k0 = lo; k0 <= hi; k0 += 32) {
+                        const int kuc = k0 + lane;
+                        if (kuc > hi) continue;
+                        int jx, jy;
+                        T fx, fy;
+                        point_pos(g, kuc, kvc, jx, fx, jy, fy);
+                        const int ox = jx - a.m + 1 - bx0, oy = jy - a.m + 1 - by0;
+                        if (ox < 0 || ox >= TS || oy < 0 || oy >= TS) continue;
+                        T wy[16];
+#pragma unroll
+                        for (int t = 0; t < 16; ++t)
+                            if (t < nt) {
+                                const T d = fy + (T)(a.m - 1 - t);
+                                wy[t] = gexp(-d * d * a.inv4beta);
+                            }
+                        T sr = 0, si = 0;
+#pragma unroll
+                        for (int sx = 0; sx < 16; ++sx) {
+                            if (sx >= nt) break;
+                            const T d = fx + (T)(a.m - 1 - sx);
+                            const T wx = gexp(-d * d * a.inv4beta);
+                            const C<T>* rowp = st + (ox + sx) * SW + oy;
+                            T rr = 0, ri = 0;
+#pragma unroll
+                            for (int t = 0; t < 16; ++t)
+                                if (t < nt) {
+                                    const C<T> pv = rowp[t];
+                                    rr += wy[t] * pv.x;
+                                    ri += wy[t] * pv.y;
+                                }
+                            sr += wx * rr;
+                            si += wx * ri;
+                        }
+                        const size_t o = orow + kuc;
+                        C<T> v = cmake<T>(sr, si);
+                        if (sub) v = csub(v, sub[o]);
+                        out[o] = v;
+                    }
+                }
+            }
+        }
+    }
+}
+
 // --------------------------------------------------------------------------
 // scatter (type 1 spreading), tile-owned, per-warp accumulators
 // --------------------------------------------------------------------------
@@ -222,87 +349,53 @@ template <> struct Acc<double> {
     }
 };
 
-// ku interval [lo, hi] (centred) of points on the line p = A ku + Cc whose
-// position lies in [bmin, bmax); conservative by one point at each end.
-template <typename T>
-__device__ __forceinline__ void clip_line(T A, T Cc, T bmin, T bmax, int& lo, int& hi) {
-    if (fabs(A) < (T)1e-6) {
-        if (!(Cc >= bmin - (T)1 && Cc < bmax + (T)1)) {
-            lo = 1;
-            hi = 0;
-        }
-        return;
-    }
-    T t0 = (bmin - Cc) / A, t1 = (bmax - Cc) / A;
-    if (t0 > t1) {
-        const T tmp = t0;
-        t0 = t1;
-        t1 = tmp;
-    }
-    // clamp before the conversion so that huge quotients stay in int range
-    t0 = fmax(t0, (T)-1e8);
-    t1 = fmin(t1, (T)1e8);
-    const int l = (int)floor(t0) - 1, h = (int)ceil(t1) + 1;
-    lo = max(lo, l);
-    hi = min(hi, h);
-}
-
-// Per-warp staging of up to 32 slice points: tap origin, weights, value.
-template <typename T> struct PointStage {
-    int jx[32], jy[32];
-    T wx[32][17], wy[32][17];  // padded: lane-strided writes stay conflict-free
-    C<T> v[32];
-};
-
-template <typename T, int NW>
-__global__ void __launch_bounds__(NW * 32) k_scatter2d(const C<T>* __restrict__ in, C<T>* __restrict__ P,
-                                                       int kv0, Usfft2dArgs<T> a) {
+// One warp owns one TS x TS tile of the padded plane and a private
+// accumulator for it (compensated in FP32); a block holds TPB tiles.  The warp
+// culls the n_theta slice lines against its tile with a lane-parallel distance
+// test, then walks each crossing line 32 points at a time, one point per lane:
+// the lane computes the point's tap window and 2 x 2m Gaussian weights in
+// registers, and the warp steps through the (2m)^2 taps in lock-step.  Window
+// origins of points 2 cells apart on one line are distinct, so the 32 lanes
+// of one tap step never touch the same cell.
+template <typename T, int TPB>
+__global__ void __launch_bounds__(TPB * 32) k_scatter2d(const C<T>* __restrict__ in, C<T>* __restrict__ P,
+                                                        int kv0, Usfft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TS = a.TS;
-    Acc<T>* acc = reinterpret_cast<Acc<T>*>(smem_raw);  // [NW][TS*TS]
-    PointStage<T>* stage = reinterpret_cast<PointStage<T>*>(smem_raw + (size_t)NW * TS * TS * sizeof(Acc<T>));
-    const int tiles_y = a.M2 / TS;
-    const int tx0 = (blockIdx.x / tiles_y) * TS, ty0 = (blockIdx.x % tiles_y) * TS;
-    const int b = blockIdx.y, kv = kv0 + b, kvc = kv - a.h / 2;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < NW * TS * TS; i += blockDim.x) acc[i].zero();
-    __syncthreads();
-    Acc<T>* my = acc + warp * TS * TS;
-    PointStage<T>& st = stage[warp];
-    const int nt = 2 * a.m, ntap = nt * nt;
+    const int tiles_x = a.M1 / TS, tiles_y = a.M2 / TS;
+    const int tile = blockIdx.x * TPB + warp;
+    if (tile >= tiles_x * tiles_y) return;  // whole warp exits; no block-wide sync below
+    Acc<T>* my = reinterpret_cast<Acc<T>*>(smem_raw) + (size_t)warp * TS * TS;
+    for (int i = lane; i < TS * TS; i += 32) my[i].zero();
+    __syncwarp();
+    const int tx0 = (tile / tiles_y) * TS, ty0 = (tile % tiles_y) * TS;
+    const int b = blockIdx.y, kv = kv0 + b, kvc = kv - a.h / 2;
+    const int nt = 2 * a.m;
     const int kmin = -a.w / 2, kmax = a.w / 2 - 1;
-    // half-extent of the box of point positions whose taps reach the tile
-    const T hx = (T)(TS + 2 * a.m) * (T)0.5, hy = hx;
+    const T hx = (T)(TS + 2 * a.m) * (T)0.5;
     for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
         const int bx0 = tx0 + ix * a.M1;
         for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
             const int by0 = ty0 + iy * a.M2;
-            // centre of the position box (positions p with taps in [b0, b0 + TS))
             const T cx = (T)bx0 + (T)(TS - 1) * (T)0.5, cy = (T)by0 + (T)(TS - 1) * (T)0.5;
             if (sqrt(cx * cx + cy * cy) > a.rmax + hx * (T)1.5) continue;
-            int seen = 0;  // crossing lines found so far (all warps see the same sequence)
             for (int base = 0; base < a.T_; base += 32) {
                 const int th = base + lane;
                 bool hit = false;
                 if (th < a.T_) {
-                    // the line p(ku) = ku A + kvc S has direction A / |A| and passes at
-                    // signed distance kvc |S| from the origin; test the distance from the
-                    // box centre against the box's support in the normal direction
                     const typename AngleT<T>::type g = a.ang[th];
                     T Ax, Cx, Ay, Cy;
                     line_coef(g, kvc, Ax, Cx, Ay, Cy);
                     const T nrm = sqrt(Ax * Ax + Ay * Ay);
                     const T nx = -Ay / nrm, ny = Ax / nrm;
                     const T dist = fabs((cx - Cx) * nx + (cy - Cy) * ny);
-                    hit = dist <= hx * fabs(nx) + hy * fabs(ny) + (T)1;
+                    hit = dist <= hx * (fabs(nx) + fabs(ny)) + (T)1;
                 }
                 unsigned mask = __ballot_sync(0xffffffffu, hit);
                 while (mask) {
-                    const int bit = __ffs(mask) - 1;
+                    const int th2 = base + __ffs(mask) - 1;
                     mask &= mask - 1;
-                    const int my_turn = (seen++ % NW) == warp;
-                    if (!my_turn) continue;
-                    const int th2 = base + bit;
                     const typename AngleT<T>::type g = a.ang[th2];
                     T Ax, Cx, Ay, Cy;
                     line_coef(g, kvc, Ax, Cx, Ay, Cy);
@@ -310,49 +403,58 @@ __global__ void __launch_bounds__(NW * 32) k_scatter2d(const C<T>* __restrict__ 
                     clip_line<T>(Ax, Cx, (T)(bx0 - a.m), (T)(bx0 + TS + a.m - 1), lo, hi);
                     clip_line<T>(Ay, Cy, (T)(by0 - a.m), (T)(by0 + TS + a.m - 1), lo, hi);
                     const C<T>* row = in + ((size_t)th2 * a.h + kv) * a.w + a.w / 2;
-                    for (int k0 = lo; k0 <= hi; k0 += 32) {
-                        const int cnt = min(32, hi - k0 + 1);
-                        if (lane < cnt) {
-                            const int kuc = k0 + lane;
+                    // lanes take points pstride apart (>= sqrt 2 cells), so their
+                    // window origins differ; pstride passes cover every point
+                    const int ps = a.pstride;
+                    for (int kq = 0; lo + (kq / ps) * 32 * ps <= hi; ++kq) {
+                        const int kuc = lo + (kq / ps) * 32 * ps + (kq % ps) + lane * ps;
+                        const bool act = kuc <= hi;
+                        int ox = -1 << 20, oy = -1 << 20;
+                        T wx[16], wy[16];
+                        C<T> v = cmake<T>(0, 0);
+                        if (act) {
                             int jx, jy;
                             T fx, fy;
                             point_pos(g, kuc, kvc, jx, fx, jy, fy);
-                            st.jx[lane] = jx - a.m + 1 - bx0;
-                            st.jy[lane] = jy - a.m + 1 - by0;
-                            for (int t = 0; t < nt; ++t) {
-                                const T dx = fx + (T)(a.m - 1 - t), dy = fy + (T)(a.m - 1 - t);
-                                st.wx[lane][t] = gexp(-dx * dx * a.inv4beta);
-                                st.wy[lane][t] = gexp(-dy * dy * a.inv4beta);
-                            }
-                            st.v[lane] = row[kuc];
-                        }
-                        __syncwarp();
-                        for (int q = 0; q < cnt; ++q) {
-                            const int ox = st.jx[q], oy = st.jy[q];
-                            const C<T> v = st.v[q];
-                            for (int ti = lane; ti < ntap; ti += 32) {
-                                const int sx = ti % nt, sy = ti / nt;
-                                const int cx2 = ox + sx, cy2 = oy + sy;
-                                if (cx2 >= 0 && cx2 < TS && cy2 >= 0 && cy2 < TS) {
-                                    const T wgt = st.wx[q][sx] * st.wy[q][sy];
-                                    my[cx2 * TS + cy2].add(wgt * v.x, wgt * v.y);
+                            ox = jx - a.m + 1 - bx0;
+                            oy = jy - a.m + 1 - by0;
+#pragma unroll
+                            for (int t = 0; t < 16; ++t) {
+                                if (t < nt) {
+                                    const T dx = fx + (T)(a.m - 1 - t), dy = fy + (T)(a.m - 1 - t);
+                                    wx[t] = gexp(-dx * dx * a.inv4beta);
+                                    wy[t] = gexp(-dy * dy * a.inv4beta);
                                 }
                             }
-                            __syncwarp();
+                            v = row[kuc];
+                        }
+#pragma unroll
+                        for (int sx = 0; sx < 16; ++sx) {
+                            if (sx >= nt) break;
+                            const int cxx = ox + sx;
+                            const bool rowin = act && cxx >= 0 && cxx < TS;
+                            const T wxs = wx[sx];
+#pragma unroll
+                            for (int sy = 0; sy < 16; ++sy) {
+                                if (sy >= nt) break;
+                                const int cyy = oy + sy;
+                                if (rowin && cyy >= 0 && cyy < TS) {
+                                    const T wgt = wxs * wy[sy];
+                                    my[cxx * TS + cyy].add(wgt * v.x, wgt * v.y);
+                                }
+                                __syncwarp();
+                            }
                         }
                     }
                 }
             }
         }
     }
-    __syncthreads();
+    __syncwarp();
     C<T>* pl = P + (size_t)b * a.M1 * a.M2;
-    for (int i = threadIdx.x; i < TS * TS; i += blockDim.x) {
-        Acc<T> tot;
-        tot.zero();
-        for (int wv = 0; wv < NW; ++wv) tot.add(acc[wv * TS * TS + i].sr, acc[wv * TS * TS + i].si);
-        const int cx = i / TS, cy = i - cx * TS;
-        pl[(size_t)(tx0 + cx) * a.M2 + ty0 + cy] = cmake<T>(tot.sr, tot.si);
+    for (int i = lane; i < TS * TS; i += 32) {
+        const int cxx = i / TS, cyy = i - cxx * TS;
+        pl[(size_t)(tx0 + cxx) * a.M2 + ty0 + cyy] = cmake<T>(my[i].sr, my[i].si);
     }
 }
 
@@ -360,7 +462,7 @@ __global__ void __launch_bounds__(NW * 32) k_scatter2d(const C<T>* __restrict__ 
 // launchers
 // --------------------------------------------------------------------------
 
-constexpr int kScatterWarps = 4;
+constexpr int kScatterWarps = 4;  // tiles (warps) per block
 
 template <typename T>
 cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* sub, int kv0, int nb,
@@ -369,7 +471,10 @@ cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* s
     const size_t sc = (size_t)a.CB * a.M1 * sizeof(C<T>);
     k_rowfft_fwd<T><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, kv0, a);
     k_colfft_fwd<T><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
-    k_gather2d<T><<<dim3(a.T_, nb), a.w < 256 ? a.w : 256, 0, s>>>(P, out, sub, kv0, a);
+    constexpr int NW = kScatterWarps;
+    const int ntiles = (a.M1 / a.TS) * (a.M2 / a.TS);
+    const size_t sg = (size_t)NW * (a.TS + 2 * a.m - 1) * (a.TS + 2 * a.m) * sizeof(C<T>);
+    k_gather2d_tiled<T, NW><<<dim3((ntiles + NW - 1) / NW, nb), NW * 32, sg, s>>>(P, out, sub, kv0, a);
     return cudaGetLastError();
 }
 
@@ -377,10 +482,11 @@ template <typename T>
 cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int kv0, int nb, const Usfft2dArgs<T>& a,
                                cudaStream_t s) {
     constexpr int NW = kScatterWarps;
-    const size_t sa = (size_t)NW * a.TS * a.TS * sizeof(Acc<T>) + (size_t)NW * sizeof(PointStage<T>);
+    const size_t sa = (size_t)NW * a.TS * a.TS * sizeof(Acc<T>);
+    const int ntiles = (a.M1 / a.TS) * (a.M2 / a.TS);
     const size_t sr = (size_t)a.RB * a.M2 * sizeof(C<T>);
     const size_t sc = (size_t)a.CB * a.M1 * sizeof(C<T>);
-    k_scatter2d<T, NW><<<dim3((a.M1 / a.TS) * (a.M2 / a.TS), nb), NW * 32, sa, s>>>(in, P, kv0, a);
+    k_scatter2d<T, NW><<<dim3((ntiles + NW - 1) / NW, nb), NW * 32, sa, s>>>(in, P, kv0, a);
     k_colfft_adj<T><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
     k_rowfft_adj<T><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(P, u1, kv0, a);
     return cudaGetLastError();
@@ -397,6 +503,7 @@ template <typename T> cudaError_t configure_usfft2d() {
     if (!e) e = cudaFuncSetAttribute(k_rowfft_adj<T>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_colfft_adj<T>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_scatter2d<T, kScatterWarps>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_gather2d_tiled<T, kScatterWarps>, at, mx);
     return e;
 }
 
