@@ -71,6 +71,17 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
                            int prec);
 lam_status lam_plan_destroy(lam_plan* plan);
 
+/* Plan options (lam_plan_set_option).
+ * LAM_OPT_DETERMINISTIC (default 0): 1 selects the adjoint spreading kernel
+ *   that accumulates each padded-plane tile with compensated (Kahan) FP32
+ *   sums in a fixed order, so results are bitwise reproducible run to run.
+ *   0 selects the faster kernel that accumulates with shared-memory atomic
+ *   adds (no compensation; summation order varies between runs, results agree
+ *   to rounding).  FP64 plans are unaffected in accuracy either way.
+ * Setting an option invalidates ADMM graphs captured with the plan. */
+enum { LAM_OPT_DETERMINISTIC = 1 };
+lam_status lam_plan_set_option(lam_plan* plan, int option, int value);
+
 /* Bytes of device scratch the operator calls need (ws argument).  The
  * workspace holds the z-transformed volume u1[h][n][n] (complex) and a batch
  * of padded planes.  Alignment: 256 bytes. */

@@ -86,6 +86,8 @@ struct lam_plan {
     int TYf, TYa, RB, CB, TS, nimg, nbatch;
     double rmax;
     int pstride;
+    int deterministic = 0;
+    int scatter_acc = 1;
     // workspace layout
     size_t ws_u1, ws_planes, ws_tmp, ws_red, ws_bytes;
     mutable std::mutex mu;
@@ -280,6 +282,8 @@ template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p) {
     a.nimg = p->nimg;
     a.rmax = (T)p->rmax;
     a.pstride = p->pstride;
+    a.deterministic = p->deterministic;
+    a.scatter_acc = p->scatter_acc;
     return a;
 }
 
@@ -568,6 +572,7 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     p->nbatch = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->h, (256u << 20) / plane));
     // LAMINO_PLANES_PER_BATCH overrides the number of padded planes processed per
     // batch (workspace size follows); for tuning
+    if (const char* env = std::getenv("LAMINO_SCATTER_ACC")) p->scatter_acc = std::atoi(env);
     if (const char* env = std::getenv("LAMINO_PLANES_PER_BATCH")) {
         const int v = std::atoi(env);
         if (v >= 1 && v <= p->h) p->nbatch = v;
@@ -581,6 +586,26 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
                   256;
     *out = p;
     return LAM_OK;
+}
+
+lam_status lam_plan_set_option(lam_plan* p, int option, int value) {
+    if (lam_status st = check_plan(p)) return st;
+    switch (option) {
+        case LAM_OPT_DETERMINISTIC:
+            p->deterministic = value != 0;
+            {
+                // captured ADMM graphs hold the old kernel choice
+                std::lock_guard<std::mutex> lk(p->mu);
+                for (auto& kv : p->admm)
+                    if (kv.second.graph) {
+                        cudaGraphExecDestroy(kv.second.graph);
+                        kv.second.graph = nullptr;
+                    }
+            }
+            return LAM_OK;
+        default:
+            return fail(LAM_EINVAL, "unknown option %d", option);
+    }
 }
 
 lam_status lam_plan_destroy(lam_plan* plan) {

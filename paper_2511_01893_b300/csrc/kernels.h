@@ -16,7 +16,6 @@ constexpr int kMaxDynSmem = 227 * 1024;
 template <typename T> cudaError_t configure_usfft1d();
 template <typename T> cudaError_t configure_usfft2d();
 template <typename T> cudaError_t configure_fft2d();
-template <typename T> size_t scatter_acc_bytes();  // per tile cell, all warps
 
 // ---- F_u1D -----------------------------------------------------------------
 template <typename T> struct Usfft1dArgs {
@@ -60,6 +59,8 @@ template <typename T> struct Usfft2dArgs {
     int nimg;                       // tile images +-1..nimg checked per line (unwrapped positions)
     T rmax;                         // bound on |slice position| in grid units
     int pstride;                    // scatter: lanes take points this far apart along a line
+    int deterministic;              // scatter: compensated lock-step kernel (bitwise reproducible)
+    int scatter_acc;                // atomic scatter accumulators: 0 FP32, 1 compensated, 2 FP64
 };
 
 // forward: planes kv0 .. kv0 + nb - 1 of u1 ([h][n1][n2]) -> out ([T][h][w]),

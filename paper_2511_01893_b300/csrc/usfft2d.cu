@@ -221,17 +221,79 @@ __device__ __forceinline__ void clip_line(T A, T Cc, T bmin, T bmax, int& lo, in
     hi = min(hi, h);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-level enumeration of the slice points that may touch one tile image.
+// The warp tests 32 lines at a time against the tile's position box (lane
+// parallel), computes each crossing line's ku interval, scans the interval
+// lengths, and hands the flattened point list out 32 points at a time, one per
+// lane, across line boundaries.  fn(th, kuc, g) is called for each lane's
+// point (with active lanes first in each batch; inactive lanes get th = -1).
+// ---------------------------------------------------------------------------
+template <typename T, typename F>
+__device__ __forceinline__ void for_tile_points(const Usfft2dArgs<T>& a, int kvc, T cx, T cy, T hbox,
+                                                T bxmin, T bxmax, T bymin, T bymax, F&& fn) {
+    const int lane = threadIdx.x & 31;
+    const int kmin = -a.w / 2, kmax = a.w / 2 - 1;
+    for (int base = 0; base < a.T_; base += 32) {
+        const int th = base + lane;
+        int lo = 1, hi = 0;
+        if (th < a.T_) {
+            const typename AngleT<T>::type g = a.ang[th];
+            T Ax, Cx, Ay, Cy;
+            line_coef(g, kvc, Ax, Cx, Ay, Cy);
+            const T nrm = sqrt(Ax * Ax + Ay * Ay);
+            const T nx = -Ay / nrm, ny = Ax / nrm;
+            const T dist = fabs((cx - Cx) * nx + (cy - Cy) * ny);
+            if (dist <= hbox * (fabs(nx) + fabs(ny)) + (T)1) {
+                lo = kmin;
+                hi = kmax;
+                clip_line<T>(Ax, Cx, bxmin, bxmax, lo, hi);
+                clip_line<T>(Ay, Cy, bymin, bymax, lo, hi);
+            }
+        }
+        const int cnt = hi >= lo ? hi - lo + 1 : 0;
+        // inclusive scan of cnt over the warp
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        const int excl = incl - cnt;
+        for (int p0 = 0; p0 < total; p0 += 32) {
+            const int p = p0 + lane;
+            // owner lane: the last lane whose exclusive prefix is <= p (with cnt > 0)
+            int owner = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int cand = owner + step;
+                const int ex = __shfl_sync(0xffffffffu, excl, cand);
+                if (ex <= p) owner = cand;
+            }
+            // skip empty intervals that share the prefix: move to the owner with cnt > 0
+            const int ocnt = __shfl_sync(0xffffffffu, cnt, owner);
+            const int oex = __shfl_sync(0xffffffffu, excl, owner);
+            const int olo = __shfl_sync(0xffffffffu, lo, owner);
+            const bool valid = p < total && ocnt > 0 && p - oex < ocnt;
+            const int kuc = olo + (p - oex);
+            fn(valid ? base + owner : -1, kuc);
+        }
+    }
+}
+
 // Tiled gather: one warp per TS x TS tile of tap-window origins.  The warp
-// stages its tile plus a (2m - 1) halo of the padded plane in shared memory,
-// culls the slice lines against the tile, and evaluates exactly the points
-// whose window origin (j0 - m + 1 in both axes, unwrapped) falls in the tile
-// (or one of its periodic images), one point per lane.  Each point is owned
-// by exactly one (tile, image), so every output is written once.
-template <typename T, int TPB>
+// stages its tile plus a (2m - 1) halo of the padded plane in shared memory
+// and evaluates exactly the points whose window origin (j0 - m + 1 in both
+// axes, unwrapped) falls in the tile or one of its periodic images, one point
+// per lane with the point list flattened across slice lines.  Each point is
+// owned by exactly one (tile, image), so every output is written once.
+template <typename T, int TPB, int MH>
 __global__ void __launch_bounds__(TPB * 32) k_gather2d_tiled(const C<T>* __restrict__ P, C<T>* __restrict__ out,
                                                              const C<T>* __restrict__ sub, int kv0, Usfft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TS = a.TS, nt = 2 * a.m;
+    constexpr int nt = 2 * MH;
+    const int TS = a.TS;
     const int SH = TS + nt - 1;  // staged rows
     const int SW = TS + nt;      // staged row stride
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -247,214 +309,290 @@ __global__ void __launch_bounds__(TPB * 32) k_gather2d_tiled(const C<T>* __restr
         st[r * SW + c] = pl[(size_t)wrap(tx0 + r, a.M1) * a.M2 + wrap(ty0 + c, a.M2)];
     }
     __syncwarp();
-    const int kmin = -a.w / 2, kmax = a.w / 2 - 1;
-    const T hx = (T)TS * (T)0.5 + (T)1;
+    const T hb = (T)TS * (T)0.5 + (T)1;
     for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
         const int bx0 = tx0 + ix * a.M1;
         for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
             const int by0 = ty0 + iy * a.M2;
             // positions whose window origin is in [b0, b0 + TS): p in [b0 + m - 1, b0 + TS + m - 1)
             const T cx = (T)(bx0 + a.m - 1) + (T)TS * (T)0.5, cy = (T)(by0 + a.m - 1) + (T)TS * (T)0.5;
-            if (sqrt(cx * cx + cy * cy) > a.rmax + hx * (T)1.5) continue;
-            for (int base = 0; base < a.T_; base += 32) {
-                const int th = base + lane;
-                bool hit = false;
-                if (th < a.T_) {
-                    const typename AngleT<T>::type g = a.ang[th];
-                    T Ax, Cx, Ay, Cy;
-                    line_coef(g, kvc, Ax, Cx, Ay, Cy);
-                    const T nrm = sqrt(Ax * Ax + Ay * Ay);
-                    const T nx = -Ay / nrm, ny = Ax / nrm;
-                    const T dist = fabs((cx - Cx) * nx + (cy - Cy) * ny);
-                    hit = dist <= hx * (fabs(nx) + fabs(ny)) + (T)1;
+            if (sqrt(cx * cx + cy * cy) > a.rmax + hb * (T)1.5) continue;
+            for_tile_points<T>(a, kvc, cx, cy, hb, (T)(bx0 + a.m - 1), (T)(bx0 + TS + a.m - 1),
+                               (T)(by0 + a.m - 1), (T)(by0 + TS + a.m - 1), [&](int th, int kuc) {
+                if (th < 0) return;
+                const typename AngleT<T>::type g = a.ang[th];
+                int jx, jy;
+                T fx, fy;
+                point_pos(g, kuc, kvc, jx, fx, jy, fy);
+                const int ox = jx - a.m + 1 - bx0, oy = jy - a.m + 1 - by0;
+                if (ox < 0 || ox >= TS || oy < 0 || oy >= TS) return;
+                T wy[nt];
+#pragma unroll
+                for (int t = 0; t < nt; ++t) {
+                    const T d = fy + (T)(MH - 1 - t);
+                    wy[t] = gexp(-d * d * a.inv4beta);
                 }
-                unsigned mask = __ballot_sync(0xffffffffu, hit);
-                while (mask) {
-                    const int th2 = base + __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const typename AngleT<T>::type g = a.ang[th2];
-                    T Ax, Cx, Ay, Cy;
-                    line_coef(g, kvc, Ax, Cx, Ay, Cy);
-                    int lo = kmin, hi = kmax;
-                    clip_line<T>(Ax, Cx, (T)(bx0 + a.m - 1), (T)(bx0 + TS + a.m - 1), lo, hi);
-                    clip_line<T>(Ay, Cy, (T)(by0 + a.m - 1), (T)(by0 + TS + a.m - 1), lo, hi);
-                    const size_t orow = ((size_t)th2 * a.h + kv) * a.w + a.w / 2;
-                    for (int k0 = lo; k0 <= hi; k0 += 32) {
-                        const int kuc = k0 + lane;
-                        if (kuc > hi) continue;
-                        int jx, jy;
-                        T fx, fy;
-                        point_pos(g, kuc, kvc, jx, fx, jy, fy);
-                        const int ox = jx - a.m + 1 - bx0, oy = jy - a.m + 1 - by0;
-                        if (ox < 0 || ox >= TS || oy < 0 || oy >= TS) continue;
-                        T wy[16];
+                T sr = 0, si = 0;
 #pragma unroll
-                        for (int t = 0; t < 16; ++t)
-                            if (t < nt) {
-                                const T d = fy + (T)(a.m - 1 - t);
-                                wy[t] = gexp(-d * d * a.inv4beta);
-                            }
-                        T sr = 0, si = 0;
+                for (int sx = 0; sx < nt; ++sx) {
+                    const T d = fx + (T)(MH - 1 - sx);
+                    const T wx = gexp(-d * d * a.inv4beta);
+                    const C<T>* rowp = st + (ox + sx) * SW + oy;
+                    T rr = 0, ri = 0;
 #pragma unroll
-                        for (int sx = 0; sx < 16; ++sx) {
-                            if (sx >= nt) break;
-                            const T d = fx + (T)(a.m - 1 - sx);
-                            const T wx = gexp(-d * d * a.inv4beta);
-                            const C<T>* rowp = st + (ox + sx) * SW + oy;
-                            T rr = 0, ri = 0;
-#pragma unroll
-                            for (int t = 0; t < 16; ++t)
-                                if (t < nt) {
-                                    const C<T> pv = rowp[t];
-                                    rr += wy[t] * pv.x;
-                                    ri += wy[t] * pv.y;
-                                }
-                            sr += wx * rr;
-                            si += wx * ri;
-                        }
-                        const size_t o = orow + kuc;
-                        C<T> v = cmake<T>(sr, si);
-                        if (sub) v = csub(v, sub[o]);
-                        out[o] = v;
+                    for (int t = 0; t < nt; ++t) {
+                        const C<T> pv = rowp[t];
+                        rr += wy[t] * pv.x;
+                        ri += wy[t] * pv.y;
                     }
+                    sr += wx * rr;
+                    si += wx * ri;
                 }
-            }
+                const size_t o = ((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2);
+                C<T> v = cmake<T>(sr, si);
+                if (sub) v = csub(v, sub[o]);
+                out[o] = v;
+            });
         }
     }
 }
 
-// --------------------------------------------------------------------------
-// scatter (type 1 spreading), tile-owned, per-warp accumulators
-// --------------------------------------------------------------------------
-
-template <typename T> struct Acc;  // accumulator cell
-template <> struct Acc<float> {
-    float sr, si, cr, ci;  // sum and Kahan compensation
-    __device__ __forceinline__ void zero() { sr = si = cr = ci = 0.f; }
-    __device__ __forceinline__ void add(float vr, float vi) {
-        const float yr = vr - cr, yi = vi - ci;
-        const float tr = sr + yr, ti = si + yi;
-        cr = (tr - sr) - yr;
-        ci = (ti - si) - yi;
-        sr = tr;
-        si = ti;
+// One warp owns one TS x TS tile of the padded plane and an accumulator for
+// it (sum and compensation in separate arrays; compensated in FP32); a block
+// holds TPB tiles.  The points that may reach the tile come from
+// for_tile_points, 32 per round, one per lane; each lane computes its point's
+// tap window and 2 x 2m Gaussian weights in registers, and the warp steps
+// through the (2m)^2 taps in lock-step.  Lanes whose window origins coincide
+// (points of different lines can share one) are ranked with __match_any_sync
+// and take successive passes, so within a pass no two lanes touch one cell.
+template <typename T> struct AccArr;
+template <> struct AccArr<float> {
+    C<float>* s;
+    C<float>* c;
+    __device__ __forceinline__ void add(int i, float vr, float vi) {
+        C<float> sum = s[i], cmp = c[i];
+        const float yr = vr - cmp.x, yi = vi - cmp.y;
+        const float tr = sum.x + yr, ti = sum.y + yi;
+        cmp.x = (tr - sum.x) - yr;
+        cmp.y = (ti - sum.y) - yi;
+        s[i] = cmake<float>(tr, ti);
+        c[i] = cmp;
     }
 };
-template <> struct Acc<double> {
-    double sr, si;
-    __device__ __forceinline__ void zero() { sr = si = 0.0; }
-    __device__ __forceinline__ void add(double vr, double vi) {
-        sr += vr;
-        si += vi;
+template <> struct AccArr<double> {
+    C<double>* s;
+    C<double>* c;
+    __device__ __forceinline__ void add(int i, double vr, double vi) {
+        C<double> sum = s[i];
+        s[i] = cmake<double>(sum.x + vr, sum.y + vi);
     }
 };
 
-// One warp owns one TS x TS tile of the padded plane and a private
-// accumulator for it (compensated in FP32); a block holds TPB tiles.  The warp
-// culls the n_theta slice lines against its tile with a lane-parallel distance
-// test, then walks each crossing line 32 points at a time, one point per lane:
-// the lane computes the point's tap window and 2 x 2m Gaussian weights in
-// registers, and the warp steps through the (2m)^2 taps in lock-step.  Window
-// origins of points 2 cells apart on one line are distinct, so the 32 lanes
-// of one tap step never touch the same cell.
-template <typename T, int TPB>
-__global__ void __launch_bounds__(TPB * 32) k_scatter2d(const C<T>* __restrict__ in, C<T>* __restrict__ P,
+template <typename T, int TPB, int MH>
+__global__ void __launch_bounds__(TPB * 32, sizeof(T) == 4 ? 4 : 1) k_scatter2d(const C<T>* __restrict__ in, C<T>* __restrict__ P,
                                                         int kv0, Usfft2dArgs<T> a) {
+    constexpr int nt = 2 * MH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TS = a.TS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_x = a.M1 / TS, tiles_y = a.M2 / TS;
     const int tile = blockIdx.x * TPB + warp;
     if (tile >= tiles_x * tiles_y) return;  // whole warp exits; no block-wide sync below
-    Acc<T>* my = reinterpret_cast<Acc<T>*>(smem_raw) + (size_t)warp * TS * TS;
-    for (int i = lane; i < TS * TS; i += 32) my[i].zero();
+    const int ncell = TS * TS;
+    AccArr<T> acc;
+    acc.s = reinterpret_cast<C<T>*>(smem_raw) + (size_t)warp * 2 * ncell;
+    acc.c = acc.s + ncell;
+    for (int i = lane; i < 2 * ncell; i += 32) acc.s[i] = cmake<T>(0, 0);
     __syncwarp();
     const int tx0 = (tile / tiles_y) * TS, ty0 = (tile % tiles_y) * TS;
     const int b = blockIdx.y, kv = kv0 + b, kvc = kv - a.h / 2;
-    const int nt = 2 * a.m;
-    const int kmin = -a.w / 2, kmax = a.w / 2 - 1;
-    const T hx = (T)(TS + 2 * a.m) * (T)0.5;
+    const T hb = (T)(TS + 2 * a.m) * (T)0.5;
     for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
         const int bx0 = tx0 + ix * a.M1;
         for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
             const int by0 = ty0 + iy * a.M2;
             const T cx = (T)bx0 + (T)(TS - 1) * (T)0.5, cy = (T)by0 + (T)(TS - 1) * (T)0.5;
-            if (sqrt(cx * cx + cy * cy) > a.rmax + hx * (T)1.5) continue;
-            for (int base = 0; base < a.T_; base += 32) {
-                const int th = base + lane;
-                bool hit = false;
-                if (th < a.T_) {
+            if (sqrt(cx * cx + cy * cy) > a.rmax + hb * (T)1.5) continue;
+            for_tile_points<T>(a, kvc, cx, cy, hb, (T)(bx0 - a.m), (T)(bx0 + TS + a.m - 1), (T)(by0 - a.m),
+                               (T)(by0 + TS + a.m - 1), [&](int th, int kuc) {
+                bool act = th >= 0;
+                int ox = 0, oy = 0;
+                T wx[nt], wy[nt];
+                C<T> v = cmake<T>(0, 0);
+                if (act) {
                     const typename AngleT<T>::type g = a.ang[th];
-                    T Ax, Cx, Ay, Cy;
-                    line_coef(g, kvc, Ax, Cx, Ay, Cy);
-                    const T nrm = sqrt(Ax * Ax + Ay * Ay);
-                    const T nx = -Ay / nrm, ny = Ax / nrm;
-                    const T dist = fabs((cx - Cx) * nx + (cy - Cy) * ny);
-                    hit = dist <= hx * (fabs(nx) + fabs(ny)) + (T)1;
-                }
-                unsigned mask = __ballot_sync(0xffffffffu, hit);
-                while (mask) {
-                    const int th2 = base + __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    const typename AngleT<T>::type g = a.ang[th2];
-                    T Ax, Cx, Ay, Cy;
-                    line_coef(g, kvc, Ax, Cx, Ay, Cy);
-                    int lo = kmin, hi = kmax;
-                    clip_line<T>(Ax, Cx, (T)(bx0 - a.m), (T)(bx0 + TS + a.m - 1), lo, hi);
-                    clip_line<T>(Ay, Cy, (T)(by0 - a.m), (T)(by0 + TS + a.m - 1), lo, hi);
-                    const C<T>* row = in + ((size_t)th2 * a.h + kv) * a.w + a.w / 2;
-                    // lanes take points pstride apart (>= sqrt 2 cells), so their
-                    // window origins differ; pstride passes cover every point
-                    const int ps = a.pstride;
-                    for (int kq = 0; lo + (kq / ps) * 32 * ps <= hi; ++kq) {
-                        const int kuc = lo + (kq / ps) * 32 * ps + (kq % ps) + lane * ps;
-                        const bool act = kuc <= hi;
-                        int ox = -1 << 20, oy = -1 << 20;
-                        T wx[16], wy[16];
-                        C<T> v = cmake<T>(0, 0);
-                        if (act) {
-                            int jx, jy;
-                            T fx, fy;
-                            point_pos(g, kuc, kvc, jx, fx, jy, fy);
-                            ox = jx - a.m + 1 - bx0;
-                            oy = jy - a.m + 1 - by0;
+                    int jx, jy;
+                    T fx, fy;
+                    point_pos(g, kuc, kvc, jx, fx, jy, fy);
+                    ox = jx - a.m + 1 - bx0;
+                    oy = jy - a.m + 1 - by0;
+                    // no tap inside the tile: drop the point
+                    act = ox > -nt && ox < TS && oy > -nt && oy < TS;
+                    if (act) {
 #pragma unroll
-                            for (int t = 0; t < 16; ++t) {
-                                if (t < nt) {
-                                    const T dx = fx + (T)(a.m - 1 - t), dy = fy + (T)(a.m - 1 - t);
-                                    wx[t] = gexp(-dx * dx * a.inv4beta);
-                                    wy[t] = gexp(-dy * dy * a.inv4beta);
-                                }
-                            }
-                            v = row[kuc];
+                        for (int t = 0; t < nt; ++t) {
+                            const T dx = fx + (T)(MH - 1 - t), dy = fy + (T)(MH - 1 - t);
+                            wx[t] = gexp(-dx * dx * a.inv4beta);
+                            wy[t] = gexp(-dy * dy * a.inv4beta);
                         }
+                        v = in[((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2)];
+                    }
+                }
+                const unsigned amask = __ballot_sync(0xffffffffu, act);
+                if (amask == 0) return;
+                // rank lanes that share a window origin
+                const int key = act ? ((ox + 64) << 10) | (oy + 64) : -1 - lane;
+                const unsigned peers = __match_any_sync(0xffffffffu, key);
+                const int rank = act ? __popc(peers & ((1u << lane) - 1)) : 0;
+                int maxrank = rank;
 #pragma unroll
-                        for (int sx = 0; sx < 16; ++sx) {
-                            if (sx >= nt) break;
-                            const int cxx = ox + sx;
-                            const bool rowin = act && cxx >= 0 && cxx < TS;
-                            const T wxs = wx[sx];
+                for (int o = 16; o > 0; o >>= 1) maxrank = max(maxrank, __shfl_xor_sync(0xffffffffu, maxrank, o));
+                for (int r = 0; r <= maxrank; ++r) {
+                    const bool go = act && rank == r;
 #pragma unroll
-                            for (int sy = 0; sy < 16; ++sy) {
-                                if (sy >= nt) break;
-                                const int cyy = oy + sy;
-                                if (rowin && cyy >= 0 && cyy < TS) {
-                                    const T wgt = wxs * wy[sy];
-                                    my[cxx * TS + cyy].add(wgt * v.x, wgt * v.y);
-                                }
-                                __syncwarp();
+                    for (int sx = 0; sx < nt; ++sx) {
+                        const int cxx = ox + sx;
+                        const bool rowin = go && cxx >= 0 && cxx < TS;
+                        const T wxs = wx[sx];
+#pragma unroll
+                        for (int sy = 0; sy < nt; ++sy) {
+                            const int cyy = oy + sy;
+                            if (rowin && cyy >= 0 && cyy < TS) {
+                                const T wgt = wxs * wy[sy];
+                                acc.add(cxx * TS + cyy, wgt * v.x, wgt * v.y);
                             }
+                            __syncwarp();
                         }
                     }
                 }
-            }
+            });
         }
     }
     __syncwarp();
     C<T>* pl = P + (size_t)b * a.M1 * a.M2;
-    for (int i = lane; i < TS * TS; i += 32) {
+    for (int i = lane; i < ncell; i += 32) {
         const int cxx = i / TS, cyy = i - cxx * TS;
-        pl[(size_t)(tx0 + cxx) * a.M2 + ty0 + cyy] = cmake<T>(my[i].sr, my[i].si);
+        pl[(size_t)(tx0 + cxx) * a.M2 + ty0 + cyy] = acc.s[i];
+    }
+}
+
+// Fast scatter: the same tile ownership and point enumeration, but each lane
+// spreads its own point's (2m)^2 taps independently with shared-memory atomic
+// adds into one FP32 (or FP64) accumulator per tile.  No lock-step, no rank
+// passes; the summation order inside a cell depends on scheduling, so results
+// agree with the deterministic kernel to rounding, not bit for bit.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+
+// Accumulator cells for the atomic scatter (ACC: 0 plain, 1 compensated, 2 FP64).
+template <typename T, int ACC> struct AtomAcc {
+    T* base;
+    int ncell;
+    __device__ __forceinline__ void zero(int lane) {
+        for (int i = lane; i < 2 * ncell * (ACC == 1 ? 2 : 1); i += 32) base[i] = (T)0;
+    }
+    __device__ __forceinline__ void add(int cell, T vr, T vi) {
+        if (ACC == 1) {
+            // the atomic returns the value it added to; two-sum recovers the
+            // exact rounding error of the stored sum, which goes to the second half
+            const T ar = atomicAdd(base + 2 * cell, vr), ai = atomicAdd(base + 2 * cell + 1, vi);
+            // (_rn intrinsics: no fma contraction with the product that formed v)
+            const T sr = add_rn(ar, vr), si = add_rn(ai, vi);
+            const T br = sub_rn(sr, ar), bi = sub_rn(si, ai);
+            const T er = add_rn(sub_rn(ar, sub_rn(sr, br)), sub_rn(vr, br));
+            const T ei = add_rn(sub_rn(ai, sub_rn(si, bi)), sub_rn(vi, bi));
+            atomicAdd(base + 2 * ncell + 2 * cell, er);
+            atomicAdd(base + 2 * ncell + 2 * cell + 1, ei);
+        } else {
+            atomicAdd(base + 2 * cell, vr);
+            atomicAdd(base + 2 * cell + 1, vi);
+        }
+    }
+    __device__ __forceinline__ C<T> get(int cell) const {
+        if (ACC == 1) return cmake<T>(base[2 * cell] + base[2 * ncell + 2 * cell], base[2 * cell + 1] + base[2 * ncell + 2 * cell + 1]);
+        return cmake<T>(base[2 * cell], base[2 * cell + 1]);
+    }
+};
+template <typename T> struct AtomAcc<T, 2> {  // FP64 cells
+    double* base;
+    int ncell;
+    __device__ __forceinline__ void zero(int lane) {
+        for (int i = lane; i < 2 * ncell; i += 32) base[i] = 0.0;
+    }
+    __device__ __forceinline__ void add(int cell, T vr, T vi) {
+        atomicAdd(base + 2 * cell, (double)vr);
+        atomicAdd(base + 2 * cell + 1, (double)vi);
+    }
+    __device__ __forceinline__ C<T> get(int cell) const { return cmake<T>((T)base[2 * cell], (T)base[2 * cell + 1]); }
+};
+template <typename T, int ACC> __host__ __device__ constexpr int atom_acc_bytes() {
+    return ACC == 2 ? 16 : (ACC == 1 ? 4 * (int)sizeof(T) : 2 * (int)sizeof(T));
+}
+
+template <typename T, int TPB, int MH, int ACC>
+__global__ void __launch_bounds__(TPB * 32, sizeof(T) == 4 ? 6 : 2) k_scatter2d_atomic(
+    const C<T>* __restrict__ in, C<T>* __restrict__ P, int kv0, Usfft2dArgs<T> a) {
+    constexpr int nt = 2 * MH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TS = a.TS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles_x = a.M1 / TS, tiles_y = a.M2 / TS;
+    const int tile = blockIdx.x * TPB + warp;
+    if (tile >= tiles_x * tiles_y) return;
+    const int ncell = TS * TS;
+    AtomAcc<T, ACC> acc;
+    acc.base = reinterpret_cast<decltype(acc.base)>(smem_raw + (size_t)warp * ncell * atom_acc_bytes<T, ACC>());
+    acc.ncell = ncell;
+    acc.zero(lane);
+    __syncwarp();
+    const int tx0 = (tile / tiles_y) * TS, ty0 = (tile % tiles_y) * TS;
+    const int b = blockIdx.y, kv = kv0 + b, kvc = kv - a.h / 2;
+    const T hb = (T)(TS + 2 * a.m) * (T)0.5;
+    for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
+        const int bx0 = tx0 + ix * a.M1;
+        for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
+            const int by0 = ty0 + iy * a.M2;
+            const T cx = (T)bx0 + (T)(TS - 1) * (T)0.5, cy = (T)by0 + (T)(TS - 1) * (T)0.5;
+            if (sqrt(cx * cx + cy * cy) > a.rmax + hb * (T)1.5) continue;
+            for_tile_points<T>(a, kvc, cx, cy, hb, (T)(bx0 - a.m), (T)(bx0 + TS + a.m - 1), (T)(by0 - a.m),
+                               (T)(by0 + TS + a.m - 1), [&](int th, int kuc) {
+                if (th < 0) return;
+                const typename AngleT<T>::type g = a.ang[th];
+                int jx, jy;
+                T fx, fy;
+                point_pos(g, kuc, kvc, jx, fx, jy, fy);
+                const int ox = jx - MH + 1 - bx0, oy = jy - MH + 1 - by0;
+                if (ox <= -nt || ox >= TS || oy <= -nt || oy >= TS) return;
+                const C<T> v = in[((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2)];
+                T wy[nt];
+#pragma unroll
+                for (int t = 0; t < nt; ++t) {
+                    const T dy = fy + (T)(MH - 1 - t);
+                    wy[t] = gexp(-dy * dy * a.inv4beta);
+                }
+#pragma unroll
+                for (int sx = 0; sx < nt; ++sx) {
+                    const int cxx = ox + sx;
+                    if (cxx < 0 || cxx >= TS) continue;
+                    const T dx = fx + (T)(MH - 1 - sx);
+                    const T wx = gexp(-dx * dx * a.inv4beta);
+                    const T vr = wx * v.x, vi = wx * v.y;
+#pragma unroll
+                    for (int sy = 0; sy < nt; ++sy) {
+                        const int cyy = oy + sy;
+                        if (cyy >= 0 && cyy < TS) acc.add(cxx * TS + cyy, wy[sy] * vr, wy[sy] * vi);
+                    }
+                }
+            });
+        }
+    }
+    __syncwarp();
+    C<T>* pl = P + (size_t)b * a.M1 * a.M2;
+    for (int i = lane; i < ncell; i += 32) {
+        const int cxx = i / TS, cyy = i - cxx * TS;
+        pl[(size_t)(tx0 + cxx) * a.M2 + ty0 + cyy] = acc.get(i);
     }
 }
 
@@ -474,7 +612,13 @@ cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* s
     constexpr int NW = kScatterWarps;
     const int ntiles = (a.M1 / a.TS) * (a.M2 / a.TS);
     const size_t sg = (size_t)NW * (a.TS + 2 * a.m - 1) * (a.TS + 2 * a.m) * sizeof(C<T>);
-    k_gather2d_tiled<T, NW><<<dim3((ntiles + NW - 1) / NW, nb), NW * 32, sg, s>>>(P, out, sub, kv0, a);
+    const dim3 grid((ntiles + NW - 1) / NW, nb);
+    switch (a.m) {
+#define LAM_G(MH) case MH: k_gather2d_tiled<T, NW, MH><<<grid, NW * 32, sg, s>>>(P, out, sub, kv0, a); break;
+        LAM_G(2) LAM_G(3) LAM_G(4) LAM_G(5) LAM_G(6) LAM_G(7) LAM_G(8)
+#undef LAM_G
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -482,17 +626,41 @@ template <typename T>
 cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int kv0, int nb, const Usfft2dArgs<T>& a,
                                cudaStream_t s) {
     constexpr int NW = kScatterWarps;
-    const size_t sa = (size_t)NW * a.TS * a.TS * sizeof(Acc<T>);
+    const size_t sa = (size_t)NW * 2 * a.TS * a.TS * sizeof(C<T>);
     const int ntiles = (a.M1 / a.TS) * (a.M2 / a.TS);
     const size_t sr = (size_t)a.RB * a.M2 * sizeof(C<T>);
     const size_t sc = (size_t)a.CB * a.M1 * sizeof(C<T>);
-    k_scatter2d<T, NW><<<dim3((ntiles + NW - 1) / NW, nb), NW * 32, sa, s>>>(in, P, kv0, a);
+    const dim3 grid((ntiles + NW - 1) / NW, nb);
+    if (a.deterministic) {
+        switch (a.m) {
+#define LAM_S(MH) case MH: k_scatter2d<T, NW, MH><<<grid, NW * 32, sa, s>>>(in, P, kv0, a); break;
+            LAM_S(2) LAM_S(3) LAM_S(4) LAM_S(5) LAM_S(6) LAM_S(7) LAM_S(8)
+#undef LAM_S
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        const int accm = a.scatter_acc;
+        const size_t cells = (size_t)NW * a.TS * a.TS;
+#define LAM_S(MH, ACC)                                                                                   \
+    case MH:                                                                                             \
+        k_scatter2d_atomic<T, NW, MH, ACC><<<grid, NW * 32, cells * atom_acc_bytes<T, ACC>(), s>>>(in, P, \
+                                                                                                kv0, a); \
+        break;
+#define LAM_SW(ACC)                                                                              \
+    switch (a.m) {                                                                               \
+        LAM_S(2, ACC) LAM_S(3, ACC) LAM_S(4, ACC) LAM_S(5, ACC) LAM_S(6, ACC) LAM_S(7, ACC) LAM_S(8, ACC) \
+        default: return cudaErrorInvalidValue;                                                   \
+    }
+        if (accm == 0) { LAM_SW(0) }
+        else if (accm == 2) { LAM_SW(2) }
+        else { LAM_SW(1) }
+#undef LAM_SW
+#undef LAM_S
+    }
     k_colfft_adj<T><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
     k_rowfft_adj<T><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(P, u1, kv0, a);
     return cudaGetLastError();
 }
-
-template <typename T> size_t scatter_acc_bytes() { return sizeof(Acc<T>) * kScatterWarps; }
 
 template <typename T> cudaError_t configure_usfft2d() {
     const int mx = kMaxDynSmem;
@@ -502,8 +670,14 @@ template <typename T> cudaError_t configure_usfft2d() {
     if (!e) e = cudaFuncSetAttribute(k_colfft_fwd<T>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_rowfft_adj<T>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_colfft_adj<T>, at, mx);
-    if (!e) e = cudaFuncSetAttribute(k_scatter2d<T, kScatterWarps>, at, mx);
-    if (!e) e = cudaFuncSetAttribute(k_gather2d_tiled<T, kScatterWarps>, at, mx);
+#define LAM_A(MH)                                                                          \
+    if (!e) e = cudaFuncSetAttribute(k_scatter2d<T, kScatterWarps, MH>, at, mx);          \
+    if (!e) e = cudaFuncSetAttribute(k_gather2d_tiled<T, kScatterWarps, MH>, at, mx);       \
+    if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 0>, at, mx);  \
+    if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 1>, at, mx);  \
+    if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 2>, at, mx);
+    LAM_A(2) LAM_A(3) LAM_A(4) LAM_A(5) LAM_A(6) LAM_A(7) LAM_A(8)
+#undef LAM_A
     return e;
 }
 
@@ -515,8 +689,6 @@ template cudaError_t launch_usfft2d_adj<float>(const C<float>*, C<float>*, C<flo
                                                const Usfft2dArgs<float>&, cudaStream_t);
 template cudaError_t launch_usfft2d_adj<double>(const C<double>*, C<double>*, C<double>*, int, int,
                                                 const Usfft2dArgs<double>&, cudaStream_t);
-template size_t scatter_acc_bytes<float>();
-template size_t scatter_acc_bytes<double>();
 template cudaError_t configure_usfft2d<float>();
 template cudaError_t configure_usfft2d<double>();
 

@@ -39,6 +39,7 @@ def lib() -> ctypes.CDLL:
         sig = {
             "lam_plan_create": [ctypes.POINTER(vp), i, i, i, i, i, ctypes.POINTER(d), d, i, i, i],
             "lam_plan_destroy": [vp],
+            "lam_plan_set_option": [vp, i, i],
             "lam_forward": [vp, vp, vp, vp, vp],
             "lam_adjoint": [vp, vp, vp, vp, vp],
             "lam_forward_hat": [vp, vp, vp, vp, vp, vp],
@@ -115,7 +116,7 @@ class Geometry:
 class Plan:
     """A plan for one geometry and precision ('f32' or 'f64') on the current device."""
 
-    def __init__(self, n, nz, h, w, theta, phi, m=4, prec="f32", device=None):
+    def __init__(self, n, nz, h, w, theta, phi, m=4, prec="f32", device=None, deterministic=False):
         if not torch.cuda.is_available():
             raise LaminoError("no CUDA device: the laminography operators run only on the GPU")
         self.device = torch.device("cuda" if device is None else device)
@@ -132,6 +133,8 @@ class Plan:
                                          2, self.m, LAM_F32 if prec == "f32" else LAM_F64),
                    "lam_plan_create")
         self._h = h_
+        if deterministic:
+            _check(lib().lam_plan_set_option(self._h, 1, 1), "lam_plan_set_option")
         nbytes = lib().lam_workspace_bytes(self._h)
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
 

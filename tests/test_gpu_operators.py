@@ -11,6 +11,7 @@ import torch
 from gpu_helpers import plan_and_geom, rand_data, rand_vol, rel, tol
 from oracle import lamino as olam
 from oracle import tv as otv
+from paper_2511_01893_b300 import lamino as glam
 
 pytestmark = pytest.mark.gpu
 
@@ -40,11 +41,14 @@ def test_u1d_forward_and_adjoint(geom, prec):
     assert rel(got, ref) < tol(prec)
 
 
+@pytest.mark.parametrize("det", [False, True], ids=["atomic", "deterministic"])
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("geom", GEOMS, ids=IDS)
-def test_u2d_forward_and_adjoint(geom, prec):
+def test_u2d_forward_and_adjoint(geom, prec, det):
     n, nz, h, w, T, phi = geom
     plan, g = plan_and_geom(n, nz, h, w, T, phi, prec)
+    if det:
+        plan = glam.Plan(n, nz, h, w, g.theta, phi, prec=prec, deterministic=True)
     rng = np.random.default_rng(4)
     u1 = rng.standard_normal((n, h, n)) + 1j * rng.standard_normal((n, h, n))
     ref = olam.f_u2d(u1, g)
@@ -108,9 +112,23 @@ def test_adjoint_identity_on_gpu_f64():
     assert abs(lhs - rhs) <= 1e-12 * Lu.norm().item() * v.norm().item()
 
 
-def test_tiny_and_ragged_batches():
-    # h not a multiple of the plane batch and a single angle
-    n, nz, h, w, T = 8, 8, 8, 8, 1
+def test_tiny_and_ragged_batches(monkeypatch):
+    # a single angle, and h = 16 planes in batches of 3 (ragged last batch)
+    n, nz, h, w, T = 8, 8, 16, 8, 1
+    monkeypatch.setenv("LAMINO_PLANES_PER_BATCH", "3")
     plan, g = plan_and_geom(n, nz, h, w, T, 0.5, "f64")
+    assert plan.info()["planes_per_batch"] == 3
     u = rand_vol(n, nz, 15)
     assert rel(plan.forward(torch.from_numpy(u)), olam.lam_forward(u, g)) < 1e-12
+    d = rand_data(T, h, w, 17)
+    assert rel(plan.adjoint(torch.from_numpy(d)), olam.lam_adjoint(d, g)) < 1e-12
+
+
+def test_deterministic_adjoint_is_bitwise_reproducible():
+    n, nz, h, w, T = 64, 32, 64, 64, 48
+    plan, _ = plan_and_geom(n, nz, h, w, T, 0.5, "f32")
+    det = glam.Plan(n, nz, h, w, plan.theta, 0.5, prec="f32", deterministic=True)
+    d = torch.from_numpy(rand_data(T, h, w, 16)).cuda()
+    a, b = det.adjoint(d), det.adjoint(d)
+    assert torch.equal(a, b)
+    assert rel(plan.adjoint(d), a) < 2e-7 * 10
