@@ -21,7 +21,8 @@ lam_status lamx_u1d_adj(const lam_plan* plan, const void* u1, void* u, void* str
 
 /* F_u2D (Section 2): u1 complex [h][n][n] -> d_hat complex [T][h][w]; if sub
  * is not NULL the output is F_u2D u1 - sub (Section 4.2's fused
- * subtraction).  Uses the plane part of ws. */
+ * subtraction).  Uses the plane part of ws.  Every plane is transformed on
+ * its own (u1 need not be the transform of a real volume). */
 lam_status lamx_u2d_fwd(const lam_plan* plan, const void* u1, void* d_hat, const void* sub, void* ws,
                         void* stream);
 
@@ -30,7 +31,9 @@ lam_status lamx_u2d_adj(const lam_plan* plan, const void* d_hat, void* u1, void*
 
 /* Launch shapes chosen by the plan, for diagnostics: out[0..count) receives
  * TY (z forward), TY (z transpose), rows per block, columns per block,
- * scatter tile side, tile images, planes per batch, jmin, jmax. */
+ * scatter tile side, tile images, planes per batch, jmin, jmax, and the
+ * number of plane jobs the full operators run (h/2 + 1 when every plane
+ * pairs with its conjugate mirror). */
 lam_status lamx_plan_info(const lam_plan* plan, int* out, int count);
 
 /* Kernel nodes in the CUDA graph admm_run captured for this state (one outer

@@ -82,12 +82,16 @@ struct lam_plan {
     void *dz, *d1, *d2, *wz, *tw, *ang;
     int *j0z, *kvlo, *kvhi;
     int jmin, jmax;
+    // plane jobs: paired (for real volumes) and one job per plane
+    int2* jobs_pair;
+    int2* jobs_all;
+    int* skip;  // [h] 1 for the mirror plane of a paired job
+    int njobs_pair;
     // launch shapes
     int TYf, TYa, RB, CB, TS, nimg, nbatch;
     double rmax;
     int pstride;
-    int deterministic = 0;
-    int scatter_acc = 1;
+    int exact_accum = 1;
     // workspace layout
     size_t ws_u1, ws_planes, ws_tmp, ws_red, ws_bytes;
     mutable std::mutex mu;
@@ -183,6 +187,44 @@ template <typename T> lam_status build_tables(lam_plan* p, const double* theta) 
     if (st) return st;
     p->kvhi = (int*)upload(p, hi, &st);
     if (st) return st;
+    // Hermitian pairs: for a real volume, u1 at -kv is the conjugate of u1 at kv
+    // when the z windows of -kv mirror those of kv (j0(-t) = -j0(t) - 1; the
+    // tap positions negate exactly); then one padded FFT serves both planes.
+    {
+        const int h = p->h;
+        std::vector<int2> jp, ja;
+        std::vector<int> skip(h, 0);
+        auto generic = [&](int kv) {  // kv in [1, h/2 - 1], partner h - kv
+            return j0[h - kv] == -j0[kv] - 1;
+        };
+        for (int kv = 0; kv <= h / 2; ++kv) {
+            int2 j;
+            j.x = kv;
+            j.y = (kv >= 1 && kv <= h / 2 - 1 && generic(kv)) ? h - kv : -1;
+            if (j.y >= 0) skip[j.y] = 1;
+            jp.push_back(j);
+        }
+        for (int kv = h / 2 + 1; kv < h; ++kv)
+            if (!generic(h - kv)) {
+                int2 j;
+                j.x = kv;
+                j.y = -1;
+                jp.push_back(j);
+            }
+        for (int kv = 0; kv < h; ++kv) {
+            int2 j;
+            j.x = kv;
+            j.y = -1;
+            ja.push_back(j);
+        }
+        p->njobs_pair = (int)jp.size();
+        p->jobs_pair = (int2*)upload(p, jp, &st);
+        if (st) return st;
+        p->jobs_all = (int2*)upload(p, ja, &st);
+        if (st) return st;
+        p->skip = (int*)upload(p, skip, &st);
+        if (st) return st;
+    }
     // twiddles exp(-2 pi i q / Nmax)
     std::vector<T> tw(2 * (size_t)p->Nmax);
     for (int q = 0; q < p->Nmax; ++q) {
@@ -229,13 +271,14 @@ template <typename T> lam_status build_tables(lam_plan* p, const double* theta) 
 // 8 * MAXB * threads, `divides` a multiple of lines, at most `cap`
 static int pick_lines(int len, size_t celem, size_t budget, int divides, int cap, int maxb, size_t extra_per_line = 0) {
     int l = cap;
-    while (l > 1 && ((size_t)l * (len * celem + extra_per_line) > budget || (long long)l * len > 8LL * maxb * 512 ||
+    while (l > 1 && ((size_t)l * ((len + len / 16 + 1) * celem + extra_per_line) > budget ||
+                     (long long)l * len > 8LL * maxb * 512 ||
                      divides % l != 0))
         l >>= 1;
     return l;
 }
 
-template <typename T> Usfft1dArgs<T> args1d(const lam_plan* p, int TY) {
+template <typename T> Usfft1dArgs<T> args1d(const lam_plan* p, int TY, bool paired) {
     Usfft1dArgs<T> a;
     a.n1 = p->n1;
     a.nz = p->nz;
@@ -254,10 +297,11 @@ template <typename T> Usfft1dArgs<T> args1d(const lam_plan* p, int TY) {
     a.jmax = p->jmax;
     a.tw = (const C<T>*)p->tw;
     a.twstride = p->Nmax / p->M0;
+    a.skip = paired ? p->skip : nullptr;
     return a;
 }
 
-template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p) {
+template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p, bool paired) {
     Usfft2dArgs<T> a;
     a.n1 = p->n1;
     a.n2 = p->n2;
@@ -282,8 +326,17 @@ template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p) {
     a.nimg = p->nimg;
     a.rmax = (T)p->rmax;
     a.pstride = p->pstride;
-    a.deterministic = p->deterministic;
-    a.scatter_acc = p->scatter_acc;
+    a.exact_accum = p->exact_accum;
+    a.jobs = paired ? p->jobs_pair : p->jobs_all;
+    a.maxabs = nullptr;
+    // points whose 2m x 2m window covers one cell: at most (2m / spacing + 2)^2 per
+    // line neighbourhood, over all T lines and all periodic images; doubled for safety
+    {
+        const double sp = std::max(1.0, (double)p->M1 / p->w);
+        const double per_line = std::ceil(2.0 * p->m * std::sqrt(2.0) / sp) + 2.0;
+        const double imgs = (2.0 * p->nimg + 1) * (2.0 * p->nimg + 1);
+        a.bound_count = (float)(2.0 * per_line * p->T * imgs);
+    }
     return a;
 }
 
@@ -307,12 +360,24 @@ lam_status fwd_hat(const lam_plan* p, const T* u, C<T>* out, const C<T>* sub, vo
     char* w = (char*)ws;
     C<T>* u1 = (C<T>*)(w + p->ws_u1);
     C<T>* P = (C<T>*)(w + p->ws_planes);
-    CK(launch_usfft1d_fwd<T>(u, u1, args1d<T>(p, p->TYf), s));
-    const Usfft2dArgs<T> a = args2d<T>(p);
-    for (int kv0 = 0; kv0 < p->h; kv0 += p->nbatch) {
-        const int nb = std::min(p->nbatch, p->h - kv0);
-        CK(launch_usfft2d_fwd<T>(u1, P, out, sub, kv0, nb, a, s));
+    CK(launch_usfft1d_fwd<T>(u, u1, args1d<T>(p, p->TYf, true), s));
+    const Usfft2dArgs<T> a = args2d<T>(p, true);
+    for (int j0 = 0; j0 < p->njobs_pair; j0 += p->nbatch) {
+        const int nb = std::min(p->nbatch, p->njobs_pair - j0);
+        CK(launch_usfft2d_fwd<T>(u1, P, out, sub, j0, nb, a, s));
     }
+    return LAM_OK;
+}
+
+// the fixed-point scatter needs a bound on its input: max(|re|, |im|) into the
+// workspace's scalar slot
+template <typename T> lam_status prep_scatter(const lam_plan* p, const C<T>* in, void* ws, cudaStream_t s,
+                                              Usfft2dArgs<T>& a) {
+    if (!p->exact_accum) return LAM_OK;
+    T* mx = (T*)((char*)ws + p->ws_red + align256(SC_COUNT * sizeof(double)) +
+                 align256((size_t)kRedBlocks * 4 * sizeof(double)) + 256);
+    CK(launch_absmax<T>(in, p->ndata(), mx, s));
+    a.maxabs = mx;
     return LAM_OK;
 }
 
@@ -320,12 +385,13 @@ template <typename T> lam_status adj_hat(const lam_plan* p, const C<T>* in, T* u
     char* w = (char*)ws;
     C<T>* u1 = (C<T>*)(w + p->ws_u1);
     C<T>* P = (C<T>*)(w + p->ws_planes);
-    const Usfft2dArgs<T> a = args2d<T>(p);
-    for (int kv0 = 0; kv0 < p->h; kv0 += p->nbatch) {
-        const int nb = std::min(p->nbatch, p->h - kv0);
-        CK(launch_usfft2d_adj<T>(in, P, u1, kv0, nb, a, s));
+    Usfft2dArgs<T> a = args2d<T>(p, true);
+    if (lam_status st = prep_scatter<T>(p, in, ws, s, a)) return st;
+    for (int j0 = 0; j0 < p->njobs_pair; j0 += p->nbatch) {
+        const int nb = std::min(p->nbatch, p->njobs_pair - j0);
+        CK(launch_usfft2d_adj<T>(in, P, u1, j0, nb, a, s));
     }
-    CK(launch_usfft1d_adj<T>(u1, u, args1d<T>(p, p->TYa), s));
+    CK(launch_usfft1d_adj<T>(u1, u, args1d<T>(p, p->TYa, true), s));
     return LAM_OK;
 }
 
@@ -473,18 +539,19 @@ __global__ void k_real_to_complex(const float* __restrict__ src, C<float>* __res
 template <typename T> lam_status u2d_fwd_t(const lam_plan* p, const void* u1, void* out, const void* sub,
                                                   void* ws, cudaStream_t s) {
     C<T>* P = (C<T>*)((char*)ws + p->ws_planes);
-    const Usfft2dArgs<T> a = args2d<T>(p);
-    for (int kv0 = 0; kv0 < p->h; kv0 += p->nbatch)
-        CK(launch_usfft2d_fwd<T>((const C<T>*)u1, P, (C<T>*)out, (const C<T>*)sub, kv0,
-                                 std::min(p->nbatch, p->h - kv0), a, s));
+    const Usfft2dArgs<T> a = args2d<T>(p, false);
+    for (int j0 = 0; j0 < p->h; j0 += p->nbatch)
+        CK(launch_usfft2d_fwd<T>((const C<T>*)u1, P, (C<T>*)out, (const C<T>*)sub, j0,
+                                 std::min(p->nbatch, p->h - j0), a, s));
     return LAM_OK;
 }
 template <typename T> lam_status u2d_adj_t(const lam_plan* p, const void* in, void* u1, void* ws,
                                                   cudaStream_t s) {
     C<T>* P = (C<T>*)((char*)ws + p->ws_planes);
-    const Usfft2dArgs<T> a = args2d<T>(p);
-    for (int kv0 = 0; kv0 < p->h; kv0 += p->nbatch)
-        CK(launch_usfft2d_adj<T>((const C<T>*)in, P, (C<T>*)u1, kv0, std::min(p->nbatch, p->h - kv0), a, s));
+    Usfft2dArgs<T> a = args2d<T>(p, false);
+    if (lam_status st = prep_scatter<T>(p, (const C<T>*)in, ws, s, a)) return st;
+    for (int j0 = 0; j0 < p->h; j0 += p->nbatch)
+        CK(launch_usfft2d_adj<T>((const C<T>*)in, P, (C<T>*)u1, j0, std::min(p->nbatch, p->h - j0), a, s));
     return LAM_OK;
 }
 
@@ -558,7 +625,7 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     p->TYa = std::max(2, pick_lines(p->nz, ce_, budget, p->n2, 16, maxb, (size_t)p->h * ce_));
     p->RB = pick_lines(p->M2, ce_, 128 * 1024, p->n1, 16, maxb);
     p->CB = pick_lines(p->M1, ce_, 128 * 1024, p->M2, 16, maxb);
-    p->TS = std::min(32, std::min(p->M1, p->M2));
+    p->TS = std::min(32, std::min(p->M1, p->M2));  // the scatter's bank swizzle assumes 32 when M >= 32
     // unwrapped slice positions reach |p| <= M (1 + sin phi) / 2 + m + 2
     const double reach = std::max(p->M1, p->M2) * (1.0 + std::sin(phi)) / 2.0 + p->m + 2;
     p->nimg = (int)std::ceil(reach / std::min(p->M1, p->M2));
@@ -569,10 +636,9 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     p->pstride = (int)std::ceil(std::sqrt(2.0) * p->w / (double)p->M1 - 1e-9);
     if (p->pstride < 1) p->pstride = 1;
     const size_t plane = (size_t)p->M1 * p->M2 * ce_;
-    p->nbatch = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->h, (256u << 20) / plane));
+    p->nbatch = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->h, ((size_t)1 << 30) / plane));
     // LAMINO_PLANES_PER_BATCH overrides the number of padded planes processed per
     // batch (workspace size follows); for tuning
-    if (const char* env = std::getenv("LAMINO_SCATTER_ACC")) p->scatter_acc = std::atoi(env);
     if (const char* env = std::getenv("LAMINO_PLANES_PER_BATCH")) {
         const int v = std::atoi(env);
         if (v >= 1 && v <= p->h) p->nbatch = v;
@@ -582,8 +648,9 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     p->ws_tmp = p->ws_planes + align256((size_t)p->nbatch * plane);
     p->ws_red = p->ws_tmp + align256((size_t)p->ndata() * ce_);
     // reduction scratch: scalars, per-block partials, completion counter
+    // + one scalar slot for the scatter's input bound
     p->ws_bytes = p->ws_red + align256(SC_COUNT * sizeof(double)) + align256((size_t)kRedBlocks * 4 * sizeof(double)) +
-                  256;
+                  256 + 256;
     *out = p;
     return LAM_OK;
 }
@@ -591,8 +658,8 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
 lam_status lam_plan_set_option(lam_plan* p, int option, int value) {
     if (lam_status st = check_plan(p)) return st;
     switch (option) {
-        case LAM_OPT_DETERMINISTIC:
-            p->deterministic = value != 0;
+        case LAM_OPT_FAST_ADJOINT:
+            p->exact_accum = value == 0;
             {
                 // captured ADMM graphs hold the old kernel choice
                 std::lock_guard<std::mutex> lk(p->mu);
@@ -895,16 +962,16 @@ lam_status reconstruct(const float* data, const double* theta, double phi, int n
 lam_status lamx_u1d_fwd(const lam_plan* p, const void* u, void* u1, void* stream) {
     if (lam_status st = check_plan(p)) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    CK(DISPATCH(p, launch_usfft1d_fwd<float>((const float*)u, (C<float>*)u1, args1d<float>(p, p->TYf), s),
-                launch_usfft1d_fwd<double>((const double*)u, (C<double>*)u1, args1d<double>(p, p->TYf), s)));
+    CK(DISPATCH(p, launch_usfft1d_fwd<float>((const float*)u, (C<float>*)u1, args1d<float>(p, p->TYf, false), s),
+                launch_usfft1d_fwd<double>((const double*)u, (C<double>*)u1, args1d<double>(p, p->TYf, false), s)));
     return LAM_OK;
 }
 
 lam_status lamx_u1d_adj(const lam_plan* p, const void* u1, void* u, void* stream) {
     if (lam_status st = check_plan(p)) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    CK(DISPATCH(p, launch_usfft1d_adj<float>((const C<float>*)u1, (float*)u, args1d<float>(p, p->TYa), s),
-                launch_usfft1d_adj<double>((const C<double>*)u1, (double*)u, args1d<double>(p, p->TYa), s)));
+    CK(DISPATCH(p, launch_usfft1d_adj<float>((const C<float>*)u1, (float*)u, args1d<float>(p, p->TYa, false), s),
+                launch_usfft1d_adj<double>((const C<double>*)u1, (double*)u, args1d<double>(p, p->TYa, false), s)));
     return LAM_OK;
 }
 
@@ -931,7 +998,7 @@ lam_status lamx_admm_graph_kernels(const lam_plan* p, void* state, size_t* count
 
 lam_status lamx_plan_info(const lam_plan* p, int* out, int count) {
     if (lam_status st = check_plan(p)) return st;
-    const int v[] = {p->TYf, p->TYa, p->RB, p->CB, p->TS, p->nimg, p->nbatch, p->jmin, p->jmax};
+    const int v[] = {p->TYf, p->TYa, p->RB, p->CB, p->TS, p->nimg, p->nbatch, p->jmin, p->jmax, p->njobs_pair};
     const int nv = (int)(sizeof(v) / sizeof(v[0]));
     for (int i = 0; i < count && i < nv; ++i) out[i] = v[i];
     return LAM_OK;

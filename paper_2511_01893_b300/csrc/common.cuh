@@ -47,7 +47,11 @@ template <int DIR, typename T> __host__ __device__ __forceinline__ C<T> cmul_i(C
 }
 
 // Fast exponential for Gaussian weights: exp(x) for x <= 0.
+#ifdef LAM_ACCURATE_EXP
+__device__ __forceinline__ float gexp(float x) { return expf(x); }
+#else
 __device__ __forceinline__ float gexp(float x) { return __expf(x); }
+#endif
 __device__ __forceinline__ double gexp(double x) { return exp(x); }
 
 // Per-angle slice-coordinate constants.  Grid position of the point (ku, kv)

@@ -5,7 +5,7 @@
 // thread of the block takes butterflies q = tid, tid + nthr, ... of a stage,
 // reads R inputs N/R apart, applies twiddles, does an in-register radix-R
 // DFT and writes the R outputs Ns apart (self-sorting, so the result is in
-// natural order).  Stages ping-pong between two buffers.
+// natural order).
 //
 // Sign convention: DIR = -1 computes sum_x a[x] exp(-2 pi i j x / N),
 // DIR = +1 computes sum_x a[x] exp(+2 pi i j x / N) (no normalisation).
@@ -54,84 +54,58 @@ template <int DIR, typename T> __device__ __forceinline__ void dft8(C<T>* v) {
     v[7] = csub(e[3], o3);
 }
 
-template <int R, int DIR, typename T>
-__device__ __forceinline__ void fft_stage(const C<T>* __restrict__ src, C<T>* __restrict__ dst,
-                                          int nlines, int lstride, int N, int Ns,
-                                          const C<T>* __restrict__ tw, int twstride, int tid,
-                                          int nthr) {
-    const int nb = N / R;  // butterflies per line
-    const int total = nlines * nb;
-    const int twstep = (N / (Ns * R)) * twstride;  // table step per unit of r*k
-    for (int q = tid; q < total; q += nthr) {
-        const int line = q / nb;
-        const int j = q - line * nb;
-        const C<T>* s = src + line * lstride;
-        C<T>* d = dst + line * lstride;
-        C<T> v[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = s[j + r * nb];
-        const int k = j & (Ns - 1);
-        if (Ns > 1) {
-#pragma unroll
-            for (int r = 1; r < R; ++r) {
-                C<T> wv = tw[r * k * twstep];
-                if (DIR > 0) wv.y = -wv.y;
-                v[r] = cmul(v[r], wv);
-            }
-        }
-        if (R == 8) dft8<DIR>(v);
-        else if (R == 4) dft4<DIR>(v);
-        else dft2<DIR>(v);
-        const int base = (j - k) * R + k;
-#pragma unroll
-        for (int r = 0; r < R; ++r) d[base + r * Ns] = v[r];
-    }
-}
-
-// Transforms the lines in `a`; returns the buffer (a or b) holding the result.
-// Callers must __syncthreads() before the call (input complete); the call
-// ends with a __syncthreads().
-template <int DIR, typename T>
-__device__ C<T>* fft_lines(C<T>* a, C<T>* b, int nlines, int lstride, int N, int logN,
-                           const C<T>* __restrict__ tw, int twstride) {
-    const int tid = threadIdx.x, nthr = blockDim.x;
-    C<T>* src = a;
-    C<T>* dst = b;
-    int Ns = 1;
-    int bits = logN;
-    while (bits > 0) {
-        if (bits >= 3 && bits != 4) {
-            fft_stage<8, DIR, T>(src, dst, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
-            Ns *= 8;
-            bits -= 3;
-        } else if (bits >= 2) {
-            fft_stage<4, DIR, T>(src, dst, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
-            Ns *= 4;
-            bits -= 2;
-        } else {
-            fft_stage<2, DIR, T>(src, dst, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
-            Ns *= 2;
-            bits -= 1;
-        }
-        __syncthreads();
-        C<T>* t = src;
-        src = dst;
-        dst = t;
-    }
-    return src;
-}
-
 // ---------------------------------------------------------------------------
 // In-place variant: one shared buffer.  Each stage first loads every
 // butterfly input the thread owns into registers (at most MAXB butterflies of
 // radix <= 8 per thread: nlines * N <= 8 * MAXB * blockDim.x), synchronises,
 // then writes the outputs.  Half the shared memory of the ping-pong form, so
 // blocks can hold twice the lines.
+//
+// Element e of a line lives at fpad(e) = e + e / 16: one pad slot per 16
+// complex values keeps the stride-R stores of the early stages free of bank
+// conflicts.  A line of length N occupies fpad_len(N) slots.
+// Twiddles: per butterfly w^1, w^2, w^4 come from the table, the rest are
+// products (w^3 = w w^2, w^5 = w w^4, w^6 = w^2 w^4, w^7 = w^3 w^4).
 // ---------------------------------------------------------------------------
+
+__host__ __device__ __forceinline__ int fpad(int e) { return e + (e >> 4); }
+__host__ __device__ __forceinline__ int fpad_len(int n) { return n + (n >> 4) + 1; }
+
+template <int R, int DIR, typename T>
+__device__ __forceinline__ void twiddles(C<T>* wv, const C<T>* __restrict__ tw, int idx1, int tmask) {
+#ifdef LAM_TW_TABLE
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+        C<T> w = tw[(r * idx1) & tmask];
+        if (DIR > 0) w.y = -w.y;
+        wv[r] = w;
+    }
+    return;
+#endif
+    // idx1 = k * twstep; table index r * idx1 reduced mod table length (tmask = len - 1)
+    C<T> w1 = tw[idx1 & tmask];
+    if (DIR > 0) w1.y = -w1.y;
+    wv[1] = w1;
+    if (R >= 4) {
+        C<T> w2 = tw[(2 * idx1) & tmask];
+        if (DIR > 0) w2.y = -w2.y;
+        wv[2] = w2;
+        wv[3] = cmul(w1, w2);
+    }
+    if (R == 8) {
+        C<T> w4 = tw[(4 * idx1) & tmask];
+        if (DIR > 0) w4.y = -w4.y;
+        wv[4] = w4;
+        wv[5] = cmul(w1, w4);
+        wv[6] = cmul(wv[2], w4);
+        wv[7] = cmul(wv[3], w4);
+    }
+}
 
 template <int R, int DIR, int MAXB, typename T>
 __device__ __forceinline__ void fft_stage_ip(C<T>* buf, int nlines, int lstride, int N, int Ns,
-                                             const C<T>* __restrict__ tw, int twstride, int tid, int nthr) {
+                                             const C<T>* __restrict__ tw, int twstride, int tmask, int tid,
+                                             int nthr) {
     const int nb = N / R;
     const int total = nlines * nb;
     const int twstep = (N / (Ns * R)) * twstride;
@@ -144,7 +118,7 @@ __device__ __forceinline__ void fft_stage_ip(C<T>* buf, int nlines, int lstride,
             const int j = q - line * nb;
             const C<T>* s = buf + line * lstride;
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[bb][r] = s[j + r * nb];
+            for (int r = 0; r < R; ++r) v[bb][r] = s[fpad(j + r * nb)];
         }
     }
     __syncthreads();
@@ -156,12 +130,10 @@ __device__ __forceinline__ void fft_stage_ip(C<T>* buf, int nlines, int lstride,
             const int j = q - line * nb;
             const int k = j & (Ns - 1);
             if (Ns > 1) {
+                C<T> wv[R];
+                twiddles<R, DIR, T>(wv, tw, k * twstep, tmask);
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    C<T> wv = tw[r * k * twstep];
-                    if (DIR > 0) wv.y = -wv.y;
-                    v[bb][r] = cmul(v[bb][r], wv);
-                }
+                for (int r = 1; r < R; ++r) v[bb][r] = cmul(v[bb][r], wv[r]);
             }
             if (R == 8) dft8<DIR>(v[bb]);
             else if (R == 4) dft4<DIR>(v[bb]);
@@ -169,17 +141,12 @@ __device__ __forceinline__ void fft_stage_ip(C<T>* buf, int nlines, int lstride,
             C<T>* d = buf + line * lstride;
             const int base = (j - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) d[base + r * Ns] = v[bb][r];
+            for (int r = 0; r < R; ++r) d[fpad(base + r * Ns)] = v[bb][r];
         }
     }
     __syncthreads();
 }
 
-// In-place FFT of nlines lines in buf (same conventions as fft_lines).  The
-// caller must __syncthreads() before; the call ends with a __syncthreads().
-// Requires nlines * N <= 8 * MAXB * blockDim.x (radix-8 stages); radix-4 and
-// radix-2 stages need at most 2x / 4x that many butterflies, which the
-// register arrays hold as well because they are sized for radix 8.
 // Butterflies per thread per radix-8 stage the in-place kernels are built for
 // (register budget at 512 threads: 2 x 8 complex floats, 1 x 8 complex doubles).
 template <typename T> struct FftMaxB;
@@ -187,23 +154,28 @@ template <> struct FftMaxB<float> { static constexpr int value = 2; };
 template <> struct FftMaxB<double> { static constexpr int value = 1; };
 constexpr int kFftThreads = 512;
 
+// In-place FFT of nlines lines in buf, line l starting at buf + l * lstride,
+// element e at fpad(e) (lstride >= fpad_len(N)).  The caller must __syncthreads() before; the call ends with a
+// __syncthreads().  Requires nlines * N <= 8 * MAXB * blockDim.x.  tlen is the
+// twiddle table length (a power of two).
 template <int DIR, int MAXB, typename T>
-__device__ __forceinline__ void fft_lines_ip(C<T>* buf, int nlines, int lstride, int N, int logN, const C<T>* __restrict__ tw,
-                             int twstride) {
+__device__ __forceinline__ void fft_lines_ip(C<T>* buf, int nlines, int lstride, int N, int logN,
+                                             const C<T>* __restrict__ tw, int twstride) {
     const int tid = threadIdx.x, nthr = blockDim.x;
+    const int tmask = N * twstride - 1;
     int Ns = 1;
     int bits = logN;
     while (bits > 0) {
         if (bits >= 3 && bits != 4) {
-            fft_stage_ip<8, DIR, MAXB, T>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
+            fft_stage_ip<8, DIR, MAXB, T>(buf, nlines, lstride, N, Ns, tw, twstride, tmask, tid, nthr);
             Ns *= 8;
             bits -= 3;
         } else if (bits >= 2) {
-            fft_stage_ip<4, DIR, 2 * MAXB, T>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
+            fft_stage_ip<4, DIR, 2 * MAXB, T>(buf, nlines, lstride, N, Ns, tw, twstride, tmask, tid, nthr);
             Ns *= 4;
             bits -= 2;
         } else {
-            fft_stage_ip<2, DIR, 4 * MAXB, T>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
+            fft_stage_ip<2, DIR, 4 * MAXB, T>(buf, nlines, lstride, N, Ns, tw, twstride, tmask, tid, nthr);
             Ns *= 2;
             bits -= 1;
         }

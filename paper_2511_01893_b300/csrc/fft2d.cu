@@ -20,19 +20,18 @@ __global__ void __launch_bounds__(kFftThreads) k_fft2d_rows(const C<T>* in, C<T>
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
     const int th = blockIdx.y, r0 = blockIdx.x * RB;
     const size_t base = ((size_t)th * a.h + r0) * a.w;
+    const int LS = fpad_len(a.w);
     for (int i = threadIdx.x; i < RB * a.w; i += blockDim.x) {
         const int r = i / a.w, k = i - r * a.w;
         const C<T> v = in[base + i];
-        bufa[i] = ((r0 + r + k) & 1) ? cmake<T>(-v.x, -v.y) : v;
+        bufa[r * LS + fpad(k)] = ((r0 + r + k) & 1) ? cmake<T>(-v.x, -v.y) : v;
     }
     __syncthreads();
-    fft_lines_ip<DIR, FftMaxB<T>::value, T>(bufa, RB, a.w, a.w, a.logw, a.tw, a.tww);
-    const C<T>* res = bufa;
+    fft_lines_ip<DIR, FftMaxB<T>::value, T>(bufa, RB, LS, a.w, a.logw, a.tw, a.tww);
     for (int i = threadIdx.x; i < RB * a.w; i += blockDim.x) {
         const int r = i / a.w, k = i - r * a.w;
-        const C<T> v = res[i];
+        const C<T> v = bufa[r * LS + fpad(k)];
         out[base + i] = (k & 1) ? cmake<T>(-v.x, -v.y) : v;
-        (void)r;
     }
 }
 
@@ -42,17 +41,17 @@ __global__ void __launch_bounds__(kFftThreads) k_fft2d_cols(C<T>* __restrict__ i
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
     const int th = blockIdx.y, c0 = blockIdx.x * CB;
     C<T>* pl = io + (size_t)th * a.h * a.w + c0;
+    const int LS = fpad_len(a.h);
     for (int i = threadIdx.x; i < a.h * CB; i += blockDim.x) {
         const int r = i / CB, c = i - r * CB;
-        bufa[c * a.h + r] = pl[(size_t)r * a.w + c];
+        bufa[c * LS + fpad(r)] = pl[(size_t)r * a.w + c];
     }
     __syncthreads();
-    fft_lines_ip<DIR, FftMaxB<T>::value, T>(bufa, CB, a.h, a.h, a.logh, a.tw, a.twh);
-    const C<T>* res = bufa;
+    fft_lines_ip<DIR, FftMaxB<T>::value, T>(bufa, CB, LS, a.h, a.logh, a.tw, a.twh);
     const int gsign = ((a.h / 2 + a.w / 2) & 1);
     for (int i = threadIdx.x; i < a.h * CB; i += blockDim.x) {
         const int r = i / CB, c = i - r * CB;
-        const C<T> v = res[c * a.h + r];
+        const C<T> v = bufa[c * LS + fpad(r)];
         const T s = ((r + gsign) & 1) ? -scale : scale;
         pl[(size_t)r * a.w + c] = cscale(v, s);
     }
@@ -63,7 +62,8 @@ __global__ void __launch_bounds__(kFftThreads) k_fft2d_cols(C<T>* __restrict__ i
 template <typename T> static int lines_per_block(int len) {
     const size_t elem = sizeof(C<T>);
     int l = 32;
-    while (l > 1 && ((size_t)l * len * elem > 128 * 1024 || l * len > 8 * FftMaxB<T>::value * kFftThreads)) l >>= 1;
+    while (l > 1 && ((size_t)l * fpad_len(len) * elem > 128 * 1024 || l * len > 8 * FftMaxB<T>::value * kFftThreads))
+        l >>= 1;
     return l;
 }
 
@@ -74,8 +74,8 @@ cudaError_t launch_fft2d_angles(const C<T>* in, C<T>* out, int dir, T scale, con
     if (RB > a.h) RB = a.h;
     int CB = lines_per_block<T>(a.h);
     if (CB > a.w) CB = a.w;
-    const size_t sr = (size_t)RB * a.w * sizeof(C<T>);
-    const size_t sc = (size_t)CB * a.h * sizeof(C<T>);
+    const size_t sr = (size_t)RB * fpad_len(a.w) * sizeof(C<T>);
+    const size_t sc = (size_t)CB * fpad_len(a.h) * sizeof(C<T>);
     if (dir > 0) {
         k_fft2d_rows<1, T><<<dim3(a.h / RB, a.T_), kFftThreads, sr, s>>>(in, out, RB, a);
         k_fft2d_cols<1, T><<<dim3(a.w / CB, a.T_), kFftThreads, sc, s>>>(out, CB, scale, a);

@@ -31,6 +31,8 @@ template <typename T> struct Usfft1dArgs {
     int jmin, jmax;    // unwrapped cell range touched by any tap
     const C<T>* tw;    // twiddles exp(-2 pi i q / Nmax)
     int twstride;      // Nmax / M0
+    const int* skip;   // [h] or nullptr: planes that are mirrors of a paired plane
+                       // (forward: not written; transpose: read as zero)
 };
 
 template <typename T>
@@ -59,20 +61,29 @@ template <typename T> struct Usfft2dArgs {
     int nimg;                       // tile images +-1..nimg checked per line (unwrapped positions)
     T rmax;                         // bound on |slice position| in grid units
     int pstride;                    // scatter: lanes take points this far apart along a line
-    int deterministic;              // scatter: compensated lock-step kernel (bitwise reproducible)
-    int scatter_acc;                // atomic scatter accumulators: 0 FP32, 1 compensated, 2 FP64
+    int exact_accum;                // scatter cells: 1 exact fixed point (default), 0 plain atomic adds
+    const int2* jobs;               // plane jobs: .x plane computed, .y its conjugate mirror plane or -1
+    const T* maxabs;                // device scalar: max |re|, |im| of the scatter input (fixed point)
+    float bound_count;              // bound on the products summed into one padded cell
 };
 
-// forward: planes kv0 .. kv0 + nb - 1 of u1 ([h][n1][n2]) -> out ([T][h][w]),
-// using the padded-plane buffer P ([nb][M1][M2]).  If sub != nullptr the
-// output is the value minus sub (same layout as out).
+// forward: plane jobs j0 .. j0 + nb - 1 of u1 ([h][n1][n2]) -> out ([T][h][w]),
+// using the padded-plane buffer P ([nb][M1][M2]).  Job j computes plane
+// jobs[j].x and, if jobs[j].y >= 0, its mirror plane from the same padded FFT
+// (P_mirror[j] = conj P[-j]).  If sub != nullptr the output is the value minus
+// sub (same layout as out).
 template <typename T>
 cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* sub, int kv0, int nb,
                                const Usfft2dArgs<T>& a, cudaStream_t s);
-// transpose: planes kv0 .. kv0 + nb - 1 of in ([T][h][w]) -> u1 ([h][n1][n2])
+// transpose: plane jobs j0 .. j0 + nb - 1 of in ([T][h][w]) -> u1 ([h][n1][n2]);
+// a paired job spreads both planes (the mirror plane mirrored and conjugated)
+// into one grid and writes u1[jobs[j].x] = u1'(kv) + conj u1'(-kv)
 template <typename T>
 cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int kv0, int nb,
                                const Usfft2dArgs<T>& a, cudaStream_t s);
+
+// max(|re|, |im|) over n complex values into the device scalar *out
+template <typename T> cudaError_t launch_absmax(const C<T>* in, long long n, T* out, cudaStream_t s);
 
 // ---- F_2D / F*_2D (centred, per angle) ----------------------------------------
 template <typename T> struct Fft2dArgs {

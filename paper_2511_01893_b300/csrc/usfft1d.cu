@@ -31,7 +31,7 @@ namespace lam {
 
 template <typename T> __device__ __forceinline__ C<T> pz_at(const C<T>* E, const C<T>* O, int j, int M0) {
     const int jj = wrap(j, M0);
-    return (jj & 1) ? O[jj >> 1] : E[jj >> 1];
+    return (jj & 1) ? O[fpad(jj >> 1)] : E[fpad(jj >> 1)];
 }
 
 template <typename T>
@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_fwd(const T* __restrict
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);  // lines 2p (E) and 2p+1 (O), length nz
     const int nz = a.nz, npair = a.TY / 2;
+    const int LS = fpad_len(nz);
     const int tiles = a.n2 / a.TY;
     const int x = blockIdx.x / tiles;
     const int y0 = (blockIdx.x - x * tiles) * a.TY;
@@ -53,18 +54,18 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_fwd(const T* __restrict
         const T va = src[(size_t)z * a.n2 + 2 * p] * d, vb = src[(size_t)z * a.n2 + 2 * p + 1] * d;
         const C<T> w = a.tw[wrap(xc, a.M0) * twM0];  // e^{-2 pi i xc / M0}
         const int q = wrap(xc, nz);
-        buf[(2 * p) * nz + q] = cmake<T>(va, vb);
-        buf[(2 * p + 1) * nz + q] = cmake<T>(va * w.x - vb * w.y, va * w.y + vb * w.x);
+        buf[(2 * p) * LS + fpad(q)] = cmake<T>(va, vb);
+        buf[(2 * p + 1) * LS + fpad(q)] = cmake<T>(va * w.x - vb * w.y, va * w.y + vb * w.x);
     }
     __syncthreads();
-    fft_lines_ip<-1, FftMaxB<T>::value, T>(buf, a.TY, nz, nz, a.logM0 - 1, a.tw, 2 * twM0);
+    fft_lines_ip<-1, FftMaxB<T>::value, T>(buf, a.TY, LS, nz, a.logM0 - 1, a.tw, 2 * twM0);
     const int nt = 2 * a.m;
     C<T>* dst = u1 + (size_t)x * a.n2 + y0;
     const size_t plane = (size_t)a.n1 * a.n2;
     for (int i = tid; i < a.h * npair; i += nthr) {
         const int kv = i / npair, p = i - kv * npair;
-        const C<T>* E = buf + (2 * p) * nz;
-        const C<T>* O = E + nz;
+        const C<T>* E = buf + (2 * p) * LS;
+        const C<T>* O = E + LS;
         const int jb = a.j0z[kv] - a.m + 1;
         const T* wz = a.wz + kv * nt;
         T sar = 0, sai = 0, sbr = 0, sbi = 0;
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_fwd(const T* __restrict
             sbr += wt * (pp.x - pm.x);
             sbi += wt * (pp.y + pm.y);
         }
+        if (a.skip && a.skip[kv]) continue;
         // a = (sa) / 2, b = (sb) / (2i) = (sb.im, -sb.re) / 2
         C<T>* o = dst + kv * plane + 2 * p;
         o[0] = cmake<T>((T)0.5 * sar, (T)0.5 * sai);
@@ -112,8 +114,9 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restr
                                                              Usfft1dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nz = a.nz, npair = a.TY / 2, M0 = a.M0;
+    const int LS = fpad_len(nz);
     C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);  // TY lines of length nz (E, O per pair)
-    C<T>* vals = buf + a.TY * nz;                  // [TY][h]
+    C<T>* vals = buf + a.TY * LS;                  // [TY][h]
     const int tiles = a.n2 / a.TY;
     const int x = blockIdx.x / tiles;
     const int y0 = (blockIdx.x - x * tiles) * a.TY;
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restr
     const size_t plane = (size_t)a.n1 * a.n2;
     for (int i = tid; i < a.h * a.TY; i += nthr) {
         const int kv = i / a.TY, c = i - kv * a.TY;
-        vals[c * a.h + kv] = src[kv * plane + c];
+        vals[c * a.h + kv] = (a.skip && a.skip[kv]) ? cmake<T>(0, 0) : src[kv * plane + c];
     }
     __syncthreads();
     const int nt = 2 * a.m;
@@ -138,19 +141,19 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restr
         const C<T> qj = cmake<T>((T)0.5 * ((ap.x + am.x) - (bp.y - bm.y)), (T)0.5 * ((ap.y - am.y) + (bp.x + bm.x)));
         // Q_c[-j] = (am + conj ap)/2 + i (bm + conj bp)/2
         const C<T> qm = cmake<T>((T)0.5 * ((am.x + ap.x) - (bm.y - bp.y)), (T)0.5 * ((am.y - ap.y) + (bm.x + bp.x)));
-        C<T>* E = buf + (2 * p) * nz;
-        C<T>* O = E + nz;
-        ((j & 1) ? O : E)[j >> 1] = qj;
-        if (jm != j) ((jm & 1) ? O : E)[jm >> 1] = qm;
+        C<T>* E = buf + (2 * p) * LS;
+        C<T>* O = E + LS;
+        ((j & 1) ? O : E)[fpad(j >> 1)] = qj;
+        if (jm != j) ((jm & 1) ? O : E)[fpad(jm >> 1)] = qm;
     }
     __syncthreads();
-    fft_lines_ip<+1, FftMaxB<T>::value, T>(buf, a.TY, nz, nz, a.logM0 - 1, a.tw, 2 * a.twstride);
+    fft_lines_ip<+1, FftMaxB<T>::value, T>(buf, a.TY, LS, nz, a.logM0 - 1, a.tw, 2 * a.twstride);
     T* dst = u + (size_t)x * nz * a.n2 + y0;
     for (int i = tid; i < nz * npair; i += nthr) {
         const int z = i / npair, p = i - z * npair;
         const int xc = z - nz / 2;
         const int q = wrap(xc, nz);
-        const C<T> e = buf[(2 * p) * nz + q], o = buf[(2 * p + 1) * nz + q];
+        const C<T> e = buf[(2 * p) * LS + fpad(q)], o = buf[(2 * p + 1) * LS + fpad(q)];
         C<T> w = a.tw[wrap(xc, M0) * a.twstride];  // e^{-2 pi i xc / M0}; use its conjugate
         const T fr = e.x + (o.x * w.x + o.y * w.y);
         const T fi = e.y + (o.y * w.x - o.x * w.y);
@@ -162,14 +165,14 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restr
 
 template <typename T>
 cudaError_t launch_usfft1d_fwd(const T* u, C<T>* u1, const Usfft1dArgs<T>& a, cudaStream_t s) {
-    const size_t smem = (size_t)a.TY * a.nz * sizeof(C<T>);
+    const size_t smem = (size_t)a.TY * fpad_len(a.nz) * sizeof(C<T>);
     k_usfft1d_fwd<T><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u, u1, a);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_usfft1d_adj(const C<T>* u1, T* u, const Usfft1dArgs<T>& a, cudaStream_t s) {
-    const size_t smem = (size_t)(a.nz + a.h) * a.TY * sizeof(C<T>);
+    const size_t smem = (size_t)(fpad_len(a.nz) + a.h) * a.TY * sizeof(C<T>);
     k_usfft1d_adj<T><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u1, u, a);
     return cudaGetLastError();
 }

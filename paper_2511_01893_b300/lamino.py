@@ -116,7 +116,7 @@ class Geometry:
 class Plan:
     """A plan for one geometry and precision ('f32' or 'f64') on the current device."""
 
-    def __init__(self, n, nz, h, w, theta, phi, m=4, prec="f32", device=None, deterministic=False):
+    def __init__(self, n, nz, h, w, theta, phi, m=4, prec="f32", device=None, fast_adjoint=False):
         if not torch.cuda.is_available():
             raise LaminoError("no CUDA device: the laminography operators run only on the GPU")
         self.device = torch.device("cuda" if device is None else device)
@@ -133,7 +133,7 @@ class Plan:
                                          2, self.m, LAM_F32 if prec == "f32" else LAM_F64),
                    "lam_plan_create")
         self._h = h_
-        if deterministic:
+        if fast_adjoint:
             _check(lib().lam_plan_set_option(self._h, 1, 1), "lam_plan_set_option")
         nbytes = lib().lam_workspace_bytes(self._h)
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
@@ -252,10 +252,10 @@ class Plan:
         return out
 
     def info(self):
-        arr = (ctypes.c_int * 9)()
-        _check(lib().lamx_plan_info(self._h, arr, 9), "lamx_plan_info")
+        arr = (ctypes.c_int * 10)()
+        _check(lib().lamx_plan_info(self._h, arr, 10), "lamx_plan_info")
         keys = ["TY_fwd", "TY_adj", "rows_per_block", "cols_per_block", "tile", "images", "planes_per_batch",
-                "jmin", "jmax"]
+                "jmin", "jmax", "plane_jobs"]
         return dict(zip(keys, list(arr)))
 
 
