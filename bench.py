@@ -68,6 +68,23 @@ def lhat_bytes(n, nz, h, w, T):
 
 
 # ---------------------------------------------------------------------------
+# multi-rank timing (replicas: no data-path collective; only the clock is reduced)
+# ---------------------------------------------------------------------------
+
+def job_seconds_per_iter(t_local, steps, world, device=None):
+    """Whole-job seconds per ADMM iteration over `world` independent replicas:
+    the slowest rank's time divided by the iterations all ranks completed."""
+    import torch
+    import torch.distributed as dist
+    t = float(t_local)
+    if world > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t = tt.item()
+    return t / (steps * world), t
+
+
+# ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
 
@@ -349,12 +366,7 @@ def run_ours(args):
         stream.synchronize()
     torch.cuda.synchronize()
     barrier()
-    t_admm = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        tt = torch.tensor([t_admm], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_admm = tt.item()
-    s_per_iter = t_admm / (args.steps * world)
+    s_per_iter, t_admm = job_seconds_per_iter(ev0.elapsed_time(ev1) / 1e3, args.steps, world, dev)
     status = admm.status()
     sc = admm.scalars()
 
@@ -420,12 +432,8 @@ def run_ours(args):
         torch.cuda.empty_cache()
         t0 = time.perf_counter()
         u_host = glam.reconstruct(d_host.numpy(), theta, phi, n, nz, args.steps, ALPHA, RHO)
-        t_e2e = time.perf_counter() - t0
-        if world > 1:
-            tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_e2e = tt.item()
-        line["e2e"] = {"value": t_e2e / (args.steps * world), "unit": "s/iter",
+        e2e_value, _ = job_seconds_per_iter(time.perf_counter() - t0, args.steps, world, dev)
+        line["e2e"] = {"value": e2e_value, "unit": "s/iter",
                        "h2d_bytes_per_step": int(d_host.numel() * 4 // args.steps),
                        "d2h_bytes_per_step": int(u_host.size * 4 // args.steps),
                        "api": "reconstruct() one call, K iterations, host data/volume, includes plan + allocation"}

@@ -433,7 +433,7 @@ template <typename T> __device__ __forceinline__ void fixed_scale(T maxabs, floa
 }
 
 template <typename T, int TPB, int MH, int ACC>
-__global__ void __launch_bounds__(TPB * 32, sizeof(T) == 4 ? 6 : 2) k_scatter2d_atomic(
+__global__ void __launch_bounds__(TPB * 32, TPB >= 16 ? (sizeof(T) == 4 ? 2 : 1) : (sizeof(T) == 4 ? 6 : 2)) k_scatter2d_atomic(
     const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, Usfft2dArgs<T> a) {
     constexpr int nt = 2 * MH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -526,7 +526,8 @@ __global__ void __launch_bounds__(TPB * 32, sizeof(T) == 4 ? 6 : 2) k_scatter2d_
 // launchers
 // --------------------------------------------------------------------------
 
-constexpr int kScatterWarps = 4;  // tiles (warps) per block
+// warps per tile-block in the gather and the scatter (16 measured slower)
+constexpr int kScatterWarps = 4;
 
 template <typename T>
 cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* sub, int j0, int nb,

@@ -1,0 +1,42 @@
+"""The bench's N > 1 path runs independent replicas and reduces only the clock:
+the whole-job value is the slowest rank's time over the iterations all ranks
+completed.  Checked with two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    t_local = [3.0, 5.0][rank]
+    value, t_max = bench.job_seconds_per_iter(t_local, steps=4, world=world)
+    out[rank] = (value, t_max)
+    dist.destroy_process_group()
+
+
+def test_replica_timing_takes_slowest_rank():
+    world, port = 2, _free_port()
+    out = mp.Manager().dict()
+    mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
+    for rank in range(world):
+        value, t_max = out[rank]
+        assert t_max == pytest.approx(5.0)
+        assert value == pytest.approx(5.0 / (4 * 2))
+
+
+def test_single_rank_needs_no_process_group():
+    value, t = bench.job_seconds_per_iter(2.0, steps=4, world=1)
+    assert (value, t) == (0.5, 2.0)
