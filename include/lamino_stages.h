@@ -29,6 +29,22 @@ lam_status lamx_u2d_fwd(const lam_plan* plan, const void* u1, void* d_hat, const
 /* F*_u2D (transpose of lamx_u2d_fwd): d_hat -> u1.  Uses the plane part of ws. */
 lam_status lamx_u2d_adj(const lam_plan* plan, const void* d_hat, void* u1, void* ws, void* stream);
 
+/* lamx_u2d_fwd without a workspace; it allocates nothing.  (The paper has no
+ * counterpart: this serves callers that cannot provide device memory, such
+ * as code running inside a device allocator's hooks or a process whose
+ * memory is all owned by another pool.)  Same arguments and result as
+ * lamx_u2d_fwd minus ws.  The padded planes live in one static 8 MiB device
+ * array inside the library, so one padded (2n)^2 plane must fit: n <= 512 in
+ * FP32, n <= 256 in FP64; larger plans get LAM_EUNSUPPORTED with nothing
+ * launched.  Planes are processed in batches of as many as fit.  The first
+ * call on each device looks the array's address up once
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The current device must be the plan's (else LAM_EINVAL).  Nothing in the
+ * array needs to start at zero.  There is one array per device, so calls
+ * that overlap in time (several streams, threads or plans) race and give
+ * wrong results: order them on one stream or synchronise between them. */
+lam_status lamx_u2d_fwd_static(const lam_plan* plan, const void* u1, void* d_hat, const void* sub, void* stream);
+
 /* Launch shapes chosen by the plan, for diagnostics: out[0..count) receives
  * TY (z forward), TY (z transpose), rows per block, columns per block,
  * scatter tile side, tile images, planes per batch, jmin, jmax, and the

@@ -560,6 +560,67 @@ lam_status check_plan(const lam_plan* p) {
     return LAM_OK;
 }
 
+
+// ---- allocation-free F_u2D (no counterpart in the paper) ----------------------
+// Some callers cannot give the library a workspace: code that runs inside a
+// device allocator's own hooks (it must not call back into the allocator), or
+// a process whose device memory is owned by another pool once it has started.
+// For them lamx_u2d_fwd_static takes its batch of padded planes from the
+// fixed array below instead of ws, and allocates nothing.  The array holds
+// kStaticPlaneBytes: one padded plane (2n)^2 of complex values fits up to
+// n = 512 in FP32 and n = 256 in FP64; larger planes are rejected.  Every
+// byte the kernels read from it is written earlier in the same call, so
+// nothing needs to start at zero.  There is one array per device: calls that
+// overlap in time (other streams, other threads, other plans) race on it.
+}  // namespace
+
+constexpr size_t kStaticPlaneBytes = (size_t)8 << 20;
+static __device__ __align__(256) unsigned char g_static_planes[kStaticPlaneBytes];
+
+namespace {
+
+// device address of g_static_planes, looked up once per device (the first
+// call on a device does the lookup)
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kStaticMaxDevices] = {};
+
+lam_status static_planes(int dev, void** out) {
+    if (dev < 0 || dev >= kStaticMaxDevices) return fail(LAM_EUNSUPPORTED, "device %d: at most %d devices", dev,
+                                                         kStaticMaxDevices);
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_static_planes);
+        if (e != cudaSuccess || !ptr)
+            return fail(LAM_ECUDA, "cudaGetSymbolAddress of the static plane scratch failed: %s",
+                        cudaGetErrorString(e));
+        g_static_ptr[dev] = ptr;
+    }
+    *out = g_static_ptr[dev];
+    return LAM_OK;
+}
+
+template <typename T> lam_status u2d_fwd_static_t(const lam_plan* p, const void* u1, void* out, const void* sub,
+                                                  cudaStream_t s) {
+    const size_t plane = (size_t)p->M1 * p->M2 * sizeof(C<T>);
+    if (plane > kStaticPlaneBytes)
+        return fail(LAM_EUNSUPPORTED, "one padded %dx%d plane needs %zu bytes; the static scratch holds %zu", p->M1,
+                    p->M2, plane, kStaticPlaneBytes);
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != p->device) return fail(LAM_EINVAL, "current device %d is not the plan's device %d", dev, p->device);
+    void* scratch = nullptr;
+    if (lam_status st = static_planes(dev, &scratch)) return st;
+    C<T>* P = (C<T>*)scratch;
+    const int nb = (int)std::min<size_t>((size_t)p->h, kStaticPlaneBytes / plane);
+    const Usfft2dArgs<T> a = args2d<T>(p, false);
+    for (int j0 = 0; j0 < p->h; j0 += nb)
+        CK(launch_usfft2d_fwd<T>((const C<T>*)u1, P, (C<T>*)out, (const C<T>*)sub, j0, std::min(nb, p->h - j0), a,
+                                 s));
+    return LAM_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -985,6 +1046,13 @@ lam_status lamx_u2d_adj(const lam_plan* p, const void* d_hat, void* u1, void* ws
     if (lam_status st = check_plan(p)) return st;
     cudaStream_t s = (cudaStream_t)stream;
     return DISPATCH(p, u2d_adj_t<float>(p, d_hat, u1, ws, s), u2d_adj_t<double>(p, d_hat, u1, ws, s));
+}
+
+lam_status lamx_u2d_fwd_static(const lam_plan* p, const void* u1, void* d_hat, const void* sub, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!u1 || !d_hat) return fail(LAM_EINVAL, "NULL array argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    return DISPATCH(p, u2d_fwd_static_t<float>(p, u1, d_hat, sub, s), u2d_fwd_static_t<double>(p, u1, d_hat, sub, s));
 }
 
 lam_status lamx_admm_graph_kernels(const lam_plan* p, void* state, size_t* count) {

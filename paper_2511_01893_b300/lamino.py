@@ -60,6 +60,7 @@ def lib() -> ctypes.CDLL:
             "lamx_u1d_adj": [vp, vp, vp, vp],
             "lamx_u2d_fwd": [vp, vp, vp, vp, vp, vp],
             "lamx_u2d_adj": [vp, vp, vp, vp, vp],
+            "lamx_u2d_fwd_static": [vp, vp, vp, vp, vp],
             "lamx_plan_info": [vp, ctypes.POINTER(i), i],
             "lamx_admm_graph_kernels": [vp, vp, ctypes.POINTER(sz)],
         }
@@ -243,6 +244,21 @@ class Plan:
         out = self._data()
         _check(lib().lamx_u2d_fwd(self._h, _ptr(u1), _ptr(out), _ptr(sub), _ptr(self.ws), _stream()),
                "lamx_u2d_fwd")
+        return out
+
+    def u2d_fwd_static(self, u1, out, sub=None):
+        """F_u2D into the caller's `out` through the library's static plane
+        scratch (no workspace, no allocation inside the call).  The tensors
+        are passed as they are: wrong dtype, device, layout or shape raises."""
+        for t, dt, shape in ((u1, self.cdtype, (self.h, self.n, self.n)), (out, self.cdtype, self.data_shape),
+                             (sub, self.cdtype, self.data_shape)):
+            if t is None:
+                continue
+            dev_ok = t.device.type == self.device.type and self.device.index in (None, t.device.index)
+            if t.dtype != dt or not dev_ok or not t.is_contiguous() or tuple(t.shape) != shape:
+                raise LaminoError(f"expected a contiguous {dt} tensor of shape {shape} on {self.device}")
+        _check(lib().lamx_u2d_fwd_static(self._h, _ptr(u1), _ptr(out), _ptr(sub), _stream()),
+               "lamx_u2d_fwd_static")
         return out
 
     def u2d_adj(self, d_hat):
