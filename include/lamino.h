@@ -72,14 +72,19 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
 lam_status lam_plan_destroy(lam_plan* plan);
 
 /* Plan options (lam_plan_set_option).
- * LAM_OPT_FAST_ADJOINT (default 0).  The adjoint spreads slice values onto
- *   the padded planes tile by tile in shared memory.  0: each cell is an exact
- *   64-bit fixed-point sum of its FP32 (FP64) products, so results are the
- *   correctly rounded sums and bitwise reproducible run to run.  1: plain
- *   floating-point atomic adds, ~40 % faster at 1024^3, rounding depends on
- *   scheduling (not reproducible bit for bit).
+ * LAM_OPT_ADJOINT_SPREAD (default LAM_SPREAD_TILES) chooses how the adjoint
+ *   spreads slice values onto the padded planes, tile by tile in shared memory:
+ *   LAM_SPREAD_TILES   every warp sums into its own tile with plain loads and
+ *                      stores (no atomics), tiles added in a fixed order:
+ *                      bitwise reproducible run to run; the fastest.
+ *   LAM_SPREAD_ATOMIC  floating-point shared-memory atomic adds; rounding
+ *                      depends on scheduling (not reproducible bit for bit).
+ *   LAM_SPREAD_EXACT   exact 64-bit fixed-point atomic adds: every cell is the
+ *                      correctly rounded sum of its products; reproducible.
+ * LAM_OPT_FAST_ADJOINT: value != 0 selects LAM_SPREAD_ATOMIC, 0 the default.
  * Setting an option invalidates ADMM graphs captured with the plan. */
-enum { LAM_OPT_FAST_ADJOINT = 1 };
+enum { LAM_OPT_FAST_ADJOINT = 1, LAM_OPT_ADJOINT_SPREAD = 2 };
+enum { LAM_SPREAD_TILES = 0, LAM_SPREAD_ATOMIC = 1, LAM_SPREAD_EXACT = 2 };
 lam_status lam_plan_set_option(lam_plan* plan, int option, int value);
 
 /* Bytes of device scratch the operator calls need (ws argument).  The

@@ -91,7 +91,7 @@ struct lam_plan {
     int TYf, TYa, RB, CB, TS, nimg, nbatch;
     double rmax;
     int pstride;
-    int exact_accum = 1;
+    int spread = kSpreadTiles;
     // workspace layout
     size_t ws_u1, ws_planes, ws_tmp, ws_red, ws_bytes;
     mutable std::mutex mu;
@@ -326,7 +326,7 @@ template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p, bool paired) {
     a.nimg = p->nimg;
     a.rmax = (T)p->rmax;
     a.pstride = p->pstride;
-    a.exact_accum = p->exact_accum;
+    a.spread = p->spread;
     a.jobs = paired ? p->jobs_pair : p->jobs_all;
     a.maxabs = nullptr;
     // points whose 2m x 2m window covers one cell: at most (2m / spacing + 2)^2 per
@@ -373,7 +373,7 @@ lam_status fwd_hat(const lam_plan* p, const T* u, C<T>* out, const C<T>* sub, vo
 // workspace's scalar slot
 template <typename T> lam_status prep_scatter(const lam_plan* p, const C<T>* in, void* ws, cudaStream_t s,
                                               Usfft2dArgs<T>& a) {
-    if (!p->exact_accum) return LAM_OK;
+    if (p->spread != kSpreadExact) return LAM_OK;
     T* mx = (T*)((char*)ws + p->ws_red + align256(SC_COUNT * sizeof(double)) +
                  align256((size_t)kRedBlocks * 4 * sizeof(double)) + 256);
     CK(launch_absmax<T>(in, p->ndata(), mx, s));
@@ -720,7 +720,12 @@ lam_status lam_plan_set_option(lam_plan* p, int option, int value) {
     if (lam_status st = check_plan(p)) return st;
     switch (option) {
         case LAM_OPT_FAST_ADJOINT:
-            p->exact_accum = value == 0;
+        case LAM_OPT_ADJOINT_SPREAD:
+            if (option == LAM_OPT_FAST_ADJOINT) p->spread = value ? kSpreadAtomic : kSpreadTiles;
+            else if (value == LAM_SPREAD_TILES) p->spread = kSpreadTiles;
+            else if (value == LAM_SPREAD_ATOMIC) p->spread = kSpreadAtomic;
+            else if (value == LAM_SPREAD_EXACT) p->spread = kSpreadExact;
+            else return fail(LAM_EINVAL, "unknown adjoint spread %d", value);
             {
                 // captured ADMM graphs hold the old kernel choice
                 std::lock_guard<std::mutex> lk(p->mu);

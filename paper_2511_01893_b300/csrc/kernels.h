@@ -13,6 +13,13 @@ namespace lam {
 // attribute calls (and stay legal under stream capture).
 constexpr int kMaxDynSmem = 227 * 1024;
 
+// adjoint spread variants (F*_u2D): per-warp tiles without atomics
+// (deterministic, default), plain shared-memory atomic adds, or exact
+// fixed-point shared-memory atomics (deterministic and correctly rounded)
+constexpr int kSpreadTiles = 0;
+constexpr int kSpreadAtomic = 1;
+constexpr int kSpreadExact = 3;
+
 template <typename T> cudaError_t configure_usfft1d();
 template <typename T> cudaError_t configure_usfft2d();
 template <typename T> cudaError_t configure_fft2d();
@@ -61,7 +68,7 @@ template <typename T> struct Usfft2dArgs {
     int nimg;                       // tile images +-1..nimg checked per line (unwrapped positions)
     T rmax;                         // bound on |slice position| in grid units
     int pstride;                    // scatter: lanes take points this far apart along a line
-    int exact_accum;                // scatter cells: 1 exact fixed point (default), 0 plain atomic adds
+    int spread;                     // adjoint spread: kSpreadTiles, kSpreadAtomic or kSpreadExact
     const int2* jobs;               // plane jobs: .x plane computed, .y its conjugate mirror plane or -1
     const T* maxabs;                // device scalar: max |re|, |im| of the scatter input (fixed point)
     float bound_count;              // bound on the products summed into one padded cell

@@ -522,6 +522,144 @@ __global__ void __launch_bounds__(TPB * 32, TPB >= 16 ? (sizeof(T) == 4 ? 2 : 1)
     (void)lane;
 }
 
+// Spread without atomics (default): every warp accumulates into its own TS x TS
+// tile in shared memory; the block's warps split the crossing lines as in the
+// atomic kernel.  Each lane first finds its own point and writes a record of
+// it (window origin, the 2m weights along x, and the 2m weights along y times
+// the value); the warp then takes the recorded points one at a time, its 32
+// lanes covering the point's (2m) x (2m) window (RPP rows of 2m columns per
+// pass), each lane a read-add-write of one cell.  One point's cells are
+// distinct, so there is no race within the warp, and a __syncwarp orders
+// consecutive points.  At the end the warp tiles are summed in warp order: the
+// result does not depend on scheduling.
+// Cells are complex, row-major, with the column XOR-swizzled by the row's
+// parity: a 4-row x 8-column window block then covers 16 distinct pairs of
+// banks (FP32), two lanes per pair, the minimum for 256 bytes.
+__device__ __forceinline__ int swz_row(int x, int y) { return y ^ ((x & 1) << 3); }
+
+template <typename T> __host__ __device__ constexpr size_t spread_tiles_smem(int nw, int ts, int mh) {
+    return (size_t)nw * ts * ts * sizeof(C<T>) + (size_t)nw * 32 * (2 * mh) * (sizeof(C<T>) + sizeof(T)) +
+           (size_t)nw * 32 * sizeof(int2);
+}
+
+template <typename T, int NW, int MH>
+__global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_tiles(
+    const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, Usfft2dArgs<T> a) {
+    constexpr int nt = 2 * MH;
+    constexpr int RPP = 32 / nt;  // window rows per pass
+    constexpr int NPASS = (nt + RPP - 1) / RPP;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TS = a.TS;
+    const int ncell = TS * TS;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C<T>* tiles = reinterpret_cast<C<T>*>(smem_raw);  // [NW][ncell]
+    C<T>* mine = tiles + (size_t)warp * ncell;
+    unsigned char* recb = smem_raw + (size_t)NW * ncell * sizeof(C<T>);
+    C<T>* r_wyv = reinterpret_cast<C<T>*>(recb) + (size_t)warp * 32 * nt;  // [32][nt]
+    T* r_wx = reinterpret_cast<T*>(recb + (size_t)NW * 32 * nt * sizeof(C<T>)) + (size_t)warp * 32 * nt;
+    int2* r_o = reinterpret_cast<int2*>(recb + (size_t)NW * 32 * nt * (sizeof(C<T>) + sizeof(T))) + warp * 32;
+    for (int i = lane; i < ncell; i += 32) mine[i] = cmake<T>(0, 0);
+    __syncwarp();
+    const int tiles_y = a.M2 / TS;
+    const int tile = blockIdx.x;
+    const int tx0 = (tile / tiles_y) * TS, ty0 = (tile % tiles_y) * TS;
+    const int b = blockIdx.y;
+    const int2 job = a.jobs[j0 + b];
+    const T hb = (T)(TS + 2 * a.m) * (T)0.5;
+    const int rr = lane / nt, sy = lane - rr * nt;
+    // pass 0: the job's own plane; pass 1: its mirror plane (conjugate values
+    // spread around the negated positions, as in the atomic kernel)
+    for (int pass = 0; pass < 2; ++pass) {
+        const int kv = pass ? job.y : job.x;
+        if (kv < 0) break;
+        const int kvc = kv - a.h / 2;
+        const T sg = pass ? (T)-1 : (T)1;
+        for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
+            const int bx0 = tx0 + ix * a.M1;
+            for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
+                const int by0 = ty0 + iy * a.M2;
+                const T cx = (T)bx0 + (T)(TS - 1) * (T)0.5, cy = (T)by0 + (T)(TS - 1) * (T)0.5;
+                if (sqrt(cx * cx + cy * cy) > a.rmax + hb * (T)1.5) continue;
+                T bxl = (T)(bx0 - a.m), bxh = (T)(bx0 + TS + a.m - 1);
+                T byl = (T)(by0 - a.m), byh = (T)(by0 + TS + a.m - 1);
+                if (pass) {
+                    const T t0 = -bxh, t1 = -bxl + (T)1, t2 = -byh, t3 = -byl + (T)1;
+                    bxl = t0; bxh = t1; byl = t2; byh = t3;
+                }
+                for_tile_points<T>(a, kvc, sg * cx, sg * cy, hb, bxl, bxh, byl, byh, warp, NW, [&](int th, int kuc) {
+                    bool ok = th >= 0;
+                    if (ok) {
+                        const typename AngleT<T>::type g = a.ang[th];
+                        int jx, jy;
+                        T fx, fy;
+                        point_pos(g, kuc, kvc, jx, fx, jy, fy);
+                        C<T> v = in[((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2)];
+                        if (pass) {
+                            jx = -jx - 1;
+                            jy = -jy - 1;
+                            fx = (T)1 - fx;
+                            fy = (T)1 - fy;
+                            v.y = -v.y;
+                        }
+                        const int ox = jx - MH + 1 - bx0, oy = jy - MH + 1 - by0;
+                        ok = !(ox <= -nt || ox >= TS || oy <= -nt || oy >= TS);
+                        if (ok) {
+#pragma unroll
+                            for (int t = 0; t < nt; ++t) {
+                                const T dx = fx + (T)(MH - 1 - t);
+                                r_wx[lane * nt + t] = gexp(-dx * dx * a.inv4beta);
+                                const T dy = fy + (T)(MH - 1 - t);
+                                const T wy = gexp(-dy * dy * a.inv4beta);
+                                r_wyv[lane * nt + t] = cmake<T>(wy * v.x, wy * v.y);
+                            }
+                            r_o[lane] = make_int2(ox, oy);
+                        }
+                    }
+                    unsigned mask = __ballot_sync(0xffffffffu, ok);
+                    __syncwarp();
+                    while (mask) {
+                        const int src = __ffs(mask) - 1;
+                        mask &= mask - 1;
+                        const int2 o = r_o[src];
+                        const int ccy = o.y + sy;
+                        if (rr < RPP && (unsigned)ccy < (unsigned)TS) {
+                            const C<T> wv = r_wyv[src * nt + sy];
+#pragma unroll
+                            for (int q = 0; q < NPASS; ++q) {
+                                const int sx = q * RPP + rr;
+                                const int ccx = o.x + sx;
+                                if (sx < nt && (unsigned)ccx < (unsigned)TS) {
+                                    const T wx = r_wx[src * nt + sx];
+                                    C<T>* c = mine + ccx * TS + swz_row(ccx, ccy);
+                                    C<T> acc = *c;
+                                    acc.x = fma(wx, wv.x, acc.x);
+                                    acc.y = fma(wx, wv.y, acc.y);
+                                    *c = acc;
+                                }
+                            }
+                        }
+                        __syncwarp();
+                    }
+                });
+            }
+        }
+    }
+    __syncthreads();
+    C<T>* pl = P + (size_t)b * a.M1 * a.M2;
+    for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
+        const int ccx = i / TS, ccy = i - ccx * TS;
+        const int si = ccx * TS + swz_row(ccx, ccy);
+        C<T> sum = tiles[si];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) {
+            const C<T> t = tiles[(size_t)w * ncell + si];
+            sum.x += t.x;
+            sum.y += t.y;
+        }
+        pl[(size_t)(tx0 + ccx) * a.M2 + ty0 + ccy] = sum;
+    }
+}
+
 // --------------------------------------------------------------------------
 // launchers
 // --------------------------------------------------------------------------
@@ -571,7 +709,15 @@ cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int j0, int nb
         LAM_S(2, ACC) LAM_S(3, ACC) LAM_S(4, ACC) LAM_S(5, ACC) LAM_S(6, ACC) LAM_S(7, ACC) LAM_S(8, ACC) \
         default: return cudaErrorInvalidValue;                                                   \
     }
-    if (a.exact_accum) { LAM_SW(3) }
+    if (a.spread == kSpreadTiles) {
+        const size_t st = spread_tiles_smem<T>(NW, a.TS, a.m);
+        switch (a.m) {
+#define LAM_T(MH) case MH: k_spread2d_tiles<T, NW, MH><<<grid1, NW * 32, st, s>>>(in, P, kv0, a); break;
+            LAM_T(2) LAM_T(3) LAM_T(4) LAM_T(5) LAM_T(6) LAM_T(7) LAM_T(8)
+#undef LAM_T
+            default: return cudaErrorInvalidValue;
+        }
+    } else if (a.spread == kSpreadExact) { LAM_SW(3) }
     else { LAM_SW(0) }
 #undef LAM_SW
 #undef LAM_S
@@ -618,7 +764,8 @@ template <typename T> cudaError_t configure_usfft2d() {
 #define LAM_A(MH)                                                                          \
     if (!e) e = cudaFuncSetAttribute(k_gather2d_tiled<T, kScatterWarps, MH>, at, mx);       \
     if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 0>, at, mx);  \
-    if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 3>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 3>, at, mx);    \
+    if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles<T, kScatterWarps, MH>, at, mx);
     LAM_A(2) LAM_A(3) LAM_A(4) LAM_A(5) LAM_A(6) LAM_A(7) LAM_A(8)
 #undef LAM_A
     return e;

@@ -117,7 +117,12 @@ class Geometry:
 class Plan:
     """A plan for one geometry and precision ('f32' or 'f64') on the current device."""
 
-    def __init__(self, n, nz, h, w, theta, phi, m=4, prec="f32", device=None, fast_adjoint=False):
+    SPREADS = {"tiles": 0, "atomic": 1, "exact": 2}
+
+    def __init__(self, n, nz, h, w, theta, phi, m=4, prec="f32", device=None, fast_adjoint=False, spread=None):
+        """spread: the adjoint's spread variant, "tiles" (default, per-warp tiles,
+        reproducible), "atomic" (floating-point atomic adds) or "exact" (exact
+        fixed-point atomic adds); fast_adjoint=True is "atomic"."""
         if not torch.cuda.is_available():
             raise LaminoError("no CUDA device: the laminography operators run only on the GPU")
         self.device = torch.device("cuda" if device is None else device)
@@ -136,6 +141,10 @@ class Plan:
         self._h = h_
         if fast_adjoint:
             _check(lib().lam_plan_set_option(self._h, 1, 1), "lam_plan_set_option")
+        if spread is not None:
+            if spread not in self.SPREADS:
+                raise LaminoError(f"spread must be one of {sorted(self.SPREADS)}")
+            _check(lib().lam_plan_set_option(self._h, 2, self.SPREADS[spread]), "lam_plan_set_option")
         nbytes = lib().lam_workspace_bytes(self._h)
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
 

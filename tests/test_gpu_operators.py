@@ -41,14 +41,13 @@ def test_u1d_forward_and_adjoint(geom, prec):
     assert rel(got, ref) < tol(prec)
 
 
-@pytest.mark.parametrize("fast", [False, True], ids=["exact", "fast_adjoint"])
+@pytest.mark.parametrize("spread", ["tiles", "atomic", "exact"])
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("geom", GEOMS, ids=IDS)
-def test_u2d_forward_and_adjoint(geom, prec, fast):
+def test_u2d_forward_and_adjoint(geom, prec, spread):
     n, nz, h, w, T, phi = geom
     plan, g = plan_and_geom(n, nz, h, w, T, phi, prec)
-    if fast:
-        plan = glam.Plan(n, nz, h, w, g.theta, phi, prec=prec, fast_adjoint=True)
+    plan = glam.Plan(n, nz, h, w, g.theta, phi, prec=prec, spread=spread)
     rng = np.random.default_rng(4)
     u1 = rng.standard_normal((n, h, n)) + 1j * rng.standard_normal((n, h, n))
     ref = olam.f_u2d(u1, g)
@@ -124,13 +123,33 @@ def test_tiny_and_ragged_batches(monkeypatch):
     assert rel(plan.adjoint(torch.from_numpy(d)), olam.lam_adjoint(d, g)) < 1e-12
 
 
-def test_exact_adjoint_is_bitwise_reproducible():
-    # the default adjoint accumulates in exact fixed point: bitwise repeatable
+@pytest.mark.parametrize("m", [2, 3, 4, 8])
+def test_adjoint_spread_variants_other_widths(m):
+    # every spread variant at other kernel half-widths (window 2m x 2m)
+    n, nz, h, w, T = 32, 16, 32, 32, 12
+    plan, g = plan_and_geom(n, nz, h, w, T, 0.5, "f32", m=m)
+    d = rand_data(T, h, w, 18)
+    ref = olam.f_u2d_adj(d, g)
+    for spread in ("tiles", "atomic", "exact"):
+        p = glam.Plan(n, nz, h, w, plan.theta, 0.5, m=m, prec="f32", spread=spread)
+        got = p.u2d_adj(torch.from_numpy(d)).cpu().numpy().transpose(1, 0, 2)
+        assert rel(got, ref) < tol("f32"), spread
+
+
+def test_adjoint_spreads_are_bitwise_reproducible():
+    # the default (per-warp tiles summed in a fixed order) and the exact
+    # fixed-point spread give the same bits on every run
     n, nz, h, w, T = 64, 32, 64, 64, 48
     plan, g = plan_and_geom(n, nz, h, w, T, 0.5, "f32")
     d = torch.from_numpy(rand_data(T, h, w, 16)).cuda()
     a, b = plan.adjoint(d), plan.adjoint(d)
     assert torch.equal(a, b)
+    exact = glam.Plan(n, nz, h, w, plan.theta, 0.5, prec="f32", spread="exact")
+    e1, e2 = exact.adjoint(d), exact.adjoint(d)
+    assert torch.equal(e1, e2)
     fast = glam.Plan(n, nz, h, w, plan.theta, 0.5, prec="f32", fast_adjoint=True)
-    assert rel(fast.adjoint(d), a) < 2e-6
-    assert rel(a, olam.lam_adjoint(d.cpu().numpy(), g)) < 1e-5
+    assert rel(fast.adjoint(d), e1) < 2e-6
+    assert rel(a, e1) < 2e-6
+    ref = olam.lam_adjoint(d.cpu().numpy(), g)
+    assert rel(a, ref) < 1e-5
+    assert rel(e1, ref) < 1e-5
