@@ -373,7 +373,10 @@ lam_status fwd_hat(const lam_plan* p, const T* u, C<T>* out, const C<T>* sub, vo
 // workspace's scalar slot
 template <typename T> lam_status prep_scatter(const lam_plan* p, const C<T>* in, void* ws, cudaStream_t s,
                                               Usfft2dArgs<T>& a) {
-    if (p->spread != kSpreadExact) return LAM_OK;
+    // the exact spread runs when chosen, and for the tile spread's small-plane
+    // fallback (tiles narrower than 32)
+    const bool exact = p->spread == kSpreadExact || (p->spread == kSpreadTiles && p->TS != 32);
+    if (!exact) return LAM_OK;
     T* mx = (T*)((char*)ws + p->ws_red + align256(SC_COUNT * sizeof(double)) +
                  align256((size_t)kRedBlocks * 4 * sizeof(double)) + 256);
     CK(launch_absmax<T>(in, p->ndata(), mx, s));

@@ -522,24 +522,30 @@ __global__ void __launch_bounds__(TPB * 32, TPB >= 16 ? (sizeof(T) == 4 ? 2 : 1)
     (void)lane;
 }
 
-// Spread without atomics (default): every warp accumulates into its own TS x TS
-// tile in shared memory; the block's warps split the crossing lines as in the
-// atomic kernel.  Each lane first finds its own point and writes a record of
-// it (window origin, the 2m weights along x, and the 2m weights along y times
-// the value); the warp then takes the recorded points one at a time, its 32
-// lanes covering the point's (2m) x (2m) window (RPP rows of 2m columns per
-// pass), each lane a read-add-write of one cell.  One point's cells are
-// distinct, so there is no race within the warp, and a __syncwarp orders
-// consecutive points.  At the end the warp tiles are summed in warp order: the
-// result does not depend on scheduling.
-// Cells are complex, row-major, with the column XOR-swizzled by the row's
-// parity: a 4-row x 8-column window block then covers 16 distinct pairs of
-// banks (FP32), two lanes per pair, the minimum for 256 bytes.
+// Spread without atomics (default): every warp accumulates into its own
+// kSpreadTS x kSpreadTS tile in shared memory; the block's warps split the
+// crossing lines as in the atomic kernel.  Each lane first finds its own point
+// and writes a record of it (window origin, the 2m weights along x, and the 2m
+// weights along y times the value); the warp then takes the recorded points
+// one at a time, its 32 lanes covering the point's (2m) x (2m) window (RPP
+// rows of 2m columns per pass), each lane a read-add-write of one cell per
+// pass.  One point's cells are distinct, so there is no race within the warp,
+// and a __syncwarp orders consecutive points.  The next point's record is read
+// before the current point's cells are updated, to overlap the two.  At the
+// end the warp tiles are summed in warp order: the result does not depend on
+// scheduling.
+// Records are stored transposed with a row pitch of 33 (lane-major writes and
+// per-row reads both free of bank conflicts).  Tile cells are complex,
+// row-major, with the column XOR-swizzled by the row's parity: the 4-row x
+// 8-column block of one pass then covers 16 distinct pairs of banks (FP32),
+// two lanes per pair, the minimum for 256 bytes.
+constexpr int kSpreadTS = 32;
+constexpr int kRecPitch = 33;
 __device__ __forceinline__ int swz_row(int x, int y) { return y ^ ((x & 1) << 3); }
 
-template <typename T> __host__ __device__ constexpr size_t spread_tiles_smem(int nw, int ts, int mh) {
-    return (size_t)nw * ts * ts * sizeof(C<T>) + (size_t)nw * 32 * (2 * mh) * (sizeof(C<T>) + sizeof(T)) +
-           (size_t)nw * 32 * sizeof(int2);
+template <typename T> __host__ __device__ constexpr size_t spread_tiles_smem(int nw, int mh) {
+    return (size_t)nw * kSpreadTS * kSpreadTS * sizeof(C<T>) +
+           (size_t)nw * (2 * mh) * kRecPitch * (sizeof(C<T>) + sizeof(T)) + (size_t)nw * 32 * sizeof(int2);
 }
 
 template <typename T, int NW, int MH>
@@ -548,16 +554,16 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
     constexpr int nt = 2 * MH;
     constexpr int RPP = 32 / nt;  // window rows per pass
     constexpr int NPASS = (nt + RPP - 1) / RPP;
+    constexpr int TS = kSpreadTS;
+    constexpr int ncell = TS * TS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TS = a.TS;
-    const int ncell = TS * TS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     C<T>* tiles = reinterpret_cast<C<T>*>(smem_raw);  // [NW][ncell]
     C<T>* mine = tiles + (size_t)warp * ncell;
     unsigned char* recb = smem_raw + (size_t)NW * ncell * sizeof(C<T>);
-    C<T>* r_wyv = reinterpret_cast<C<T>*>(recb) + (size_t)warp * 32 * nt;  // [32][nt]
-    T* r_wx = reinterpret_cast<T*>(recb + (size_t)NW * 32 * nt * sizeof(C<T>)) + (size_t)warp * 32 * nt;
-    int2* r_o = reinterpret_cast<int2*>(recb + (size_t)NW * 32 * nt * (sizeof(C<T>) + sizeof(T))) + warp * 32;
+    C<T>* r_wyv = reinterpret_cast<C<T>*>(recb) + (size_t)warp * nt * kRecPitch;  // [nt][pitch]
+    T* r_wx = reinterpret_cast<T*>(recb + (size_t)NW * nt * kRecPitch * sizeof(C<T>)) + (size_t)warp * nt * kRecPitch;
+    int2* r_o = reinterpret_cast<int2*>(recb + (size_t)NW * nt * kRecPitch * (sizeof(C<T>) + sizeof(T))) + warp * 32;
     for (int i = lane; i < ncell; i += 32) mine[i] = cmake<T>(0, 0);
     __syncwarp();
     const int tiles_y = a.M2 / TS;
@@ -567,6 +573,7 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
     const int2 job = a.jobs[j0 + b];
     const T hb = (T)(TS + 2 * a.m) * (T)0.5;
     const int rr = lane / nt, sy = lane - rr * nt;
+    const bool lane_on = rr < RPP;
     // pass 0: the job's own plane; pass 1: its mirror plane (conjugate values
     // spread around the negated positions, as in the atomic kernel)
     for (int pass = 0; pass < 2; ++pass) {
@@ -607,38 +614,61 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
 #pragma unroll
                             for (int t = 0; t < nt; ++t) {
                                 const T dx = fx + (T)(MH - 1 - t);
-                                r_wx[lane * nt + t] = gexp(-dx * dx * a.inv4beta);
+                                r_wx[t * kRecPitch + lane] = gexp(-dx * dx * a.inv4beta);
                                 const T dy = fy + (T)(MH - 1 - t);
                                 const T wy = gexp(-dy * dy * a.inv4beta);
-                                r_wyv[lane * nt + t] = cmake<T>(wy * v.x, wy * v.y);
+                                r_wyv[t * kRecPitch + lane] = cmake<T>(wy * v.x, wy * v.y);
                             }
                             r_o[lane] = make_int2(ox, oy);
                         }
                     }
                     unsigned mask = __ballot_sync(0xffffffffu, ok);
                     __syncwarp();
-                    while (mask) {
-                        const int src = __ffs(mask) - 1;
-                        mask &= mask - 1;
-                        const int2 o = r_o[src];
-                        const int ccy = o.y + sy;
-                        if (rr < RPP && (unsigned)ccy < (unsigned)TS) {
-                            const C<T> wv = r_wyv[src * nt + sy];
+                    if (!mask) return;
+                    int src = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    int2 o = r_o[src];
+                    C<T> wv = r_wyv[sy * kRecPitch + src];
+                    T wx[NPASS];
 #pragma unroll
-                            for (int q = 0; q < NPASS; ++q) {
-                                const int sx = q * RPP + rr;
-                                const int ccx = o.x + sx;
-                                if (sx < nt && (unsigned)ccx < (unsigned)TS) {
-                                    const T wx = r_wx[src * nt + sx];
-                                    C<T>* c = mine + ccx * TS + swz_row(ccx, ccy);
-                                    C<T> acc = *c;
-                                    acc.x = fma(wx, wv.x, acc.x);
-                                    acc.y = fma(wx, wv.y, acc.y);
-                                    *c = acc;
-                                }
+                    for (int q = 0; q < NPASS; ++q) {
+                        const int sx = q * RPP + rr;
+                        wx[q] = sx < nt ? r_wx[sx * kRecPitch + src] : (T)0;
+                    }
+                    while (true) {
+                        // read the next record first (its latency overlaps the update)
+                        const bool more = mask != 0;
+                        const int nsrc = more ? __ffs(mask) - 1 : src;
+                        mask &= mask - 1;
+                        const int2 no = r_o[nsrc];
+                        const C<T> nwv = r_wyv[sy * kRecPitch + nsrc];
+                        T nwx[NPASS];
+#pragma unroll
+                        for (int q = 0; q < NPASS; ++q) {
+                            const int sx = q * RPP + rr;
+                            nwx[q] = sx < nt ? r_wx[sx * kRecPitch + nsrc] : (T)0;
+                        }
+                        const int ccy = o.y + sy;
+                        const bool yok = lane_on && (unsigned)ccy < (unsigned)TS;
+#pragma unroll
+                        for (int q = 0; q < NPASS; ++q) {
+                            const int sx = q * RPP + rr;
+                            const int ccx = o.x + sx;
+                            if (yok && sx < nt && (unsigned)ccx < (unsigned)TS) {
+                                C<T>* c = mine + ccx * TS + swz_row(ccx, ccy);
+                                C<T> acc = *c;
+                                acc.x = fma(wx[q], wv.x, acc.x);
+                                acc.y = fma(wx[q], wv.y, acc.y);
+                                *c = acc;
                             }
                         }
                         __syncwarp();
+                        if (!more) break;
+                        src = nsrc;
+                        o = no;
+                        wv = nwv;
+#pragma unroll
+                        for (int q = 0; q < NPASS; ++q) wx[q] = nwx[q];
                     }
                 });
             }
@@ -709,15 +739,17 @@ cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int j0, int nb
         LAM_S(2, ACC) LAM_S(3, ACC) LAM_S(4, ACC) LAM_S(5, ACC) LAM_S(6, ACC) LAM_S(7, ACC) LAM_S(8, ACC) \
         default: return cudaErrorInvalidValue;                                                   \
     }
-    if (a.spread == kSpreadTiles) {
-        const size_t st = spread_tiles_smem<T>(NW, a.TS, a.m);
+    // the tile spread is built for 32 x 32 tiles; planes smaller than that
+    // (n < 16) take the exact atomic spread
+    if (a.spread == kSpreadTiles && a.TS == kSpreadTS) {
+        const size_t st = spread_tiles_smem<T>(NW, a.m);
         switch (a.m) {
 #define LAM_T(MH) case MH: k_spread2d_tiles<T, NW, MH><<<grid1, NW * 32, st, s>>>(in, P, kv0, a); break;
             LAM_T(2) LAM_T(3) LAM_T(4) LAM_T(5) LAM_T(6) LAM_T(7) LAM_T(8)
 #undef LAM_T
             default: return cudaErrorInvalidValue;
         }
-    } else if (a.spread == kSpreadExact) { LAM_SW(3) }
+    } else if (a.spread != kSpreadAtomic) { LAM_SW(3) }
     else { LAM_SW(0) }
 #undef LAM_SW
 #undef LAM_S
