@@ -524,29 +524,53 @@ __global__ void __launch_bounds__(TPB * 32, TPB >= 16 ? (sizeof(T) == 4 ? 2 : 1)
 
 // Spread without atomics (default): every warp accumulates into its own
 // kSpreadTS x kSpreadTS tile in shared memory; the block's warps split the
-// crossing lines as in the atomic kernel.  Each lane first finds its own point
-// and writes a record of it (window origin, the 2m weights along x, and the 2m
-// weights along y times the value); the warp then takes the recorded points
-// one at a time, its 32 lanes covering the point's (2m) x (2m) window (RPP
-// rows of 2m columns per pass), each lane a read-add-write of one cell per
-// pass.  One point's cells are distinct, so there is no race within the warp,
-// and a __syncwarp orders consecutive points.  The next point's record is read
-// before the current point's cells are updated, to overlap the two.  At the
-// end the warp tiles are summed in warp order: the result does not depend on
-// scheduling.
+// crossing lines as in the atomic kernel.  Each lane first finds its own point;
+// the warp compacts the points whose window meets the tile into a list of
+// records (window origin, the 2m weights along x, the 2m weights along y
+// times the value), then takes them one at a time, its 32 lanes covering the
+// point's (2m) x (2m) window (RPP rows of 2m columns per pass), each lane a
+// read-add-write of one cell per pass.  One point's cells are distinct, so
+// there is no race within the warp, and a __syncwarp orders consecutive
+// points.  The next record is read before the current point's cells are
+// updated, to overlap the two.  At the end the warp tiles are summed in warp
+// order: the result does not depend on scheduling.
 // Records are stored transposed with a row pitch of 33 (lane-major writes and
-// per-row reads both free of bank conflicts).  Tile cells are complex,
-// row-major, with the column XOR-swizzled by the row's parity: the 4-row x
-// 8-column block of one pass then covers 16 distinct pairs of banks (FP32),
-// two lanes per pair, the minimum for 256 bytes.
+// per-row reads both free of bank conflicts); a lane's x weights for all its
+// passes are adjacent.  Tile cells are complex, row-major, with the column
+// XOR-swizzled by the row's parity: the 4-row x 8-column block of one pass
+// then covers 16 distinct pairs of banks (FP32), two lanes per pair, the
+// minimum for 256 bytes.
 constexpr int kSpreadTS = 32;
 constexpr int kRecPitch = 33;
 __device__ __forceinline__ int swz_row(int x, int y) { return y ^ ((x & 1) << 3); }
 
-template <typename T> __host__ __device__ constexpr size_t spread_tiles_smem(int nw, int mh) {
-    return (size_t)nw * kSpreadTS * kSpreadTS * sizeof(C<T>) +
-           (size_t)nw * (2 * mh) * kRecPitch * (sizeof(C<T>) + sizeof(T)) + (size_t)nw * 32 * sizeof(int2);
+// x-weight slots per record: RPP rows x NPASS passes (>= 2m)
+__host__ __device__ constexpr int spread_wx_slots(int mh) {
+    return (32 / (2 * mh)) * ((2 * mh + 32 / (2 * mh) - 1) / (32 / (2 * mh)));
 }
+template <typename T> __host__ __device__ constexpr size_t spread_tiles_smem(int nw, int mh) {
+    return (size_t)nw * kSpreadTS * kSpreadTS * sizeof(C<T>) + (size_t)nw * (2 * mh) * kRecPitch * sizeof(C<T>) +
+           (size_t)nw * spread_wx_slots(mh) * kRecPitch * sizeof(T) + (size_t)nw * 32 * sizeof(int2);
+}
+
+__device__ __forceinline__ void lds_c(unsigned ad, C<float>& v) {
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(ad) : "memory");
+}
+__device__ __forceinline__ void lds_c(unsigned ad, C<double>& v) {
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(ad) : "memory");
+}
+__device__ __forceinline__ void sts_c(unsigned ad, const C<float>& v) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(ad), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void sts_c(unsigned ad, const C<double>& v) {
+    asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(ad), "d"(v.x), "d"(v.y) : "memory");
+}
+
+// N values loaded together: vector-aligned when N is a power of two
+template <typename T, int N>
+struct alignas((N & (N - 1)) == 0 ? (N * sizeof(T) < 16 ? N * sizeof(T) : 16) : sizeof(T)) Vec {
+    T v[N];
+};
 
 template <typename T, int NW, int MH>
 __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_tiles(
@@ -556,14 +580,20 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
     constexpr int NPASS = (nt + RPP - 1) / RPP;
     constexpr int TS = kSpreadTS;
     constexpr int ncell = TS * TS;
+    constexpr unsigned kCell = sizeof(C<T>);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     C<T>* tiles = reinterpret_cast<C<T>*>(smem_raw);  // [NW][ncell]
     C<T>* mine = tiles + (size_t)warp * ncell;
     unsigned char* recb = smem_raw + (size_t)NW * ncell * sizeof(C<T>);
-    C<T>* r_wyv = reinterpret_cast<C<T>*>(recb) + (size_t)warp * nt * kRecPitch;  // [nt][pitch]
-    T* r_wx = reinterpret_cast<T*>(recb + (size_t)NW * nt * kRecPitch * sizeof(C<T>)) + (size_t)warp * nt * kRecPitch;
-    int2* r_o = reinterpret_cast<int2*>(recb + (size_t)NW * nt * kRecPitch * (sizeof(C<T>) + sizeof(T))) + warp * 32;
+    // records: wyv[sy][pitch] (complex), wx[rr][pitch][NPASS], origin[32]
+    C<T>* r_wyv = reinterpret_cast<C<T>*>(recb) + (size_t)warp * nt * kRecPitch;
+    T* r_wx = reinterpret_cast<T*>(recb + (size_t)NW * nt * kRecPitch * sizeof(C<T>)) +
+              (size_t)warp * RPP * kRecPitch * NPASS;
+    static_assert(RPP * NPASS == spread_wx_slots(MH), "record layout");
+    int2* r_o = reinterpret_cast<int2*>(recb + (size_t)NW * nt * kRecPitch * sizeof(C<T>) +
+                                        (size_t)NW * RPP * NPASS * kRecPitch * sizeof(T)) +
+                warp * 32;
     for (int i = lane; i < ncell; i += 32) mine[i] = cmake<T>(0, 0);
     __syncwarp();
     const int tiles_y = a.M2 / TS;
@@ -574,6 +604,12 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
     const T hb = (T)(TS + 2 * a.m) * (T)0.5;
     const int rr = lane / nt, sy = lane - rr * nt;
     const bool lane_on = rr < RPP;
+    const int rrc = lane_on ? rr : 0;
+    // lane-constant shared addresses of the record entries this lane reads
+    const unsigned tile_ad = (unsigned)__cvta_generic_to_shared(mine);
+    const unsigned wyv_ad = (unsigned)__cvta_generic_to_shared(r_wyv + sy * kRecPitch);
+    const T* wx_lane = r_wx + (size_t)rrc * kRecPitch * NPASS;
+    const unsigned lt = (1u << lane) - 1u;
     // pass 0: the job's own plane; pass 1: its mirror plane (conjugate values
     // spread around the negated positions, as in the atomic kernel)
     for (int pass = 0; pass < 2; ++pass) {
@@ -595,12 +631,14 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
                 }
                 for_tile_points<T>(a, kvc, sg * cx, sg * cy, hb, bxl, bxh, byl, byh, warp, NW, [&](int th, int kuc) {
                     bool ok = th >= 0;
+                    int ox = 0, oy = 0;
+                    T fx = 0, fy = 0;
+                    C<T> v = cmake<T>(0, 0);
                     if (ok) {
                         const typename AngleT<T>::type g = a.ang[th];
                         int jx, jy;
-                        T fx, fy;
                         point_pos(g, kuc, kvc, jx, fx, jy, fy);
-                        C<T> v = in[((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2)];
+                        v = in[((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2)];
                         if (pass) {
                             jx = -jx - 1;
                             jy = -jy - 1;
@@ -608,67 +646,60 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
                             fy = (T)1 - fy;
                             v.y = -v.y;
                         }
-                        const int ox = jx - MH + 1 - bx0, oy = jy - MH + 1 - by0;
+                        ox = jx - MH + 1 - bx0;
+                        oy = jy - MH + 1 - by0;
                         ok = !(ox <= -nt || ox >= TS || oy <= -nt || oy >= TS);
-                        if (ok) {
-#pragma unroll
-                            for (int t = 0; t < nt; ++t) {
-                                const T dx = fx + (T)(MH - 1 - t);
-                                r_wx[t * kRecPitch + lane] = gexp(-dx * dx * a.inv4beta);
-                                const T dy = fy + (T)(MH - 1 - t);
-                                const T wy = gexp(-dy * dy * a.inv4beta);
-                                r_wyv[t * kRecPitch + lane] = cmake<T>(wy * v.x, wy * v.y);
-                            }
-                            r_o[lane] = make_int2(ox, oy);
-                        }
                     }
-                    unsigned mask = __ballot_sync(0xffffffffu, ok);
-                    __syncwarp();
+                    const unsigned mask = __ballot_sync(0xffffffffu, ok);
                     if (!mask) return;
-                    int src = __ffs(mask) - 1;
-                    mask &= mask - 1;
-                    int2 o = r_o[src];
-                    C<T> wv = r_wyv[sy * kRecPitch + src];
-                    T wx[NPASS];
+                    if (ok) {
+                        const int k = __popc(mask & lt);  // compacted record index
 #pragma unroll
-                    for (int q = 0; q < NPASS; ++q) {
-                        const int sx = q * RPP + rr;
-                        wx[q] = sx < nt ? r_wx[sx * kRecPitch + src] : (T)0;
-                    }
-                    while (true) {
-                        // read the next record first (its latency overlaps the update)
-                        const bool more = mask != 0;
-                        const int nsrc = more ? __ffs(mask) - 1 : src;
-                        mask &= mask - 1;
-                        const int2 no = r_o[nsrc];
-                        const C<T> nwv = r_wyv[sy * kRecPitch + nsrc];
-                        T nwx[NPASS];
-#pragma unroll
-                        for (int q = 0; q < NPASS; ++q) {
-                            const int sx = q * RPP + rr;
-                            nwx[q] = sx < nt ? r_wx[sx * kRecPitch + nsrc] : (T)0;
+                        for (int t = 0; t < nt; ++t) {
+                            const T dx = fx + (T)(MH - 1 - t);
+                            const int q = t / RPP, r = t - q * RPP;
+                            r_wx[((size_t)r * kRecPitch + k) * NPASS + q] = gexp(-dx * dx * a.inv4beta);
+                            const T dy = fy + (T)(MH - 1 - t);
+                            const T wy = gexp(-dy * dy * a.inv4beta);
+                            r_wyv[t * kRecPitch + k] = cmake<T>(wy * v.x, wy * v.y);
                         }
-                        const int ccy = o.y + sy;
+                        r_o[k] = make_int2(ox, oy);
+                    }
+                    __syncwarp();
+                    const int cnt = __popc(mask);
+                    int2 o = r_o[0];
+                    C<T> wv;
+                    lds_c(wyv_ad, wv);
+                    Vec<T, NPASS> wx = *reinterpret_cast<const Vec<T, NPASS>*>(wx_lane);
+                    for (int k = 0; k < cnt; ++k) {
+                        // read the next record first (its latency overlaps the update)
+                        const int kn = k + 1 < cnt ? k + 1 : k;
+                        const int2 no = r_o[kn];
+                        C<T> nwv;
+                        lds_c(wyv_ad + kn * kCell, nwv);
+                        const Vec<T, NPASS> nwx = *reinterpret_cast<const Vec<T, NPASS>*>(wx_lane + kn * NPASS);
+                        const int cx0 = o.x + rrc, ccy = o.y + sy;
+                        const int col = ccy ^ ((cx0 & 1) << 3);
+                        const unsigned ad0 = tile_ad + (unsigned)(cx0 * TS + col) * kCell;
                         const bool yok = lane_on && (unsigned)ccy < (unsigned)TS;
 #pragma unroll
                         for (int q = 0; q < NPASS; ++q) {
-                            const int sx = q * RPP + rr;
-                            const int ccx = o.x + sx;
-                            if (yok && sx < nt && (unsigned)ccx < (unsigned)TS) {
-                                C<T>* c = mine + ccx * TS + swz_row(ccx, ccy);
-                                C<T> acc = *c;
-                                acc.x = fma(wx[q], wv.x, acc.x);
-                                acc.y = fma(wx[q], wv.y, acc.y);
-                                *c = acc;
+                            const int row = cx0 + q * RPP;
+                            // rows q * RPP apart: same swizzle when RPP is even
+                            const unsigned ad = ((q * RPP) & 1) ? tile_ad + (unsigned)(row * TS + (col ^ 8)) * kCell
+                                                                : ad0 + (unsigned)(q * RPP * TS) * kCell;
+                            if (yok && q * RPP + rr < nt && (unsigned)row < (unsigned)TS) {
+                                C<T> acc;
+                                lds_c(ad, acc);
+                                acc.x = fma(wx.v[q], wv.x, acc.x);
+                                acc.y = fma(wx.v[q], wv.y, acc.y);
+                                sts_c(ad, acc);
                             }
                         }
                         __syncwarp();
-                        if (!more) break;
-                        src = nsrc;
                         o = no;
                         wv = nwv;
-#pragma unroll
-                        for (int q = 0; q < NPASS; ++q) wx[q] = nwx[q];
+                        wx = nwx;
                     }
                 });
             }
