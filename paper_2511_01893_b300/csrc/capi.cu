@@ -88,7 +88,7 @@ struct lam_plan {
     int* skip;  // [h] 1 for the mirror plane of a paired job
     int njobs_pair;
     // launch shapes
-    int TYf, TYa, RB, CB, TS, nimg, nbatch;
+    int TYf, TYa, RB, CB, TS, TG, nimg, nbatch;
     double rmax;
     int pstride;
     int spread = kSpreadTiles;
@@ -323,6 +323,7 @@ template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p, bool paired) {
     a.RB = p->RB;
     a.CB = p->CB;
     a.TS = p->TS;
+    a.TG = p->TG;
     a.nimg = p->nimg;
     a.rmax = (T)p->rmax;
     a.pstride = p->pstride;
@@ -690,6 +691,12 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     p->RB = pick_lines(p->M2, ce_, 128 * 1024, p->n1, 16, maxb);
     p->CB = pick_lines(p->M1, ce_, 128 * 1024, p->M2, 16, maxb);
     p->TS = std::min(32, std::min(p->M1, p->M2));  // the scatter's bank swizzle assumes 32 when M >= 32
+    // gather tiles: larger tiles amortise the per-block line tests over more points
+    p->TG = std::min(64, std::min(p->M1, p->M2));
+    if (const char* env = std::getenv("LAMINO_GATHER_TILE")) {
+        const int v = std::atoi(env);
+        if (v >= 16 && v <= std::min(p->M1, p->M2) && (v & (v - 1)) == 0) p->TG = v;
+    }
     // unwrapped slice positions reach |p| <= M (1 + sin phi) / 2 + m + 2
     const double reach = std::max(p->M1, p->M2) * (1.0 + std::sin(phi)) / 2.0 + p->m + 2;
     p->nimg = (int)std::ceil(reach / std::min(p->M1, p->M2));

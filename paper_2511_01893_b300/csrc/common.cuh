@@ -59,8 +59,9 @@ __device__ __forceinline__ double gexp(double x) { return exp(x); }
 // M1 sin phi sin th / h; a = y: M2 sin th / w, -M2 sin phi cos th / h).
 // FP32 kernels carry each constant as an unevaluated sum hi + lo so that the
 // position keeps ~1e-7 absolute accuracy at |position| ~ 2000.
-struct AngleF {
-    float ax_hi, ax_lo, sx_hi, sx_lo, ay_hi, ay_lo, sy_hi, sy_lo;
+// high parts first: the line tests read only them (one 16-byte load)
+struct __align__(16) AngleF {
+    float ax_hi, sx_hi, ay_hi, sy_hi, ax_lo, sx_lo, ay_lo, sy_lo;
 };
 struct AngleD {
     double ax, sx, ay, sy;

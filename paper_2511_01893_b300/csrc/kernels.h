@@ -65,6 +65,7 @@ template <typename T> struct Usfft2dArgs {
     int RB;                         // rows per block (row passes)
     int CB;                         // columns per block (column passes)
     int TS;                         // scatter tile side
+    int TG;                         // gather tile side
     int nimg;                       // tile images +-1..nimg checked per line (unwrapped positions)
     T rmax;                         // bound on |slice position| in grid units
     int pstride;                    // scatter: lanes take points this far apart along a line

@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(TPB * 32) k_gather2d_tiled(const C<T>* __restr
                                                              const C<T>* __restrict__ sub, int j0, Usfft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int nt = 2 * MH;
-    const int TS = a.TS;
+    const int TS = a.TG;
     const int SH = TS + nt - 1;  // staged rows
     const int SW = TS + nt + 1;  // staged row stride (odd: lanes two rows apart hit different banks)
     const int warp = threadIdx.x >> 5;
@@ -737,8 +737,8 @@ cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* s
     k_rowfft_fwd<T><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, kv0, a);
     k_colfft_fwd<T><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
     constexpr int NW = kScatterWarps;
-    const int ntiles = (a.M1 / a.TS) * (a.M2 / a.TS);
-    const size_t sg = (size_t)(a.TS + 2 * a.m - 1) * (a.TS + 2 * a.m + 1) * sizeof(C<T>);
+    const int ntiles = (a.M1 / a.TG) * (a.M2 / a.TG);
+    const size_t sg = (size_t)(a.TG + 2 * a.m - 1) * (a.TG + 2 * a.m + 1) * sizeof(C<T>);
     const dim3 grid(ntiles, nb, 2);
     switch (a.m) {
 #define LAM_G(MH) case MH: k_gather2d_tiled<T, NW, MH><<<grid, NW * 32, sg, s>>>(P, out, sub, kv0, a); break;
