@@ -45,17 +45,32 @@ struct AdmmRed {
     unsigned int* counter;  // zero between reductions
 };
 
-// volume [n1][nz][n2], N = n1 * nz * n2; nz and n2 are powers of two
-// (ln2 = log2 n2, lnz = log2 nz), so coordinates come from shifts and masks
+// volume [n1][nz][n2], N = n1 * nz * n2.  When nz and n2 are powers of two
+// (ln2 = log2 n2, lnz = log2 nz) coordinates come from shifts and masks; else
+// ln2 = lnz = -1 and they come from divisions (32-bit when N < 2^31).
 struct Vol {
     int n1, nz, n2;
     int ln2, lnz;
     long long N;
     __device__ __forceinline__ void coords(long long i, int& x, int& z, int& y) const {
-        y = (int)(i & (n2 - 1));
-        const long long t = i >> ln2;
-        z = (int)(t & (nz - 1));
-        x = (int)(t >> lnz);
+        if (ln2 >= 0) {
+            y = (int)(i & (n2 - 1));
+            const long long t = i >> ln2;
+            z = (int)(t & (nz - 1));
+            x = (int)(t >> lnz);
+        } else if (N < (1LL << 31)) {
+            const unsigned ii = (unsigned)i, t = ii / (unsigned)n2;
+            y = (int)(ii - t * (unsigned)n2);
+            const unsigned xx = t / (unsigned)nz;
+            z = (int)(t - xx * (unsigned)nz);
+            x = (int)xx;
+        } else {
+            const long long t = i / n2;
+            y = (int)(i - t * n2);
+            const long long xx = t / nz;
+            z = (int)(t - xx * nz);
+            x = (int)xx;
+        }
     }
 };
 

@@ -22,6 +22,7 @@
 #include "../../include/lamino.h"
 #include "../../include/lamino_stages.h"
 #include "admm.h"
+#include "fft.cuh"
 #include "kernels.h"
 
 using namespace lam;
@@ -269,11 +270,14 @@ template <typename T> lam_status build_tables(lam_plan* p, const double* theta) 
 // lines per block for the in-place FFT kernels: shared memory (extra + lines *
 // len elements) within `budget`, lines * len within the register budget
 // 8 * MAXB * threads, `divides` a multiple of lines, at most `cap`
+// lines per block for an in-place FFT of length len: within the shared-memory
+// budget, within the FFT's register capacity (lines * len <= capacity * 512
+// threads), and dividing `divides` (the grid covers it exactly)
 static int pick_lines(int len, size_t celem, size_t budget, int divides, int cap, int maxb, size_t extra_per_line = 0) {
+    const long long capacity = (long long)fft_capacity(fft_code(len), maxb) * kFftThreads;
     int l = cap;
     while (l > 1 && ((size_t)l * ((len + len / 16 + 1) * celem + extra_per_line) > budget ||
-                     (long long)l * len > 8LL * maxb * 512 ||
-                     divides % l != 0))
+                     (long long)l * len > capacity || divides % l != 0))
         l >>= 1;
     return l;
 }
@@ -285,7 +289,7 @@ template <typename T> Usfft1dArgs<T> args1d(const lam_plan* p, int TY, bool pair
     a.n2 = p->n2;
     a.h = p->h;
     a.M0 = p->M0;
-    a.logM0 = ilog2(p->M0);
+    a.fcz = fft_code(p->nz);
     a.m = p->m;
     a.TY = TY;
     a.dz = (const T*)p->dz;
@@ -310,8 +314,8 @@ template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p, bool paired) {
     a.T_ = p->T;
     a.M1 = p->M1;
     a.M2 = p->M2;
-    a.logM1 = ilog2(p->M1);
-    a.logM2 = ilog2(p->M2);
+    a.fcM1 = fft_code(p->M1);
+    a.fcM2 = fft_code(p->M2);
     a.m = p->m;
     a.inv4beta = (T)(1.0 / (4.0 * p->beta));
     a.d1 = (const T*)p->d1;
@@ -346,8 +350,8 @@ template <typename T> Fft2dArgs<T> argsfft(const lam_plan* p) {
     a.T_ = p->T;
     a.h = p->h;
     a.w = p->w;
-    a.logh = ilog2(p->h);
-    a.logw = ilog2(p->w);
+    a.fch = fft_code(p->h);
+    a.fcw = fft_code(p->w);
     a.tw = (const C<T>*)p->tw;
     a.twh = p->Nmax / p->h;
     a.tww = p->Nmax / p->w;
@@ -486,8 +490,9 @@ template <typename T> Admm<T> admm_ops(const lam_plan* p) {
     a.v.n1 = p->n1;
     a.v.nz = p->nz;
     a.v.n2 = p->n2;
-    a.v.ln2 = ilog2(p->n2);
-    a.v.lnz = ilog2(p->nz);
+    const bool shifts = pow2(p->n2) && pow2(p->nz);
+    a.v.ln2 = shifts ? ilog2(p->n2) : -1;
+    a.v.lnz = shifts ? ilog2(p->nz) : -1;
     a.v.N = p->nvox();
     return a;
 }
@@ -642,8 +647,9 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     const int dims[4] = {n, nz, det_h, det_w};
     const char* names[4] = {"n", "nz", "det_h", "det_w"};
     for (int i = 0; i < 4; ++i)
-        if (!pow2(dims[i]) || dims[i] < 8 || dims[i] > 2048)
-            return fail(LAM_EUNSUPPORTED, "%s = %d: must be a power of two in [8, 2048]", names[i], dims[i]);
+        if (dims[i] < 8 || dims[i] > 2048 || dims[i] % 2 != 0 || fft_code(dims[i]) < 0)
+            return fail(LAM_EUNSUPPORTED, "%s = %d: must be even, 2^a 3^b 5^c, in [8, 2048]", names[i], dims[i]);
+    if (n % 8 != 0) return fail(LAM_EUNSUPPORTED, "n = %d: must be a multiple of 8 (plane tiles)", n);
     if (n_theta < 1 || n_theta > 65536) return fail(LAM_EINVAL, "n_theta = %d out of range", n_theta);
     if (!theta) return fail(LAM_EINVAL, "theta is NULL");
     for (int k = 0; k < n_theta; ++k)
@@ -666,7 +672,21 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     p->M0 = 2 * nz;
     p->M1 = 2 * n;
     p->M2 = 2 * n;
-    p->Nmax = std::max(std::max(p->M0, p->M1), std::max(p->h, p->w));
+    // twiddle table length: a common multiple of every FFT length the plan runs
+    {
+        long long L = 1;
+        for (int v : {p->nz, p->M0, p->M1, p->M2, p->h, p->w}) {
+            long long a = L, b = v;
+            while (b) { const long long t = a % b; a = b; b = t; }
+            L = L / a * v;
+        }
+        if (L > (1LL << 22)) {
+            delete p;
+            return fail(LAM_EUNSUPPORTED, "sizes n = %d, nz = %d, det %d x %d need a twiddle table of %lld entries",
+                        n, nz, det_h, det_w, L);
+        }
+        p->Nmax = (int)L;
+    }
     p->beta = half_width * 2.0 / (4.0 * M_PI * 1.5);
     if (cudaGetDevice(&p->device) != cudaSuccess) {
         delete p;
@@ -690,9 +710,11 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     p->TYa = std::max(2, pick_lines(p->nz, ce_, budget, p->n2, 16, maxb, (size_t)p->h * ce_));
     p->RB = pick_lines(p->M2, ce_, 128 * 1024, p->n1, 16, maxb);
     p->CB = pick_lines(p->M1, ce_, 128 * 1024, p->M2, 16, maxb);
-    p->TS = std::min(32, std::min(p->M1, p->M2));  // the scatter's bank swizzle assumes 32 when M >= 32
-    // gather tiles: larger tiles amortise the per-block line tests over more points
-    p->TG = std::min(64, std::min(p->M1, p->M2));
+    // plane tiles divide M1 = M2 = 2n (a multiple of 16): spread tiles 32 (the
+    // tile spread's size) when possible; gather tiles up to 64, since larger
+    // tiles amortise the per-block line tests over more points
+    p->TS = p->M1 % 32 == 0 ? 32 : 16;
+    p->TG = p->M1 % 64 == 0 ? 64 : p->TS;
     if (const char* env = std::getenv("LAMINO_GATHER_TILE")) {
         const int v = std::atoi(env);
         if (v >= 16 && v <= std::min(p->M1, p->M2) && (v & (v - 1)) == 0) p->TG = v;

@@ -110,9 +110,11 @@ __device__ __forceinline__ void grid_pos(int ku, int kv, double a, double s, int
     fr = p - fl;
 }
 
+// j mod M in [0, M) for any M >= 1 (a mask when M is a power of two)
 __host__ __device__ __forceinline__ int wrap(int j, int M) {
-    // M is a power of two
-    return j & (M - 1);
+    if ((M & (M - 1)) == 0) return j & (M - 1);
+    const int r = j % M;
+    return r < 0 ? r + M : r;
 }
 
 }  // namespace lam

@@ -1,16 +1,17 @@
-// fft.cuh - batched power-of-two FFTs in shared memory (Stockham autosort).
+// fft.cuh - batched mixed-radix FFTs in shared memory (Stockham autosort).
 //
-// Each call transforms `nlines` lines of length N stored at stride `lstride`
-// in shared memory.  Stages are radix 8 (then one radix 4 or 2 stage); every
-// thread of the block takes butterflies q = tid, tid + nthr, ... of a stage,
-// reads R inputs N/R apart, applies twiddles, does an in-register radix-R
-// DFT and writes the R outputs Ns apart (self-sorting, so the result is in
-// natural order).
+// Each call transforms `nlines` lines of length N = 2^a 3^b 5^c stored at
+// stride `lstride` in shared memory.  The power-of-two part runs as radix-8
+// stages (then one radix-4 or radix-2 stage), followed by radix-3 and radix-5
+// stages; every thread of the block takes butterflies q = tid, tid + nthr, ...
+// of a stage, reads R inputs N/R apart, applies twiddles, does an in-register
+// radix-R DFT and writes the R outputs Ns apart (self-sorting, so the result
+// is in natural order).  The stage sequence is a code from fft_code(N).
 //
 // Sign convention: DIR = -1 computes sum_x a[x] exp(-2 pi i j x / N),
 // DIR = +1 computes sum_x a[x] exp(+2 pi i j x / N) (no normalisation).
 // Twiddles come from a table tw[q] = exp(-2 pi i q / Nmax), q < Nmax, where
-// Nmax is a power-of-two multiple of N (twstride = Nmax / N).
+// Nmax is a multiple of N (twstride = Nmax / N).
 #pragma once
 
 #include "common.cuh"
@@ -54,6 +55,99 @@ template <int DIR, typename T> __device__ __forceinline__ void dft8(C<T>* v) {
     v[7] = csub(e[3], o3);
 }
 
+// radix-3 DFT: with c = -1/2 and s = DIR sqrt(3)/2 (the primitive cube root
+// of unity e^{DIR 2 pi i / 3} = c + i s)
+template <int DIR, typename T> __device__ __forceinline__ void dft3(C<T>* v) {
+    const T hs = (T)0.86602540378443864676;
+    const C<T> b = cadd(v[1], v[2]);
+    const C<T> d = csub(v[1], v[2]);
+    const C<T> t = cmake<T>(v[0].x - (T)0.5 * b.x, v[0].y - (T)0.5 * b.y);
+    const C<T> e = cmul_i<DIR>(cmake<T>(hs * d.x, hs * d.y));
+    v[0] = cadd(v[0], b);
+    v[1] = cadd(t, e);
+    v[2] = csub(t, e);
+}
+
+// radix-5 DFT from the pairs b_k = a_k + a_{5-k}, d_k = a_k - a_{5-k}:
+// y_1,4 = a_0 + c1 b_1 + c2 b_2 +- DIR i (s1 d_1 + s2 d_2),
+// y_2,3 = a_0 + c2 b_1 + c1 b_2 +- DIR i (s2 d_1 - s1 d_2),
+// c_k = cos(2 pi k / 5), s_k = sin(2 pi k / 5)
+template <int DIR, typename T> __device__ __forceinline__ void dft5(C<T>* v) {
+    const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
+    const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
+    const C<T> b1 = cadd(v[1], v[4]), d1 = csub(v[1], v[4]);
+    const C<T> b2 = cadd(v[2], v[3]), d2 = csub(v[2], v[3]);
+    const C<T> t1 = cmake<T>(v[0].x + c1 * b1.x + c2 * b2.x, v[0].y + c1 * b1.y + c2 * b2.y);
+    const C<T> t2 = cmake<T>(v[0].x + c2 * b1.x + c1 * b2.x, v[0].y + c2 * b1.y + c1 * b2.y);
+    const C<T> e1 = cmul_i<DIR>(cmake<T>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y));
+    const C<T> e2 = cmul_i<DIR>(cmake<T>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y));
+    v[0] = cadd(v[0], cadd(b1, b2));
+    v[1] = cadd(t1, e1);
+    v[4] = csub(t1, e1);
+    v[2] = cadd(t2, e2);
+    v[3] = csub(t2, e2);
+}
+
+// ---------------------------------------------------------------------------
+// Stage codes: 3 bits per stage, first stage in the low bits; 1 -> radix 2,
+// 2 -> radix 4, 3 -> radix 8, 4 -> radix 3, 5 -> radix 5, 0 ends.  The
+// power-of-two stages come first, so Ns is a power of two in them.
+// ---------------------------------------------------------------------------
+
+__host__ __device__ constexpr int fft_stage_radix(int c) {
+    return c == 1 ? 2 : c == 2 ? 4 : c == 3 ? 8 : c == 4 ? 3 : c == 5 ? 5 : 1;
+}
+
+// code for length N, or -1 if N is not 2^a 3^b 5^c (N >= 2) or needs more
+// than 10 stages
+inline int fft_code(int N) {
+    if (N < 2) return -1;
+    int a = 0, m = N;
+    while (m % 2 == 0) { m /= 2; ++a; }
+    int codes[16], ns = 0;
+    while (a > 0) {
+        if (a >= 3 && a != 4) { codes[ns++] = 3; a -= 3; }
+        else if (a >= 2) { codes[ns++] = 2; a -= 2; }
+        else { codes[ns++] = 1; a -= 1; }
+        if (ns > 10) return -1;
+    }
+    while (m % 3 == 0) { m /= 3; codes[ns++] = 4; if (ns > 10) return -1; }
+    while (m % 5 == 0) { m /= 5; codes[ns++] = 5; if (ns > 10) return -1; }
+    if (m != 1) return -1;
+    int code = 0;
+    for (int i = ns - 1; i >= 0; --i) code = (code << 3) | codes[i];
+    return code;
+}
+
+// Butterflies per thread of a radix-R stage for a register budget MAXB (in
+// radix-8 butterflies): the power-of-two stages hold 8 MAXB values; the
+// radix-3 and radix-5 stages, whose butterflies need more temporaries, hold
+// fewer (4 MAXB / 2 MAXB butterflies -> 12 / 10 values at MAXB = 2).
+__host__ __device__ constexpr int fft_stage_maxb(int R, int maxb) {
+    return R == 3 ? 2 * maxb : R == 5 ? maxb : (8 * maxb) / R;
+}
+
+// true when the code has a radix-3 or radix-5 stage (those kernels are built
+// separately: the extra stage kinds cost registers in the power-of-two ones)
+inline bool fft_mixed(int code) {
+    for (int c = code; c; c >>= 3)
+        if ((c & 7) == 4 || (c & 7) == 5) return true;
+    return false;
+}
+
+// Most elements per thread the stages of `code` cover: the minimum of
+// R * fft_stage_maxb(R) over its radices; a call needs
+// nlines * N <= fft_capacity(code, MAXB) * blockDim.x.
+inline int fft_capacity(int code, int maxb) {
+    int cap = 8 * maxb;
+    for (int c = code; c; c >>= 3) {
+        const int R = fft_stage_radix(c & 7);
+        const int v = R * fft_stage_maxb(R, maxb);
+        if (v < cap) cap = v;
+    }
+    return cap;
+}
+
 // ---------------------------------------------------------------------------
 // In-place variant: one shared buffer.  Each stage first loads every
 // butterfly input the thread owns into registers (at most MAXB butterflies of
@@ -71,41 +165,44 @@ template <int DIR, typename T> __device__ __forceinline__ void dft8(C<T>* v) {
 __host__ __device__ __forceinline__ int fpad(int e) { return e + (e >> 4); }
 __host__ __device__ __forceinline__ int fpad_len(int n) { return n + (n >> 4) + 1; }
 
+// idx1 = k * twstep with k < Ns and twstep = (N / (Ns R)) twstride, so
+// r * idx1 < Nmax for every r < R: the table needs no index reduction.
 template <int R, int DIR, typename T>
-__device__ __forceinline__ void twiddles(C<T>* wv, const C<T>* __restrict__ tw, int idx1, int tmask) {
-#ifdef LAM_TW_TABLE
-#pragma unroll
-    for (int r = 1; r < R; ++r) {
-        C<T> w = tw[(r * idx1) & tmask];
-        if (DIR > 0) w.y = -w.y;
-        wv[r] = w;
-    }
-    return;
+__device__ __forceinline__ void twiddles(C<T>* wv, const C<T>* __restrict__ tw, int idx1) {
+#ifndef LAM_TW_TABLE
+    if constexpr (R == 2 || R == 4 || R == 8) {
+        C<T> w1 = tw[idx1];
+        if (DIR > 0) w1.y = -w1.y;
+        wv[1] = w1;
+        if constexpr (R >= 4) {
+            C<T> w2 = tw[2 * idx1];
+            if (DIR > 0) w2.y = -w2.y;
+            wv[2] = w2;
+            wv[3] = cmul(w1, w2);
+        }
+        if constexpr (R == 8) {
+            C<T> w4 = tw[4 * idx1];
+            if (DIR > 0) w4.y = -w4.y;
+            wv[4] = w4;
+            wv[5] = cmul(w1, w4);
+            wv[6] = cmul(wv[2], w4);
+            wv[7] = cmul(wv[3], w4);
+        }
+    } else
 #endif
-    // idx1 = k * twstep; table index r * idx1 reduced mod table length (tmask = len - 1)
-    C<T> w1 = tw[idx1 & tmask];
-    if (DIR > 0) w1.y = -w1.y;
-    wv[1] = w1;
-    if (R >= 4) {
-        C<T> w2 = tw[(2 * idx1) & tmask];
-        if (DIR > 0) w2.y = -w2.y;
-        wv[2] = w2;
-        wv[3] = cmul(w1, w2);
-    }
-    if (R == 8) {
-        C<T> w4 = tw[(4 * idx1) & tmask];
-        if (DIR > 0) w4.y = -w4.y;
-        wv[4] = w4;
-        wv[5] = cmul(w1, w4);
-        wv[6] = cmul(wv[2], w4);
-        wv[7] = cmul(wv[3], w4);
+    {
+#pragma unroll
+        for (int r = 1; r < R; ++r) {
+            C<T> w = tw[r * idx1];
+            if (DIR > 0) w.y = -w.y;
+            wv[r] = w;
+        }
     }
 }
 
 template <int R, int DIR, int MAXB, typename T>
 __device__ __forceinline__ void fft_stage_ip(C<T>* buf, int nlines, int lstride, int N, int Ns,
-                                             const C<T>* __restrict__ tw, int twstride, int tmask, int tid,
-                                             int nthr) {
+                                             const C<T>* __restrict__ tw, int twstride, int tid, int nthr) {
     const int nb = N / R;
     const int total = nlines * nb;
     const int twstep = (N / (Ns * R)) * twstride;
@@ -128,15 +225,18 @@ __device__ __forceinline__ void fft_stage_ip(C<T>* buf, int nlines, int lstride,
         if (q < total) {
             const int line = q / nb;
             const int j = q - line * nb;
-            const int k = j & (Ns - 1);
+            // Ns is a power of two in the radix-2/4/8 stages (they come first)
+            const int k = (R == 3 || R == 5) ? j % Ns : (j & (Ns - 1));
             if (Ns > 1) {
                 C<T> wv[R];
-                twiddles<R, DIR, T>(wv, tw, k * twstep, tmask);
+                twiddles<R, DIR, T>(wv, tw, k * twstep);
 #pragma unroll
                 for (int r = 1; r < R; ++r) v[bb][r] = cmul(v[bb][r], wv[r]);
             }
             if (R == 8) dft8<DIR>(v[bb]);
+            else if (R == 5) dft5<DIR>(v[bb]);
             else if (R == 4) dft4<DIR>(v[bb]);
+            else if (R == 3) dft3<DIR>(v[bb]);
             else dft2<DIR>(v[bb]);
             C<T>* d = buf + line * lstride;
             const int base = (j - k) * R + k;
@@ -155,29 +255,43 @@ template <> struct FftMaxB<double> { static constexpr int value = 1; };
 constexpr int kFftThreads = 512;
 
 // In-place FFT of nlines lines in buf, line l starting at buf + l * lstride,
-// element e at fpad(e) (lstride >= fpad_len(N)).  The caller must __syncthreads() before; the call ends with a
-// __syncthreads().  Requires nlines * N <= 8 * MAXB * blockDim.x.  tlen is the
-// twiddle table length (a power of two).
-template <int DIR, int MAXB, typename T>
-__device__ __forceinline__ void fft_lines_ip(C<T>* buf, int nlines, int lstride, int N, int logN,
+// element e at fpad(e) (lstride >= fpad_len(N)).  The caller must
+// __syncthreads() before; the call ends with a __syncthreads().  Requires
+// nlines * N <= fft_capacity(code, MAXB) * blockDim.x; code = fft_code(N); tw
+// has Nmax = N * twstride entries.  MIXED must be true when the code has
+// radix-3 or radix-5 stages (fft_mixed).
+template <int DIR, int MAXB, typename T, bool MIXED>
+__device__ __forceinline__ void fft_lines_ip(C<T>* buf, int nlines, int lstride, int N, int code,
                                              const C<T>* __restrict__ tw, int twstride) {
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int tmask = N * twstride - 1;
     int Ns = 1;
-    int bits = logN;
-    while (bits > 0) {
-        if (bits >= 3 && bits != 4) {
-            fft_stage_ip<8, DIR, MAXB, T>(buf, nlines, lstride, N, Ns, tw, twstride, tmask, tid, nthr);
-            Ns *= 8;
-            bits -= 3;
-        } else if (bits >= 2) {
-            fft_stage_ip<4, DIR, 2 * MAXB, T>(buf, nlines, lstride, N, Ns, tw, twstride, tmask, tid, nthr);
-            Ns *= 4;
-            bits -= 2;
-        } else {
-            fft_stage_ip<2, DIR, 4 * MAXB, T>(buf, nlines, lstride, N, Ns, tw, twstride, tmask, tid, nthr);
-            Ns *= 2;
-            bits -= 1;
+    for (int c = code; c; c >>= 3) {
+        switch (c & 7) {
+            case 3:
+                fft_stage_ip<8, DIR, fft_stage_maxb(8, MAXB), T>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
+                Ns *= 8;
+                break;
+            case 2:
+                fft_stage_ip<4, DIR, fft_stage_maxb(4, MAXB), T>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
+                Ns *= 4;
+                break;
+            case 1:
+                fft_stage_ip<2, DIR, fft_stage_maxb(2, MAXB), T>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
+                Ns *= 2;
+                break;
+            default:
+                if constexpr (MIXED) {
+                    if ((c & 7) == 4) {
+                        fft_stage_ip<3, DIR, fft_stage_maxb(3, MAXB), T>(buf, nlines, lstride, N, Ns, tw, twstride,
+                                                                         tid, nthr);
+                        Ns *= 3;
+                    } else {
+                        fft_stage_ip<5, DIR, fft_stage_maxb(5, MAXB), T>(buf, nlines, lstride, N, Ns, tw, twstride,
+                                                                         tid, nthr);
+                        Ns *= 5;
+                    }
+                }
+                break;
         }
     }
 }

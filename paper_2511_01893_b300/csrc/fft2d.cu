@@ -13,7 +13,7 @@
 
 namespace lam {
 
-template <int DIR, typename T>
+template <int DIR, typename T, bool MIXED>
 __global__ void __launch_bounds__(kFftThreads) k_fft2d_rows(const C<T>* in, C<T>* out,
                                                     int RB, Fft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft2d_rows(const C<T>* in, C<T>
         bufa[r * LS + fpad(k)] = ((r0 + r + k) & 1) ? cmake<T>(-v.x, -v.y) : v;
     }
     __syncthreads();
-    fft_lines_ip<DIR, FftMaxB<T>::value, T>(bufa, RB, LS, a.w, a.logw, a.tw, a.tww);
+    fft_lines_ip<DIR, FftMaxB<T>::value, T, MIXED>(bufa, RB, LS, a.w, a.fcw, a.tw, a.tww);
     for (int i = threadIdx.x; i < RB * a.w; i += blockDim.x) {
         const int r = i / a.w, k = i - r * a.w;
         const C<T> v = bufa[r * LS + fpad(k)];
@@ -35,7 +35,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft2d_rows(const C<T>* in, C<T>
     }
 }
 
-template <int DIR, typename T>
+template <int DIR, typename T, bool MIXED>
 __global__ void __launch_bounds__(kFftThreads) k_fft2d_cols(C<T>* __restrict__ io, int CB, T scale, Fft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(kFftThreads) k_fft2d_cols(C<T>* __restrict__ i
         bufa[c * LS + fpad(r)] = pl[(size_t)r * a.w + c];
     }
     __syncthreads();
-    fft_lines_ip<DIR, FftMaxB<T>::value, T>(bufa, CB, LS, a.h, a.logh, a.tw, a.twh);
+    fft_lines_ip<DIR, FftMaxB<T>::value, T, MIXED>(bufa, CB, LS, a.h, a.fch, a.tw, a.twh);
     const int gsign = ((a.h / 2 + a.w / 2) & 1);
     for (int i = threadIdx.x; i < a.h * CB; i += blockDim.x) {
         const int r = i / CB, c = i - r * CB;
@@ -58,11 +58,13 @@ __global__ void __launch_bounds__(kFftThreads) k_fft2d_cols(C<T>* __restrict__ i
 }
 
 // lines per block: at most 128 KB of shared memory, within the in-place FFT's
-// register budget (lines * len <= 8 * MAXB * threads), at most 32 lines
-template <typename T> static int lines_per_block(int len) {
+// register capacity (lines * len <= capacity * threads), at most 32 lines,
+// dividing the number of lines
+template <typename T> static int lines_per_block(int len, int code, int nlines) {
     const size_t elem = sizeof(C<T>);
+    const int capacity = fft_capacity(code, FftMaxB<T>::value) * kFftThreads;
     int l = 32;
-    while (l > 1 && ((size_t)l * fpad_len(len) * elem > 128 * 1024 || l * len > 8 * FftMaxB<T>::value * kFftThreads))
+    while (l > 1 && ((size_t)l * fpad_len(len) * elem > 128 * 1024 || l * len > capacity || nlines % l != 0))
         l >>= 1;
     return l;
 }
@@ -70,29 +72,35 @@ template <typename T> static int lines_per_block(int len) {
 template <typename T>
 cudaError_t launch_fft2d_angles(const C<T>* in, C<T>* out, int dir, T scale, const Fft2dArgs<T>& a,
                                 cudaStream_t s) {
-    int RB = lines_per_block<T>(a.w);
-    if (RB > a.h) RB = a.h;
-    int CB = lines_per_block<T>(a.h);
-    if (CB > a.w) CB = a.w;
+    const int RB = lines_per_block<T>(a.w, a.fcw, a.h);
+    const int CB = lines_per_block<T>(a.h, a.fch, a.w);
     const size_t sr = (size_t)RB * fpad_len(a.w) * sizeof(C<T>);
     const size_t sc = (size_t)CB * fpad_len(a.h) * sizeof(C<T>);
+    const bool mixed = fft_mixed(a.fch) || fft_mixed(a.fcw);
+#define LAM_F2(D, MX)                                                                              \
+    k_fft2d_rows<D, T, MX><<<dim3(a.h / RB, a.T_), kFftThreads, sr, s>>>(in, out, RB, a);          \
+    k_fft2d_cols<D, T, MX><<<dim3(a.w / CB, a.T_), kFftThreads, sc, s>>>(out, CB, scale, a);
     if (dir > 0) {
-        k_fft2d_rows<1, T><<<dim3(a.h / RB, a.T_), kFftThreads, sr, s>>>(in, out, RB, a);
-        k_fft2d_cols<1, T><<<dim3(a.w / CB, a.T_), kFftThreads, sc, s>>>(out, CB, scale, a);
+        if (mixed) { LAM_F2(1, true) } else { LAM_F2(1, false) }
     } else {
-        k_fft2d_rows<-1, T><<<dim3(a.h / RB, a.T_), kFftThreads, sr, s>>>(in, out, RB, a);
-        k_fft2d_cols<-1, T><<<dim3(a.w / CB, a.T_), kFftThreads, sc, s>>>(out, CB, scale, a);
+        if (mixed) { LAM_F2(-1, true) } else { LAM_F2(-1, false) }
     }
+#undef LAM_F2
     return cudaGetLastError();
 }
 
 template <typename T> cudaError_t configure_fft2d() {
     const int mx = kMaxDynSmem;
     cudaError_t e = cudaSuccess;
-    if (!e) e = cudaFuncSetAttribute(k_fft2d_rows<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (!e) e = cudaFuncSetAttribute(k_fft2d_rows<-1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (!e) e = cudaFuncSetAttribute(k_fft2d_cols<1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (!e) e = cudaFuncSetAttribute(k_fft2d_cols<-1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    if (!e) e = cudaFuncSetAttribute(k_fft2d_rows<1, T, false>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_fft2d_rows<-1, T, false>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_fft2d_cols<1, T, false>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_fft2d_cols<-1, T, false>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_fft2d_rows<1, T, true>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_fft2d_rows<-1, T, true>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_fft2d_cols<1, T, true>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_fft2d_cols<-1, T, true>, at, mx);
     return e;
 }
 

@@ -27,7 +27,7 @@ template <typename T> cudaError_t configure_fft2d();
 // ---- F_u1D -----------------------------------------------------------------
 template <typename T> struct Usfft1dArgs {
     int n1, nz, n2, h;
-    int M0, logM0;
+    int M0, fcz;       // fcz: FFT stage code of length nz (fft_code)
     int m;             // half-width; 2m taps
     int TY;            // columns per block (divides n2)
     const T* dz;       // [nz] deapodisation along z
@@ -54,7 +54,7 @@ template <> struct AngleT<double> { typedef AngleD type; };
 
 template <typename T> struct Usfft2dArgs {
     int n1, n2, h, w, T_;          // T_ = number of angles
-    int M1, M2, logM1, logM2;
+    int M1, M2, fcM1, fcM2;         // fc*: FFT stage codes (fft_code)
     int m;
     T inv4beta;                     // 1 / (4 beta)
     const T* d1;                    // [n1] deapodisation along x
@@ -95,7 +95,7 @@ template <typename T> cudaError_t launch_absmax(const C<T>* in, long long n, T* 
 
 // ---- F_2D / F*_2D (centred, per angle) ----------------------------------------
 template <typename T> struct Fft2dArgs {
-    int T_, h, w, logh, logw;
+    int T_, h, w, fch, fcw;         // fc*: FFT stage codes (fft_code)
     const C<T>* tw;
     int twh, tww;                   // Nmax / h, Nmax / w
 };

@@ -34,7 +34,7 @@ template <typename T> __device__ __forceinline__ C<T> pz_at(const C<T>* E, const
     return (jj & 1) ? O[fpad(jj >> 1)] : E[fpad(jj >> 1)];
 }
 
-template <typename T>
+template <typename T, bool MIXED>
 __global__ void __launch_bounds__(kFftThreads) k_usfft1d_fwd(const T* __restrict__ u, C<T>* __restrict__ u1,
                                                              Usfft1dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -58,7 +58,7 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_fwd(const T* __restrict
         buf[(2 * p + 1) * LS + fpad(q)] = cmake<T>(va * w.x - vb * w.y, va * w.y + vb * w.x);
     }
     __syncthreads();
-    fft_lines_ip<-1, FftMaxB<T>::value, T>(buf, a.TY, LS, nz, a.logM0 - 1, a.tw, 2 * twM0);
+    fft_lines_ip<-1, FftMaxB<T>::value, T, MIXED>(buf, a.TY, LS, nz, a.fcz, a.tw, 2 * twM0);
     const int nt = 2 * a.m;
     C<T>* dst = u1 + (size_t)x * a.n2 + y0;
     const size_t plane = (size_t)a.n1 * a.n2;
@@ -109,7 +109,7 @@ __device__ __forceinline__ C<T> spread_at(const C<T>* vals, int j, const Usfft1d
     return cmake<T>(sr, si);
 }
 
-template <typename T>
+template <typename T, bool MIXED>
 __global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restrict__ u1, T* __restrict__ u,
                                                              Usfft1dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restr
         if (jm != j) ((jm & 1) ? O : E)[fpad(jm >> 1)] = qm;
     }
     __syncthreads();
-    fft_lines_ip<+1, FftMaxB<T>::value, T>(buf, a.TY, LS, nz, a.logM0 - 1, a.tw, 2 * a.twstride);
+    fft_lines_ip<+1, FftMaxB<T>::value, T, MIXED>(buf, a.TY, LS, nz, a.fcz, a.tw, 2 * a.twstride);
     T* dst = u + (size_t)x * nz * a.n2 + y0;
     for (int i = tid; i < nz * npair; i += nthr) {
         const int z = i / npair, p = i - z * npair;
@@ -166,21 +166,26 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restr
 template <typename T>
 cudaError_t launch_usfft1d_fwd(const T* u, C<T>* u1, const Usfft1dArgs<T>& a, cudaStream_t s) {
     const size_t smem = (size_t)a.TY * fpad_len(a.nz) * sizeof(C<T>);
-    k_usfft1d_fwd<T><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u, u1, a);
+    if (fft_mixed(a.fcz)) k_usfft1d_fwd<T, true><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u, u1, a);
+    else k_usfft1d_fwd<T, false><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u, u1, a);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_usfft1d_adj(const C<T>* u1, T* u, const Usfft1dArgs<T>& a, cudaStream_t s) {
     const size_t smem = (size_t)(fpad_len(a.nz) + a.h) * a.TY * sizeof(C<T>);
-    k_usfft1d_adj<T><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u1, u, a);
+    if (fft_mixed(a.fcz)) k_usfft1d_adj<T, true><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u1, u, a);
+    else k_usfft1d_adj<T, false><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u1, u, a);
     return cudaGetLastError();
 }
 
 template <typename T> cudaError_t configure_usfft1d() {
     const int mx = kMaxDynSmem;
-    cudaError_t e = cudaFuncSetAttribute(k_usfft1d_fwd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    if (!e) e = cudaFuncSetAttribute(k_usfft1d_adj<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
+    cudaError_t e = cudaFuncSetAttribute(k_usfft1d_fwd<T, false>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_usfft1d_adj<T, false>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_usfft1d_fwd<T, true>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_usfft1d_adj<T, true>, at, mx);
     return e;
 }
 

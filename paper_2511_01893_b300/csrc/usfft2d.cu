@@ -36,7 +36,7 @@ __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(
 // row / column passes
 // --------------------------------------------------------------------------
 
-template <typename T>
+template <typename T, bool MIXED>
 __global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(const C<T>* __restrict__ u1, C<T>* __restrict__ P,
                                                     int j0, Usfft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(const C<T>* __restri
         bufa[r * LS + fpad(wrap(y - a.n2 / 2, a.M2))] = cscale(src[i], s);
     }
     __syncthreads();
-    fft_lines_ip<-1, FftMaxB<T>::value, T>(bufa, a.RB, LS, a.M2, a.logM2, a.tw, a.tw2);
+    fft_lines_ip<-1, FftMaxB<T>::value, T, MIXED>(bufa, a.RB, LS, a.M2, a.fcM2, a.tw, a.tw2);
     C<T>* dst = P + (size_t)b * a.M1 * a.M2;
     for (int i = tid; i < a.RB * a.M2; i += nthr) {
         const int r = i / a.M2, j = i - r * a.M2;
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(const C<T>* __restri
     }
 }
 
-template <typename T>
+template <typename T, bool MIXED>
 __global__ void __launch_bounds__(kFftThreads) k_colfft_fwd(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
@@ -79,14 +79,14 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_fwd(C<T>* __restrict__ P
         bufa[c * LS + fpad(row)] = pl[(size_t)row * a.M2 + c];
     }
     __syncthreads();
-    fft_lines_ip<-1, FftMaxB<T>::value, T>(bufa, a.CB, LS, a.M1, a.logM1, a.tw, a.tw1);
+    fft_lines_ip<-1, FftMaxB<T>::value, T, MIXED>(bufa, a.CB, LS, a.M1, a.fcM1, a.tw, a.tw1);
     for (int i = tid; i < a.M1 * a.CB; i += nthr) {
         const int j = i / a.CB, c = i - j * a.CB;
         pl[(size_t)j * a.M2 + c] = bufa[c * LS + fpad(j)];
     }
 }
 
-template <typename T>
+template <typename T, bool MIXED>
 __global__ void __launch_bounds__(kFftThreads) k_colfft_adj(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_adj(C<T>* __restrict__ P
         bufa[c * LS + fpad(j)] = pl[(size_t)j * a.M2 + c];
     }
     __syncthreads();
-    fft_lines_ip<+1, FftMaxB<T>::value, T>(bufa, a.CB, LS, a.M1, a.logM1, a.tw, a.tw1);
+    fft_lines_ip<+1, FftMaxB<T>::value, T, MIXED>(bufa, a.CB, LS, a.M1, a.fcM1, a.tw, a.tw1);
     for (int i = tid; i < a.n1 * a.CB; i += nthr) {
         const int x = i / a.CB, c = i - x * a.CB;
         const int row = wrap(x - a.n1 / 2, a.M1);
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_adj(C<T>* __restrict__ P
     }
 }
 
-template <typename T>
+template <typename T, bool MIXED>
 __global__ void __launch_bounds__(kFftThreads) k_rowfft_adj(const C<T>* __restrict__ P, C<T>* __restrict__ u1,
                                                     int j0, Usfft2dArgs<T> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kFftThreads) k_rowfft_adj(const C<T>* __restri
         bufa[r * LS + fpad(j)] = pl[(size_t)wrap(x0 + r - a.n1 / 2, a.M1) * a.M2 + j];
     }
     __syncthreads();
-    fft_lines_ip<+1, FftMaxB<T>::value, T>(bufa, a.RB, LS, a.M2, a.logM2, a.tw, a.tw2);
+    fft_lines_ip<+1, FftMaxB<T>::value, T, MIXED>(bufa, a.RB, LS, a.M2, a.fcM2, a.tw, a.tw2);
     C<T>* dst = u1 + ((size_t)kv * a.n1 + x0) * a.n2;
     for (int i = tid; i < a.RB * a.n2; i += nthr) {
         const int r = i / a.n2, y = i - r * a.n2;
@@ -734,8 +734,13 @@ cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* s
     const int kv0 = j0;
     const size_t sr = (size_t)a.RB * fpad_len(a.M2) * sizeof(C<T>);
     const size_t sc = (size_t)a.CB * fpad_len(a.M1) * sizeof(C<T>);
-    k_rowfft_fwd<T><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, kv0, a);
-    k_colfft_fwd<T><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+    if (fft_mixed(a.fcM1) || fft_mixed(a.fcM2)) {
+        k_rowfft_fwd<T, true><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, kv0, a);
+        k_colfft_fwd<T, true><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+    } else {
+        k_rowfft_fwd<T, false><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, kv0, a);
+        k_colfft_fwd<T, false><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+    }
     constexpr int NW = kScatterWarps;
     const int ntiles = (a.M1 / a.TG) * (a.M2 / a.TG);
     const size_t sg = (size_t)(a.TG + 2 * a.m - 1) * (a.TG + 2 * a.m + 1) * sizeof(C<T>);
@@ -784,8 +789,13 @@ cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int j0, int nb
     else { LAM_SW(0) }
 #undef LAM_SW
 #undef LAM_S
-    k_colfft_adj<T><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
-    k_rowfft_adj<T><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(P, u1, kv0, a);
+    if (fft_mixed(a.fcM1) || fft_mixed(a.fcM2)) {
+        k_colfft_adj<T, true><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+        k_rowfft_adj<T, true><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(P, u1, kv0, a);
+    } else {
+        k_colfft_adj<T, false><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+        k_rowfft_adj<T, false><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(P, u1, kv0, a);
+    }
     return cudaGetLastError();
 }
 
@@ -820,10 +830,14 @@ template <typename T> cudaError_t configure_usfft2d() {
     const int mx = kMaxDynSmem;
     cudaError_t e = cudaSuccess;
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
-    if (!e) e = cudaFuncSetAttribute(k_rowfft_fwd<T>, at, mx);
-    if (!e) e = cudaFuncSetAttribute(k_colfft_fwd<T>, at, mx);
-    if (!e) e = cudaFuncSetAttribute(k_rowfft_adj<T>, at, mx);
-    if (!e) e = cudaFuncSetAttribute(k_colfft_adj<T>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_rowfft_fwd<T, false>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_colfft_fwd<T, false>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_rowfft_adj<T, false>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_colfft_adj<T, false>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_rowfft_fwd<T, true>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_colfft_fwd<T, true>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_rowfft_adj<T, true>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_colfft_adj<T, true>, at, mx);
 #define LAM_A(MH)                                                                          \
     if (!e) e = cudaFuncSetAttribute(k_gather2d_tiled<T, kScatterWarps, MH>, at, mx);       \
     if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 0>, at, mx);  \

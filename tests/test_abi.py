@@ -53,8 +53,12 @@ def test_host_side_argument_errors_need_no_gpu(so):
     lib = lamino.lib()
     h = ctypes.c_void_p()
     th = (ctypes.c_double * 4)(0, 1, 2, 3)
-    assert lib.lam_plan_create(ctypes.byref(h), 12, 16, 16, 16, 4, th, 0.5, 2, 4, 0) == -6   # n not pow2
-    assert b"power of two" in lib.lam_last_error()
+    assert lib.lam_plan_create(ctypes.byref(h), 12, 16, 16, 16, 4, th, 0.5, 2, 4, 0) == -6   # n not a multiple of 8
+    assert b"multiple of 8" in lib.lam_last_error()
+    assert lib.lam_plan_create(ctypes.byref(h), 16, 14, 16, 16, 4, th, 0.5, 2, 4, 0) == -6   # nz = 2 * 7
+    assert b"2^a 3^b 5^c" in lib.lam_last_error()
+    assert lib.lam_plan_create(ctypes.byref(h), 16, 16, 15, 16, 4, th, 0.5, 2, 4, 0) == -6   # odd det_h
+    assert b"even" in lib.lam_last_error()
     assert lib.lam_plan_create(ctypes.byref(h), 16, 16, 16, 16, 4, th, 2.0, 2, 4, 0) == -1   # phi >= pi/2
     assert lib.lam_plan_create(ctypes.byref(h), 16, 16, 16, 16, 4, th, 0.5, 3, 4, 0) == -6   # oversample
     assert lib.lam_plan_create(ctypes.byref(h), 16, 16, 16, 16, 4, None, 0.5, 2, 4, 0) == -1

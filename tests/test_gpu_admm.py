@@ -149,3 +149,20 @@ def test_reconstruct_one_call_matches_state_api(case):
     u_dev = glam.reconstruct(torch.from_numpy(case["d"].real.astype(np.float32)).cuda(), case["theta"], PHI, N, NZ,
                              3, ALPHA, RHO)
     assert np.array_equal(u_dev.cpu().numpy(), u_host)
+
+
+def test_admm_f64_matches_oracle_at_mixed_radix_size():
+    # n = 48, nz = 24, detector 40 x 48: FFT lengths 24, 40, 48, 96 (radix 3, 5)
+    n, nz, h, w, T = 48, 24, 40, 48, 24
+    theta = inputs.angles(T)
+    g = oracle_geom(n, nz, h, w, theta, PHI)
+    u = inputs.ellipsoid_phantom(n, nz, 8, seed=77).numpy()
+    clean = olam.lam_forward(u, g)
+    d = clean + 0.01 * np.abs(clean.real).max() * inputs.noise((T, h, w), seed=78).numpy()
+    u_ref, info = oadmm.admm(d, g, ALPHA, RHO, 3, 2, adapt_rho=True)
+    plan = glam.Plan(n, nz, h, w, theta, PHI, prec="f64")
+    a = glam.Admm(plan).init(torch.from_numpy(d), ALPHA, RHO, 2, adapt_rho=True)
+    a.run(3)
+    assert a.status() == 0
+    assert rel(a.u, u_ref) < 1e-10
+    assert np.allclose(a.history()[:, 0], info["objective"], rtol=1e-10)

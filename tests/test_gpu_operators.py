@@ -22,8 +22,11 @@ GEOMS = [
     (64, 32, 64, 32, 40, np.deg2rad(20.0)),
     (32, 32, 32, 32, 24, 0.0),
     (16, 8, 16, 16, 9, np.deg2rad(70.0)),
+    # sizes with factors 3 and 5 (mixed-radix FFTs, 32 x 32 plane tiles)
+    (48, 24, 40, 48, 30, np.deg2rad(25.0)),
+    (80, 40, 60, 80, 18, np.deg2rad(35.0)),
 ]
-IDS = ["cube16", "flat32", "mixed64", "phi0", "steep"]
+IDS = ["cube16", "flat32", "mixed64", "phi0", "steep", "radix3", "radix5"]
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
