@@ -200,6 +200,41 @@ lam_status reconstruct(const float* data, const double* theta, double phi, int n
                        int det_h, int det_w, int n_theta, int iters, double alpha, double rho,
                        float* u_out);
 
+/* ---------------------------------------------------------------------------
+ * Batches: several reconstructions of uneven sizes run together.  Every
+ * plane-stage operator step (z transform, row and column FFTs, gather,
+ * spread) is one persistent launch over a work list that concatenates all
+ * problems' blocks, instead of one launch per problem (Section 4.2's
+ * batching of the per-chunk work, across problems).
+ * ------------------------------------------------------------------------- */
+typedef struct lam_batch lam_batch;
+
+/* Binds up to 32 plans (same precision and half-width, plans on the current
+ * device, n a multiple of 16) to their workspaces (ws[i] of
+ * lam_workspace_bytes(plans[i]) bytes, holding all of the plan's plane jobs:
+ * the default for planes up to 1 GiB in total).  Allocates one small device
+ * table; the batch does not own the plans or workspaces, which must outlive
+ * it.  The batched adjoint always uses the tile spread (LAM_SPREAD_TILES). */
+lam_status lam_batch_create(lam_batch** out, const lam_plan* const* plans, void* const* ws, int count);
+lam_status lam_batch_destroy(lam_batch* batch);
+
+/* L_hat / L_hat^H / L / L^H of every problem i of the batch: u[i] and d[i]
+ * as in the single-plan calls (device arrays of plan i's shapes).  Results
+ * are bitwise equal to the single-plan calls.  The full L and L^H run F*_2D /
+ * F_2D per problem around the batched stages. */
+lam_status lam_forward_hat_batched(const lam_batch* batch, const void* const* u, void* const* d_hat, void* stream);
+lam_status lam_adjoint_hat_batched(const lam_batch* batch, const void* const* d_hat, void* const* u, void* stream);
+lam_status lam_forward_batched(const lam_batch* batch, const void* const* u, void* const* d, void* stream);
+lam_status lam_adjoint_batched(const lam_batch* batch, const void* const* d, void* const* u, void* stream);
+
+/* `iters` ADMM outer iterations of every problem: states[i] initialised with
+ * admm_init on plan i (all with the same n_inner).  The operators run
+ * batched; the elementwise steps run per problem in admm_step's order, so
+ * each state evolves bitwise as under admm_step.  use_graph != 0 captures
+ * one outer iteration of the whole batch as a CUDA graph (re-captured when
+ * the states change) and replays it; it needs a non-default stream. */
+lam_status admm_run_batched(lam_batch* batch, void* const* states, int iters, int use_graph, void* stream);
+
 /* Thread-local message for the last non-OK status returned on this thread. */
 const char* lam_last_error(void);
 

@@ -52,6 +52,12 @@ lam_status lamx_u2d_fwd_static(const lam_plan* plan, const void* u1, void* d_hat
  * pairs with its conjugate mirror). */
 lam_status lamx_plan_info(const lam_plan* plan, int* out, int count);
 
+/* Batch diagnostics: out[2 s], out[2 s + 1] = work items and persistent grid
+ * of batched stage s (z forward, row FFT, column FFT, gather, spread, column
+ * FFT^H, row FFT^H, z transpose); out[16] = kernel nodes of the captured
+ * ADMM graph (0 before the first graph run). */
+lam_status lamx_batch_info(const lam_batch* batch, int* out, int count);
+
 /* Kernel nodes in the CUDA graph admm_run captured for this state (one outer
  * iteration); 0 before the first graph run. */
 lam_status lamx_admm_graph_kernels(const lam_plan* plan, void* state, size_t* count);

@@ -15,6 +15,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -102,6 +103,24 @@ struct lam_plan {
     size_t celem() const { return 2 * elem(); }
     long long nvox() const { return (long long)n1 * nz * n2; }
     long long ndata() const { return (long long)T * h * w; }
+};
+
+// a batch of plans run together by the batched operators (lam_batch_create)
+struct lam_batch {
+    int count = 0;
+    int prec = LAM_F32;
+    int device = -1;
+    int m = 4;
+    bool mixed = false;  // some problem has radix-3/5 FFT lengths
+    std::vector<const lam_plan*> plans;
+    std::vector<void*> ws;
+    void* dev = nullptr;  // BatchTable<T> in device memory
+    BatchLaunch L[kBStages];
+    int total[kBStages] = {};
+    // ADMM graph of one outer iteration over the states it was captured for
+    std::vector<void*> graph_states;
+    cudaGraphExec_t graph = nullptr;
+    size_t graph_kernels = 0;
 };
 
 namespace {
@@ -569,6 +588,129 @@ lam_status check_plan(const lam_plan* p) {
     return LAM_OK;
 }
 
+
+// ---- batches -------------------------------------------------------------------
+
+template <typename T> lam_status batch_build(lam_batch* b) {
+    std::unique_ptr<BatchTable<T>> H(new BatchTable<T>());
+    std::memset(H.get(), 0, sizeof(BatchTable<T>));
+    H->count = b->count;
+    int nsm = 0;
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, b->device));
+    size_t smem[kBStages] = {};
+    const size_t ce = sizeof(C<T>);
+    for (int i = 0; i < b->count; ++i) {
+        const lam_plan* q = b->plans[i];
+        char* w = (char*)b->ws[i];
+        H->zf[i] = args1d<T>(q, q->TYf, true);
+        H->za[i] = args1d<T>(q, q->TYa, true);
+        H->a2[i] = args2d<T>(q, true);
+        H->u1[i] = (C<T>*)(w + q->ws_u1);
+        H->P[i] = (C<T>*)(w + q->ws_planes);
+        const int nj = q->njobs_pair;
+        const int gx[kBStages] = {q->n1 * (q->n2 / q->TYf),          q->n1 / q->RB, q->M2 / q->CB,
+                                  (q->M1 / q->TG) * (q->M2 / q->TG), (q->M1 / q->TS) * (q->M2 / q->TS),
+                                  q->M2 / q->CB,                     q->n1 / q->RB, q->n1 * (q->n2 / q->TYa)};
+        const int gy[kBStages] = {1, nj, nj, nj, nj, nj, nj, 1};
+        const int gz[kBStages] = {1, 1, 1, 2, 1, 1, 1, 1};
+        const size_t sm[kBStages] = {(size_t)q->TYf * fpad_len(q->nz) * ce,
+                                     (size_t)q->RB * fpad_len(q->M2) * ce,
+                                     (size_t)q->CB * fpad_len(q->M1) * ce,
+                                     (size_t)(q->TG + 2 * q->m - 1) * (q->TG + 2 * q->m + 1) * ce,
+                                     spread_tiles_bytes<T>(q->m),
+                                     (size_t)q->CB * fpad_len(q->M1) * ce,
+                                     (size_t)q->RB * fpad_len(q->M2) * ce,
+                                     (size_t)(fpad_len(q->nz) + q->h) * q->TYa * ce};
+        for (int st = 0; st < kBStages; ++st) {
+            H->start[st][i] = b->total[st];
+            H->gx[st][i] = gx[st];
+            H->gy[st][i] = gy[st];
+            const long long add = (long long)gx[st] * gy[st] * gz[st];
+            if ((long long)b->total[st] + add > (1LL << 30)) return fail(LAM_EUNSUPPORTED, "batch too large");
+            b->total[st] += (int)add;
+            smem[st] = std::max(smem[st], sm[st]);
+        }
+    }
+    for (int st = 0; st < kBStages; ++st) {
+        H->start[st][b->count] = b->total[st];
+        const int occ = st == kBZFwd   ? batch_occupancy_z<T>(true, b->mixed, smem[st])
+                        : st == kBZAdj ? batch_occupancy_z<T>(false, b->mixed, smem[st])
+                                       : batch_occupancy<T>(st, b->mixed, b->m, smem[st]);
+        if (occ < 1) return fail(LAM_EUNSUPPORTED, "batched stage %d does not fit on an SM (%zu bytes)", st, smem[st]);
+        b->L[st].grid = std::max(1, std::min(b->total[st], occ * nsm));
+        b->L[st].smem = smem[st];
+    }
+    if (cudaMalloc(&b->dev, sizeof(BatchTable<T>)) != cudaSuccess)
+        return fail(LAM_ENOMEM, "cudaMalloc of the batch table failed");
+    CK(cudaMemcpy(b->dev, H.get(), sizeof(BatchTable<T>), cudaMemcpyHostToDevice));
+    return LAM_OK;
+}
+
+template <typename T>
+lam_status batch_fwd_hat(const lam_batch* b, const void* const* in, void* const* out, cudaStream_t s) {
+    BatchPtrs ptrs{};
+    for (int i = 0; i < b->count; ++i) {
+        ptrs.in[i] = in[i];
+        ptrs.out[i] = out[i];
+    }
+    BatchTable<T>* dev = (BatchTable<T>*)b->dev;
+    CK(launch_batch_ptrs<T>(dev, ptrs, b->count, s));
+    CK(launch_batch_z<T>(dev, true, b->mixed, b->L[kBZFwd], s));
+    for (int st : {(int)kBRowFwd, (int)kBColFwd, (int)kBGather})
+        CK(launch_batch_plane<T>(dev, st, b->mixed, b->m, b->L[st], s));
+    return LAM_OK;
+}
+
+template <typename T>
+lam_status batch_adj_hat(const lam_batch* b, const void* const* in, void* const* out, cudaStream_t s) {
+    BatchPtrs ptrs{};
+    for (int i = 0; i < b->count; ++i) {
+        ptrs.in[i] = in[i];
+        ptrs.out[i] = out[i];
+    }
+    BatchTable<T>* dev = (BatchTable<T>*)b->dev;
+    CK(launch_batch_ptrs<T>(dev, ptrs, b->count, s));
+    for (int st : {(int)kBSpread, (int)kBColAdj, (int)kBRowAdj})
+        CK(launch_batch_plane<T>(dev, st, b->mixed, b->m, b->L[st], s));
+    CK(launch_batch_z<T>(dev, false, b->mixed, b->L[kBZAdj], s));
+    return LAM_OK;
+}
+
+// one ADMM outer iteration of every problem: the operators run batched, the
+// elementwise steps per problem (Section 2: LSP in the Algorithm 2 form, RSP,
+// multiplier and penalty updates), in the order admm_step uses
+template <typename T> lam_status batch_admm_step(const lam_batch* b, void* const* states, int n_inner, cudaStream_t s) {
+    std::vector<StatePtrs<T>> S;
+    std::vector<Admm<T>> ops;
+    for (int i = 0; i < b->count; ++i) {
+        S.push_back(ptrs<T>(b->plans[i], states[i]));
+        ops.push_back(admm_ops<T>(b->plans[i]));
+    }
+    const void* in[kMaxBatch];
+    void* out[kMaxBatch];
+    for (int k = 0; k < n_inner; ++k) {
+        for (int i = 0; i < b->count; ++i) {
+            in[i] = S[i].r;
+            out[i] = S[i].Gd;
+        }
+        if (lam_status st = batch_adj_hat<T>(b, in, out, s)) return st;
+        for (int i = 0; i < b->count; ++i) {
+            T* Gc = (k & 1) ? S[i].G1 : S[i].G0;
+            T* Gp = (k & 1) ? S[i].G0 : S[i].G1;
+            CK(ops[i].lsp_G(S[i].Gd, S[i].du, S[i].e, S[i].lam, S[i].p, Gp, Gc, k == 0, S[i].red, s));
+            CK(ops[i].lsp_p(Gc, S[i].p, S[i].red, s));
+            in[i] = S[i].p;
+            out[i] = S[i].Lp;
+        }
+        if (lam_status st = batch_fwd_hat<T>(b, in, out, s)) return st;
+        for (int i = 0; i < b->count; ++i)
+            CK(ops[i].lsp_update(S[i].du, S[i].u, S[i].p, k == 0, k == n_inner - 1, S[i].r, S[i].Lp,
+                                 b->plans[i]->ndata(), S[i].red, s));
+    }
+    for (int i = 0; i < b->count; ++i)
+        CK(ops[i].rsp(S[i].u, S[i].du, S[i].e, S[i].lam, S[i].dpsi, S[i].red, S[i].hist, kHistCap, s));
+    return LAM_OK;
+}
 
 // ---- allocation-free F_u2D (no counterpart in the paper) ----------------------
 // Some callers cannot give the library a workspace: code that runs inside a
@@ -1090,6 +1232,177 @@ lam_status lamx_u2d_fwd_static(const lam_plan* p, const void* u1, void* d_hat, c
     if (!u1 || !d_hat) return fail(LAM_EINVAL, "NULL array argument");
     cudaStream_t s = (cudaStream_t)stream;
     return DISPATCH(p, u2d_fwd_static_t<float>(p, u1, d_hat, sub, s), u2d_fwd_static_t<double>(p, u1, d_hat, sub, s));
+}
+
+// ---- batched operators and ADMM ------------------------------------------------
+
+lam_status lam_batch_create(lam_batch** out, const lam_plan* const* plans, void* const* ws, int count) {
+    if (!out) return fail(LAM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!plans || !ws) return fail(LAM_EINVAL, "NULL array argument");
+    if (count < 1 || count > kMaxBatch) return fail(LAM_EINVAL, "count = %d not in [1, %d]", count, kMaxBatch);
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    for (int i = 0; i < count; ++i) {
+        const lam_plan* q = plans[i];
+        if (!q || !ws[i]) return fail(LAM_EINVAL, "plan or workspace %d is NULL", i);
+        if (q->prec != plans[0]->prec || q->m != plans[0]->m)
+            return fail(LAM_EINVAL, "plan %d: every plan of a batch needs the same precision and half-width", i);
+        if (q->device != dev) return fail(LAM_EINVAL, "plan %d lives on device %d, not the current %d", i, q->device, dev);
+        if (q->TS != 32)
+            return fail(LAM_EUNSUPPORTED, "plan %d: batched adjoints use 32 x 32 spread tiles (n a multiple of 16)", i);
+        if (q->nbatch < q->njobs_pair)
+            return fail(LAM_EUNSUPPORTED, "plan %d: its workspace holds %d planes; a batch runs all %d plane jobs at once",
+                        i, q->nbatch, q->njobs_pair);
+    }
+    lam_batch* b = new lam_batch();
+    b->count = count;
+    b->prec = plans[0]->prec;
+    b->device = dev;
+    b->m = plans[0]->m;
+    for (int i = 0; i < count; ++i) {
+        const lam_plan* q = plans[i];
+        b->plans.push_back(q);
+        b->ws.push_back(ws[i]);
+        if (fft_mixed(fft_code(q->nz)) || fft_mixed(fft_code(q->M1))) b->mixed = true;
+    }
+    cudaError_t ce = b->prec == LAM_F32 ? configure_batch_plane<float>() : configure_batch_plane<double>();
+    if (!ce) ce = b->prec == LAM_F32 ? configure_batch_z<float>() : configure_batch_z<double>();
+    lam_status st = ce ? fail(LAM_ECUDA, "batched kernel configuration failed: %s", cudaGetErrorString(ce)) : LAM_OK;
+    if (!st) st = b->prec == LAM_F32 ? batch_build<float>(b) : batch_build<double>(b);
+    if (st) {
+        lam_batch_destroy(b);
+        return st;
+    }
+    *out = b;
+    return LAM_OK;
+}
+
+lam_status lam_batch_destroy(lam_batch* b) {
+    if (!b) return LAM_OK;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->dev) cudaFree(b->dev);
+    delete b;
+    return LAM_OK;
+}
+
+static lam_status check_batch_arrays(const lam_batch* b, const void* const* a, const void* const* c) {
+    if (!b) return fail(LAM_EINVAL, "batch is NULL");
+    if (!a || !c) return fail(LAM_EINVAL, "NULL array argument");
+    for (int i = 0; i < b->count; ++i)
+        if (!a[i] || !c[i]) return fail(LAM_EINVAL, "array %d is NULL", i);
+    return LAM_OK;
+}
+
+lam_status lam_forward_hat_batched(const lam_batch* b, const void* const* u, void* const* d_hat, void* stream) {
+    if (lam_status st = check_batch_arrays(b, u, (const void* const*)d_hat)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return b->prec == LAM_F32 ? batch_fwd_hat<float>(b, u, d_hat, s) : batch_fwd_hat<double>(b, u, d_hat, s);
+}
+
+lam_status lam_adjoint_hat_batched(const lam_batch* b, const void* const* d_hat, void* const* u, void* stream) {
+    if (lam_status st = check_batch_arrays(b, d_hat, (const void* const*)u)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    return b->prec == LAM_F32 ? batch_adj_hat<float>(b, d_hat, u, s) : batch_adj_hat<double>(b, d_hat, u, s);
+}
+
+lam_status lam_forward_batched(const lam_batch* b, const void* const* u, void* const* d, void* stream) {
+    if (lam_status st = lam_forward_hat_batched(b, u, d, stream)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int i = 0; i < b->count; ++i) {
+        const lam_plan* p = b->plans[i];
+        const double sc = 1.0 / ((double)p->h * p->w);
+        if (lam_status st = DISPATCH(p, fft2d<float>(p, (const C<float>*)d[i], (C<float>*)d[i], +1, (float)sc, s),
+                                     fft2d<double>(p, (const C<double>*)d[i], (C<double>*)d[i], +1, sc, s)))
+            return st;
+    }
+    return LAM_OK;
+}
+
+lam_status lam_adjoint_batched(const lam_batch* b, const void* const* d, void* const* u, void* stream) {
+    if (lam_status st = check_batch_arrays(b, d, (const void* const*)u)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const void* tmp[kMaxBatch];
+    for (int i = 0; i < b->count; ++i) {
+        const lam_plan* p = b->plans[i];
+        void* t = (char*)b->ws[i] + p->ws_tmp;
+        const double sc = 1.0 / ((double)p->h * p->w);
+        if (lam_status st = DISPATCH(p, fft2d<float>(p, (const C<float>*)d[i], (C<float>*)t, -1, (float)sc, s),
+                                     fft2d<double>(p, (const C<double>*)d[i], (C<double>*)t, -1, sc, s)))
+            return st;
+        tmp[i] = t;
+    }
+    return lam_adjoint_hat_batched(b, tmp, u, stream);
+}
+
+lam_status admm_run_batched(lam_batch* b, void* const* states, int iters, int use_graph, void* stream) {
+    if (!b) return fail(LAM_EINVAL, "batch is NULL");
+    if (!states) return fail(LAM_EINVAL, "states is NULL");
+    if (iters < 0) return fail(LAM_EINVAL, "iters = %d", iters);
+    int n_inner = -1;
+    for (int i = 0; i < b->count; ++i) {
+        if (!states[i]) return fail(LAM_EINVAL, "state %d is NULL", i);
+        AdmmHost* h;
+        if (lam_status st = lookup(b->plans[i], states[i], &h)) return st;
+        if (n_inner >= 0 && h->n_inner != n_inner)
+            return fail(LAM_EINVAL, "state %d: every state of a batch needs the same number of CG steps", i);
+        n_inner = h->n_inner;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    auto step = [&]() -> lam_status {
+        return b->prec == LAM_F32 ? batch_admm_step<float>(b, states, n_inner, s)
+                                  : batch_admm_step<double>(b, states, n_inner, s);
+    };
+    if (!use_graph) {
+        for (int k = 0; k < iters; ++k)
+            if (lam_status st = step()) return st;
+        return LAM_OK;
+    }
+    if (s == nullptr) return fail(LAM_EINVAL, "graph replay needs a non-default stream");
+    std::vector<void*> sv(states, states + b->count);
+    if (!b->graph || b->graph_states != sv) {
+        if (b->graph) cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_states = sv;
+        CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        lam_status st = step();
+        cudaGraph_t g = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(s, &g);
+        if (st) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (ce != cudaSuccess) return fail(LAM_ECUDA, "stream capture failed: %s", cudaGetErrorString(ce));
+        size_t nn = 0;
+        b->graph_kernels = 0;
+        if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+            std::vector<cudaGraphNode_t> nodes(nn);
+            if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+                for (size_t i = 0; i < nn; ++i) {
+                    cudaGraphNodeType ty;
+                    if (cudaGraphNodeGetType(nodes[i], &ty) == cudaSuccess && ty == cudaGraphNodeTypeKernel)
+                        ++b->graph_kernels;
+                }
+        }
+        ce = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) return fail(LAM_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(ce));
+    }
+    for (int k = 0; k < iters; ++k) CK(cudaGraphLaunch(b->graph, s));
+    return LAM_OK;
+}
+
+lam_status lamx_batch_info(const lam_batch* b, int* out, int count) {
+    if (!b || !out) return fail(LAM_EINVAL, "NULL argument");
+    // per stage: total work items and persistent grid; then graph kernel nodes
+    int v[2 * kBStages + 1];
+    for (int st = 0; st < kBStages; ++st) {
+        v[2 * st] = b->total[st];
+        v[2 * st + 1] = b->L[st].grid;
+    }
+    v[2 * kBStages] = (int)b->graph_kernels;
+    for (int i = 0; i < count && i < 2 * kBStages + 1; ++i) out[i] = v[i];
+    return LAM_OK;
 }
 
 lam_status lamx_admm_graph_kernels(const lam_plan* p, void* state, size_t* count) {

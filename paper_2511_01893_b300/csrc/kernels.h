@@ -104,4 +104,54 @@ template <typename T>
 cudaError_t launch_fft2d_angles(const C<T>* in, C<T>* out, int dir, T scale, const Fft2dArgs<T>& a,
                                 cudaStream_t s);
 
+// ---- batched operators -------------------------------------------------------
+// A batch runs the plane-stage operators of up to kMaxBatch plans (of one
+// precision and half-width, uneven sizes) in one persistent launch per stage:
+// the grid strides over a work list that concatenates every problem's blocks;
+// a block finds its problem from the prefix table, copies that problem's
+// argument block into shared memory and runs the single-problem kernel body.
+// All of a problem's plane jobs go in one launch (its workspace holds them).
+constexpr int kMaxBatch = 32;
+enum BatchStage { kBZFwd = 0, kBRowFwd, kBColFwd, kBGather, kBSpread, kBColAdj, kBRowAdj, kBZAdj, kBStages };
+
+template <typename T> struct BatchTable {
+    int count;
+    int start[kBStages][kMaxBatch + 1];  // first work item of each problem (prefix of block counts)
+    int gx[kBStages][kMaxBatch];         // block grid of each problem: x extent,
+    int gy[kBStages][kMaxBatch];         // y extent (z follows)
+    Usfft1dArgs<T> zf[kMaxBatch];        // z stage, forward and transpose shapes
+    Usfft1dArgs<T> za[kMaxBatch];
+    Usfft2dArgs<T> a2[kMaxBatch];
+    C<T>* u1[kMaxBatch];                 // per-problem workspace pieces (bound at creation)
+    C<T>* P[kMaxBatch];
+    const void* in[kMaxBatch];           // per-call operands (set by launch_batch_ptrs)
+    void* out[kMaxBatch];
+};
+
+struct BatchPtrs {
+    const void* in[kMaxBatch];
+    void* out[kMaxBatch];
+};
+
+// launch facts of one batched stage, fixed at batch creation
+struct BatchLaunch {
+    int grid;       // persistent grid (blocks)
+    size_t smem;    // dynamic shared memory (maximum over the problems)
+};
+
+template <typename T> cudaError_t launch_batch_ptrs(BatchTable<T>* dev, const BatchPtrs& ptrs, int count, cudaStream_t s);
+// stage launches; mixed: some problem has radix-3/5 FFT lengths; m: half-width
+template <typename T>
+cudaError_t launch_batch_z(const BatchTable<T>* dev, bool fwd, bool mixed, const BatchLaunch& L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_batch_plane(const BatchTable<T>* dev, int stage, bool mixed, int m, const BatchLaunch& L,
+                               cudaStream_t s);
+// resident blocks per SM of a batched stage kernel with `smem` dynamic bytes
+template <typename T> int batch_occupancy(int stage, bool mixed, int m, size_t smem);
+template <typename T> int batch_occupancy_z(bool fwd, bool mixed, size_t smem);
+template <typename T> cudaError_t configure_batch_plane();
+// dynamic shared memory of the tile spread for half-width m
+template <typename T> size_t spread_tiles_bytes(int m);
+template <typename T> cudaError_t configure_batch_z();
+
 }  // namespace lam

@@ -35,15 +35,14 @@ template <typename T> __device__ __forceinline__ C<T> pz_at(const C<T>* E, const
 }
 
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kFftThreads) k_usfft1d_fwd(const T* __restrict__ u, C<T>* __restrict__ u1,
-                                                             Usfft1dArgs<T> a) {
+__device__ __forceinline__ void k_usfft1d_fwd_body(const T* __restrict__ u, C<T>* __restrict__ u1, const Usfft1dArgs<T>& a, int bx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);  // lines 2p (E) and 2p+1 (O), length nz
     const int nz = a.nz, npair = a.TY / 2;
     const int LS = fpad_len(nz);
     const int tiles = a.n2 / a.TY;
-    const int x = blockIdx.x / tiles;
-    const int y0 = (blockIdx.x - x * tiles) * a.TY;
+    const int x = bx / tiles;
+    const int y0 = (bx - x * tiles) * a.TY;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int twM0 = a.twstride;  // Nmax / M0
     const T* src = u + (size_t)x * nz * a.n2 + y0;
@@ -86,6 +85,12 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_fwd(const T* __restrict
     }
 }
 
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(kFftThreads) k_usfft1d_fwd(const T* __restrict__ u, C<T>* __restrict__ u1,
+                                                             Usfft1dArgs<T> a) {
+    k_usfft1d_fwd_body<T, MIXED>(u, u1, a, (int)blockIdx.x);
+}
+
 // Transpose.  For real outputs only the Hermitian part of each spread column
 // matters, Re IDFT(Q) = IDFT((Q[j] + conj Q[-j]) / 2), so two columns pack as
 //   Q_c[j] = (Q_a[j] + conj Q_a[-j]) / 2 + i (Q_b[j] + conj Q_b[-j]) / 2,
@@ -110,16 +115,15 @@ __device__ __forceinline__ C<T> spread_at(const C<T>* vals, int j, const Usfft1d
 }
 
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restrict__ u1, T* __restrict__ u,
-                                                             Usfft1dArgs<T> a) {
+__device__ __forceinline__ void k_usfft1d_adj_body(const C<T>* __restrict__ u1, T* __restrict__ u, const Usfft1dArgs<T>& a, int bx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nz = a.nz, npair = a.TY / 2, M0 = a.M0;
     const int LS = fpad_len(nz);
     C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);  // TY lines of length nz (E, O per pair)
     C<T>* vals = buf + a.TY * LS;                  // [TY][h]
     const int tiles = a.n2 / a.TY;
-    const int x = blockIdx.x / tiles;
-    const int y0 = (blockIdx.x - x * tiles) * a.TY;
+    const int x = bx / tiles;
+    const int y0 = (bx - x * tiles) * a.TY;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const C<T>* src = u1 + (size_t)x * a.n2 + y0;
     const size_t plane = (size_t)a.n1 * a.n2;
@@ -163,6 +167,12 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restr
     }
 }
 
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restrict__ u1, T* __restrict__ u,
+                                                             Usfft1dArgs<T> a) {
+    k_usfft1d_adj_body<T, MIXED>(u1, u, a, (int)blockIdx.x);
+}
+
 template <typename T>
 cudaError_t launch_usfft1d_fwd(const T* u, C<T>* u1, const Usfft1dArgs<T>& a, cudaStream_t s) {
     const size_t smem = (size_t)a.TY * fpad_len(a.nz) * sizeof(C<T>);
@@ -188,6 +198,68 @@ template <typename T> cudaError_t configure_usfft1d() {
     if (!e) e = cudaFuncSetAttribute(k_usfft1d_adj<T, true>, at, mx);
     return e;
 }
+
+// batched z stage: one persistent launch over every problem's column tiles
+template <typename A> __device__ __forceinline__ void copy_block_args_z(A& dst, const A& src) {
+    static_assert(sizeof(A) % 4 == 0, "argument block size");
+    const int* s = reinterpret_cast<const int*>(&src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(A) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+template <typename T, bool MIXED, bool FWD>
+__global__ void __launch_bounds__(kFftThreads) kb_z(const BatchTable<T>* __restrict__ bt) {
+    __shared__ Usfft1dArgs<T> sa;
+    constexpr int STAGE = FWD ? kBZFwd : kBZAdj;
+    const int* st = bt->start[STAGE];
+    const int total = st[bt->count];
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        int p = 0;
+        while (p + 1 < bt->count && w >= st[p + 1]) ++p;
+        copy_block_args_z(sa, FWD ? bt->zf[p] : bt->za[p]);
+        __syncthreads();
+        const int l = w - st[p];
+        if (FWD) k_usfft1d_fwd_body<T, MIXED>((const T*)bt->in[p], bt->u1[p], sa, l);
+        else k_usfft1d_adj_body<T, MIXED>(bt->u1[p], (T*)bt->out[p], sa, l);
+        __syncthreads();
+    }
+}
+
+template <typename T> static const void* batch_z_kernel(bool fwd, bool mixed) {
+    if (fwd) return mixed ? (const void*)kb_z<T, true, true> : (const void*)kb_z<T, false, true>;
+    return mixed ? (const void*)kb_z<T, true, false> : (const void*)kb_z<T, false, false>;
+}
+
+template <typename T>
+cudaError_t launch_batch_z(const BatchTable<T>* dev, bool fwd, bool mixed, const BatchLaunch& L, cudaStream_t s) {
+    void* args[] = {(void*)&dev};
+    return cudaLaunchKernel(batch_z_kernel<T>(fwd, mixed), dim3(L.grid), dim3(kFftThreads), args, L.smem, s);
+}
+
+template <typename T> int batch_occupancy_z(bool fwd, bool mixed, size_t smem) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_z_kernel<T>(fwd, mixed), kFftThreads, smem) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+template <typename T> cudaError_t configure_batch_z() {
+    cudaError_t e = cudaSuccess;
+    for (bool fwd : {false, true})
+        for (bool mixed : {false, true})
+            if (!e)
+                e = cudaFuncSetAttribute(batch_z_kernel<T>(fwd, mixed), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kMaxDynSmem - 2048);
+    return e;
+}
+
+template cudaError_t launch_batch_z<float>(const BatchTable<float>*, bool, bool, const BatchLaunch&, cudaStream_t);
+template cudaError_t launch_batch_z<double>(const BatchTable<double>*, bool, bool, const BatchLaunch&, cudaStream_t);
+template int batch_occupancy_z<float>(bool, bool, size_t);
+template int batch_occupancy_z<double>(bool, bool, size_t);
+template cudaError_t configure_batch_z<float>();
+template cudaError_t configure_batch_z<double>();
 
 template cudaError_t launch_usfft1d_fwd<float>(const float*, C<float>*, const Usfft1dArgs<float>&, cudaStream_t);
 template cudaError_t launch_usfft1d_fwd<double>(const double*, C<double>*, const Usfft1dArgs<double>&, cudaStream_t);

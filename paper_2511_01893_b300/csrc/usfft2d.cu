@@ -37,12 +37,11 @@ __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(
 // --------------------------------------------------------------------------
 
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(const C<T>* __restrict__ u1, C<T>* __restrict__ P,
-                                                    int j0, Usfft2dArgs<T> a) {
+__device__ __forceinline__ void k_rowfft_fwd_body(const C<T>* __restrict__ u1, C<T>* __restrict__ P, int j0, const Usfft2dArgs<T>& a, int bx, int by) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    const int b = blockIdx.y, kv = a.jobs[j0 + b].x;
-    const int x0 = blockIdx.x * a.RB;
+    const int b = by, kv = a.jobs[j0 + b].x;
+    const int x0 = bx * a.RB;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int LS = fpad_len(a.M2);
     for (int i = tid; i < a.RB * LS; i += nthr) bufa[i] = cmake<T>(0, 0);
@@ -63,11 +62,17 @@ __global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(const C<T>* __restri
 }
 
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kFftThreads) k_colfft_fwd(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
+__global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(const C<T>* __restrict__ u1, C<T>* __restrict__ P,
+                                                    int j0, Usfft2dArgs<T> a) {
+    k_rowfft_fwd_body<T, MIXED>(u1, P, j0, a, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+template <typename T, bool MIXED>
+__device__ __forceinline__ void k_colfft_fwd_body(C<T>* __restrict__ P, const Usfft2dArgs<T>& a, int bx, int by) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    const int b = blockIdx.y;
-    const int c0 = blockIdx.x * a.CB;
+    const int b = by;
+    const int c0 = bx * a.CB;
     const int tid = threadIdx.x, nthr = blockDim.x;
     C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
     const int LS = fpad_len(a.M1);
@@ -87,11 +92,16 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_fwd(C<T>* __restrict__ P
 }
 
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kFftThreads) k_colfft_adj(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
+__global__ void __launch_bounds__(kFftThreads) k_colfft_fwd(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
+    k_colfft_fwd_body<T, MIXED>(P, a, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+template <typename T, bool MIXED>
+__device__ __forceinline__ void k_colfft_adj_body(C<T>* __restrict__ P, const Usfft2dArgs<T>& a, int bx, int by) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    const int b = blockIdx.y;
-    const int c0 = blockIdx.x * a.CB;
+    const int b = by;
+    const int c0 = bx * a.CB;
     const int tid = threadIdx.x, nthr = blockDim.x;
     C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
     const int LS = fpad_len(a.M1);
@@ -109,12 +119,16 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_adj(C<T>* __restrict__ P
 }
 
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kFftThreads) k_rowfft_adj(const C<T>* __restrict__ P, C<T>* __restrict__ u1,
-                                                    int j0, Usfft2dArgs<T> a) {
+__global__ void __launch_bounds__(kFftThreads) k_colfft_adj(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
+    k_colfft_adj_body<T, MIXED>(P, a, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+template <typename T, bool MIXED>
+__device__ __forceinline__ void k_rowfft_adj_body(const C<T>* __restrict__ P, C<T>* __restrict__ u1, int j0, const Usfft2dArgs<T>& a, int bx, int by) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
-    const int b = blockIdx.y, kv = a.jobs[j0 + b].x;
-    const int x0 = blockIdx.x * a.RB;
+    const int b = by, kv = a.jobs[j0 + b].x;
+    const int x0 = bx * a.RB;
     const int tid = threadIdx.x, nthr = blockDim.x;
     const C<T>* pl = P + (size_t)b * a.M1 * a.M2;
     const int LS = fpad_len(a.M2);
@@ -130,6 +144,12 @@ __global__ void __launch_bounds__(kFftThreads) k_rowfft_adj(const C<T>* __restri
         const T s = a.d1[x0 + r] * a.d2[y];
         dst[i] = cscale(bufa[r * LS + fpad(wrap(y - a.n2 / 2, a.M2))], s);
     }
+}
+
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(kFftThreads) k_rowfft_adj(const C<T>* __restrict__ P, C<T>* __restrict__ u1,
+                                                    int j0, Usfft2dArgs<T> a) {
+    k_rowfft_adj_body<T, MIXED>(P, u1, j0, a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // --------------------------------------------------------------------------
@@ -257,8 +277,7 @@ __device__ __forceinline__ void for_tile_points(const Usfft2dArgs<T>& a, int kvc
 // list flattened across lines.  Each point is
 // owned by exactly one (tile, image), so every output is written once.
 template <typename T, int TPB, int MH>
-__global__ void __launch_bounds__(TPB * 32) k_gather2d_tiled(const C<T>* __restrict__ P, C<T>* __restrict__ out,
-                                                             const C<T>* __restrict__ sub, int j0, Usfft2dArgs<T> a) {
+__device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P, C<T>* __restrict__ out, const C<T>* __restrict__ sub, int j0, const Usfft2dArgs<T>& a, int bx, int by, int bz) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int nt = 2 * MH;
     const int TS = a.TG;
@@ -266,12 +285,12 @@ __global__ void __launch_bounds__(TPB * 32) k_gather2d_tiled(const C<T>* __restr
     const int SW = TS + nt + 1;  // staged row stride (odd: lanes two rows apart hit different banks)
     const int warp = threadIdx.x >> 5;
     const int tiles_y = a.M2 / TS;
-    const int tile = blockIdx.x;
+    const int tile = bx;
     C<T>* st = reinterpret_cast<C<T>*>(smem_raw);
     const int tx0 = (tile / tiles_y) * TS, ty0 = (tile % tiles_y) * TS;
-    const int b = blockIdx.y;
+    const int b = by;
     const int2 job = a.jobs[j0 + b];
-    const bool mirror = blockIdx.z == 1;  // the conjugate-mirror plane of this job
+    const bool mirror = bz == 1;  // the conjugate-mirror plane of this job
     if (mirror && job.y < 0) return;
     const int kv = mirror ? job.y : job.x, kvc = kv - a.h / 2;
     const C<T>* pl = P + (size_t)b * a.M1 * a.M2;
@@ -345,6 +364,12 @@ __global__ void __launch_bounds__(TPB * 32) k_gather2d_tiled(const C<T>* __restr
             });
         }
     }
+}
+
+template <typename T, int TPB, int MH>
+__global__ void __launch_bounds__(TPB * 32) k_gather2d_tiled(const C<T>* __restrict__ P, C<T>* __restrict__ out,
+                                                             const C<T>* __restrict__ sub, int j0, Usfft2dArgs<T> a) {
+    k_gather2d_tiled_body<T, TPB, MH>(P, out, sub, j0, a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
 }
 
 // Cells are stored planar (real parts, then imaginary parts) with the column
@@ -573,8 +598,7 @@ struct alignas((N & (N - 1)) == 0 ? (N * sizeof(T) < 16 ? N * sizeof(T) : 16) : 
 };
 
 template <typename T, int NW, int MH>
-__global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_tiles(
-    const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, Usfft2dArgs<T> a) {
+__device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, const Usfft2dArgs<T>& a, int bx, int by) {
     constexpr int nt = 2 * MH;
     constexpr int RPP = 32 / nt;  // window rows per pass
     constexpr int NPASS = (nt + RPP - 1) / RPP;
@@ -597,9 +621,9 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
     for (int i = lane; i < ncell; i += 32) mine[i] = cmake<T>(0, 0);
     __syncwarp();
     const int tiles_y = a.M2 / TS;
-    const int tile = blockIdx.x;
+    const int tile = bx;
     const int tx0 = (tile / tiles_y) * TS, ty0 = (tile % tiles_y) * TS;
-    const int b = blockIdx.y;
+    const int b = by;
     const int2 job = a.jobs[j0 + b];
     const T hb = (T)(TS + 2 * a.m) * (T)0.5;
     const int rr = lane / nt, sy = lane - rr * nt;
@@ -719,6 +743,12 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
         }
         pl[(size_t)(tx0 + ccx) * a.M2 + ty0 + ccy] = sum;
     }
+}
+
+template <typename T, int NW, int MH>
+__global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_tiles(
+    const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, Usfft2dArgs<T> a) {
+    k_spread2d_tiles_body<T, NW, MH>(in, P, j0, a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // --------------------------------------------------------------------------
@@ -847,6 +877,155 @@ template <typename T> cudaError_t configure_usfft2d() {
 #undef LAM_A
     return e;
 }
+
+// ---------------------------------------------------------------------------
+// batched stages (one persistent launch per stage over a work list)
+// ---------------------------------------------------------------------------
+
+// copies an argument block (a plain struct) with the whole thread block
+template <typename A> __device__ __forceinline__ void copy_block_args(A& dst, const A& src) {
+    static_assert(sizeof(A) % 4 == 0, "argument block size");
+    const int* s = reinterpret_cast<const int*>(&src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(A) / 4); i += blockDim.x) d[i] = s[i];
+}
+
+// problem owning work item w (start[p] <= w < start[p + 1])
+__device__ __forceinline__ int batch_problem(const int* start, int count, int w) {
+    int p = 0;
+    while (p + 1 < count && w >= start[p + 1]) ++p;
+    return p;
+}
+
+constexpr size_t kBatchDynSmem = kMaxDynSmem - 2048;  // room for the static argument copy
+
+template <typename T>
+__global__ void kb_set_ptrs(BatchTable<T>* __restrict__ bt, BatchPtrs ptrs, int count) {
+    const int t = threadIdx.x;
+    if (t < count) {
+        bt->in[t] = ptrs.in[t];
+        bt->out[t] = ptrs.out[t];
+    }
+}
+
+template <typename T, bool MIXED, int STAGE>
+__global__ void __launch_bounds__(kFftThreads) kb_plane_fft(const BatchTable<T>* __restrict__ bt) {
+    __shared__ Usfft2dArgs<T> sa;
+    const int* st = bt->start[STAGE];
+    const int total = st[bt->count];
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        const int p = batch_problem(st, bt->count, w);
+        copy_block_args(sa, bt->a2[p]);
+        __syncthreads();
+        const int l = w - st[p], gx = bt->gx[STAGE][p];
+        const int bx = l % gx, by = l / gx;
+        if (STAGE == kBRowFwd) k_rowfft_fwd_body<T, MIXED>(bt->u1[p], bt->P[p], 0, sa, bx, by);
+        else if (STAGE == kBColFwd) k_colfft_fwd_body<T, MIXED>(bt->P[p], sa, bx, by);
+        else if (STAGE == kBColAdj) k_colfft_adj_body<T, MIXED>(bt->P[p], sa, bx, by);
+        else k_rowfft_adj_body<T, MIXED>(bt->P[p], bt->u1[p], 0, sa, bx, by);
+        __syncthreads();
+    }
+}
+
+template <typename T, int NW, int MH>
+__global__ void __launch_bounds__(NW * 32) kb_gather(const BatchTable<T>* __restrict__ bt) {
+    __shared__ Usfft2dArgs<T> sa;
+    const int* st = bt->start[kBGather];
+    const int total = st[bt->count];
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        const int p = batch_problem(st, bt->count, w);
+        copy_block_args(sa, bt->a2[p]);
+        __syncthreads();
+        const int l = w - st[p], gx = bt->gx[kBGather][p], gy = bt->gy[kBGather][p];
+        const int t = l / gx;
+        k_gather2d_tiled_body<T, NW, MH>(bt->P[p], (C<T>*)bt->out[p], nullptr, 0, sa, l - t * gx, t % gy, t / gy);
+        __syncthreads();
+    }
+}
+
+template <typename T, int NW, int MH>
+__global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) kb_spread(const BatchTable<T>* __restrict__ bt) {
+    __shared__ Usfft2dArgs<T> sa;
+    const int* st = bt->start[kBSpread];
+    const int total = st[bt->count];
+    for (int w = blockIdx.x; w < total; w += gridDim.x) {
+        const int p = batch_problem(st, bt->count, w);
+        copy_block_args(sa, bt->a2[p]);
+        __syncthreads();
+        const int l = w - st[p], gx = bt->gx[kBSpread][p];
+        k_spread2d_tiles_body<T, NW, MH>((const C<T>*)bt->in[p], bt->P[p], 0, sa, l % gx, l / gx);
+        __syncthreads();
+    }
+}
+
+template <typename T> cudaError_t launch_batch_ptrs(BatchTable<T>* dev, const BatchPtrs& ptrs, int count, cudaStream_t s) {
+    kb_set_ptrs<T><<<1, kMaxBatch, 0, s>>>(dev, ptrs, count);
+    return cudaGetLastError();
+}
+
+// the kernel of a batched plane stage, as a void pointer for occupancy queries
+template <typename T> const void* batch_plane_kernel(int stage, bool mixed, int m) {
+    constexpr int NW = kScatterWarps;
+#define LAM_FFTK(ST) return mixed ? (const void*)kb_plane_fft<T, true, ST> : (const void*)kb_plane_fft<T, false, ST>;
+    switch (stage) {
+        case kBRowFwd: LAM_FFTK(kBRowFwd)
+        case kBColFwd: LAM_FFTK(kBColFwd)
+        case kBColAdj: LAM_FFTK(kBColAdj)
+        case kBRowAdj: LAM_FFTK(kBRowAdj)
+        default: break;
+    }
+#undef LAM_FFTK
+#define LAM_MH(MH) case MH: return stage == kBGather ? (const void*)kb_gather<T, NW, MH> : (const void*)kb_spread<T, NW, MH>;
+    switch (m) {
+        LAM_MH(2) LAM_MH(3) LAM_MH(4) LAM_MH(5) LAM_MH(6) LAM_MH(7) LAM_MH(8)
+        default: return nullptr;
+    }
+#undef LAM_MH
+}
+
+template <typename T>
+cudaError_t launch_batch_plane(const BatchTable<T>* dev, int stage, bool mixed, int m, const BatchLaunch& L,
+                               cudaStream_t s) {
+    const void* k = batch_plane_kernel<T>(stage, mixed, m);
+    if (!k) return cudaErrorInvalidValue;
+    const int threads = (stage == kBGather || stage == kBSpread) ? kScatterWarps * 32 : kFftThreads;
+    void* args[] = {(void*)&dev};
+    return cudaLaunchKernel(k, dim3(L.grid), dim3(threads), args, L.smem, s);
+}
+
+template <typename T> int batch_occupancy(int stage, bool mixed, int m, size_t smem) {
+    const void* k = batch_plane_kernel<T>(stage, mixed, m);
+    const int threads = (stage == kBGather || stage == kBSpread) ? kScatterWarps * 32 : kFftThreads;
+    int nb = 0;
+    if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
+template <typename T> cudaError_t configure_batch_plane() {
+    cudaError_t e = cudaSuccess;
+    for (int stage : {kBRowFwd, kBColFwd, kBColAdj, kBRowAdj, kBGather, kBSpread})
+        for (bool mixed : {false, true})
+            for (int m = 2; m <= 8; ++m) {
+                const void* k = batch_plane_kernel<T>(stage, mixed, m);
+                if (!e && k) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBatchDynSmem);
+                if (stage != kBGather && stage != kBSpread) break;  // the FFT stages do not depend on m
+            }
+    return e;
+}
+
+template <typename T> size_t spread_tiles_bytes(int m) { return spread_tiles_smem<T>(kScatterWarps, m); }
+template size_t spread_tiles_bytes<float>(int);
+template size_t spread_tiles_bytes<double>(int);
+
+template cudaError_t launch_batch_ptrs<float>(BatchTable<float>*, const BatchPtrs&, int, cudaStream_t);
+template cudaError_t launch_batch_ptrs<double>(BatchTable<double>*, const BatchPtrs&, int, cudaStream_t);
+template cudaError_t launch_batch_plane<float>(const BatchTable<float>*, int, bool, int, const BatchLaunch&, cudaStream_t);
+template cudaError_t launch_batch_plane<double>(const BatchTable<double>*, int, bool, int, const BatchLaunch&,
+                                                cudaStream_t);
+template int batch_occupancy<float>(int, bool, int, size_t);
+template int batch_occupancy<double>(int, bool, int, size_t);
+template cudaError_t configure_batch_plane<float>();
+template cudaError_t configure_batch_plane<double>();
 
 template cudaError_t launch_usfft2d_fwd<float>(const C<float>*, C<float>*, C<float>*, const C<float>*, int, int,
                                                const Usfft2dArgs<float>&, cudaStream_t);

@@ -63,6 +63,14 @@ def lib() -> ctypes.CDLL:
             "lamx_u2d_fwd_static": [vp, vp, vp, vp, vp],
             "lamx_plan_info": [vp, ctypes.POINTER(i), i],
             "lamx_admm_graph_kernels": [vp, vp, ctypes.POINTER(sz)],
+            "lam_batch_create": [ctypes.POINTER(vp), vp, vp, i],
+            "lam_batch_destroy": [vp],
+            "lam_forward_hat_batched": [vp, vp, vp, vp],
+            "lam_adjoint_hat_batched": [vp, vp, vp, vp],
+            "lam_forward_batched": [vp, vp, vp, vp],
+            "lam_adjoint_batched": [vp, vp, vp, vp],
+            "admm_run_batched": [vp, vp, i, i, vp],
+            "lamx_batch_info": [vp, ctypes.POINTER(i), i],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -384,6 +392,65 @@ class Admm:
 
     def status(self) -> int:
         return lib().admm_status(self.plan._h, _ptr(self.state), _stream())
+
+
+def _ptr_array(items):
+    return (ctypes.c_void_p * len(items))(*[t.data_ptr() if isinstance(t, torch.Tensor) else t for t in items])
+
+
+class Batch:
+    """Several plans run together: every plane-stage step of L_hat / L_hat^H is
+    one persistent launch over all problems (lam_batch_create)."""
+
+    STAGES = ["z_fwd", "row_fwd", "col_fwd", "gather", "spread", "col_adj", "row_adj", "z_adj"]
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        hs = (ctypes.c_void_p * len(self.plans))(*[p._h.value for p in self.plans])
+        ws = _ptr_array([p.ws for p in self.plans])
+        h_ = ctypes.c_void_p()
+        _check(lib().lam_batch_create(ctypes.byref(h_), hs, ws, len(self.plans)), "lam_batch_create")
+        self._h = h_
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.lam_batch_destroy(h)
+
+    def _run(self, name, xs, in_kind, out_kind):
+        xs = [p._inp(x, p.rdtype if in_kind == "vol" else p.cdtype, p.vol_shape if in_kind == "vol" else p.data_shape)
+              for p, x in zip(self.plans, xs)]
+        outs = [p._vol() if out_kind == "vol" else p._data() for p in self.plans]
+        _check(getattr(lib(), name)(self._h, _ptr_array(xs), _ptr_array(outs), _stream()), name)
+        return outs
+
+    def forward_hat(self, us):
+        return self._run("lam_forward_hat_batched", us, "vol", "data")
+
+    def adjoint_hat(self, ds):
+        return self._run("lam_adjoint_hat_batched", ds, "data", "vol")
+
+    def forward(self, us):
+        return self._run("lam_forward_batched", us, "vol", "data")
+
+    def adjoint(self, ds):
+        return self._run("lam_adjoint_batched", ds, "data", "vol")
+
+    def admm_run(self, admms, iters, graph=False):
+        """`iters` outer iterations of every Admm (one per plan, same order)."""
+        if len(admms) != len(self.plans) or any(a.plan is not p for a, p in zip(admms, self.plans)):
+            raise LaminoError("one Admm per plan of the batch, in order")
+        _check(lib().admm_run_batched(self._h, _ptr_array([a.state for a in admms]), int(iters), int(bool(graph)),
+                                      _stream()), "admm_run_batched")
+        for a in admms:
+            a.iters += iters
+
+    def info(self):
+        arr = (ctypes.c_int * 17)()
+        _check(lib().lamx_batch_info(self._h, arr, 17), "lamx_batch_info")
+        out = {st: {"work": arr[2 * k], "grid": arr[2 * k + 1]} for k, st in enumerate(self.STAGES)}
+        out["graph_kernels"] = arr[16]
+        return out
 
 
 def reconstruct(data, theta, phi, n, nz, iters, alpha, rho):
