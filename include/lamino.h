@@ -87,6 +87,18 @@ enum { LAM_OPT_FAST_ADJOINT = 1, LAM_OPT_ADJOINT_SPREAD = 2 };
 enum { LAM_SPREAD_TILES = 0, LAM_SPREAD_ATOMIC = 1, LAM_SPREAD_EXACT = 2 };
 lam_status lam_plan_set_option(lam_plan* plan, int option, int value);
 
+/* Autotuner (a set-up call; synchronises `stream`, not under capture): times
+ * L_hat + L_hat^H (mean of `reps` after one warm-up) for candidate launch
+ * shapes by coordinate descent: gather tile side (16 / 32 / 64, dividing
+ * 2n), rows and columns per plane-FFT block and columns per z-stage block
+ * (the plan's choice and its halvings), keeping the fastest in the plan.
+ * u, d_hat: device buffers of the plan's volume and data shapes (scratch,
+ * overwritten); ws: the workspace.  *seconds (if not NULL) receives the best
+ * pair time.  Results do not depend on the shapes.  ADMM graphs captured with
+ * the plan are invalidated.  Batches read the shapes at lam_batch_create. */
+lam_status lam_plan_autotune(lam_plan* plan, void* u, void* d_hat, void* ws, int reps, double* seconds,
+                             void* stream);
+
 /* Bytes of device scratch the operator calls need (ws argument).  The
  * workspace holds the z-transformed volume u1[h][n][n] (complex) and a batch
  * of padded planes.  Alignment: 256 bytes. */

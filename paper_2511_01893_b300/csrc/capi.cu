@@ -1234,6 +1234,92 @@ lam_status lamx_u2d_fwd_static(const lam_plan* p, const void* u1, void* d_hat, c
     return DISPATCH(p, u2d_fwd_static_t<float>(p, u1, d_hat, sub, s), u2d_fwd_static_t<double>(p, u1, d_hat, sub, s));
 }
 
+// ---- autotuner ------------------------------------------------------------------
+
+static void drop_admm_graphs(const lam_plan* p) {
+    std::lock_guard<std::mutex> lk(p->mu);
+    for (auto& kv : p->admm)
+        if (kv.second.graph) {
+            cudaGraphExecDestroy(kv.second.graph);
+            kv.second.graph = nullptr;
+        }
+}
+
+lam_status lam_plan_autotune(lam_plan* p, void* u, void* d_hat, void* ws, int reps, double* seconds, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!u || !d_hat || !ws) return fail(LAM_EINVAL, "NULL array argument");
+    if (reps < 1) reps = 1;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cs;
+    CK(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return fail(LAM_EINVAL, "autotuning cannot run under stream capture");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(LAM_ECUDA, "cudaEventCreate failed");
+    }
+    lam_status err = LAM_OK;
+    // one L_hat + L_hat^H pair: warm once, then the mean of reps
+    auto measure = [&](double* t) -> lam_status {
+        for (int r = -1; r < reps; ++r) {
+            if (r == 0 && cudaEventRecord(e0, s) != cudaSuccess) return fail(LAM_ECUDA, "cudaEventRecord failed");
+            if (lam_status st = lam_forward_hat(p, u, d_hat, nullptr, ws, stream)) return st;
+            if (lam_status st = lam_adjoint_hat(p, d_hat, u, ws, stream)) return st;
+        }
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        *t = ms * 1e-3 / reps;
+        return LAM_OK;
+    };
+    // coordinate descent over the launch shapes; candidates keep every
+    // divisibility and shared-memory rule the plan's own choice obeys
+    double best = 0;
+    err = measure(&best);
+    struct Knob {
+        int* v;
+        std::vector<int> cand;
+    };
+    std::vector<Knob> knobs;
+    {
+        std::vector<int> tg;
+        for (int c : {16, 32, 64})
+            if (p->M1 % c == 0 && p->M2 % c == 0) tg.push_back(c);
+        knobs.push_back({&p->TG, tg});
+        auto halves = [](int v, int lo) {
+            std::vector<int> c;
+            for (int x = v; x >= lo; x /= 2) c.push_back(x);
+            return c;
+        };
+        knobs.push_back({&p->RB, halves(p->RB, 1)});
+        knobs.push_back({&p->CB, halves(p->CB, 1)});
+        knobs.push_back({&p->TYf, halves(p->TYf, 2)});
+        knobs.push_back({&p->TYa, halves(p->TYa, 2)});
+    }
+    for (size_t k = 0; k < knobs.size() && !err; ++k) {
+        const int keep = *knobs[k].v;
+        int chosen = keep;
+        for (int c : knobs[k].cand) {
+            if (c == keep) continue;
+            *knobs[k].v = c;
+            double t = 0;
+            if ((err = measure(&t))) break;
+            if (t < best) {
+                best = t;
+                chosen = c;
+            }
+        }
+        *knobs[k].v = chosen;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    drop_admm_graphs(p);
+    if (seconds) *seconds = best;
+    return err;
+}
+
 // ---- batched operators and ADMM ------------------------------------------------
 
 lam_status lam_batch_create(lam_batch** out, const lam_plan* const* plans, void* const* ws, int count) {
@@ -1416,7 +1502,7 @@ lam_status lamx_admm_graph_kernels(const lam_plan* p, void* state, size_t* count
 
 lam_status lamx_plan_info(const lam_plan* p, int* out, int count) {
     if (lam_status st = check_plan(p)) return st;
-    const int v[] = {p->TYf, p->TYa, p->RB, p->CB, p->TS, p->nimg, p->nbatch, p->jmin, p->jmax, p->njobs_pair};
+    const int v[] = {p->TYf, p->TYa, p->RB, p->CB, p->TS, p->nimg, p->nbatch, p->jmin, p->jmax, p->njobs_pair, p->TG};
     const int nv = (int)(sizeof(v) / sizeof(v[0]));
     for (int i = 0; i < count && i < nv; ++i) out[i] = v[i];
     return LAM_OK;

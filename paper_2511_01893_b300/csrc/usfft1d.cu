@@ -213,11 +213,15 @@ __global__ void __launch_bounds__(kFftThreads) kb_z(const BatchTable<T>* __restr
     constexpr int STAGE = FWD ? kBZFwd : kBZAdj;
     const int* st = bt->start[STAGE];
     const int total = st[bt->count];
+    int cur = -1;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         int p = 0;
         while (p + 1 < bt->count && w >= st[p + 1]) ++p;
-        copy_block_args_z(sa, FWD ? bt->zf[p] : bt->za[p]);
-        __syncthreads();
+        if (p != cur) {  // block-uniform; the previous item ended with a barrier
+            copy_block_args_z(sa, FWD ? bt->zf[p] : bt->za[p]);
+            __syncthreads();
+            cur = p;
+        }
         const int l = w - st[p];
         if (FWD) k_usfft1d_fwd_body<T, MIXED>((const T*)bt->in[p], bt->u1[p], sa, l);
         else k_usfft1d_adj_body<T, MIXED>(bt->u1[p], (T*)bt->out[p], sa, l);

@@ -913,10 +913,14 @@ __global__ void __launch_bounds__(kFftThreads) kb_plane_fft(const BatchTable<T>*
     __shared__ Usfft2dArgs<T> sa;
     const int* st = bt->start[STAGE];
     const int total = st[bt->count];
+    int cur = -1;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int p = batch_problem(st, bt->count, w);
-        copy_block_args(sa, bt->a2[p]);
-        __syncthreads();
+        if (p != cur) {  // block-uniform; the previous item ended with a barrier
+            copy_block_args(sa, bt->a2[p]);
+            __syncthreads();
+            cur = p;
+        }
         const int l = w - st[p], gx = bt->gx[STAGE][p];
         const int bx = l % gx, by = l / gx;
         if (STAGE == kBRowFwd) k_rowfft_fwd_body<T, MIXED>(bt->u1[p], bt->P[p], 0, sa, bx, by);
@@ -932,10 +936,14 @@ __global__ void __launch_bounds__(NW * 32) kb_gather(const BatchTable<T>* __rest
     __shared__ Usfft2dArgs<T> sa;
     const int* st = bt->start[kBGather];
     const int total = st[bt->count];
+    int cur = -1;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int p = batch_problem(st, bt->count, w);
-        copy_block_args(sa, bt->a2[p]);
-        __syncthreads();
+        if (p != cur) {  // block-uniform; the previous item ended with a barrier
+            copy_block_args(sa, bt->a2[p]);
+            __syncthreads();
+            cur = p;
+        }
         const int l = w - st[p], gx = bt->gx[kBGather][p], gy = bt->gy[kBGather][p];
         const int t = l / gx;
         k_gather2d_tiled_body<T, NW, MH>(bt->P[p], (C<T>*)bt->out[p], nullptr, 0, sa, l - t * gx, t % gy, t / gy);
@@ -948,10 +956,14 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) kb_spread(con
     __shared__ Usfft2dArgs<T> sa;
     const int* st = bt->start[kBSpread];
     const int total = st[bt->count];
+    int cur = -1;
     for (int w = blockIdx.x; w < total; w += gridDim.x) {
         const int p = batch_problem(st, bt->count, w);
-        copy_block_args(sa, bt->a2[p]);
-        __syncthreads();
+        if (p != cur) {  // block-uniform; the previous item ended with a barrier
+            copy_block_args(sa, bt->a2[p]);
+            __syncthreads();
+            cur = p;
+        }
         const int l = w - st[p], gx = bt->gx[kBSpread][p];
         k_spread2d_tiles_body<T, NW, MH>((const C<T>*)bt->in[p], bt->P[p], 0, sa, l % gx, l / gx);
         __syncthreads();

@@ -63,6 +63,7 @@ def lib() -> ctypes.CDLL:
             "lamx_u2d_fwd_static": [vp, vp, vp, vp, vp],
             "lamx_plan_info": [vp, ctypes.POINTER(i), i],
             "lamx_admm_graph_kernels": [vp, vp, ctypes.POINTER(sz)],
+            "lam_plan_autotune": [vp, vp, vp, vp, i, ctypes.POINTER(d), vp],
             "lam_batch_create": [ctypes.POINTER(vp), vp, vp, i],
             "lam_batch_destroy": [vp],
             "lam_forward_hat_batched": [vp, vp, vp, vp],
@@ -284,11 +285,21 @@ class Plan:
         _check(lib().lamx_u2d_adj(self._h, _ptr(d_hat), _ptr(out), _ptr(self.ws), _stream()), "lamx_u2d_adj")
         return out
 
+    def autotune(self, reps=2):
+        """Pick launch shapes by timing L_hat + L_hat^H (scratch buffers are
+        allocated here); returns the best pair time in seconds."""
+        u = self._vol().normal_()
+        d = self._data()
+        t = ctypes.c_double()
+        _check(lib().lam_plan_autotune(self._h, _ptr(u), _ptr(d), _ptr(self.ws), int(reps), ctypes.byref(t),
+                                       _stream()), "lam_plan_autotune")
+        return t.value
+
     def info(self):
-        arr = (ctypes.c_int * 10)()
-        _check(lib().lamx_plan_info(self._h, arr, 10), "lamx_plan_info")
+        arr = (ctypes.c_int * 11)()
+        _check(lib().lamx_plan_info(self._h, arr, 11), "lamx_plan_info")
         keys = ["TY_fwd", "TY_adj", "rows_per_block", "cols_per_block", "tile", "images", "planes_per_batch",
-                "jmin", "jmax", "plane_jobs"]
+                "jmin", "jmax", "plane_jobs", "gather_tile"]
         return dict(zip(keys, list(arr)))
 
 

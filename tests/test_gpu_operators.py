@@ -156,3 +156,18 @@ def test_adjoint_spreads_are_bitwise_reproducible():
     ref = olam.lam_adjoint(d.cpu().numpy(), g)
     assert rel(a, ref) < 1e-5
     assert rel(e1, ref) < 1e-5
+
+
+@pytest.mark.parametrize("n", [48, 64])
+def test_autotune_keeps_results_bitwise(n):
+    # launch shapes change only how lines and points are grouped into blocks
+    plan, g = plan_and_geom(n, n // 2, n, n, n, 0.4, "f32")
+    u = torch.from_numpy(rand_vol(n, n // 2, 19)).cuda().float()
+    d = torch.from_numpy(rand_data(n, n, n, 20)).cuda().to(torch.complex64)
+    f0, a0 = plan.forward(u), plan.adjoint(d)
+    t = plan.autotune(reps=1)
+    assert t > 0
+    info = plan.info()
+    assert info["gather_tile"] in (16, 32, 64) and (2 * n) % info["gather_tile"] == 0
+    assert torch.equal(plan.forward(u), f0)
+    assert torch.equal(plan.adjoint(d), a0)
