@@ -72,6 +72,50 @@ def lhat_bytes(n, nz, h, w, T):
 # multi-rank timing (replicas: no data-path collective; only the clock is reduced)
 # ---------------------------------------------------------------------------
 
+def lhat_flops(n, nz, h, w, T, m=4):
+    """Algorithmic FP32 flops of one L-hat (5 N log2 N per complex FFT of
+    length N): the z stage's n^2 FFTs of length 2 nz; per kv plane n row FFTs
+    and 2n column FFTs of length 2n (zero rows pruned); the 2D gather's
+    (2m)^2 taps x 4 flops + 4m weight exponentials per slice point; the 1D
+    gather's 2m taps x 4 flops per (x, kv, y).  L-hat^H has the same count."""
+    M0, M = 2 * nz, 2 * n
+    z = n * n * 5 * M0 * np.log2(M0)
+    planes = h * (n + M) * 5 * M * np.log2(M)
+    g2 = T * h * w * ((2 * m) ** 2 * 4 + 4 * m)
+    g1 = n * n * h * 2 * m * 4
+    return float(z + planes + g2 + g1)
+
+
+def plane_fft_comparator(plan, glam, dev, stream, reps=3):
+    """The forward's plane FFTs (ours: deapodise, pad, pruned row FFTs, column
+    FFTs) against torch.fft.fft2 (cuFFT) on the same number of zero-padded
+    2n x 2n planes; cuFFT is a comparator only, never on the path."""
+    import torch
+    n = plan.n
+    nb = min(32, plan.info()["planes_per_batch"], plan.h)
+    u1 = torch.randn((nb, n, n), dtype=torch.complex64, device=dev)
+    P = torch.empty((nb, 2 * n, 2 * n), dtype=torch.complex64, device=dev)
+    Pin = torch.zeros((nb, 2 * n, 2 * n), dtype=torch.complex64, device=dev)
+    Pin[:, n // 2:n // 2 + n, n // 2:n // 2 + n] = u1
+    times = {"ours": [], "cufft": []}
+    with torch.cuda.stream(stream):
+        for r in range(reps + 1):
+            for kind in ("ours", "cufft"):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if kind == "ours":
+                    plan.plane_ffts(u1, P)
+                else:
+                    torch.fft.fft2(Pin)
+                e1.record(stream)
+                stream.synchronize()
+                if r:
+                    times[kind].append(e0.elapsed_time(e1) / 1e3 / nb)
+    return {"planes": nb, "ours_s_per_plane": statistics.median(times["ours"]),
+            "cufft_fft2_s_per_plane": statistics.median(times["cufft"]),
+            "note": "ours prunes the n zero rows and folds deapodisation; cuFFT does the full padded 2D FFT"}
+
+
 def job_seconds_per_iter(t_local, steps, world, device=None):
     """Whole-job seconds per ADMM iteration over `world` independent replicas:
     the slowest rank's time divided by the iterations all ranks completed."""
@@ -479,6 +523,10 @@ def run_ours(args):
         if tj.get("size") == n:
             traffic = tj.get("lhat_pair_dram_bytes")
     del p, out_c, out_r
+    fma = glam.fma_peak(dev)
+    op_flops = 2 * lhat_flops(n, nz, h, w, T)
+    alu_achieved = op_flops / (t_fwd + t_adj)
+    comparator = plane_fft_comparator(plan, glam, dev, stream) if rank == 0 else None
 
     line = {
         "metric": "ADMM-TV seconds per iteration", "value": s_per_iter, "unit": "s/iter", "n_gpus": world,
@@ -491,6 +539,10 @@ def run_ours(args):
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "kernel": "L-hat + L-hat^H operator pair (all stage kernels)",
                      "algorithmic_bytes": op_bytes, "t_lhat_s": t_fwd, "t_lhat_adj_s": t_adj},
+        "roofline_alu": {"bound": "alu", "unit": "TFLOP/s", "achieved": alu_achieved / 1e12,
+                         "peak": fma / 1e12, "frac": alu_achieved / fma, "peak_source": "measured FMA probe",
+                         "kernel": "L-hat + L-hat^H operator pair", "algorithmic_flops": op_flops},
+        "plane_fft_comparator": comparator,
         "gpu_launches": launches_per_step * args.steps,
         "admm": {"status": status, "objective": sc["objective"], "rho": sc["rho"], "iters_done": sc["iter"]},
     }

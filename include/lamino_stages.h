@@ -58,6 +58,18 @@ lam_status lamx_plan_info(const lam_plan* plan, int* out, int count);
  * ADMM graph (0 before the first graph run). */
 lam_status lamx_batch_info(const lam_batch* batch, int* out, int count);
 
+/* The forward's plane FFTs alone: planes j0 .. j0 + nb - 1 of u1 (complex
+ * [h][n][n]) deapodised, padded to 2n x 2n and transformed (rows, then
+ * columns) into P (complex [nb][2n][2n], device).  For timing against
+ * library FFTs. */
+lam_status lamx_plane_ffts(const lam_plan* plan, const void* u1, void* P, int j0, int nb, void* stream);
+
+/* FP32 FMA throughput of the current device (eight independent FMA chains
+ * per thread, 8 blocks of 256 threads per SM; CUDA-event timed, synchronises
+ * `stream`): *flops_per_s = 2 x FMAs / s.  sink: a device buffer of
+ * sink_floats >= 8 x SM-count floats (never written in practice). */
+lam_status lamx_fma_peak(void* sink, int sink_floats, double* flops_per_s, void* stream);
+
 /* Kernel nodes in the CUDA graph admm_run captured for this state (one outer
  * iteration); 0 before the first graph run. */
 lam_status lamx_admm_graph_kernels(const lam_plan* plan, void* state, size_t* count);

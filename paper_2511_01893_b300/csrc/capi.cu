@@ -237,6 +237,11 @@ template <typename T> lam_status build_tables(lam_plan* p, const double* theta) 
             j.y = -1;
             ja.push_back(j);
         }
+        // planes near kv = h/2 carry the densest tiles (every slice line passes
+        // close to the origin there): run them first, so their heaviest blocks
+        // start early instead of forming a tail
+        std::stable_sort(jp.begin(), jp.end(),
+                         [h](const int2& a, const int2& b) { return std::abs(a.x - h / 2) < std::abs(b.x - h / 2); });
         p->njobs_pair = (int)jp.size();
         p->jobs_pair = (int2*)upload(p, jp, &st);
         if (st) return st;
@@ -379,6 +384,13 @@ template <typename T> Fft2dArgs<T> argsfft(const lam_plan* p) {
 
 // ---- operator sequences ----------------------------------------------------
 
+// planes per launch: the workspace holds p->nbatch planes; split njobs into
+// equal launches (no small last batch)
+int even_batch(const lam_plan* p, int njobs) {
+    const int nlaunch = (njobs + p->nbatch - 1) / p->nbatch;
+    return (njobs + nlaunch - 1) / nlaunch;
+}
+
 template <typename T>
 lam_status fwd_hat(const lam_plan* p, const T* u, C<T>* out, const C<T>* sub, void* ws, cudaStream_t s) {
     char* w = (char*)ws;
@@ -386,8 +398,9 @@ lam_status fwd_hat(const lam_plan* p, const T* u, C<T>* out, const C<T>* sub, vo
     C<T>* P = (C<T>*)(w + p->ws_planes);
     CK(launch_usfft1d_fwd<T>(u, u1, args1d<T>(p, p->TYf, true), s));
     const Usfft2dArgs<T> a = args2d<T>(p, true);
-    for (int j0 = 0; j0 < p->njobs_pair; j0 += p->nbatch) {
-        const int nb = std::min(p->nbatch, p->njobs_pair - j0);
+    const int per = even_batch(p, p->njobs_pair);
+    for (int j0 = 0; j0 < p->njobs_pair; j0 += per) {
+        const int nb = std::min(per, p->njobs_pair - j0);
         CK(launch_usfft2d_fwd<T>(u1, P, out, sub, j0, nb, a, s));
     }
     return LAM_OK;
@@ -414,8 +427,9 @@ template <typename T> lam_status adj_hat(const lam_plan* p, const C<T>* in, T* u
     C<T>* P = (C<T>*)(w + p->ws_planes);
     Usfft2dArgs<T> a = args2d<T>(p, true);
     if (lam_status st = prep_scatter<T>(p, in, ws, s, a)) return st;
-    for (int j0 = 0; j0 < p->njobs_pair; j0 += p->nbatch) {
-        const int nb = std::min(p->nbatch, p->njobs_pair - j0);
+    const int per = even_batch(p, p->njobs_pair);
+    for (int j0 = 0; j0 < p->njobs_pair; j0 += per) {
+        const int nb = std::min(per, p->njobs_pair - j0);
         CK(launch_usfft2d_adj<T>(in, P, u1, j0, nb, a, s));
     }
     CK(launch_usfft1d_adj<T>(u1, u, args1d<T>(p, p->TYa, true), s));
@@ -1488,6 +1502,45 @@ lam_status lamx_batch_info(const lam_batch* b, int* out, int count) {
     }
     v[2 * kBStages] = (int)b->graph_kernels;
     for (int i = 0; i < count && i < 2 * kBStages + 1; ++i) out[i] = v[i];
+    return LAM_OK;
+}
+
+lam_status lamx_plane_ffts(const lam_plan* p, const void* u1, void* P, int j0, int nb, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!u1 || !P) return fail(LAM_EINVAL, "NULL array argument");
+    if (j0 < 0 || nb < 1 || j0 + nb > p->h) return fail(LAM_EINVAL, "planes %d + %d out of [0, %d)", j0, nb, p->h);
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(DISPATCH(p, launch_usfft2d_planes<float>((const C<float>*)u1, (C<float>*)P, j0, nb, args2d<float>(p, false), s),
+                launch_usfft2d_planes<double>((const C<double>*)u1, (C<double>*)P, j0, nb, args2d<double>(p, false),
+                                              s)));
+    return LAM_OK;
+}
+
+lam_status lamx_fma_peak(void* sink, int sink_floats, double* flops_per_s, void* stream) {
+    if (!sink || !flops_per_s) return fail(LAM_EINVAL, "NULL argument");
+    int dev = 0, nsm = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = nsm * 8, iters = 1 << 16;
+    if (sink_floats < blocks) return fail(LAM_EINVAL, "sink holds %d floats; %d needed", sink_floats, blocks);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(LAM_ECUDA, "cudaEventCreate failed");
+    }
+    cudaError_t e = launch_fma_peak((float*)sink, blocks, iters, s);
+    if (!e) e = cudaEventRecord(e0, s);
+    if (!e) e = launch_fma_peak((float*)sink, blocks, iters, s);
+    if (!e) e = cudaEventRecord(e1, s);
+    if (!e) e = cudaEventSynchronize(e1);
+    float ms = 0;
+    if (!e) e = cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (e) return fail(LAM_ECUDA, "FMA probe failed: %s", cudaGetErrorString(e));
+    *flops_per_s = 2.0 * 8.0 * iters * (double)blocks * 256 / (ms * 1e-3);
     return LAM_OK;
 }
 

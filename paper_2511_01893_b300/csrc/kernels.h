@@ -91,6 +91,9 @@ cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int kv0, int n
                                const Usfft2dArgs<T>& a, cudaStream_t s);
 
 // max(|re|, |im|) over n complex values into the device scalar *out
+template <typename T>
+cudaError_t launch_usfft2d_planes(const C<T>* u1, C<T>* P, int j0, int nb, const Usfft2dArgs<T>& a, cudaStream_t s);
+cudaError_t launch_fma_peak(float* sink, int blocks, int iters, cudaStream_t s);
 template <typename T> cudaError_t launch_absmax(const C<T>* in, long long n, T* out, cudaStream_t s);
 
 // ---- F_2D / F*_2D (centred, per angle) ----------------------------------------

@@ -784,6 +784,42 @@ cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* s
     return cudaGetLastError();
 }
 
+// the plane FFTs of the forward alone (deapodise, pad, row and column FFTs of
+// planes j0 .. j0 + nb - 1 into P), for timing against library FFTs
+template <typename T>
+cudaError_t launch_usfft2d_planes(const C<T>* u1, C<T>* P, int j0, int nb, const Usfft2dArgs<T>& a, cudaStream_t s) {
+    const size_t sr = (size_t)a.RB * fpad_len(a.M2) * sizeof(C<T>);
+    const size_t sc = (size_t)a.CB * fpad_len(a.M1) * sizeof(C<T>);
+    if (fft_mixed(a.fcM1) || fft_mixed(a.fcM2)) {
+        k_rowfft_fwd<T, true><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, j0, a);
+        k_colfft_fwd<T, true><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+    } else {
+        k_rowfft_fwd<T, false><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, j0, a);
+        k_colfft_fwd<T, false><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+    }
+    return cudaGetLastError();
+}
+
+// FP32 FMA throughput probe: eight independent FMA chains per thread
+__global__ void __launch_bounds__(256) k_fma_peak(float* sink, int iters, float a, float b) {
+    float x[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = (float)(threadIdx.x + k);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) x[k] = fmaf(x[k], a, b);
+    }
+    float t = 0;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) t += x[k];
+    if (t == 1.2345f) sink[blockIdx.x] = t;  // never true: keeps the chains live
+}
+
+cudaError_t launch_fma_peak(float* sink, int blocks, int iters, cudaStream_t s) {
+    k_fma_peak<<<blocks, 256, 0, s>>>(sink, iters, 0.99999994f, 1e-7f);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int j0, int nb, const Usfft2dArgs<T>& a,
                                cudaStream_t s) {
@@ -1043,6 +1079,10 @@ template cudaError_t launch_usfft2d_fwd<float>(const C<float>*, C<float>*, C<flo
                                                const Usfft2dArgs<float>&, cudaStream_t);
 template cudaError_t launch_usfft2d_fwd<double>(const C<double>*, C<double>*, C<double>*, const C<double>*, int,
                                                 int, const Usfft2dArgs<double>&, cudaStream_t);
+template cudaError_t launch_usfft2d_planes<float>(const C<float>*, C<float>*, int, int, const Usfft2dArgs<float>&,
+                                                  cudaStream_t);
+template cudaError_t launch_usfft2d_planes<double>(const C<double>*, C<double>*, int, int, const Usfft2dArgs<double>&,
+                                                   cudaStream_t);
 template cudaError_t launch_usfft2d_adj<float>(const C<float>*, C<float>*, C<float>*, int, int,
                                                const Usfft2dArgs<float>&, cudaStream_t);
 template cudaError_t launch_usfft2d_adj<double>(const C<double>*, C<double>*, C<double>*, int, int,

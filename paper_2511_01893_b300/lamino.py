@@ -64,6 +64,8 @@ def lib() -> ctypes.CDLL:
             "lamx_plan_info": [vp, ctypes.POINTER(i), i],
             "lamx_admm_graph_kernels": [vp, vp, ctypes.POINTER(sz)],
             "lam_plan_autotune": [vp, vp, vp, vp, i, ctypes.POINTER(d), vp],
+            "lamx_plane_ffts": [vp, vp, vp, i, i, vp],
+            "lamx_fma_peak": [vp, i, ctypes.POINTER(d), vp],
             "lam_batch_create": [ctypes.POINTER(vp), vp, vp, i],
             "lam_batch_destroy": [vp],
             "lam_forward_hat_batched": [vp, vp, vp, vp],
@@ -285,6 +287,13 @@ class Plan:
         _check(lib().lamx_u2d_adj(self._h, _ptr(d_hat), _ptr(out), _ptr(self.ws), _stream()), "lamx_u2d_adj")
         return out
 
+    def plane_ffts(self, u1, P, j0=0):
+        """The forward's plane FFTs alone for planes j0 .. j0 + len(P) - 1 of u1
+        (u1 needs at least j0 + len(P) planes) into P [nb][2n][2n]."""
+        _check(lib().lamx_plane_ffts(self._h, _ptr(u1), _ptr(P), int(j0), int(P.shape[0]), _stream()),
+               "lamx_plane_ffts")
+        return P
+
     def autotune(self, reps=2):
         """Pick launch shapes by timing L_hat + L_hat^H (scratch buffers are
         allocated here); returns the best pair time in seconds."""
@@ -403,6 +412,17 @@ class Admm:
 
     def status(self) -> int:
         return lib().admm_status(self.plan._h, _ptr(self.state), _stream())
+
+
+def fma_peak(device=None) -> float:
+    """Measured FP32 FMA throughput of the device (flop/s)."""
+    dev = torch.device("cuda" if device is None else device)
+    sink = torch.empty(8 * torch.cuda.get_device_properties(dev).multi_processor_count, dtype=torch.float32,
+                       device=dev)
+    out = ctypes.c_double()
+    with torch.cuda.device(dev):
+        _check(lib().lamx_fma_peak(_ptr(sink), sink.numel(), ctypes.byref(out), _stream()), "lamx_fma_peak")
+    return out.value
 
 
 def _ptr_array(items):
