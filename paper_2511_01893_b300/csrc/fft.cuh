@@ -200,10 +200,19 @@ __device__ __forceinline__ void twiddles(C<T>* wv, const C<T>* __restrict__ tw, 
     }
 }
 
-template <int R, int DIR, int MAXB, typename T>
+// q / d for a block-uniform divisor: a shift when d is a power of two (P2 says
+// it always is; otherwise it is tested), a division otherwise
+template <bool P2> __device__ __forceinline__ int udiv(int q, int d, int ld) {
+    if (P2 || (d & (d - 1)) == 0) return q >> ld;
+    return q / d;
+}
+__device__ __forceinline__ int ilog2_pow2(int d) { return __ffs(d) - 1; }
+
+template <int R, int DIR, int MAXB, typename T, bool P2>
 __device__ __forceinline__ void fft_stage_ip(C<T>* buf, int nlines, int lstride, int N, int Ns,
                                              const C<T>* __restrict__ tw, int twstride, int tid, int nthr) {
     const int nb = N / R;
+    const int lnb = ilog2_pow2(nb);
     const int total = nlines * nb;
     const int twstep = (N / (Ns * R)) * twstride;
     C<T> v[MAXB][R];
@@ -211,7 +220,7 @@ __device__ __forceinline__ void fft_stage_ip(C<T>* buf, int nlines, int lstride,
     for (int bb = 0; bb < MAXB; ++bb) {
         const int q = tid + bb * nthr;
         if (q < total) {
-            const int line = q / nb;
+            const int line = q / nb;  // (a shift here raises the register count past the budget)
             const int j = q - line * nb;
             const C<T>* s = buf + line * lstride;
 #pragma unroll
@@ -223,7 +232,7 @@ __device__ __forceinline__ void fft_stage_ip(C<T>* buf, int nlines, int lstride,
     for (int bb = 0; bb < MAXB; ++bb) {
         const int q = tid + bb * nthr;
         if (q < total) {
-            const int line = q / nb;
+            const int line = udiv<P2>(q, nb, lnb);
             const int j = q - line * nb;
             // Ns is a power of two in the radix-2/4/8 stages (they come first)
             const int k = (R == 3 || R == 5) ? j % Ns : (j & (Ns - 1));
@@ -268,25 +277,25 @@ __device__ __forceinline__ void fft_lines_ip(C<T>* buf, int nlines, int lstride,
     for (int c = code; c; c >>= 3) {
         switch (c & 7) {
             case 3:
-                fft_stage_ip<8, DIR, fft_stage_maxb(8, MAXB), T>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
+                fft_stage_ip<8, DIR, fft_stage_maxb(8, MAXB), T, !MIXED>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
                 Ns *= 8;
                 break;
             case 2:
-                fft_stage_ip<4, DIR, fft_stage_maxb(4, MAXB), T>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
+                fft_stage_ip<4, DIR, fft_stage_maxb(4, MAXB), T, !MIXED>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
                 Ns *= 4;
                 break;
             case 1:
-                fft_stage_ip<2, DIR, fft_stage_maxb(2, MAXB), T>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
+                fft_stage_ip<2, DIR, fft_stage_maxb(2, MAXB), T, !MIXED>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
                 Ns *= 2;
                 break;
             default:
                 if constexpr (MIXED) {
                     if ((c & 7) == 4) {
-                        fft_stage_ip<3, DIR, fft_stage_maxb(3, MAXB), T>(buf, nlines, lstride, N, Ns, tw, twstride,
+                        fft_stage_ip<3, DIR, fft_stage_maxb(3, MAXB), T, !MIXED>(buf, nlines, lstride, N, Ns, tw, twstride,
                                                                          tid, nthr);
                         Ns *= 3;
                     } else {
-                        fft_stage_ip<5, DIR, fft_stage_maxb(5, MAXB), T>(buf, nlines, lstride, N, Ns, tw, twstride,
+                        fft_stage_ip<5, DIR, fft_stage_maxb(5, MAXB), T, !MIXED>(buf, nlines, lstride, N, Ns, tw, twstride,
                                                                          tid, nthr);
                         Ns *= 5;
                     }

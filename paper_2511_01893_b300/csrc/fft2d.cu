@@ -22,14 +22,14 @@ __global__ void __launch_bounds__(kFftThreads) k_fft2d_rows(const C<T>* in, C<T>
     const size_t base = ((size_t)th * a.h + r0) * a.w;
     const int LS = fpad_len(a.w);
     for (int i = threadIdx.x; i < RB * a.w; i += blockDim.x) {
-        const int r = i / a.w, k = i - r * a.w;
+        const int r = udiv<!MIXED>(i, a.w, ilog2_pow2(a.w)), k = i - r * a.w;
         const C<T> v = in[base + i];
         bufa[r * LS + fpad(k)] = ((r0 + r + k) & 1) ? cmake<T>(-v.x, -v.y) : v;
     }
     __syncthreads();
     fft_lines_ip<DIR, FftMaxB<T>::value, T, MIXED>(bufa, RB, LS, a.w, a.fcw, a.tw, a.tww);
     for (int i = threadIdx.x; i < RB * a.w; i += blockDim.x) {
-        const int r = i / a.w, k = i - r * a.w;
+        const int r = udiv<!MIXED>(i, a.w, ilog2_pow2(a.w)), k = i - r * a.w;
         const C<T> v = bufa[r * LS + fpad(k)];
         out[base + i] = (k & 1) ? cmake<T>(-v.x, -v.y) : v;
     }
@@ -43,14 +43,14 @@ __global__ void __launch_bounds__(kFftThreads) k_fft2d_cols(C<T>* __restrict__ i
     C<T>* pl = io + (size_t)th * a.h * a.w + c0;
     const int LS = fpad_len(a.h);
     for (int i = threadIdx.x; i < a.h * CB; i += blockDim.x) {
-        const int r = i / CB, c = i - r * CB;
+        const int r = i >> ilog2_pow2(CB), c = i - r * CB;  // CB is a power of two
         bufa[c * LS + fpad(r)] = pl[(size_t)r * a.w + c];
     }
     __syncthreads();
     fft_lines_ip<DIR, FftMaxB<T>::value, T, MIXED>(bufa, CB, LS, a.h, a.fch, a.tw, a.twh);
     const int gsign = ((a.h / 2 + a.w / 2) & 1);
     for (int i = threadIdx.x; i < a.h * CB; i += blockDim.x) {
-        const int r = i / CB, c = i - r * CB;
+        const int r = i >> ilog2_pow2(CB), c = i - r * CB;  // CB is a power of two
         const C<T> v = bufa[c * LS + fpad(r)];
         const T s = ((r + gsign) & 1) ? -scale : scale;
         pl[(size_t)r * a.w + c] = cscale(v, s);

@@ -47,7 +47,7 @@ __device__ __forceinline__ void k_usfft1d_fwd_body(const T* __restrict__ u, C<T>
     const int twM0 = a.twstride;  // Nmax / M0
     const T* src = u + (size_t)x * nz * a.n2 + y0;
     for (int i = tid; i < nz * npair; i += nthr) {
-        const int z = i / npair, p = i - z * npair;
+        const int z = i >> ilog2_pow2(npair), p = i - z * npair;  // npair = TY / 2, a power of two
         const int xc = z - nz / 2;
         const T d = a.dz[z];
         const T va = src[(size_t)z * a.n2 + 2 * p] * d, vb = src[(size_t)z * a.n2 + 2 * p + 1] * d;
@@ -62,7 +62,7 @@ __device__ __forceinline__ void k_usfft1d_fwd_body(const T* __restrict__ u, C<T>
     C<T>* dst = u1 + (size_t)x * a.n2 + y0;
     const size_t plane = (size_t)a.n1 * a.n2;
     for (int i = tid; i < a.h * npair; i += nthr) {
-        const int kv = i / npair, p = i - kv * npair;
+        const int kv = i >> ilog2_pow2(npair), p = i - kv * npair;
         const C<T>* E = buf + (2 * p) * LS;
         const C<T>* O = E + LS;
         const int jb = a.j0z[kv] - a.m + 1;
@@ -128,14 +128,17 @@ __device__ __forceinline__ void k_usfft1d_adj_body(const C<T>* __restrict__ u1, 
     const C<T>* src = u1 + (size_t)x * a.n2 + y0;
     const size_t plane = (size_t)a.n1 * a.n2;
     for (int i = tid; i < a.h * a.TY; i += nthr) {
-        const int kv = i / a.TY, c = i - kv * a.TY;
+        const int kv = i >> ilog2_pow2(a.TY), c = i - kv * a.TY;  // TY is a power of two
         vals[c * a.h + kv] = (a.skip && a.skip[kv]) ? cmake<T>(0, 0) : src[kv * plane + c];
     }
     __syncthreads();
     const int nt = 2 * a.m;
     const int half = M0 / 2;
+    // i / (half + 1) through FP32: i < 2^24 and (i + 1/2) / (half + 1) stays at
+    // least 1 / (2 half + 2) away from an integer, far above the rounding error
+    const float rcp = 1.0f / (float)(half + 1);
     for (int i = tid; i < npair * (half + 1); i += nthr) {
-        const int p = i / (half + 1), j = i - p * (half + 1);
+        const int p = (int)(((float)i + 0.5f) * rcp), j = i - p * (half + 1);
         const int jm = wrap(-j, M0);
         const C<T>* va = vals + (2 * p) * a.h;
         const C<T>* vb = va + a.h;
@@ -154,7 +157,7 @@ __device__ __forceinline__ void k_usfft1d_adj_body(const C<T>* __restrict__ u1, 
     fft_lines_ip<+1, FftMaxB<T>::value, T, MIXED>(buf, a.TY, LS, nz, a.fcz, a.tw, 2 * a.twstride);
     T* dst = u + (size_t)x * nz * a.n2 + y0;
     for (int i = tid; i < nz * npair; i += nthr) {
-        const int z = i / npair, p = i - z * npair;
+        const int z = i >> ilog2_pow2(npair), p = i - z * npair;  // npair = TY / 2, a power of two
         const int xc = z - nz / 2;
         const int q = wrap(xc, nz);
         const C<T> e = buf[(2 * p) * LS + fpad(q)], o = buf[(2 * p + 1) * LS + fpad(q)];

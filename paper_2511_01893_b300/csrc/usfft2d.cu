@@ -48,7 +48,7 @@ __device__ __forceinline__ void k_rowfft_fwd_body(const C<T>* __restrict__ u1, C
     __syncthreads();
     const C<T>* src = u1 + ((size_t)kv * a.n1 + x0) * a.n2;
     for (int i = tid; i < a.RB * a.n2; i += nthr) {
-        const int r = i / a.n2, y = i - r * a.n2;
+        const int r = udiv<!MIXED>(i, a.n2, ilog2_pow2(a.n2)), y = i - r * a.n2;
         const T s = a.d1[x0 + r] * a.d2[y];
         bufa[r * LS + fpad(wrap(y - a.n2 / 2, a.M2))] = cscale(src[i], s);
     }
@@ -56,7 +56,7 @@ __device__ __forceinline__ void k_rowfft_fwd_body(const C<T>* __restrict__ u1, C
     fft_lines_ip<-1, FftMaxB<T>::value, T, MIXED>(bufa, a.RB, LS, a.M2, a.fcM2, a.tw, a.tw2);
     C<T>* dst = P + (size_t)b * a.M1 * a.M2;
     for (int i = tid; i < a.RB * a.M2; i += nthr) {
-        const int r = i / a.M2, j = i - r * a.M2;
+        const int r = udiv<!MIXED>(i, a.M2, ilog2_pow2(a.M2)), j = i - r * a.M2;
         dst[(size_t)wrap(x0 + r - a.n1 / 2, a.M1) * a.M2 + j] = bufa[r * LS + fpad(j)];
     }
 }
@@ -79,14 +79,14 @@ __device__ __forceinline__ void k_colfft_fwd_body(C<T>* __restrict__ P, const Us
     for (int i = tid; i < a.CB * LS; i += nthr) bufa[i] = cmake<T>(0, 0);
     __syncthreads();
     for (int i = tid; i < a.n1 * a.CB; i += nthr) {
-        const int x = i / a.CB, c = i - x * a.CB;
+        const int x = i >> ilog2_pow2(a.CB), c = i - x * a.CB;  // CB is a power of two
         const int row = wrap(x - a.n1 / 2, a.M1);
         bufa[c * LS + fpad(row)] = pl[(size_t)row * a.M2 + c];
     }
     __syncthreads();
     fft_lines_ip<-1, FftMaxB<T>::value, T, MIXED>(bufa, a.CB, LS, a.M1, a.fcM1, a.tw, a.tw1);
     for (int i = tid; i < a.M1 * a.CB; i += nthr) {
-        const int j = i / a.CB, c = i - j * a.CB;
+        const int j = i >> ilog2_pow2(a.CB), c = i - j * a.CB;
         pl[(size_t)j * a.M2 + c] = bufa[c * LS + fpad(j)];
     }
 }
@@ -106,13 +106,13 @@ __device__ __forceinline__ void k_colfft_adj_body(C<T>* __restrict__ P, const Us
     C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
     const int LS = fpad_len(a.M1);
     for (int i = tid; i < a.M1 * a.CB; i += nthr) {
-        const int j = i / a.CB, c = i - j * a.CB;
+        const int j = i >> ilog2_pow2(a.CB), c = i - j * a.CB;
         bufa[c * LS + fpad(j)] = pl[(size_t)j * a.M2 + c];
     }
     __syncthreads();
     fft_lines_ip<+1, FftMaxB<T>::value, T, MIXED>(bufa, a.CB, LS, a.M1, a.fcM1, a.tw, a.tw1);
     for (int i = tid; i < a.n1 * a.CB; i += nthr) {
-        const int x = i / a.CB, c = i - x * a.CB;
+        const int x = i >> ilog2_pow2(a.CB), c = i - x * a.CB;  // CB is a power of two
         const int row = wrap(x - a.n1 / 2, a.M1);
         pl[(size_t)row * a.M2 + c] = bufa[c * LS + fpad(row)];
     }
@@ -133,14 +133,14 @@ __device__ __forceinline__ void k_rowfft_adj_body(const C<T>* __restrict__ P, C<
     const C<T>* pl = P + (size_t)b * a.M1 * a.M2;
     const int LS = fpad_len(a.M2);
     for (int i = tid; i < a.RB * a.M2; i += nthr) {
-        const int r = i / a.M2, j = i - r * a.M2;
+        const int r = udiv<!MIXED>(i, a.M2, ilog2_pow2(a.M2)), j = i - r * a.M2;
         bufa[r * LS + fpad(j)] = pl[(size_t)wrap(x0 + r - a.n1 / 2, a.M1) * a.M2 + j];
     }
     __syncthreads();
     fft_lines_ip<+1, FftMaxB<T>::value, T, MIXED>(bufa, a.RB, LS, a.M2, a.fcM2, a.tw, a.tw2);
     C<T>* dst = u1 + ((size_t)kv * a.n1 + x0) * a.n2;
     for (int i = tid; i < a.RB * a.n2; i += nthr) {
-        const int r = i / a.n2, y = i - r * a.n2;
+        const int r = udiv<!MIXED>(i, a.n2, ilog2_pow2(a.n2)), y = i - r * a.n2;
         const T s = a.d1[x0 + r] * a.d2[y];
         dst[i] = cscale(bufa[r * LS + fpad(wrap(y - a.n2 / 2, a.M2))], s);
     }
@@ -561,7 +561,7 @@ __global__ void __launch_bounds__(TPB * 32, TPB >= 16 ? (sizeof(T) == 4 ? 2 : 1)
 // order: the result does not depend on scheduling.
 // Records are stored transposed with a row pitch of 33 (lane-major writes and
 // per-row reads both free of bank conflicts); a lane's x weights for all its
-// passes are adjacent.  Tile cells are complex, row-major, with the column
+// passes sit next to the window origin, one load.  Tile cells are complex, row-major, with the column
 // XOR-swizzled by the row's parity: the 4-row x 8-column block of one pass
 // then covers 16 distinct pairs of banks (FP32), two lanes per pair, the
 // minimum for 256 bytes.
@@ -569,13 +569,28 @@ constexpr int kSpreadTS = 32;
 constexpr int kRecPitch = 33;
 __device__ __forceinline__ int swz_row(int x, int y) { return y ^ ((x & 1) << 3); }
 
-// x-weight slots per record: RPP rows x NPASS passes (>= 2m)
-__host__ __device__ constexpr int spread_wx_slots(int mh) {
-    return (32 / (2 * mh)) * ((2 * mh + 32 / (2 * mh) - 1) / (32 / (2 * mh)));
+// a lane's view of a point record: its x weights for every pass and the
+// window origin, read with one load (16 bytes for FP32 at m = 4)
+template <typename T, int NPASS> struct alignas(sizeof(T) * NPASS + 8 == 16 ? 16 : 8) SpreadRec {
+    T wx[NPASS];
+    int ox, oy;
+};
+__host__ __device__ constexpr int spread_rpp(int mh) { return 32 / (2 * mh); }
+__host__ __device__ constexpr int spread_npass(int mh) { return (2 * mh + spread_rpp(mh) - 1) / spread_rpp(mh); }
+template <typename T> size_t spread_rec_bytes(int mh) {
+    switch (spread_npass(mh)) {
+        case 1: return sizeof(SpreadRec<T, 1>);
+        case 2: return sizeof(SpreadRec<T, 2>);
+        case 3: return sizeof(SpreadRec<T, 3>);
+        case 4: return sizeof(SpreadRec<T, 4>);
+        case 6: return sizeof(SpreadRec<T, 6>);
+        case 7: return sizeof(SpreadRec<T, 7>);
+        default: return sizeof(SpreadRec<T, 8>);
+    }
 }
-template <typename T> __host__ __device__ constexpr size_t spread_tiles_smem(int nw, int mh) {
+template <typename T> size_t spread_tiles_smem(int nw, int mh) {
     return (size_t)nw * kSpreadTS * kSpreadTS * sizeof(C<T>) + (size_t)nw * (2 * mh) * kRecPitch * sizeof(C<T>) +
-           (size_t)nw * spread_wx_slots(mh) * kRecPitch * sizeof(T) + (size_t)nw * 32 * sizeof(int2);
+           (size_t)nw * spread_rpp(mh) * kRecPitch * spread_rec_bytes<T>(mh);
 }
 
 __device__ __forceinline__ void lds_c(unsigned ad, C<float>& v) {
@@ -591,11 +606,6 @@ __device__ __forceinline__ void sts_c(unsigned ad, const C<double>& v) {
     asm volatile("st.shared.v2.f64 [%0], {%1, %2};" ::"r"(ad), "d"(v.x), "d"(v.y) : "memory");
 }
 
-// N values loaded together: vector-aligned when N is a power of two
-template <typename T, int N>
-struct alignas((N & (N - 1)) == 0 ? (N * sizeof(T) < 16 ? N * sizeof(T) : 16) : sizeof(T)) Vec {
-    T v[N];
-};
 
 template <typename T, int NW, int MH>
 __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, const Usfft2dArgs<T>& a, int bx, int by) {
@@ -610,14 +620,12 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
     C<T>* tiles = reinterpret_cast<C<T>*>(smem_raw);  // [NW][ncell]
     C<T>* mine = tiles + (size_t)warp * ncell;
     unsigned char* recb = smem_raw + (size_t)NW * ncell * sizeof(C<T>);
-    // records: wyv[sy][pitch] (complex), wx[rr][pitch][NPASS], origin[32]
+    // records: wyv[sy][pitch] (complex), then rec[rr][pitch] (x weights of the
+    // lane row's passes + window origin)
+    typedef SpreadRec<T, NPASS> Rec;
     C<T>* r_wyv = reinterpret_cast<C<T>*>(recb) + (size_t)warp * nt * kRecPitch;
-    T* r_wx = reinterpret_cast<T*>(recb + (size_t)NW * nt * kRecPitch * sizeof(C<T>)) +
-              (size_t)warp * RPP * kRecPitch * NPASS;
-    static_assert(RPP * NPASS == spread_wx_slots(MH), "record layout");
-    int2* r_o = reinterpret_cast<int2*>(recb + (size_t)NW * nt * kRecPitch * sizeof(C<T>) +
-                                        (size_t)NW * RPP * NPASS * kRecPitch * sizeof(T)) +
-                warp * 32;
+    Rec* r_rec = reinterpret_cast<Rec*>(recb + (size_t)NW * nt * kRecPitch * sizeof(C<T>)) +
+                 (size_t)warp * RPP * kRecPitch;
     for (int i = lane; i < ncell; i += 32) mine[i] = cmake<T>(0, 0);
     __syncwarp();
     const int tiles_y = a.M2 / TS;
@@ -632,7 +640,7 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
     // lane-constant shared addresses of the record entries this lane reads
     const unsigned tile_ad = (unsigned)__cvta_generic_to_shared(mine);
     const unsigned wyv_ad = (unsigned)__cvta_generic_to_shared(r_wyv + sy * kRecPitch);
-    const T* wx_lane = r_wx + (size_t)rrc * kRecPitch * NPASS;
+    const Rec* rec_lane = r_rec + (size_t)rrc * kRecPitch;
     const unsigned lt = (1u << lane) - 1u;
     // pass 0: the job's own plane; pass 1: its mirror plane (conjugate values
     // spread around the negated positions, as in the atomic kernel)
@@ -680,28 +688,36 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
                         const int k = __popc(mask & lt);  // compacted record index
 #pragma unroll
                         for (int t = 0; t < nt; ++t) {
-                            const T dx = fx + (T)(MH - 1 - t);
-                            const int q = t / RPP, r = t - q * RPP;
-                            r_wx[((size_t)r * kRecPitch + k) * NPASS + q] = gexp(-dx * dx * a.inv4beta);
                             const T dy = fy + (T)(MH - 1 - t);
                             const T wy = gexp(-dy * dy * a.inv4beta);
                             r_wyv[t * kRecPitch + k] = cmake<T>(wy * v.x, wy * v.y);
                         }
-                        r_o[k] = make_int2(ox, oy);
+#pragma unroll
+                        for (int r = 0; r < RPP; ++r) {
+                            Rec rc;
+#pragma unroll
+                            for (int q = 0; q < NPASS; ++q) {
+                                const int t = q * RPP + r;
+                                const T dx = fx + (T)(MH - 1 - t);
+                                rc.wx[q] = t < nt ? gexp(-dx * dx * a.inv4beta) : (T)0;
+                            }
+                            rc.ox = ox;
+                            rc.oy = oy;
+                            r_rec[r * kRecPitch + k] = rc;
+                        }
                     }
                     __syncwarp();
                     const int cnt = __popc(mask);
-                    int2 o = r_o[0];
+                    Rec rc = rec_lane[0];
                     C<T> wv;
                     lds_c(wyv_ad, wv);
-                    Vec<T, NPASS> wx = *reinterpret_cast<const Vec<T, NPASS>*>(wx_lane);
                     for (int k = 0; k < cnt; ++k) {
                         // read the next record first (its latency overlaps the update)
                         const int kn = k + 1 < cnt ? k + 1 : k;
-                        const int2 no = r_o[kn];
+                        const Rec nrc = rec_lane[kn];
                         C<T> nwv;
                         lds_c(wyv_ad + kn * kCell, nwv);
-                        const Vec<T, NPASS> nwx = *reinterpret_cast<const Vec<T, NPASS>*>(wx_lane + kn * NPASS);
+                        const int2 o = make_int2(rc.ox, rc.oy);
                         const int cx0 = o.x + rrc, ccy = o.y + sy;
                         const int col = ccy ^ ((cx0 & 1) << 3);
                         const unsigned ad0 = tile_ad + (unsigned)(cx0 * TS + col) * kCell;
@@ -715,15 +731,14 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
                             if (yok && q * RPP + rr < nt && (unsigned)row < (unsigned)TS) {
                                 C<T> acc;
                                 lds_c(ad, acc);
-                                acc.x = fma(wx.v[q], wv.x, acc.x);
-                                acc.y = fma(wx.v[q], wv.y, acc.y);
+                                acc.x = fma(rc.wx[q], wv.x, acc.x);
+                                acc.y = fma(rc.wx[q], wv.y, acc.y);
                                 sts_c(ad, acc);
                             }
                         }
                         __syncwarp();
-                        o = no;
+                        rc = nrc;
                         wv = nwv;
-                        wx = nwx;
                     }
                 });
             }
