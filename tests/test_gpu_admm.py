@@ -83,13 +83,13 @@ def test_precision_workload_f32_vs_f64():
     the plain workload) is the reference at this size, where the oracle would
     need about an hour.
 
-    Measured FP32 drift (bitwise reproducible with the exact adjoint): 3e-7
-    after the first outer iteration, ~6e-5 once psi and lambda are active,
-    1.1-2.5e-4 from 8 to 32 iterations depending on the rounding of the
-    build.  It comes from FP32 storage of the CG residual updates L_hat p:
-    their rounding (eps |d_hat| in the first, large steps) is large against
-    the LSP gradient of later steps.  The 1e-4 target is missed by up to
-    ~2.5x here; the bounds guard against regressions.
+    The default (tile) spread is bitwise reproducible, so the FP32 trajectory
+    is fixed for a build: measured 2.0e-5 after 16 and 4.9e-5 after 32
+    iterations, inside the 1e-4 target.  The drift comes from FP32 rounding
+    of the CG residual updates L_hat p amplified by the LSP's weakly
+    determined directions; the exact fixed-point spread lands at 1.2e-4 /
+    2.5e-4 on the same problem (rounding differences alone), so the target
+    is checked for the default path only.
     """
     n = 256
     theta = inputs.angles(n)
@@ -108,8 +108,8 @@ def test_precision_workload_f32_vs_f64():
         assert a.status() == 0
         res[prec, 32] = a.u.double().clone()
         del a
-    assert rel(res["f32", 16], res["f64", 16]) < 3 * TOL_F32_ADMM
-    assert rel(res["f32", 32], res["f64", 32]) < 3 * TOL_F32_ADMM
+    assert rel(res["f32", 16], res["f64", 16]) < TOL_F32_ADMM
+    assert rel(res["f32", 32], res["f64", 32]) < TOL_F32_ADMM
 
 
 def test_graph_replay_is_bitwise_equal_to_eager(case):
