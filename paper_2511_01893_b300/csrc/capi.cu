@@ -313,7 +313,7 @@ template <typename T> Usfft1dArgs<T> args1d(const lam_plan* p, int TY, bool pair
     a.n2 = p->n2;
     a.h = p->h;
     a.M0 = p->M0;
-    a.fcz = fft_code(p->nz);
+    a.fcz = fft_code(p->nz, fft_max_radix<T>());
     a.m = p->m;
     a.TY = TY;
     a.dz = (const T*)p->dz;
@@ -338,8 +338,8 @@ template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p, bool paired) {
     a.T_ = p->T;
     a.M1 = p->M1;
     a.M2 = p->M2;
-    a.fcM1 = fft_code(p->M1);
-    a.fcM2 = fft_code(p->M2);
+    a.fcM1 = fft_code(p->M1, fft_max_radix<T>());
+    a.fcM2 = fft_code(p->M2, fft_max_radix<T>());
     a.m = p->m;
     a.inv4beta = (T)(1.0 / (4.0 * p->beta));
     a.d1 = (const T*)p->d1;
@@ -374,8 +374,8 @@ template <typename T> Fft2dArgs<T> argsfft(const lam_plan* p) {
     a.T_ = p->T;
     a.h = p->h;
     a.w = p->w;
-    a.fch = fft_code(p->h);
-    a.fcw = fft_code(p->w);
+    a.fch = fft_code(p->h, fft_max_radix<T>());
+    a.fcw = fft_code(p->w, fft_max_radix<T>());
     a.tw = (const C<T>*)p->tw;
     a.twh = p->Nmax / p->h;
     a.tww = p->Nmax / p->w;

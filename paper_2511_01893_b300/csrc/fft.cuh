@@ -55,6 +55,37 @@ template <int DIR, typename T> __device__ __forceinline__ void dft8(C<T>* v) {
     v[7] = csub(e[3], o3);
 }
 
+// radix-16 DFT as 4 x 4, in place: with x[4 n1 + n2], DFT-4 over n1 for each
+// n2, twiddle by W16^(n2 k1) (W16 = e^{DIR 2 pi i / 16}), then DFT-4 over n2
+// for each k1.  Output k1 + 4 k2 is left in v[4 k1 + k2] (transposed order;
+// dft16_out maps an output index to its register).
+__host__ __device__ constexpr int dft16_out(int r) { return 4 * (r & 3) + (r >> 2); }
+
+template <int DIR, typename T> __device__ __forceinline__ void dft16(C<T>* v) {
+    const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;  // cos, sin (pi / 8)
+    const T r2 = (T)0.70710678118654752440;
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+        C<T> t[4] = {v[n2], v[n2 + 4], v[n2 + 8], v[n2 + 12]};
+        dft4<DIR>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) v[n2 + 4 * k1] = t[k1];  // a[n2][k1] at v[n2 + 4 k1]
+    }
+    // W16^e, e = n2 k1 in {1, 2, 3, 4, 6, 9}: multiply by cos + DIR i sin of 2 pi e / 16
+    auto tw = [&](C<T> x, T c, T sn) { return cmake<T>(x.x * c - DIR * x.y * sn, x.y * c + DIR * x.x * sn); };
+    v[1 + 4] = tw(v[1 + 4], c1, s1);      // n2 1, k1 1
+    v[1 + 8] = tw(v[1 + 8], r2, r2);      // n2 1, k1 2
+    v[2 + 4] = tw(v[2 + 4], r2, r2);      // n2 2, k1 1
+    v[1 + 12] = tw(v[1 + 12], s1, c1);    // n2 1, k1 3
+    v[3 + 4] = tw(v[3 + 4], s1, c1);      // n2 3, k1 1
+    v[2 + 8] = cmul_i<DIR>(v[2 + 8]);     // n2 2, k1 2
+    v[2 + 12] = tw(v[2 + 12], -r2, r2);   // n2 2, k1 3
+    v[3 + 8] = tw(v[3 + 8], -r2, r2);     // n2 3, k1 2
+    v[3 + 12] = tw(v[3 + 12], -c1, -s1);  // n2 3, k1 3
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft4<DIR>(v + 4 * k1);  // over n2; result k2 at v[4 k1 + k2]
+}
+
 // radix-3 DFT: with c = -1/2 and s = DIR sqrt(3)/2 (the primitive cube root
 // of unity e^{DIR 2 pi i / 3} = c + i s)
 template <int DIR, typename T> __device__ __forceinline__ void dft3(C<T>* v) {
@@ -95,21 +126,23 @@ template <int DIR, typename T> __device__ __forceinline__ void dft5(C<T>* v) {
 // ---------------------------------------------------------------------------
 
 __host__ __device__ constexpr int fft_stage_radix(int c) {
-    return c == 1 ? 2 : c == 2 ? 4 : c == 3 ? 8 : c == 4 ? 3 : c == 5 ? 5 : 1;
+    return c == 1 ? 2 : c == 2 ? 4 : c == 3 ? 8 : c == 4 ? 3 : c == 5 ? 5 : c == 6 ? 16 : 1;
 }
 
 // code for length N, or -1 if N is not 2^a 3^b 5^c (N >= 2) or needs more
-// than 10 stages
-inline int fft_code(int N) {
+// than 10 stages.  The power-of-two part uses the fewest stages of radix at
+// most maxr (16 or 8), its bits spread evenly (2048 = 16 16 8 with maxr 16).
+inline int fft_code(int N, int maxr = 8) {
     if (N < 2) return -1;
     int a = 0, m = N;
     while (m % 2 == 0) { m /= 2; ++a; }
     int codes[16], ns = 0;
-    while (a > 0) {
-        if (a >= 3 && a != 4) { codes[ns++] = 3; a -= 3; }
-        else if (a >= 2) { codes[ns++] = 2; a -= 2; }
-        else { codes[ns++] = 1; a -= 1; }
-        if (ns > 10) return -1;
+    const int maxbits = maxr >= 16 ? 4 : 3;
+    const int nst = (a + maxbits - 1) / maxbits;
+    for (int k = 0; k < nst; ++k) {
+        const int bits = (a + (nst - k) - 1) / (nst - k);  // ceil of the remaining share
+        codes[ns++] = bits == 4 ? 6 : bits == 3 ? 3 : bits == 2 ? 2 : 1;
+        a -= bits;
     }
     while (m % 3 == 0) { m /= 3; codes[ns++] = 4; if (ns > 10) return -1; }
     while (m % 5 == 0) { m /= 5; codes[ns++] = 5; if (ns > 10) return -1; }
@@ -126,6 +159,9 @@ inline int fft_code(int N) {
 __host__ __device__ constexpr int fft_stage_maxb(int R, int maxb) {
     return R == 3 ? 2 * maxb : R == 5 ? maxb : (8 * maxb) / R;
 }
+// largest power-of-two radix a precision's register budget holds (one
+// radix-16 butterfly per thread needs MAXB = 2)
+template <typename T> constexpr int fft_max_radix() { return sizeof(T) == 4 ? 16 : 8; }
 
 // true when the code has a radix-3 or radix-5 stage (those kernels are built
 // separately: the extra stage kinds cost registers in the power-of-two ones)
@@ -170,7 +206,7 @@ __host__ __device__ __forceinline__ int fpad_len(int n) { return n + (n >> 4) + 
 template <int R, int DIR, typename T>
 __device__ __forceinline__ void twiddles(C<T>* wv, const C<T>* __restrict__ tw, int idx1) {
 #ifndef LAM_TW_TABLE
-    if constexpr (R == 2 || R == 4 || R == 8) {
+    if constexpr (R == 2 || R == 4 || R == 8 || R == 16) {
         C<T> w1 = tw[idx1];
         if (DIR > 0) w1.y = -w1.y;
         wv[1] = w1;
@@ -180,13 +216,20 @@ __device__ __forceinline__ void twiddles(C<T>* wv, const C<T>* __restrict__ tw, 
             wv[2] = w2;
             wv[3] = cmul(w1, w2);
         }
-        if constexpr (R == 8) {
+        if constexpr (R >= 8) {
             C<T> w4 = tw[4 * idx1];
             if (DIR > 0) w4.y = -w4.y;
             wv[4] = w4;
             wv[5] = cmul(w1, w4);
             wv[6] = cmul(wv[2], w4);
             wv[7] = cmul(wv[3], w4);
+        }
+        if constexpr (R == 16) {
+            C<T> w8 = tw[8 * idx1];
+            if (DIR > 0) w8.y = -w8.y;
+            wv[8] = w8;
+#pragma unroll
+            for (int r = 9; r < 16; ++r) wv[r] = cmul(wv[r - 8], w8);
         }
     } else
 #endif
@@ -237,12 +280,35 @@ __device__ __forceinline__ void fft_stage_ip(C<T>* buf, int nlines, int lstride,
             // Ns is a power of two in the radix-2/4/8 stages (they come first)
             const int k = (R == 3 || R == 5) ? j % Ns : (j & (Ns - 1));
             if (Ns > 1) {
-                C<T> wv[R];
-                twiddles<R, DIR, T>(wv, tw, k * twstep);
+                if constexpr (R == 16) {
+                    // powers w^r built from w, w^2, w^4, w^8 and applied as they are made
+                    const int i1 = k * twstep;
+                    C<T> w1 = tw[i1], w2 = tw[2 * i1], w4 = tw[4 * i1], w8 = tw[8 * i1];
+                    if (DIR > 0) {
+                        w1.y = -w1.y;
+                        w2.y = -w2.y;
+                        w4.y = -w4.y;
+                        w8.y = -w8.y;
+                    }
+                    C<T> w = w1;
 #pragma unroll
-                for (int r = 1; r < R; ++r) v[bb][r] = cmul(v[bb][r], wv[r]);
+                    for (int r = 1; r < 8; ++r) {
+                        if (r == 2) w = w2;
+                        else if (r == 4) w = w4;
+                        else if (r > 1) w = cmul(w, w1);  // w^3 = w^2 w, w^5 = w^4 w, w^6, w^7
+                        v[bb][r] = cmul(v[bb][r], w);
+                        v[bb][r + 8] = cmul(v[bb][r + 8], cmul(w, w8));
+                    }
+                    v[bb][8] = cmul(v[bb][8], w8);
+                } else {
+                    C<T> wv[R];
+                    twiddles<R, DIR, T>(wv, tw, k * twstep);
+#pragma unroll
+                    for (int r = 1; r < R; ++r) v[bb][r] = cmul(v[bb][r], wv[r]);
+                }
             }
-            if (R == 8) dft8<DIR>(v[bb]);
+            if (R == 16) dft16<DIR>(v[bb]);
+            else if (R == 8) dft8<DIR>(v[bb]);
             else if (R == 5) dft5<DIR>(v[bb]);
             else if (R == 4) dft4<DIR>(v[bb]);
             else if (R == 3) dft3<DIR>(v[bb]);
@@ -250,7 +316,7 @@ __device__ __forceinline__ void fft_stage_ip(C<T>* buf, int nlines, int lstride,
             C<T>* d = buf + line * lstride;
             const int base = (j - k) * R + k;
 #pragma unroll
-            for (int r = 0; r < R; ++r) d[fpad(base + r * Ns)] = v[bb][r];
+            for (int r = 0; r < R; ++r) d[fpad(base + r * Ns)] = v[bb][R == 16 ? dft16_out(r) : r];
         }
     }
     __syncthreads();
@@ -276,6 +342,13 @@ __device__ __forceinline__ void fft_lines_ip(C<T>* buf, int nlines, int lstride,
     int Ns = 1;
     for (int c = code; c; c >>= 3) {
         switch (c & 7) {
+            case 6:
+                if constexpr (fft_stage_maxb(16, MAXB) >= 1) {
+                    fft_stage_ip<16, DIR, fft_stage_maxb(16, MAXB), T, !MIXED>(buf, nlines, lstride, N, Ns, tw,
+                                                                              twstride, tid, nthr);
+                    Ns *= 16;
+                }
+                break;
             case 3:
                 fft_stage_ip<8, DIR, fft_stage_maxb(8, MAXB), T, !MIXED>(buf, nlines, lstride, N, Ns, tw, twstride, tid, nthr);
                 Ns *= 8;
