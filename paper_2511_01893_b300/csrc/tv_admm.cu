@@ -24,7 +24,8 @@
 // formed without cancellation.  psi itself is never stored.
 //
 // Reductions are deterministic: each block folds its elements (FP32 partial
-// sums of at most 8 terms per thread in the FP32 path, then FP64), writes one
+// sums of at most 8 terms per thread in the FP32 path, then FP64; threads take
+// four consecutive voxels per pass, so their loads overlap), writes one
 // FP64 partial per quantity, and the last block to finish sums the partials in
 // a fixed order.  Scalars (rho, beta, gamma, norms) stay in device memory so a
 // whole outer iteration can be replayed as a CUDA graph.
@@ -49,6 +50,23 @@ __device__ __forceinline__ long long astride(int a, const Vol& v) {
 }
 __device__ __forceinline__ int acoord(int a, int x, int z, int y) { return a == 0 ? x : (a == 1 ? z : y); }
 __device__ __forceinline__ int alen(int a, const Vol& v) { return a == 0 ? v.n1 : (a == 1 ? v.nz : v.n2); }
+
+// Grid-stride walk over the volume four voxels at a time: a thread takes four
+// consecutive y (n2 is a multiple of 4) and runs body(i, x, z, y) for each,
+// fully unrolled, so the four voxels' loads are independent and in flight
+// together.  after_quad() runs once per four voxels.
+template <typename F, typename G>
+__device__ __forceinline__ void for_voxel_quads(const Vol& v, F body, G after_quad) {
+    const long long nq = v.N >> 2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq; q += (long long)gridDim.x * blockDim.x) {
+        const long long i0 = q << 2;
+        int x, z, y;
+        v.coords(i0, x, z, y);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) body(i0 + k, x, z, y + k);
+        after_quad();
+    }
+}
 
 // ---------------------------------------------------------------------------
 // deterministic block + grid reduction of K doubles
@@ -148,9 +166,7 @@ __global__ void __launch_bounds__(256) k_lsp_G(const T* __restrict__ Gd, const T
     double acc[3] = {0, 0, 0};
     T loc[3] = {0, 0, 0};
     int cnt = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
-        int x, z, y;
-        v.coords(i, x, z, y);
+    for_voxel_quads(v, [&](long long i, int x, int z, int y) {
         auto q = [&](int a, long long j) -> T {
             T d = 0;
             if (!first) {
@@ -172,11 +188,12 @@ __global__ void __launch_bounds__(256) k_lsp_G(const T* __restrict__ Gd, const T
             loc[1] += pi * g;
             loc[2] += pi * Gprev[i];
         }
-        if (++cnt == 8) {
+    }, [&]() {
+        if (++cnt == 2) {  // FP32 partials of at most 8 terms
             for (int k = 0; k < 3; ++k) { acc[k] += (double)loc[k]; loc[k] = 0; }
             cnt = 0;
         }
-    }
+    });
     for (int k = 0; k < 3; ++k) acc[k] += (double)loc[k];
     reduce_store<3>(acc, r.partials, r.counter, r.sc, SC_GG);
 }
@@ -211,15 +228,14 @@ __global__ void __launch_bounds__(256) k_gradnorm2(const T* __restrict__ f, Admm
     double acc[1] = {0};
     T loc = 0;
     int cnt = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
-        int x, z, y;
-        v.coords(i, x, z, y);
+    for_voxel_quads(v, [&](long long i, int x, int z, int y) {
         for (int a = 0; a < 3; ++a) {
             const T d = fdiff(f, i, x, z, y, a, v);
             loc += d * d;
         }
-        if (++cnt == 8) { acc[0] += (double)loc; loc = 0; cnt = 0; }
-    }
+    }, [&]() {
+        if (++cnt == 2) { acc[0] += (double)loc; loc = 0; cnt = 0; }
+    });
     acc[0] += (double)loc;
     reduce_store<1>(acc, r.partials, r.counter, r.sc, dst);
 }
@@ -230,10 +246,21 @@ __global__ void __launch_bounds__(256) k_cnorm2(const C<T>* __restrict__ c, long
     double acc[1] = {0};
     T loc = 0;
     int cnt = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    // four consecutive values per thread and pass (n is a multiple of 4), so
+    // four independent loads are in flight per thread
+    const long long nq = n >> 2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq; q += (long long)gridDim.x * blockDim.x) {
+        C<T> z[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) z[k] = c[4 * q + k];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) loc += z[k].x * z[k].x + z[k].y * z[k].y;
+        if (++cnt == 2) { acc[0] += (double)loc; loc = 0; cnt = 0; }
+    }
+    for (long long i = 4 * nq + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
         const C<T> z = c[i];
         loc += z.x * z.x + z.y * z.y;
-        if (++cnt == 8) { acc[0] += (double)loc; loc = 0; cnt = 0; }
     }
     acc[0] += (double)loc;
     reduce_store<1>(acc, r.partials, r.counter, r.sc, dst);
@@ -298,9 +325,7 @@ __global__ void __launch_bounds__(256) k_rsp(const T* __restrict__ u, const T* _
     double acc[2] = {0, 0};
     T loc[2] = {0, 0};
     int cnt = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
-        int x, z, y;
-        v.coords(i, x, z, y);
+    for_voxel_quads(v, [&](long long i, int x, int z, int y) {
         T gu[3], zz[3], lm[3];
         T m2 = 0, g2 = 0;
         for (int a = 0; a < 3; ++a) {
@@ -325,13 +350,14 @@ __global__ void __launch_bounds__(256) k_rsp(const T* __restrict__ u, const T* _
         }
         loc[0] += e2;
         loc[1] += sqrt(g2);
-        if (++cnt == 8) {
+    }, [&]() {
+        if (++cnt == 2) {
             acc[0] += (double)loc[0];
             acc[1] += (double)loc[1];
             loc[0] = loc[1] = 0;
             cnt = 0;
         }
-    }
+    });
     acc[0] += (double)loc[0];
     acc[1] += (double)loc[1];
     reduce_store<2>(acc, r.partials, r.counter, r.sc, SC_RP2);
@@ -343,13 +369,12 @@ __global__ void __launch_bounds__(256) k_divnorm2(const T* __restrict__ p, AdmmR
     double acc[1] = {0};
     T loc = 0;
     int cnt = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v.N; i += (long long)gridDim.x * blockDim.x) {
-        int x, z, y;
-        v.coords(i, x, z, y);
+    for_voxel_quads(v, [&](long long i, int x, int z, int y) {
         const T d = div_at([&](int a, long long j) { return p[a * v.N + j]; }, i, x, z, y, v);
         loc += d * d;
-        if (++cnt == 8) { acc[0] += (double)loc; loc = 0; cnt = 0; }
-    }
+    }, [&]() {
+        if (++cnt == 2) { acc[0] += (double)loc; loc = 0; cnt = 0; }
+    });
     acc[0] += (double)loc;
     reduce_store<1>(acc, r.partials, r.counter, r.sc, SC_SD2);
 }
