@@ -208,35 +208,35 @@ __device__ __forceinline__ void clip_line(T A, T Cc, T bmin, T bmax, int& lo, in
 // ---------------------------------------------------------------------------
 // Warp-level enumeration of the slice points that may touch one tile image.
 // The warp tests 32 lines at a time against the tile's position box (lane
-// parallel), computes each crossing line's ku interval, scans the interval
-// lengths, and hands the flattened point list out 32 points at a time, one per
-// lane, across line boundaries.  fn(th, kuc, g) is called for each lane's
-// point (with active lanes first in each batch; inactive lanes get th = -1).
+// parallel, a distance test only) and appends the crossing lines to a per-warp
+// list in shared memory.  Each time 32 lines are listed (and once at the end)
+// it computes their ku intervals (clipping to the box), scans the interval
+// lengths and hands the flattened point list out 32 points at a time, one per
+// lane, across line boundaries.  Lines keep their order and points their ku
+// order, so the sequence of points a warp sees does not depend on how they
+// are batched.  fn(th, kuc) is called for each lane's point (active lanes
+// first in each batch; inactive lanes get th = -1), by all lanes together.
 // ---------------------------------------------------------------------------
-// Lines are dealt to the block's warps interleaved: warp w of nw tests lines
-// th = (base + lane) * nw + w, so the (clustered) crossing lines of a tile
-// spread evenly over the warps.
-template <typename T, typename F>
+template <typename T, int NW, typename F>
 __device__ __forceinline__ void for_tile_points(const Usfft2dArgs<T>& a, int kvc, T cx, T cy, T hbox,
-                                                T bxmin, T bxmax, T bymin, T bymax, int w, int nw, F&& fn) {
+                                                T bxmin, T bxmax, T bymin, T bymax, int w, F&& fn) {
+    __shared__ int s_lines[NW][64];
+    int* list = s_lines[w];
     const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const int kmin = -a.w / 2, kmax = a.w / 2 - 1;
-    for (int base = 0; base * nw < a.T_; base += 32) {
-        const int th = (base + lane) * nw + w;
+    // clip up to 32 listed lines (lane i takes list[i]) and enumerate their points
+    auto flush = [&](int count) {
+        const int th = lane < count ? list[lane] : -1;
         int lo = 1, hi = 0;
-        if (th < a.T_) {
+        if (th >= 0) {
             const typename AngleT<T>::type g = a.ang[th];
             T Ax, Cx, Ay, Cy;
             line_coef(g, kvc, Ax, Cx, Ay, Cy);
-            const T nrm = sqrt(Ax * Ax + Ay * Ay);
-            const T nx = -Ay / nrm, ny = Ax / nrm;
-            const T dist = fabs((cx - Cx) * nx + (cy - Cy) * ny);
-            if (dist <= hbox * (fabs(nx) + fabs(ny)) + (T)1) {
-                lo = kmin;
-                hi = kmax;
-                clip_line<T>(Ax, Cx, bxmin, bxmax, lo, hi);
-                clip_line<T>(Ay, Cy, bymin, bymax, lo, hi);
-            }
+            lo = kmin;
+            hi = kmax;
+            clip_line<T>(Ax, Cx, bxmin, bxmax, lo, hi);
+            clip_line<T>(Ay, Cy, bymin, bymax, lo, hi);
         }
         const int cnt = hi >= lo ? hi - lo + 1 : 0;
         // inclusive scan of cnt over the warp
@@ -258,15 +258,45 @@ __device__ __forceinline__ void for_tile_points(const Usfft2dArgs<T>& a, int kvc
                 const int ex = __shfl_sync(0xffffffffu, excl, cand);
                 if (ex <= p) owner = cand;
             }
-            // skip empty intervals that share the prefix: move to the owner with cnt > 0
             const int ocnt = __shfl_sync(0xffffffffu, cnt, owner);
             const int oex = __shfl_sync(0xffffffffu, excl, owner);
             const int olo = __shfl_sync(0xffffffffu, lo, owner);
+            const int oth = __shfl_sync(0xffffffffu, th, owner);
             const bool valid = p < total && ocnt > 0 && p - oex < ocnt;
             const int kuc = olo + (p - oex);
-            fn(valid ? (base + owner) * nw + w : -1, kuc);
+            fn(valid ? oth : -1, kuc);
+        }
+    };
+    int nlist = 0;  // warp-uniform
+    for (int base = 0; base * NW < a.T_; base += 32) {
+        const int th = (base + lane) * NW + w;
+        bool pass = false;
+        if (th < a.T_) {
+            const typename AngleT<T>::type g = a.ang[th];
+            T Ax, Cx, Ay, Cy;
+            line_coef(g, kvc, Ax, Cx, Ay, Cy);
+            const T nrm = sqrt(Ax * Ax + Ay * Ay);
+            const T nx = -Ay / nrm, ny = Ax / nrm;
+            const T dist = fabs((cx - Cx) * nx + (cy - Cy) * ny);
+            pass = dist <= hbox * (fabs(nx) + fabs(ny)) + (T)1;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        if (pass) list[nlist + __popc(m & lt)] = th;
+        nlist += __popc(m);
+        __syncwarp();
+        if (nlist >= 32) {
+            flush(32);
+            // keep the overflow (fewer than 32 lines) at the front of the list
+            const int rest = nlist - 32;
+            const int v = lane < rest ? list[32 + lane] : 0;
+            __syncwarp();
+            if (lane < rest) list[lane] = v;
+            __syncwarp();
+            nlist = rest;
         }
     }
+    if (nlist > 0) flush(nlist);
+    __syncwarp();
 }
 
 // Tiled gather: one block per TS x TS tile of tap-window origins.  The block
@@ -312,8 +342,8 @@ __device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P
             // positions whose window origin is in [b0, b0 + TS): p in [b0 + m - 1, b0 + TS + m - 1)
             const T cx = (T)(bx0 + a.m - 1) + (T)TS * (T)0.5, cy = (T)(by0 + a.m - 1) + (T)TS * (T)0.5;
             if (sqrt(cx * cx + cy * cy) > a.rmax + hb * (T)1.5) continue;
-            for_tile_points<T>(a, kvc, cx, cy, hb, (T)(bx0 + a.m - 1), (T)(bx0 + TS + a.m - 1),
-                               (T)(by0 + a.m - 1), (T)(by0 + TS + a.m - 1), warp, TPB, [&](int th, int kuc) {
+            for_tile_points<T, TPB>(a, kvc, cx, cy, hb, (T)(bx0 + a.m - 1), (T)(bx0 + TS + a.m - 1),
+                               (T)(by0 + a.m - 1), (T)(by0 + TS + a.m - 1), warp, [&](int th, int kuc) {
                 if (th < 0) return;
                 const typename AngleT<T>::type g = a.ang[th];
                 int jx, jy;
@@ -499,7 +529,7 @@ __global__ void __launch_bounds__(TPB * 32, TPB >= 16 ? (sizeof(T) == 4 ? 2 : 1)
                     const T t0 = -bxh, t1 = -bxl + (T)1, t2 = -byh, t3 = -byl + (T)1;
                     bxl = t0; bxh = t1; byl = t2; byh = t3;
                 }
-                for_tile_points<T>(a, kvc, sg * cx, sg * cy, hb, bxl, bxh, byl, byh, warp, TPB, [&](int th, int kuc) {
+                for_tile_points<T, TPB>(a, kvc, sg * cx, sg * cy, hb, bxl, bxh, byl, byh, warp, [&](int th, int kuc) {
                     if (th < 0) return;
                     const typename AngleT<T>::type g = a.ang[th];
                     int jx, jy;
@@ -661,7 +691,7 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
                     const T t0 = -bxh, t1 = -bxl + (T)1, t2 = -byh, t3 = -byl + (T)1;
                     bxl = t0; bxh = t1; byl = t2; byh = t3;
                 }
-                for_tile_points<T>(a, kvc, sg * cx, sg * cy, hb, bxl, bxh, byl, byh, warp, NW, [&](int th, int kuc) {
+                for_tile_points<T, NW>(a, kvc, sg * cx, sg * cy, hb, bxl, bxh, byl, byh, warp, [&](int th, int kuc) {
                     bool ok = th >= 0;
                     int ox = 0, oy = 0;
                     T fx = 0, fy = 0;
@@ -919,11 +949,13 @@ template <typename T> cudaError_t configure_usfft2d() {
     if (!e) e = cudaFuncSetAttribute(k_colfft_fwd<T, true>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_rowfft_adj<T, true>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_colfft_adj<T, true>, at, mx);
+    // the tile kernels also hold static shared memory (the per-warp line lists)
+    const int mt = kMaxDynSmem - 4096;
 #define LAM_A(MH)                                                                          \
-    if (!e) e = cudaFuncSetAttribute(k_gather2d_tiled<T, kScatterWarps, MH>, at, mx);       \
-    if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 0>, at, mx);  \
-    if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 3>, at, mx);    \
-    if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles<T, kScatterWarps, MH>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_gather2d_tiled<T, kScatterWarps, MH>, at, mt);       \
+    if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 0>, at, mt);  \
+    if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 3>, at, mt);    \
+    if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles<T, kScatterWarps, MH>, at, mt);
     LAM_A(2) LAM_A(3) LAM_A(4) LAM_A(5) LAM_A(6) LAM_A(7) LAM_A(8)
 #undef LAM_A
     return e;
@@ -948,7 +980,7 @@ __device__ __forceinline__ int batch_problem(const int* start, int count, int w)
     return p;
 }
 
-constexpr size_t kBatchDynSmem = kMaxDynSmem - 2048;  // room for the static argument copy
+constexpr size_t kBatchDynSmem = kMaxDynSmem - 6144;  // room for the static argument copy and line lists
 
 template <typename T>
 __global__ void kb_set_ptrs(BatchTable<T>* __restrict__ bt, BatchPtrs ptrs, int count) {
