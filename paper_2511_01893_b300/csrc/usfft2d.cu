@@ -123,6 +123,122 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_adj(C<T>* __restrict__ P
     k_colfft_adj_body<T, MIXED>(P, a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined column passes: persistent blocks walk the (plane, column strip)
+// items with two shared-memory buffers; the next strip's loads (cp.async)
+// are in flight while the current strip is transformed and stored.
+// ---------------------------------------------------------------------------
+
+template <typename T> __device__ __forceinline__ void cp_async_elem(C<T>* dst, const C<T>* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(C<T>) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// forward: rows wrap(x - n1/2) (x < n1) hold data, the others are zero padding;
+// the FFT overwrites every row, so after the stores the padding rows are
+// zeroed again for the buffer's next strip
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(kFftThreads) k_colfft_fwd_pipe(C<T>* __restrict__ P, Usfft2dArgs<T> a, int nb) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int LS = fpad_len(a.M1);
+    C<T>* buf[2] = {reinterpret_cast<C<T>*>(smem_raw), reinterpret_cast<C<T>*>(smem_raw) + a.CB * LS};
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lcb = ilog2_pow2(a.CB);
+    const int ncg = a.M2 / a.CB, total = ncg * nb;
+    const int half = a.n1 / 2, hi0 = a.M1 - half;  // data rows: [0, half) and [hi0, M1)
+    for (int i = tid; i < 2 * a.CB * LS; i += nthr) buf[0][i] = cmake<T>(0, 0);
+    __syncthreads();
+    auto issue = [&](int w, C<T>* bb) {
+        const int b = w / ncg, c0 = (w - b * ncg) * a.CB;
+        const C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
+        for (int i = tid; i < a.n1 * a.CB; i += nthr) {
+            const int x = i >> lcb, c = i - (x << lcb);
+            const int row = wrap(x - half, a.M1);
+            cp_async_elem<T>(bb + c * LS + fpad(row), pl + (size_t)row * a.M2 + c);
+        }
+        cp_async_commit();
+    };
+    int k = 0;
+    if ((int)blockIdx.x < total) issue(blockIdx.x, buf[0]);
+    for (int w = blockIdx.x; w < total; w += gridDim.x, ++k) {
+        C<T>* cur = buf[k & 1];
+        const int wn = w + gridDim.x;
+        if (wn < total) issue(wn, buf[(k + 1) & 1]);
+        else cp_async_commit();  // an empty group keeps the wait count uniform
+        cp_async_wait_prev();
+        __syncthreads();
+        fft_lines_ip<-1, FftMaxB<T>::value, T, MIXED>(cur, a.CB, LS, a.M1, a.fcM1, a.tw, a.tw1);
+        const int b = w / ncg, c0 = (w - b * ncg) * a.CB;
+        C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
+        for (int i = tid; i < a.M1 * a.CB; i += nthr) {
+            const int j = i >> lcb, c = i - (j << lcb);
+            C<T>* e = cur + c * LS + fpad(j);
+            pl[(size_t)j * a.M2 + c] = *e;
+            if (j >= half && j < hi0) *e = cmake<T>(0, 0);
+        }
+        __syncthreads();  // cur is free before it is refilled two items later
+    }
+    cp_async_wait_all();
+}
+
+// transpose: every row is loaded; the n1 rows the crop keeps are stored
+template <typename T, bool MIXED>
+__global__ void __launch_bounds__(kFftThreads) k_colfft_adj_pipe(C<T>* __restrict__ P, Usfft2dArgs<T> a, int nb) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int LS = fpad_len(a.M1);
+    C<T>* buf[2] = {reinterpret_cast<C<T>*>(smem_raw), reinterpret_cast<C<T>*>(smem_raw) + a.CB * LS};
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int lcb = ilog2_pow2(a.CB);
+    const int ncg = a.M2 / a.CB, total = ncg * nb;
+    auto issue = [&](int w, C<T>* bb) {
+        const int b = w / ncg, c0 = (w - b * ncg) * a.CB;
+        const C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
+        for (int i = tid; i < a.M1 * a.CB; i += nthr) {
+            const int j = i >> lcb, c = i - (j << lcb);
+            cp_async_elem<T>(bb + c * LS + fpad(j), pl + (size_t)j * a.M2 + c);
+        }
+        cp_async_commit();
+    };
+    int k = 0;
+    if ((int)blockIdx.x < total) issue(blockIdx.x, buf[0]);
+    for (int w = blockIdx.x; w < total; w += gridDim.x, ++k) {
+        C<T>* cur = buf[k & 1];
+        const int wn = w + gridDim.x;
+        if (wn < total) issue(wn, buf[(k + 1) & 1]);
+        else cp_async_commit();
+        cp_async_wait_prev();
+        __syncthreads();
+        fft_lines_ip<+1, FftMaxB<T>::value, T, MIXED>(cur, a.CB, LS, a.M1, a.fcM1, a.tw, a.tw1);
+        const int b = w / ncg, c0 = (w - b * ncg) * a.CB;
+        C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
+        for (int i = tid; i < a.n1 * a.CB; i += nthr) {
+            const int x = i >> lcb, c = i - (x << lcb);
+            const int row = wrap(x - a.n1 / 2, a.M1);
+            pl[(size_t)row * a.M2 + c] = cur[c * LS + fpad(row)];
+        }
+        __syncthreads();
+    }
+    cp_async_wait_all();
+}
+
+// persistent grid of a pipelined column pass: one block per SM (the FFT
+// blocks use 512 threads at ~125 registers), at most one per item
+static int pipe_grid(int items) {
+    static int nsm = 0;
+    if (!nsm) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            nsm = 148;
+    }
+    return items < nsm ? items : nsm;
+}
+
 template <typename T, bool MIXED>
 __device__ __forceinline__ void k_rowfft_adj_body(const C<T>* __restrict__ P, C<T>* __restrict__ u1, int j0, const Usfft2dArgs<T>& a, int bx, int by) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -809,12 +925,13 @@ cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* s
     const int kv0 = j0;
     const size_t sr = (size_t)a.RB * fpad_len(a.M2) * sizeof(C<T>);
     const size_t sc = (size_t)a.CB * fpad_len(a.M1) * sizeof(C<T>);
+    const int gp = pipe_grid((a.M2 / a.CB) * nb);
     if (fft_mixed(a.fcM1) || fft_mixed(a.fcM2)) {
         k_rowfft_fwd<T, true><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, kv0, a);
-        k_colfft_fwd<T, true><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+        k_colfft_fwd_pipe<T, true><<<gp, kFftThreads, 2 * sc, s>>>(P, a, nb);
     } else {
         k_rowfft_fwd<T, false><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, kv0, a);
-        k_colfft_fwd<T, false><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+        k_colfft_fwd_pipe<T, false><<<gp, kFftThreads, 2 * sc, s>>>(P, a, nb);
     }
     constexpr int NW = kScatterWarps;
     const int ntiles = (a.M1 / a.TG) * (a.M2 / a.TG);
@@ -835,12 +952,13 @@ template <typename T>
 cudaError_t launch_usfft2d_planes(const C<T>* u1, C<T>* P, int j0, int nb, const Usfft2dArgs<T>& a, cudaStream_t s) {
     const size_t sr = (size_t)a.RB * fpad_len(a.M2) * sizeof(C<T>);
     const size_t sc = (size_t)a.CB * fpad_len(a.M1) * sizeof(C<T>);
+    const int gp = pipe_grid((a.M2 / a.CB) * nb);
     if (fft_mixed(a.fcM1) || fft_mixed(a.fcM2)) {
         k_rowfft_fwd<T, true><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, j0, a);
-        k_colfft_fwd<T, true><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+        k_colfft_fwd_pipe<T, true><<<gp, kFftThreads, 2 * sc, s>>>(P, a, nb);
     } else {
         k_rowfft_fwd<T, false><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, j0, a);
-        k_colfft_fwd<T, false><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+        k_colfft_fwd_pipe<T, false><<<gp, kFftThreads, 2 * sc, s>>>(P, a, nb);
     }
     return cudaGetLastError();
 }
@@ -900,11 +1018,12 @@ cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int j0, int nb
     else { LAM_SW(0) }
 #undef LAM_SW
 #undef LAM_S
+    const int gp = pipe_grid((a.M2 / a.CB) * nb);
     if (fft_mixed(a.fcM1) || fft_mixed(a.fcM2)) {
-        k_colfft_adj<T, true><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+        k_colfft_adj_pipe<T, true><<<gp, kFftThreads, 2 * sc, s>>>(P, a, nb);
         k_rowfft_adj<T, true><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(P, u1, kv0, a);
     } else {
-        k_colfft_adj<T, false><<<dim3(a.M2 / a.CB, nb), kFftThreads, sc, s>>>(P, a);
+        k_colfft_adj_pipe<T, false><<<gp, kFftThreads, 2 * sc, s>>>(P, a, nb);
         k_rowfft_adj<T, false><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(P, u1, kv0, a);
     }
     return cudaGetLastError();
@@ -949,6 +1068,10 @@ template <typename T> cudaError_t configure_usfft2d() {
     if (!e) e = cudaFuncSetAttribute(k_colfft_fwd<T, true>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_rowfft_adj<T, true>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_colfft_adj<T, true>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_colfft_fwd_pipe<T, false>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_colfft_fwd_pipe<T, true>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_colfft_adj_pipe<T, false>, at, mx);
+    if (!e) e = cudaFuncSetAttribute(k_colfft_adj_pipe<T, true>, at, mx);
     // the tile kernels also hold static shared memory (the per-warp line lists)
     const int mt = kMaxDynSmem - 4096;
 #define LAM_A(MH)                                                                          \
