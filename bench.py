@@ -72,6 +72,20 @@ def lhat_bytes(n, nz, h, w, T):
 # multi-rank timing (replicas: no data-path collective; only the clock is reduced)
 # ---------------------------------------------------------------------------
 
+def source_hash():
+    """SHA-256 of the CUDA sources (csrc/*.cu, *.cuh, *.h in name order): ties a
+    stored DRAM-traffic figure to the kernels it was measured on."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2511_01893_b300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()
+
+
 def lhat_flops(n, nz, h, w, T, m=4):
     """Algorithmic FP32 flops of one L-hat (5 N log2 N per complex FFT of
     length N): the z stage's n^2 FFTs of length 2 nz; per kv plane n row FFTs
@@ -520,7 +534,8 @@ def run_ours(args):
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         tj = json.load(open(prof))
-        if tj.get("size") == n:
+        # only while the kernels are the ones the counters were taken on
+        if tj.get("size") == n and tj.get("source_sha256") == source_hash():
             traffic = tj.get("lhat_pair_dram_bytes")
     del p, out_c, out_r
     fma = glam.fma_peak(dev)
