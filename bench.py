@@ -46,10 +46,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
-    ap.add_argument("--op", choices=["admm", "lhat_pair", "batch"], default="admm",
+    ap.add_argument("--op", choices=["admm", "lhat_pair", "batch", "ablation"], default="admm",
                     help="lhat_pair: time only L-hat + L-hat^H on the workload (no ADMM state); "
                          "a small footprint for profiling.  batch: the batching workload (16 "
-                         "reconstructions of uneven sizes, batched operators, graph-captured ADMM)")
+                         "reconstructions of uneven sizes, batched operators, graph-captured ADMM).  "
+                         "ablation: the plain LSP form (Algorithm 1) against the cancelled and fused "
+                         "form (Algorithm 2) on the workload")
     return ap.parse_args()
 
 
@@ -369,6 +371,54 @@ def run_op_pair(args):
     return 0
 
 
+def run_ablation(args):
+    """Algorithm 1 (each CG step: r = L u - d with the full L, the full L^H, and
+    L of the direction: two L and one L^H, F*_2D / F_2D each time) against
+    Algorithm 2 (F*_2D / F_2D cancelled, subtraction fused, residual carried
+    by linearity: one L_hat and one L_hat^H) on the workload, FP32, graph
+    replay.  Prints one JSON line."""
+    import torch
+
+    from paper_2511_01893_b300 import inputs
+    from paper_2511_01893_b300 import lamino as glam
+    n = args.size
+    dev = torch.device("cuda", 0)
+    theta = inputs.angles(n)
+    plan = glam.Plan(n, n, n, n, theta, np.deg2rad(PHI_DEG), prec="f32", device=dev)
+    s = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(s):
+        u_true = inputs.ellipsoid_circuit_phantom(n, n, seed=1238, device=dev, dtype=torch.float32)
+        d = plan.forward(u_true)
+        del u_true
+        gen = torch.Generator(device=dev).manual_seed(99)
+        d.real.add_(torch.randn(d.shape, generator=gen, device=dev, dtype=torch.float32),
+                    alpha=0.01 * d.real.abs().max().item())
+    s.synchronize()
+    res, us = {}, {}
+    for form in (1, 2):
+        a = glam.Admm(plan)
+        with torch.cuda.stream(s):
+            a.init(d, ALPHA, RHO, N_INNER, form=form)
+            a.run(args.warmup, graph=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            a.run(args.steps, graph=True)
+            e1.record(s)
+        s.synchronize()
+        res[form] = e0.elapsed_time(e1) / 1e3 / max(args.steps, 1)
+        us[form] = a.u.clone()
+        res[f"status{form}"] = a.status()
+        del a
+        torch.cuda.empty_cache()
+    diff = (us[1].double() - us[2].double()).norm().item() / us[2].double().norm().item()
+    print(json.dumps({"op": "ablation", "size": n, "steps": args.steps, "warmup": args.warmup,
+                      "alg1_s_per_iter": res[1], "alg2_s_per_iter": res[2], "speedup_alg2": res[1] / res[2],
+                      "rel_l2_u_alg1_vs_alg2": diff, "status": max(res["status1"], res["status2"]),
+                      "note": "FP32; both forms from the same data, same number of outer iterations"}),
+          flush=True)
+    return 0
+
+
 BATCH_SIZES = [96, 128, 160, 192]
 
 
@@ -638,6 +688,8 @@ def main():
         return run_op_pair(args)
     if args.op == "batch":
         return run_batch(args)
+    if args.op == "ablation":
+        return run_ablation(args)
     return run_ours(args)
 
 

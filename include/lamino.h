@@ -82,8 +82,15 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *   LAM_SPREAD_EXACT   exact 64-bit fixed-point atomic adds: every cell is the
  *                      correctly rounded sum of its products; reproducible.
  * LAM_OPT_FAST_ADJOINT: value != 0 selects LAM_SPREAD_ATOMIC, 0 the default.
+ * LAM_OPT_LSP_FORM (default 2) is the LSP form that ADMM states initialised
+ *   afterwards use: 2 = Algorithm 2 (operation cancellation: the LSP works on
+ *   d_hat = F_2D d with F*_2D / F_2D cancelled, the residual carried by
+ *   linearity: one L_hat and one L_hat^H per CG step); 1 = Algorithm 1 (the
+ *   plain form: each CG step forms r = L u - d with the full L, applies the
+ *   full L^H, and applies L to the direction: two L and one L^H).  Both give
+ *   the same iterates up to rounding; the option exists for the comparison.
  * Setting an option invalidates ADMM graphs captured with the plan. */
-enum { LAM_OPT_FAST_ADJOINT = 1, LAM_OPT_ADJOINT_SPREAD = 2 };
+enum { LAM_OPT_FAST_ADJOINT = 1, LAM_OPT_ADJOINT_SPREAD = 2, LAM_OPT_LSP_FORM = 3 };
 enum { LAM_SPREAD_TILES = 0, LAM_SPREAD_ATOMIC = 1, LAM_SPREAD_EXACT = 2 };
 lam_status lam_plan_set_option(lam_plan* plan, int option, int value);
 

@@ -86,6 +86,8 @@ template <typename T> struct Admm {
     cudaError_t rsp(const T* u, const T* du, T* e, T* lam, T* dpsi, const AdmmRed& r, double* hist, int hist_cap,
                     cudaStream_t s) const;
     cudaError_t neg_copy(const C<T>* src, C<T>* dst, long long n, cudaStream_t s) const;
+    cudaError_t csub(const C<T>* src, C<T>* dst, long long n, cudaStream_t s) const;
+    cudaError_t vadd(const T* a, const T* b, T* out, cudaStream_t s) const;
     cudaError_t tv_smooth(const T* u, T* g, double eps, const AdmmRed& r, int dst, cudaStream_t s) const;
     cudaError_t residual_norm(const C<T>* res, long long n, const AdmmRed& r, cudaStream_t s) const;
 };

@@ -58,6 +58,7 @@ namespace {
 
 struct AdmmHost {
     int n_inner = 4;
+    int form = 2;  // LSP form: 2 (Algorithm 2, default) or 1 (Algorithm 1)
     void* ws = nullptr;
     cudaGraphExec_t graph = nullptr;
     size_t graph_kernels = 0;  // kernel nodes in the captured outer iteration
@@ -94,6 +95,7 @@ struct lam_plan {
     double rmax;
     int pstride;
     int spread = kSpreadTiles;
+    int lsp_form = 2;  // LSP form new ADMM states take (LAM_OPT_LSP_FORM)
     // workspace layout
     size_t ws_u1, ws_planes, ws_tmp, ws_red, ws_bytes;
     mutable std::mutex mu;
@@ -532,7 +534,7 @@ template <typename T> Admm<T> admm_ops(const lam_plan* p) {
 
 template <typename T>
 lam_status admm_init_t(const lam_plan* p, void* state, const void* d, double alpha, double rho, int adapt,
-                       cudaStream_t s) {
+                       int form, cudaStream_t s) {
     const StateLayout L = layout(p);
     StatePtrs<T> S = ptrs<T>(p, state);
     const size_t vb = (size_t)p->nvox() * p->elem();
@@ -541,31 +543,59 @@ lam_status admm_init_t(const lam_plan* p, void* state, const void* d, double alp
     CK(cudaMemsetAsync(S.e, 0, 3 * vb, s));
     CK(cudaMemsetAsync(S.lam, 0, 3 * vb, s));
     (void)L;
-    k_init_scalars<<<1, 32, 0, s>>>(S.red.sc, rho, alpha, 1.0 / ((double)p->h * p->w), adapt ? 1.0 : 0.0,
-                                    S.red.counter);
+    // Algorithm 2 works on d_hat = F_2D d with the Parseval weight 1/(hw);
+    // Algorithm 1 keeps d in the data space (the slot holds d) with weight 1
+    k_init_scalars<<<1, 32, 0, s>>>(S.red.sc, rho, alpha, form == 1 ? 1.0 : 1.0 / ((double)p->h * p->w),
+                                    adapt ? 1.0 : 0.0, S.red.counter);
     CK(cudaGetLastError());
-    lam_status st = fft2d<T>(p, (const C<T>*)d, S.dhat, -1, (T)1, s);
-    if (st) return st;
+    if (form == 1) {
+        CK(cudaMemcpyAsync(S.dhat, d, (size_t)p->ndata() * p->celem(), cudaMemcpyDeviceToDevice, s));
+    } else {
+        lam_status st = fft2d<T>(p, (const C<T>*)d, S.dhat, -1, (T)1, s);
+        if (st) return st;
+    }
     const Admm<T> ops = admm_ops<T>(p);
     CK(ops.neg_copy(S.dhat, S.r, p->ndata(), s));
     CK(ops.residual_norm(S.r, p->ndata(), S.red, s));
     return LAM_OK;
 }
 
-template <typename T> lam_status admm_step_t(const lam_plan* p, void* state, void* ws, int n_inner, cudaStream_t s) {
+template <typename T>
+lam_status admm_step_t(const lam_plan* p, void* state, void* ws, int n_inner, int form, cudaStream_t s) {
     StatePtrs<T> S = ptrs<T>(p, state);
     const Admm<T> ops = admm_ops<T>(p);
     const long long nd = p->ndata();
+    const T sc = (T)(1.0 / ((double)p->h * p->w));
+    C<T>* tmp = (C<T>*)((char*)ws + p->ws_tmp);
     lam_status st;
     for (int i = 0; i < n_inner; ++i) {
         T* Gc = (i & 1) ? S.G1 : S.G0;
         T* Gp = (i & 1) ? S.G0 : S.G1;
-        // adjoint pass: G = Re L_hat^H r / (hw) - rho div(grad u - g)
-        if ((st = adj_hat<T>(p, S.r, S.Gd, ws, s))) return st;
+        if (form == 1) {
+            // Algorithm 1: r = L u_k - d in the data space (F*_2D after L_hat) for
+            // the current iterate u_k (u + du after the first step: u takes the
+            // LSP increment du only at its end), then G = Re L^H r - rho div(...)
+            // with L^H = L_hat^H F_2D / (hw).  Gd holds u + du until the adjoint
+            // pass overwrites it.
+            const T* uk = S.u;
+            if (i > 0) {
+                CK(ops.vadd(S.u, S.du, S.Gd, s));
+                uk = S.Gd;
+            }
+            if ((st = fwd_hat<T>(p, uk, S.r, nullptr, ws, s))) return st;
+            if ((st = fft2d<T>(p, S.r, S.r, +1, sc, s))) return st;
+            CK(ops.csub(S.dhat, S.r, nd, s));
+            if ((st = fft2d<T>(p, S.r, tmp, -1, sc, s))) return st;
+            if ((st = adj_hat<T>(p, tmp, S.Gd, ws, s))) return st;
+        } else {
+            // adjoint pass: G = Re L_hat^H r / (hw) - rho div(grad u - g)
+            if ((st = adj_hat<T>(p, S.r, S.Gd, ws, s))) return st;
+        }
         CK(ops.lsp_G(S.Gd, S.du, S.e, S.lam, S.p, Gp, Gc, i == 0, S.red, s));
         // CG direction and its forward pass
         CK(ops.lsp_p(Gc, S.p, S.red, s));
         if ((st = fwd_hat<T>(p, S.p, S.Lp, nullptr, ws, s))) return st;
+        if (form == 1 && (st = fft2d<T>(p, S.Lp, S.Lp, +1, sc, s))) return st;
         // exact line search, increment and residual update (u += du on the last step)
         CK(ops.lsp_update(S.du, S.u, S.p, i == 0, i == n_inner - 1, S.r, S.Lp, nd, S.red, s));
     }
@@ -924,6 +954,10 @@ lam_status lam_plan_set_option(lam_plan* p, int option, int value) {
                     }
             }
             return LAM_OK;
+        case LAM_OPT_LSP_FORM:
+            if (value != 1 && value != 2) return fail(LAM_EINVAL, "LSP form %d: 1 or 2", value);
+            p->lsp_form = value;
+            return LAM_OK;
         default:
             return fail(LAM_EINVAL, "unknown option %d", option);
     }
@@ -1050,9 +1084,10 @@ lam_status admm_init(const lam_plan* p, void* state, const void* d, double alpha
         h.graph = nullptr;
         h.n_inner = n_inner;
         h.ws = ws;
+        h.form = p->lsp_form;
     }
-    return DISPATCH(p, admm_init_t<float>(p, state, d, alpha, rho, adapt_rho, s),
-                    admm_init_t<double>(p, state, d, alpha, rho, adapt_rho, s));
+    return DISPATCH(p, admm_init_t<float>(p, state, d, alpha, rho, adapt_rho, p->lsp_form, s),
+                    admm_init_t<double>(p, state, d, alpha, rho, adapt_rho, p->lsp_form, s));
 }
 
 static lam_status lookup(const lam_plan* p, void* state, AdmmHost** h) {
@@ -1069,8 +1104,8 @@ lam_status admm_step(const lam_plan* p, void* state, void* ws, void* stream) {
     AdmmHost* h;
     if (lam_status st = lookup(p, state, &h)) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    return DISPATCH(p, admm_step_t<float>(p, state, ws, h->n_inner, s),
-                    admm_step_t<double>(p, state, ws, h->n_inner, s));
+    return DISPATCH(p, admm_step_t<float>(p, state, ws, h->n_inner, h->form, s),
+                    admm_step_t<double>(p, state, ws, h->n_inner, h->form, s));
 }
 
 lam_status admm_run(const lam_plan* p, void* state, void* ws, int iters, int use_graph, void* stream) {
@@ -1446,6 +1481,7 @@ lam_status admm_run_batched(lam_batch* b, void* const* states, int iters, int us
         if (lam_status st = lookup(b->plans[i], states[i], &h)) return st;
         if (n_inner >= 0 && h->n_inner != n_inner)
             return fail(LAM_EINVAL, "state %d: every state of a batch needs the same number of CG steps", i);
+        if (h->form != 2) return fail(LAM_EUNSUPPORTED, "state %d: batched ADMM runs the Algorithm 2 form", i);
         n_inner = h->n_inner;
     }
     cudaStream_t s = (cudaStream_t)stream;

@@ -505,6 +505,34 @@ cudaError_t Admm<T>::rsp(const T* u, const T* du, T* e, T* lam, T* dpsi, const A
     k_outer_scalars<<<1, 32, 0, s>>>(r.sc, hist, hist_cap);
     return cudaGetLastError();
 }
+// out = a + b (the current LSP iterate u + du of the Algorithm 1 form)
+template <typename T>
+__global__ void k_vadd(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = a[i] + b[i];
+}
+
+template <typename T>
+cudaError_t Admm<T>::vadd(const T* a, const T* b, T* out, cudaStream_t s) const {
+    k_vadd<T><<<egrid(v.N), 256, 0, s>>>(a, b, out, v.N);
+    return cudaGetLastError();
+}
+
+// dst -= src (the data-space residual of the Algorithm 1 form)
+template <typename T>
+__global__ void k_csub(const C<T>* __restrict__ src, C<T>* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const C<T> a = dst[i], b = src[i];
+        dst[i] = cmake<T>(a.x - b.x, a.y - b.y);
+    }
+}
+
+template <typename T>
+cudaError_t Admm<T>::csub(const C<T>* src, C<T>* dst, long long n, cudaStream_t s) const {
+    k_csub<T><<<egrid(n), 256, 0, s>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t Admm<T>::neg_copy(const C<T>* src, C<T>* dst, long long n, cudaStream_t s) const {
     k_neg_copy<T><<<egrid(n), 256, 0, s>>>(src, dst, n);

@@ -366,8 +366,10 @@ class Admm:
         self.state = torch.empty(nb.value, dtype=torch.uint8, device=plan.device)
         self.iters = 0
 
-    def init(self, d, alpha, rho, n_inner=4, adapt_rho=True):
+    def init(self, d, alpha, rho, n_inner=4, adapt_rho=True, form=2):
+        """form: the LSP form, 2 (Algorithm 2, default) or 1 (Algorithm 1)."""
         d = self.plan._inp(d, self.plan.cdtype, self.plan.data_shape)
+        _check(lib().lam_plan_set_option(self.plan._h, 3, int(form)), "lam_plan_set_option")
         _check(lib().admm_init(self.plan._h, _ptr(self.state), _ptr(d), float(alpha), float(rho), int(n_inner),
                                int(bool(adapt_rho)), _ptr(self.plan.ws), _stream()), "admm_init")
         self.iters = 0

@@ -169,3 +169,19 @@ def test_admm_f64_matches_oracle_at_mixed_radix_size():
     assert a.status() == 0
     assert rel(a.u, u_ref) < 1e-10
     assert np.allclose(a.history()[:, 0], info["objective"], rtol=1e-10)
+
+
+def test_admm_algorithm1_form_matches_oracle_and_algorithm2(case):
+    """The plain LSP form (Algorithm 1: full L and L^H, residual recomputed each
+    CG step) against the oracle's Algorithm 1 and the GPU Algorithm 2 form."""
+    theta, g, d = case["theta"], case["g"], case["d"]
+    u_ref, info = oadmm.admm(d, g, ALPHA, RHO, 3, N_INNER, adapt_rho=True, form="alg1")
+    plan = glam.Plan(N, NZ, H, W, theta, PHI, prec="f64")
+    a1 = glam.Admm(plan).init(torch.from_numpy(d), ALPHA, RHO, N_INNER, form=1)
+    a1.run(3)
+    assert a1.status() == 0
+    assert rel(a1.u, u_ref) < 1e-10
+    a2 = glam.Admm(plan).init(torch.from_numpy(d), ALPHA, RHO, N_INNER, form=2)
+    a2.run(3)
+    assert rel(a1.u, a2.u) < 1e-10
+    assert np.allclose(a1.history()[:, 0], a2.history()[:, 0], rtol=1e-10)
