@@ -81,6 +81,9 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *                      depends on scheduling (not reproducible bit for bit).
  *   LAM_SPREAD_EXACT   exact 64-bit fixed-point atomic adds: every cell is the
  *                      correctly rounded sum of its products; reproducible.
+ *   LAM_SPREAD_HALO    per-warp tiles extended by a halo: each slice point is
+ *                      visited once (by the tile of its window origin); the
+ *                      halos are summed in a second pass; reproducible.
  * LAM_OPT_FAST_ADJOINT: value != 0 selects LAM_SPREAD_ATOMIC, 0 the default.
  * LAM_OPT_LSP_FORM (default 2) is the LSP form that ADMM states initialised
  *   afterwards use: 2 = Algorithm 2 (operation cancellation: the LSP works on
@@ -91,7 +94,7 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *   the same iterates up to rounding; the option exists for the comparison.
  * Setting an option invalidates ADMM graphs captured with the plan. */
 enum { LAM_OPT_FAST_ADJOINT = 1, LAM_OPT_ADJOINT_SPREAD = 2, LAM_OPT_LSP_FORM = 3 };
-enum { LAM_SPREAD_TILES = 0, LAM_SPREAD_ATOMIC = 1, LAM_SPREAD_EXACT = 2 };
+enum { LAM_SPREAD_TILES = 0, LAM_SPREAD_ATOMIC = 1, LAM_SPREAD_EXACT = 2, LAM_SPREAD_HALO = 3 };
 lam_status lam_plan_set_option(lam_plan* plan, int option, int value);
 
 /* Autotuner (a set-up call; synchronises `stream`, not under capture): times

@@ -97,7 +97,7 @@ struct lam_plan {
     int spread = kSpreadTiles;
     int lsp_form = 2;  // LSP form new ADMM states take (LAM_OPT_LSP_FORM)
     // workspace layout
-    size_t ws_u1, ws_planes, ws_tmp, ws_red, ws_bytes;
+    size_t ws_u1, ws_planes, ws_halo, ws_tmp, ws_red, ws_bytes;
     mutable std::mutex mu;
     mutable std::map<void*, AdmmHost> admm;
 
@@ -360,6 +360,7 @@ template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p, bool paired) {
     a.spread = p->spread;
     a.jobs = paired ? p->jobs_pair : p->jobs_all;
     a.maxabs = nullptr;
+    a.halo = nullptr;
     // points whose 2m x 2m window covers one cell: at most (2m / spacing + 2)^2 per
     // line neighbourhood, over all T lines and all periodic images; doubled for safety
     {
@@ -414,7 +415,7 @@ template <typename T> lam_status prep_scatter(const lam_plan* p, const C<T>* in,
                                               Usfft2dArgs<T>& a) {
     // the exact spread runs when chosen, and for the tile spread's small-plane
     // fallback (tiles narrower than 32)
-    const bool exact = p->spread == kSpreadExact || (p->spread == kSpreadTiles && p->TS != 32);
+    const bool exact = p->spread == kSpreadExact || ((p->spread == kSpreadTiles || p->spread == kSpreadHalo) && p->TS != 32);
     if (!exact) return LAM_OK;
     T* mx = (T*)((char*)ws + p->ws_red + align256(SC_COUNT * sizeof(double)) +
                  align256((size_t)kRedBlocks * 4 * sizeof(double)) + 256);
@@ -428,6 +429,7 @@ template <typename T> lam_status adj_hat(const lam_plan* p, const C<T>* in, T* u
     C<T>* u1 = (C<T>*)(w + p->ws_u1);
     C<T>* P = (C<T>*)(w + p->ws_planes);
     Usfft2dArgs<T> a = args2d<T>(p, true);
+    a.halo = (C<T>*)(w + p->ws_halo);
     if (lam_status st = prep_scatter<T>(p, in, ws, s, a)) return st;
     const int per = even_batch(p, p->njobs_pair);
     for (int j0 = 0; j0 < p->njobs_pair; j0 += per) {
@@ -621,6 +623,7 @@ template <typename T> lam_status u2d_adj_t(const lam_plan* p, const void* in, vo
                                                   cudaStream_t s) {
     C<T>* P = (C<T>*)((char*)ws + p->ws_planes);
     Usfft2dArgs<T> a = args2d<T>(p, false);
+    a.halo = (C<T>*)((char*)ws + p->ws_halo);
     if (lam_status st = prep_scatter<T>(p, (const C<T>*)in, ws, s, a)) return st;
     for (int j0 = 0; j0 < p->h; j0 += p->nbatch)
         CK(launch_usfft2d_adj<T>((const C<T>*)in, P, (C<T>*)u1, j0, std::min(p->nbatch, p->h - j0), a, s));
@@ -924,7 +927,13 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     }
     p->ws_u1 = 0;
     p->ws_planes = align256((size_t)p->h * p->n1 * p->n2 * ce_);
-    p->ws_tmp = p->ws_planes + align256((size_t)p->nbatch * plane);
+    // halo spread: a batch of extended tiles (core + halo) per plane
+    p->ws_halo = p->ws_planes + align256((size_t)p->nbatch * plane);
+    {
+        const size_t ext = 32 + 2 * (size_t)p->m - 1;
+        const size_t ntiles = p->TS == 32 ? (size_t)(p->M1 / 32) * (p->M2 / 32) : 0;
+        p->ws_tmp = p->ws_halo + align256((size_t)p->nbatch * ntiles * ext * ext * ce_);
+    }
     p->ws_red = p->ws_tmp + align256((size_t)p->ndata() * ce_);
     // reduction scratch: scalars, per-block partials, completion counter
     // + one scalar slot for the scatter's input bound
@@ -943,6 +952,7 @@ lam_status lam_plan_set_option(lam_plan* p, int option, int value) {
             else if (value == LAM_SPREAD_TILES) p->spread = kSpreadTiles;
             else if (value == LAM_SPREAD_ATOMIC) p->spread = kSpreadAtomic;
             else if (value == LAM_SPREAD_EXACT) p->spread = kSpreadExact;
+            else if (value == LAM_SPREAD_HALO) p->spread = kSpreadHalo;
             else return fail(LAM_EINVAL, "unknown adjoint spread %d", value);
             {
                 // captured ADMM graphs hold the old kernel choice

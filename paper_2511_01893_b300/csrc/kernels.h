@@ -19,6 +19,7 @@ constexpr int kMaxDynSmem = 227 * 1024;
 constexpr int kSpreadTiles = 0;
 constexpr int kSpreadAtomic = 1;
 constexpr int kSpreadExact = 3;
+constexpr int kSpreadHalo = 4;  // owner-tile spread with halos (one visit per point)
 
 template <typename T> cudaError_t configure_usfft1d();
 template <typename T> cudaError_t configure_usfft2d();
@@ -69,7 +70,8 @@ template <typename T> struct Usfft2dArgs {
     int nimg;                       // tile images +-1..nimg checked per line (unwrapped positions)
     T rmax;                         // bound on |slice position| in grid units
     int pstride;                    // scatter: lanes take points this far apart along a line
-    int spread;                     // adjoint spread: kSpreadTiles, kSpreadAtomic or kSpreadExact
+    int spread;                     // adjoint spread: kSpreadTiles, kSpreadHalo, kSpreadAtomic or kSpreadExact
+    C<T>* halo;                     // workspace of the halo spread: [nb][tiles][ext][ext] (ext = 32 + 2m - 1)
     const int2* jobs;               // plane jobs: .x plane computed, .y its conjugate mirror plane or -1
     const T* maxabs;                // device scalar: max |re|, |im| of the scatter input (fixed point)
     float bound_count;              // bound on the products summed into one padded cell

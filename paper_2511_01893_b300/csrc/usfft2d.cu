@@ -906,6 +906,214 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
     }
 }
 
+// Owner-tile (halo) spread: every slice point is visited once, by the tile
+// that holds its window origin.  Each warp sums into a private extended tile
+// of (TS + 2m - 1)^2 cells (core + halo), so every window fits, all lanes are
+// active and no bounds checks are needed; a row pitch of 8 (mod 16) cells
+// keeps a 4-row x 8-column pass on 16 distinct bank pairs without a swizzle.
+// The warp tiles are summed in a fixed order into H[b][tile]; k_halo_sum then
+// adds the overlapping halos into the padded plane (fixed order as well).
+__host__ __device__ constexpr int spread_halo_pitch(int mh) { return ((32 + 2 * mh - 1 + 7) / 16) * 16 + 8; }
+template <typename T> size_t spread_halo_smem(int nw, int mh) {
+    return (size_t)nw * (32 + 2 * mh - 1) * spread_halo_pitch(mh) * sizeof(C<T>) +
+           (size_t)nw * (2 * mh) * kRecPitch * sizeof(C<T>) + (size_t)nw * spread_rpp(mh) * kRecPitch * spread_rec_bytes<T>(mh);
+}
+
+template <typename T, int NW, int MH>
+__device__ __forceinline__ void k_spread2d_halo_body(const C<T>* __restrict__ in, C<T>* __restrict__ H, int j0, const Usfft2dArgs<T>& a, int bx, int by) {
+    constexpr int nt = 2 * MH;
+    constexpr int RPP = 32 / nt;  // window rows per pass
+    constexpr int NPASS = (nt + RPP - 1) / RPP;
+    constexpr int TS = kSpreadTS;
+    constexpr int EXT = TS + nt - 1;        // core + halo rows / columns
+    constexpr int PITCH = spread_halo_pitch(MH);
+    constexpr int ncell = EXT * PITCH;
+    constexpr unsigned kCell = sizeof(C<T>);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    C<T>* tiles = reinterpret_cast<C<T>*>(smem_raw);  // [NW][ncell]
+    C<T>* mine = tiles + (size_t)warp * ncell;
+    unsigned char* recb = smem_raw + (size_t)NW * ncell * sizeof(C<T>);
+    // records: wyv[sy][pitch] (complex), then rec[rr][pitch] (x weights of the
+    // lane row's passes + window origin)
+    typedef SpreadRec<T, NPASS> Rec;
+    C<T>* r_wyv = reinterpret_cast<C<T>*>(recb) + (size_t)warp * nt * kRecPitch;
+    Rec* r_rec = reinterpret_cast<Rec*>(recb + (size_t)NW * nt * kRecPitch * sizeof(C<T>)) +
+                 (size_t)warp * RPP * kRecPitch;
+    for (int i = lane; i < ncell; i += 32) mine[i] = cmake<T>(0, 0);
+    __syncwarp();
+    const int tiles_y = a.M2 / TS;
+    const int tile = bx;
+    const int tx0 = (tile / tiles_y) * TS, ty0 = (tile % tiles_y) * TS;
+    const int b = by;
+    const int2 job = a.jobs[j0 + b];
+    const T hb = (T)TS * (T)0.5 + (T)1;
+    const int rr = lane / nt, sy = lane - rr * nt;
+    const bool lane_on = rr < RPP;
+    const int rrc = lane_on ? rr : 0;
+    // lane-constant shared addresses of the record entries this lane reads
+    const unsigned tile_ad = (unsigned)__cvta_generic_to_shared(mine);
+    const unsigned wyv_ad = (unsigned)__cvta_generic_to_shared(r_wyv + sy * kRecPitch);
+    const Rec* rec_lane = r_rec + (size_t)rrc * kRecPitch;
+    const unsigned lt = (1u << lane) - 1u;
+    // pass 0: the job's own plane; pass 1: its mirror plane (conjugate values
+    // spread around the negated positions, as in the atomic kernel)
+    for (int pass = 0; pass < 2; ++pass) {
+        const int kv = pass ? job.y : job.x;
+        if (kv < 0) break;
+        const int kvc = kv - a.h / 2;
+        const T sg = pass ? (T)-1 : (T)1;
+        for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
+            const int bx0 = tx0 + ix * a.M1;
+            for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
+                const int by0 = ty0 + iy * a.M2;
+                // positions whose window origin lies in the core [b0, b0 + TS)
+                const T cx = (T)(bx0 + a.m - 1) + (T)TS * (T)0.5, cy = (T)(by0 + a.m - 1) + (T)TS * (T)0.5;
+                if (sqrt(cx * cx + cy * cy) > a.rmax + hb * (T)1.5) continue;
+                T bxl = (T)(bx0 + a.m - 1), bxh = (T)(bx0 + TS + a.m - 1);
+                T byl = (T)(by0 + a.m - 1), byh = (T)(by0 + TS + a.m - 1);
+                if (pass) {
+                    const T t0 = -bxh, t1 = -bxl + (T)1, t2 = -byh, t3 = -byl + (T)1;
+                    bxl = t0; bxh = t1; byl = t2; byh = t3;
+                }
+                for_tile_points<T, NW>(a, kvc, sg * cx, sg * cy, hb, bxl, bxh, byl, byh, warp, [&](int th, int kuc) {
+                    bool ok = th >= 0;
+                    int ox = 0, oy = 0;
+                    T fx = 0, fy = 0;
+                    C<T> v = cmake<T>(0, 0);
+                    if (ok) {
+                        const typename AngleT<T>::type g = a.ang[th];
+                        int jx, jy;
+                        point_pos(g, kuc, kvc, jx, fx, jy, fy);
+                        v = in[((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2)];
+                        if (pass) {
+                            jx = -jx - 1;
+                            jy = -jy - 1;
+                            fx = (T)1 - fx;
+                            fy = (T)1 - fy;
+                            v.y = -v.y;
+                        }
+                        ox = jx - MH + 1 - bx0;
+                        oy = jy - MH + 1 - by0;
+                        ok = ox >= 0 && ox < TS && oy >= 0 && oy < TS;
+                    }
+                    const unsigned mask = __ballot_sync(0xffffffffu, ok);
+                    if (!mask) return;
+                    if (ok) {
+                        const int k = __popc(mask & lt);  // compacted record index
+#pragma unroll
+                        for (int t = 0; t < nt; ++t) {
+                            const T dy = fy + (T)(MH - 1 - t);
+                            const T wy = gexp(-dy * dy * a.inv4beta);
+                            r_wyv[t * kRecPitch + k] = cmake<T>(wy * v.x, wy * v.y);
+                        }
+#pragma unroll
+                        for (int r = 0; r < RPP; ++r) {
+                            Rec rc;
+#pragma unroll
+                            for (int q = 0; q < NPASS; ++q) {
+                                const int t = q * RPP + r;
+                                const T dx = fx + (T)(MH - 1 - t);
+                                rc.wx[q] = t < nt ? gexp(-dx * dx * a.inv4beta) : (T)0;
+                            }
+                            rc.ox = ox;
+                            rc.oy = oy;
+                            r_rec[r * kRecPitch + k] = rc;
+                        }
+                    }
+                    __syncwarp();
+                    const int cnt = __popc(mask);
+                    Rec rc = rec_lane[0];
+                    C<T> wv;
+                    lds_c(wyv_ad, wv);
+                    for (int k = 0; k < cnt; ++k) {
+                        // read the next record first (its latency overlaps the update)
+                        const int kn = k + 1 < cnt ? k + 1 : k;
+                        const Rec nrc = rec_lane[kn];
+                        C<T> nwv;
+                        lds_c(wyv_ad + kn * kCell, nwv);
+                        const int2 o = make_int2(rc.ox, rc.oy);
+                        // the window lies inside the extended tile: no bounds checks
+                        const unsigned ad0 = tile_ad + (unsigned)((o.x + rrc) * PITCH + o.y + sy) * kCell;
+#pragma unroll
+                        for (int q = 0; q < NPASS; ++q) {
+                            const unsigned ad = ad0 + (unsigned)(q * RPP * PITCH) * kCell;
+                            if (lane_on && q * RPP + rr < nt) {
+                                C<T> acc;
+                                lds_c(ad, acc);
+                                acc.x = fma(rc.wx[q], wv.x, acc.x);
+                                acc.y = fma(rc.wx[q], wv.y, acc.y);
+                                sts_c(ad, acc);
+                            }
+                        }
+                        __syncwarp();
+                        rc = nrc;
+                        wv = nwv;
+                    }
+                });
+            }
+        }
+    }
+    __syncthreads();
+    // the extended tile (core + halo) of this job's plane: H[b][tile][EXT][EXT]
+    const int ntiles = (a.M1 / TS) * tiles_y;
+    C<T>* ht = H + ((size_t)b * ntiles + tile) * EXT * EXT;
+    for (int i = threadIdx.x; i < EXT * EXT; i += blockDim.x) {
+        const int r = i / EXT, c = i - r * EXT;
+        const int si = r * PITCH + c;
+        C<T> sum = tiles[si];
+#pragma unroll
+        for (int w = 1; w < NW; ++w) {
+            const C<T> t = tiles[(size_t)w * ncell + si];
+            sum.x += t.x;
+            sum.y += t.y;
+        }
+        ht[i] = sum;
+    }
+}
+
+template <typename T, int NW, int MH>
+__global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 3 : 2) k_spread2d_halo(
+    const C<T>* __restrict__ in, C<T>* __restrict__ H, int j0, Usfft2dArgs<T> a) {
+    k_spread2d_halo_body<T, NW, MH>(in, H, j0, a, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+// P[b][x][y] = the core cell of tile (x / TS, y / TS) plus the halo cells of the
+// tiles before it in x, in y and in both (periodic), added in that order
+template <typename T>
+__global__ void __launch_bounds__(256) k_halo_sum(const C<T>* __restrict__ H, C<T>* __restrict__ P, int nb,
+                                                 int ext, Usfft2dArgs<T> a) {
+    constexpr int TS = kSpreadTS;
+    const int tx_n = a.M1 / TS, ty_n = a.M2 / TS, ntiles = tx_n * ty_n;
+    const int hw = ext - TS;
+    const long long n = (long long)nb * a.M1 * a.M2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long bp = i / ((long long)a.M1 * a.M2);
+        const int rem = (int)(i - bp * a.M1 * a.M2);
+        const int x = rem / a.M2, y = rem - x * a.M2;
+        const int tx = x / TS, dx = x - tx * TS, ty = y / TS, dy = y - ty * TS;
+        const int txm = tx == 0 ? tx_n - 1 : tx - 1, tym = ty == 0 ? ty_n - 1 : ty - 1;
+        const C<T>* hb = H + (size_t)bp * ntiles * ext * ext;
+        C<T> s = hb[((size_t)(tx * ty_n + ty) * ext + dx) * ext + dy];
+        if (dx < hw) {
+            const C<T> t = hb[((size_t)(txm * ty_n + ty) * ext + dx + TS) * ext + dy];
+            s.x += t.x;
+            s.y += t.y;
+        }
+        if (dy < hw) {
+            const C<T> t = hb[((size_t)(tx * ty_n + tym) * ext + dx) * ext + dy + TS];
+            s.x += t.x;
+            s.y += t.y;
+        }
+        if (dx < hw && dy < hw) {
+            const C<T> t = hb[((size_t)(txm * ty_n + tym) * ext + dx + TS) * ext + dy + TS];
+            s.x += t.x;
+            s.y += t.y;
+        }
+        P[i] = s;
+    }
+}
+
 template <typename T, int NW, int MH>
 __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_tiles(
     const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, Usfft2dArgs<T> a) {
@@ -1004,9 +1212,20 @@ cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int j0, int nb
         LAM_S(2, ACC) LAM_S(3, ACC) LAM_S(4, ACC) LAM_S(5, ACC) LAM_S(6, ACC) LAM_S(7, ACC) LAM_S(8, ACC) \
         default: return cudaErrorInvalidValue;                                                   \
     }
-    // the tile spread is built for 32 x 32 tiles; planes smaller than that
-    // (n < 16) take the exact atomic spread
-    if (a.spread == kSpreadTiles && a.TS == kSpreadTS) {
+    // the tile and halo spreads are built for 32 x 32 tiles; planes smaller
+    // than that (n < 16) take the exact atomic spread
+    if (a.spread == kSpreadHalo && a.TS == kSpreadTS && a.halo) {
+        const size_t st = spread_halo_smem<T>(NW, a.m);
+        switch (a.m) {
+#define LAM_H(MH) case MH: k_spread2d_halo<T, NW, MH><<<grid1, NW * 32, st, s>>>(in, a.halo, kv0, a); break;
+            LAM_H(2) LAM_H(3) LAM_H(4) LAM_H(5) LAM_H(6) LAM_H(7) LAM_H(8)
+#undef LAM_H
+            default: return cudaErrorInvalidValue;
+        }
+        const long long ncells = (long long)nb * a.M1 * a.M2;
+        const long long hb = (ncells + 255) / 256;
+        k_halo_sum<T><<<(int)(hb < 148 * 8 ? hb : 148 * 8), 256, 0, s>>>(a.halo, P, nb, kSpreadTS + 2 * a.m - 1, a);
+    } else if ((a.spread == kSpreadTiles || a.spread == kSpreadHalo) && a.TS == kSpreadTS) {
         const size_t st = spread_tiles_smem<T>(NW, a.m);
         switch (a.m) {
 #define LAM_T(MH) case MH: k_spread2d_tiles<T, NW, MH><<<grid1, NW * 32, st, s>>>(in, P, kv0, a); break;
@@ -1078,7 +1297,8 @@ template <typename T> cudaError_t configure_usfft2d() {
     if (!e) e = cudaFuncSetAttribute(k_gather2d_tiled<T, kScatterWarps, MH>, at, mt);       \
     if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 0>, at, mt);  \
     if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 3>, at, mt);    \
-    if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles<T, kScatterWarps, MH>, at, mt);
+    if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles<T, kScatterWarps, MH>, at, mt);    \
+    if (!e) e = cudaFuncSetAttribute(k_spread2d_halo<T, kScatterWarps, MH>, at, mt);
     LAM_A(2) LAM_A(3) LAM_A(4) LAM_A(5) LAM_A(6) LAM_A(7) LAM_A(8)
 #undef LAM_A
     return e;

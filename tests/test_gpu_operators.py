@@ -44,7 +44,7 @@ def test_u1d_forward_and_adjoint(geom, prec):
     assert rel(got, ref) < tol(prec)
 
 
-@pytest.mark.parametrize("spread", ["tiles", "atomic", "exact"])
+@pytest.mark.parametrize("spread", ["tiles", "halo", "atomic", "exact"])
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("geom", GEOMS, ids=IDS)
 def test_u2d_forward_and_adjoint(geom, prec, spread):
@@ -133,7 +133,7 @@ def test_adjoint_spread_variants_other_widths(m):
     plan, g = plan_and_geom(n, nz, h, w, T, 0.5, "f32", m=m)
     d = rand_data(T, h, w, 18)
     ref = olam.f_u2d_adj(d, g)
-    for spread in ("tiles", "atomic", "exact"):
+    for spread in ("tiles", "halo", "atomic", "exact"):
         p = glam.Plan(n, nz, h, w, plan.theta, 0.5, m=m, prec="f32", spread=spread)
         got = p.u2d_adj(torch.from_numpy(d)).cpu().numpy().transpose(1, 0, 2)
         assert rel(got, ref) < tol("f32"), spread
