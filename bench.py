@@ -75,13 +75,14 @@ def lhat_bytes(n, nz, h, w, T):
 # ---------------------------------------------------------------------------
 
 def source_hash():
-    """SHA-256 of the CUDA sources (csrc/*.cu, *.cuh, *.h in name order): ties a
-    stored DRAM-traffic figure to the kernels it was measured on."""
+    """SHA-256 of the device-code sources (csrc/*.cu, *.cuh, *.h in name order,
+    without the host-side C ABI in capi.cu): ties a stored DRAM-traffic figure
+    to the kernels it was measured on."""
     import hashlib
     d = os.path.join(ROOT, "paper_2511_01893_b300", "csrc")
     h = hashlib.sha256()
     for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
+        if f.endswith((".cu", ".cuh", ".h")) and f != "capi.cu":
             h.update(f.encode())
             with open(os.path.join(d, f), "rb") as fh:
                 h.update(fh.read())
@@ -343,7 +344,7 @@ def run_op_pair(args):
     from paper_2511_01893_b300 import lamino as glam
     n = args.size
     dev = torch.device("cuda", 0)
-    plan = glam.Plan(n, n, n, n, inputs.angles(n), np.deg2rad(PHI_DEG), prec="f32", device=dev)
+    plan = glam.Plan(n, n, n, n, inputs.angles(n), np.deg2rad(PHI_DEG), prec="f32", device=dev, workspace="hat")
     u = torch.rand((n, n, n), device=dev, dtype=torch.float32)
     d = torch.empty(plan.data_shape, dtype=plan.cdtype, device=dev)
     v = torch.empty_like(u)

@@ -114,6 +114,12 @@ lam_status lam_plan_autotune(lam_plan* plan, void* u, void* d_hat, void* ws, int
  * of padded planes.  Alignment: 256 bytes. */
 size_t lam_workspace_bytes(const lam_plan* plan);
 
+/* Bytes of the workspace prefix that lam_forward_hat, lam_adjoint_hat,
+ * lam_forward and tv_smooth use (everything but the data-space buffer that
+ * lam_adjoint and the Algorithm 1 ADMM form need at the end).  A buffer of
+ * this size serves those calls; the others need lam_workspace_bytes. */
+size_t lam_workspace_bytes_hat(const lam_plan* plan);
+
 /* L (Section 2, Algorithm 1 forward pass: F*_2D F_u2D F_u1D):
  *   d[th][v][u] = 1/(h w) sum_{kv,ku} u^(xi(th,kv,ku)) exp(+2 pi i (ku s/w + kv t/h)),
  * u^ evaluated by the Gaussian USFFT (oversampling 2, half-width m).

@@ -932,13 +932,15 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     {
         const size_t ext = 32 + 2 * (size_t)p->m - 1;
         const size_t ntiles = p->TS == 32 ? (size_t)(p->M1 / 32) * (p->M2 / 32) : 0;
-        p->ws_tmp = p->ws_halo + align256((size_t)p->nbatch * ntiles * ext * ext * ce_);
+        p->ws_red = p->ws_halo + align256((size_t)p->nbatch * ntiles * ext * ext * ce_);
     }
-    p->ws_red = p->ws_tmp + align256((size_t)p->ndata() * ce_);
     // reduction scratch: scalars, per-block partials, completion counter
     // + one scalar slot for the scatter's input bound
-    p->ws_bytes = p->ws_red + align256(SC_COUNT * sizeof(double)) + align256((size_t)kRedBlocks * 4 * sizeof(double)) +
-                  256 + 256;
+    p->ws_tmp = p->ws_red + align256(SC_COUNT * sizeof(double)) + align256((size_t)kRedBlocks * 4 * sizeof(double)) +
+                256 + 256;
+    // last: the data-space buffer only L^H (lam_adjoint) and the Algorithm 1
+    // form use; the L_hat / L_hat^H calls need only the workspace before it
+    p->ws_bytes = p->ws_tmp + align256((size_t)p->ndata() * ce_);
     *out = p;
     return LAM_OK;
 }
@@ -983,6 +985,7 @@ lam_status lam_plan_destroy(lam_plan* plan) {
 }
 
 size_t lam_workspace_bytes(const lam_plan* plan) { return plan ? plan->ws_bytes : 0; }
+size_t lam_workspace_bytes_hat(const lam_plan* plan) { return plan ? plan->ws_tmp : 0; }
 
 #define DISPATCH(p, F32CALL, F64CALL) ((p)->prec == LAM_F32 ? (F32CALL) : (F64CALL))
 

@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
             fn.restype = ctypes.c_int
         L.lam_workspace_bytes.argtypes = [vp]
         L.lam_workspace_bytes.restype = sz
+        L.lam_workspace_bytes_hat.argtypes = [vp]
+        L.lam_workspace_bytes_hat.restype = sz
         L.admm_u.argtypes = [vp, vp]
         L.admm_u.restype = vp
         L.lam_last_error.argtypes = []
@@ -130,7 +132,8 @@ class Plan:
 
     SPREADS = {"tiles": 0, "atomic": 1, "exact": 2, "halo": 3}
 
-    def __init__(self, n, nz, h, w, theta, phi, m=4, prec="f32", device=None, fast_adjoint=False, spread=None):
+    def __init__(self, n, nz, h, w, theta, phi, m=4, prec="f32", device=None, fast_adjoint=False, spread=None,
+                 workspace="full"):
         """spread: the adjoint's spread variant, "tiles" (default, per-warp tiles,
         reproducible), "atomic" (floating-point atomic adds) or "exact" (exact
         fixed-point atomic adds); fast_adjoint=True is "atomic"."""
@@ -156,7 +159,12 @@ class Plan:
             if spread not in self.SPREADS:
                 raise LaminoError(f"spread must be one of {sorted(self.SPREADS)}")
             _check(lib().lam_plan_set_option(self._h, 2, self.SPREADS[spread]), "lam_plan_set_option")
-        nbytes = lib().lam_workspace_bytes(self._h)
+        # "hat": only the prefix the L_hat / L_hat^H / L calls use (saves a
+        # data-sized buffer; adjoint() and ADMM then refuse to run)
+        if workspace not in ("full", "hat"):
+            raise LaminoError('workspace must be "full" or "hat"')
+        self.workspace = workspace
+        nbytes = (lib().lam_workspace_bytes if workspace == "full" else lib().lam_workspace_bytes_hat)(self._h)
         self.ws = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
 
     def __del__(self):
@@ -195,7 +203,12 @@ class Plan:
         _check(lib().lam_forward(self._h, _ptr(u), _ptr(out), _ptr(self.ws), _stream()), "lam_forward")
         return out
 
+    def _need_full(self, what):
+        if self.workspace != "full":
+            raise LaminoError(f"{what} needs the full workspace (plan created with workspace='hat')")
+
     def adjoint(self, d, out=None):
+        self._need_full("adjoint")
         d = self._inp(d, self.cdtype, self.data_shape)
         out = self._vol() if out is None else out
         _check(lib().lam_adjoint(self._h, _ptr(d), _ptr(out), _ptr(self.ws), _stream()), "lam_adjoint")
@@ -360,6 +373,7 @@ class Admm:
     """ADMM-TV state on the device (caller-allocated through torch)."""
 
     def __init__(self, plan: Plan):
+        plan._need_full("ADMM")
         self.plan = plan
         nb = ctypes.c_size_t()
         _check(lib().admm_state_bytes(plan._h, ctypes.byref(nb)), "admm_state_bytes")

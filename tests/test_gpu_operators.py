@@ -171,3 +171,17 @@ def test_autotune_keeps_results_bitwise(n):
     assert info["gather_tile"] in (16, 32, 64) and (2 * n) % info["gather_tile"] == 0
     assert torch.equal(plan.forward(u), f0)
     assert torch.equal(plan.adjoint(d), a0)
+
+
+def test_hat_workspace_serves_the_hat_operators():
+    n, nz, h, w, T = 32, 16, 32, 32, 12
+    full, g = plan_and_geom(n, nz, h, w, T, 0.4, "f32")
+    hat = glam.Plan(n, nz, h, w, full.theta, 0.4, prec="f32", workspace="hat")
+    assert hat.ws.numel() < full.ws.numel()
+    u = torch.from_numpy(rand_vol(n, nz, 21)).cuda().float()
+    d = torch.from_numpy(rand_data(T, h, w, 22)).cuda().to(torch.complex64)
+    assert torch.equal(hat.forward_hat(u), full.forward_hat(u))
+    assert torch.equal(hat.adjoint_hat(d), full.adjoint_hat(d))
+    assert torch.equal(hat.forward(u), full.forward(u))
+    with pytest.raises(glam.LaminoError, match="full workspace"):
+        hat.adjoint(d)
