@@ -11,8 +11,9 @@
  * Conventions shared by every entry point
  * ---------------------------------------
  * Sizes.  n = n1 = n2 (lateral, x and y), nz = n0 (z, the rotation axis),
- *   det_h = h and det_w = w (detector rows and columns), n_theta = T.  All of
- *   n, nz, h, w must be powers of two in [8, 2048]; T >= 1.
+ *   det_h = h and det_w = w (detector rows and columns), n_theta = T.  Each of
+ *   n, nz, h, w must be even, of the form 2^a 3^b 5^c and in [8, 2048], n
+ *   also a multiple of 8; 1 <= T <= 65536.
  * Layouts (row-major, last index fastest):
  *   volume u       real      [n][nz][n]   = u[x][z][y]
  *   data d, d_hat  complex   [T][h][w]    = d[theta][v][u]   (interleaved re, im)
@@ -24,6 +25,10 @@
  *   tomography about z).  Slice frequencies are
  *     xi = (ku/w) (cos th, sin th, 0) + (kv/h) (sin phi sin th, -sin phi cos th, cos phi),
  *   ku in [-w/2, w/2), kv in [-h/2, h/2); coordinates are centred.
+ * Alignment.  Arrays are aligned to their element type (complex arrays to
+ *   the complex element: 8 bytes FP32, 16 bytes FP64); a real volume u passed
+ *   to a forward call must start on a two-element boundary (8 / 16 bytes), or
+ *   the call returns LAM_EINVAL.
  * Pointers.  Every array argument is a device pointer owned by the caller
  *   (reconstruct() alone also accepts host pointers).  Nothing on the
  *   operator or ADMM path allocates: scratch comes from the caller's

@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdarg>
+#include <cstdint>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -989,9 +990,21 @@ size_t lam_workspace_bytes_hat(const lam_plan* plan) { return plan ? plan->ws_tm
 
 #define DISPATCH(p, F32CALL, F64CALL) ((p)->prec == LAM_F32 ? (F32CALL) : (F64CALL))
 
+// the z stage copies volume columns in pairs (one complex element each), so
+// a real volume must start on a two-element boundary
+static lam_status check_vol_align(int prec, const void* u, int i = -1) {
+    const size_t al = prec == LAM_F32 ? 8 : 16;
+    if ((uintptr_t)u % al) {
+        if (i >= 0) return fail(LAM_EINVAL, "volume %d is not %zu-byte aligned", i, al);
+        return fail(LAM_EINVAL, "volume is not %zu-byte aligned", al);
+    }
+    return LAM_OK;
+}
+
 lam_status lam_forward_hat(const lam_plan* p, const void* u, void* d_hat, const void* sub, void* ws, void* stream) {
     if (lam_status st = check_plan(p)) return st;
     if (!u || !d_hat || !ws) return fail(LAM_EINVAL, "NULL array argument");
+    if (lam_status st = check_vol_align(p->prec, u)) return st;
     cudaStream_t s = (cudaStream_t)stream;
     return DISPATCH(p, fwd_hat<float>(p, (const float*)u, (C<float>*)d_hat, (const C<float>*)sub, ws, s),
                     fwd_hat<double>(p, (const double*)u, (C<double>*)d_hat, (const C<double>*)sub, ws, s));
@@ -1263,6 +1276,7 @@ lam_status reconstruct(const float* data, const double* theta, double phi, int n
 
 lam_status lamx_u1d_fwd(const lam_plan* p, const void* u, void* u1, void* stream) {
     if (lam_status st = check_plan(p)) return st;
+    if (lam_status st = check_vol_align(p->prec, u)) return st;
     cudaStream_t s = (cudaStream_t)stream;
     CK(DISPATCH(p, launch_usfft1d_fwd<float>((const float*)u, (C<float>*)u1, args1d<float>(p, p->TYf, false), s),
                 launch_usfft1d_fwd<double>((const double*)u, (C<double>*)u1, args1d<double>(p, p->TYf, false), s)));
@@ -1444,6 +1458,8 @@ static lam_status check_batch_arrays(const lam_batch* b, const void* const* a, c
 
 lam_status lam_forward_hat_batched(const lam_batch* b, const void* const* u, void* const* d_hat, void* stream) {
     if (lam_status st = check_batch_arrays(b, u, (const void* const*)d_hat)) return st;
+    for (int i = 0; i < b->count; ++i)
+        if (lam_status st = check_vol_align(b->prec, u[i], i)) return st;
     cudaStream_t s = (cudaStream_t)stream;
     return b->prec == LAM_F32 ? batch_fwd_hat<float>(b, u, d_hat, s) : batch_fwd_hat<double>(b, u, d_hat, s);
 }

@@ -117,4 +117,19 @@ __host__ __device__ __forceinline__ int wrap(int j, int M) {
     return r < 0 ? r + M : r;
 }
 
+// Asynchronous global -> shared copy of one complex element (cp.async: no
+// register staging, so every copy a thread issues is in flight at once).
+// After cp_async_wait_all() a thread sees its own copies; other threads'
+// copies need a barrier as well.
+template <typename T> __device__ __forceinline__ void cp_async_elem(C<T>* dst, const C<T>* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    if constexpr (sizeof(C<T>) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 }  // namespace lam

@@ -46,13 +46,24 @@ __device__ __forceinline__ void k_usfft1d_fwd_body(const T* __restrict__ u, C<T>
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int twM0 = a.twstride;  // Nmax / M0
     const T* src = u + (size_t)x * nz * a.n2 + y0;
+    // the column pair (2p, 2p + 1) is one aligned complex element (n2, y0 even);
+    // it is copied raw into the even line, then scaled and twiddled in place by
+    // the thread that copied it
     for (int i = tid; i < nz * npair; i += nthr) {
         const int z = i >> ilog2_pow2(npair), p = i - z * npair;  // npair = TY / 2, a power of two
+        const int q = wrap(z - nz / 2, nz);
+        cp_async_elem<T>(buf + (2 * p) * LS + fpad(q), reinterpret_cast<const C<T>*>(src + (size_t)z * a.n2 + 2 * p));
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    for (int i = tid; i < nz * npair; i += nthr) {
+        const int z = i >> ilog2_pow2(npair), p = i - z * npair;
         const int xc = z - nz / 2;
-        const T d = a.dz[z];
-        const T va = src[(size_t)z * a.n2 + 2 * p] * d, vb = src[(size_t)z * a.n2 + 2 * p + 1] * d;
-        const C<T> w = a.tw[wrap(xc, a.M0) * twM0];  // e^{-2 pi i xc / M0}
         const int q = wrap(xc, nz);
+        const T d = a.dz[z];
+        const C<T> raw = buf[(2 * p) * LS + fpad(q)];
+        const T va = raw.x * d, vb = raw.y * d;
+        const C<T> w = a.tw[wrap(xc, a.M0) * twM0];  // e^{-2 pi i xc / M0}
         buf[(2 * p) * LS + fpad(q)] = cmake<T>(va, vb);
         buf[(2 * p + 1) * LS + fpad(q)] = cmake<T>(va * w.x - vb * w.y, va * w.y + vb * w.x);
     }
@@ -129,8 +140,11 @@ __device__ __forceinline__ void k_usfft1d_adj_body(const C<T>* __restrict__ u1, 
     const size_t plane = (size_t)a.n1 * a.n2;
     for (int i = tid; i < a.h * a.TY; i += nthr) {
         const int kv = i >> ilog2_pow2(a.TY), c = i - kv * a.TY;  // TY is a power of two
-        vals[c * a.h + kv] = (a.skip && a.skip[kv]) ? cmake<T>(0, 0) : src[kv * plane + c];
+        if (a.skip && a.skip[kv]) vals[c * a.h + kv] = cmake<T>(0, 0);
+        else cp_async_elem<T>(vals + c * a.h + kv, src + kv * plane + c);
     }
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
     const int nt = 2 * a.m;
     const int half = M0 / 2;

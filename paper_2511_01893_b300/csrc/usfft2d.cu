@@ -49,8 +49,15 @@ __device__ __forceinline__ void k_rowfft_fwd_body(const C<T>* __restrict__ u1, C
     const C<T>* src = u1 + ((size_t)kv * a.n1 + x0) * a.n2;
     for (int i = tid; i < a.RB * a.n2; i += nthr) {
         const int r = udiv<!MIXED>(i, a.n2, ilog2_pow2(a.n2)), y = i - r * a.n2;
-        const T s = a.d1[x0 + r] * a.d2[y];
-        bufa[r * LS + fpad(wrap(y - a.n2 / 2, a.M2))] = cscale(src[i], s);
+        cp_async_elem<T>(bufa + r * LS + fpad(wrap(y - a.n2 / 2, a.M2)), src + i);
+    }
+    cp_async_commit();
+    cp_async_wait_all();
+    // each thread deapodises the elements it copied
+    for (int i = tid; i < a.RB * a.n2; i += nthr) {
+        const int r = udiv<!MIXED>(i, a.n2, ilog2_pow2(a.n2)), y = i - r * a.n2;
+        C<T>* e = bufa + r * LS + fpad(wrap(y - a.n2 / 2, a.M2));
+        *e = cscale(*e, a.d1[x0 + r] * a.d2[y]);
     }
     __syncthreads();
     fft_lines_ip<-1, FftMaxB<T>::value, T, MIXED>(bufa, a.RB, LS, a.M2, a.fcM2, a.tw, a.tw2);
@@ -129,16 +136,6 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_adj(C<T>* __restrict__ P
 // are in flight while the current strip is transformed and stored.
 // ---------------------------------------------------------------------------
 
-template <typename T> __device__ __forceinline__ void cp_async_elem(C<T>* dst, const C<T>* src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    if constexpr (sizeof(C<T>) == 8)
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
-    else
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
 // forward: rows wrap(x - n1/2) (x < n1) hold data, the others are zero padding;
 // the FFT overwrites every row, so after the stores the padding rows are
@@ -250,8 +247,10 @@ __device__ __forceinline__ void k_rowfft_adj_body(const C<T>* __restrict__ P, C<
     const int LS = fpad_len(a.M2);
     for (int i = tid; i < a.RB * a.M2; i += nthr) {
         const int r = udiv<!MIXED>(i, a.M2, ilog2_pow2(a.M2)), j = i - r * a.M2;
-        bufa[r * LS + fpad(j)] = pl[(size_t)wrap(x0 + r - a.n1 / 2, a.M1) * a.M2 + j];
+        cp_async_elem<T>(bufa + r * LS + fpad(j), pl + (size_t)wrap(x0 + r - a.n1 / 2, a.M1) * a.M2 + j);
     }
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
     fft_lines_ip<+1, FftMaxB<T>::value, T, MIXED>(bufa, a.RB, LS, a.M2, a.fcM2, a.tw, a.tw2);
     C<T>* dst = u1 + ((size_t)kv * a.n1 + x0) * a.n2;
@@ -440,15 +439,16 @@ __device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P
     if (mirror && job.y < 0) return;
     const int kv = mirror ? job.y : job.x, kvc = kv - a.h / 2;
     const C<T>* pl = P + (size_t)b * a.M1 * a.M2;
+    // P_mirror[j] = conj P[-j]: the mirror plane stages P[-j] and conjugates
+    // the result (the weights are real, so sum w conj P = conj sum w P,
+    // bitwise)
     for (int i = threadIdx.x; i < SH * SH; i += blockDim.x) {
         const int r = i / SH, c = i - r * SH;
-        if (!mirror) {
-            st[r * SW + c] = pl[(size_t)wrap(tx0 + r, a.M1) * a.M2 + wrap(ty0 + c, a.M2)];
-        } else {  // P_mirror[j] = conj P[-j]
-            const C<T> v = pl[(size_t)wrap(-(tx0 + r), a.M1) * a.M2 + wrap(-(ty0 + c), a.M2)];
-            st[r * SW + c] = cmake<T>(v.x, -v.y);
-        }
+        const int gx = mirror ? -(tx0 + r) : tx0 + r, gy = mirror ? -(ty0 + c) : ty0 + c;
+        cp_async_elem<T>(st + r * SW + c, pl + (size_t)wrap(gx, a.M1) * a.M2 + wrap(gy, a.M2));
     }
+    cp_async_commit();
+    cp_async_wait_all();
     __syncthreads();
     const T hb = (T)TS * (T)0.5 + (T)1;
     for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
@@ -504,7 +504,7 @@ __device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P
 #endif
                 }
                 const size_t o = ((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2);
-                C<T> v = cmake<T>(sr, si);
+                C<T> v = cmake<T>(sr, mirror ? -si : si);
                 if (sub) v = csub(v, sub[o]);
                 out[o] = v;
             });
