@@ -97,8 +97,18 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *   plain form: each CG step forms r = L u - d with the full L, applies the
  *   full L^H, and applies L to the direction: two L and one L^H).  Both give
  *   the same iterates up to rounding; the option exists for the comparison.
+ * LAM_OPT_Z_THREADS, LAM_OPT_PLANE_FFT_THREADS (256 or 512) are the threads
+ *   per block of the z-stage kernels and of the plane row / column FFT
+ *   kernels.  The columns, rows or lines per block are picked again to fit;
+ *   256 lets two blocks share an SM.  Results do not depend on either.
  * Setting an option invalidates ADMM graphs captured with the plan. */
-enum { LAM_OPT_FAST_ADJOINT = 1, LAM_OPT_ADJOINT_SPREAD = 2, LAM_OPT_LSP_FORM = 3 };
+enum {
+    LAM_OPT_FAST_ADJOINT = 1,
+    LAM_OPT_ADJOINT_SPREAD = 2,
+    LAM_OPT_LSP_FORM = 3,
+    LAM_OPT_Z_THREADS = 4,
+    LAM_OPT_PLANE_FFT_THREADS = 5
+};
 enum { LAM_SPREAD_TILES = 0, LAM_SPREAD_ATOMIC = 1, LAM_SPREAD_EXACT = 2, LAM_SPREAD_HALO = 3 };
 lam_status lam_plan_set_option(lam_plan* plan, int option, int value);
 

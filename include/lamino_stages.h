@@ -49,7 +49,8 @@ lam_status lamx_u2d_fwd_static(const lam_plan* plan, const void* u1, void* d_hat
  * TY (z forward), TY (z transpose), rows per block, columns per block,
  * scatter tile side, tile images, planes per batch, jmin, jmax, the
  * number of plane jobs the full operators run (h/2 + 1 when every plane
- * pairs with its conjugate mirror), and the gather tile side. */
+ * pairs with its conjugate mirror), the gather tile side, and the threads
+ * per block of the z stage and of the plane FFTs. */
 lam_status lamx_plan_info(const lam_plan* plan, int* out, int count);
 
 /* Batch diagnostics: out[2 s], out[2 s + 1] = work items and persistent grid

@@ -61,16 +61,32 @@ def centred(n: int) -> np.ndarray:
     return np.arange(n, dtype=np.float64) - n // 2
 
 
+def _xi(th, kv, ku, phi):
+    """xi = ku e_u + kv e_v for kv, ku already divided by h, w (broadcasting)."""
+    sp, cp = np.sin(phi), np.cos(phi)
+    xi_x = ku * np.cos(th) + kv * sp * np.sin(th)
+    xi_y = ku * np.sin(th) - kv * sp * np.cos(th)
+    xi_z = kv * cp
+    return xi_x, xi_y, xi_z
+
+
 def slice_frequencies(g: Geometry):
     """(xi_x, xi_y) of shape [n_theta, h, w] and xi_z of shape [h]."""
     th = np.asarray(g.theta, dtype=np.float64)[:, None, None]
     kv = centred(g.h)[None, :, None] / g.h
     ku = centred(g.w)[None, None, :] / g.w
-    sp, cp = np.sin(g.phi), np.cos(g.phi)
-    xi_x = ku * np.cos(th) + kv * sp * np.sin(th)
-    xi_y = ku * np.sin(th) - kv * sp * np.cos(th)
-    xi_z = centred(g.h) / g.h * cp
+    xi_x, xi_y, _ = _xi(th, kv, ku, g.phi)
+    _, _, xi_z = _xi(0.0, centred(g.h) / g.h, 0.0, g.phi)
     return xi_x, xi_y, xi_z
+
+
+def slice_frequency_points(g: Geometry, t, kv, ku):
+    """(xi_x, xi_y, xi_z) of the slice points (theta index t, row kv in [0, h),
+    column ku in [0, w)), given as equal-length index arrays."""
+    th = np.asarray(g.theta, dtype=np.float64)[np.asarray(t)]
+    kvr = (np.asarray(kv, dtype=np.float64) - g.h // 2) / g.h
+    kur = (np.asarray(ku, dtype=np.float64) - g.w // 2) / g.w
+    return _xi(th, kvr, kur, g.phi)
 
 
 # ----------------------------------------------------------------------------
@@ -179,6 +195,80 @@ def lhat_exact(u: np.ndarray, g: Geometry) -> np.ndarray:
         uz = np.tensordot(u, ez, axes=([1], [0]))                    # [n1, n2]
         out[:, kv, :] = np.einsum("twa,ab,twb->tw", ex, uz, ey)
     return out
+
+
+def lhat_exact_points(voxels, values, g: Geometry, t, kv, ku) -> np.ndarray:
+    """u^(xi) at the slice points (t[i], kv[i], ku[i]) for a volume that is zero
+    except u[ix, iz, iy] = values[k] at voxels[k] = (ix, iz, iy): the direct sum
+    of the definition, at any size (cost: points x voxels)."""
+    xi_x, xi_y, xi_z = slice_frequency_points(g, t, kv, ku)
+    vox = np.asarray(voxels, dtype=np.float64)
+    rx = vox[:, 0] - g.n1 // 2
+    rz = vox[:, 1] - g.n0 // 2
+    ry = vox[:, 2] - g.n2 // 2
+    phase = np.outer(xi_x, rx) + np.outer(xi_y, ry) + np.outer(xi_z, rz)
+    return np.exp(-2j * np.pi * phase) @ np.asarray(values, dtype=np.complex128)
+
+
+def lhat_adj_exact_points(t, kv, ku, values, g: Geometry, voxels, real: bool = True) -> np.ndarray:
+    """(L-hat^H r)[ix, iz, iy] at voxels[k] = (ix, iz, iy) for data that is zero
+    except r[t[i], kv[i], ku[i]] = values[i]: sum_i r_i exp(+2 pi i xi_i . r),
+    the transpose of lhat_exact under Re <a, b> (Re for a real u)."""
+    xi_x, xi_y, xi_z = slice_frequency_points(g, t, kv, ku)
+    vox = np.asarray(voxels, dtype=np.float64)
+    rx = vox[:, 0] - g.n1 // 2
+    rz = vox[:, 1] - g.n0 // 2
+    ry = vox[:, 2] - g.n2 // 2
+    phase = np.outer(rx, xi_x) + np.outer(ry, xi_y) + np.outer(rz, xi_z)
+    v = np.exp(2j * np.pi * phase) @ np.asarray(values, dtype=np.complex128)
+    return v.real if real else v
+
+
+def _xi_z(g: Geometry) -> np.ndarray:
+    return _xi(0.0, centred(g.h) / g.h, 0.0, g.phi)[2]
+
+
+def lhat_sparse_points(voxels, values, g: Geometry, t, kv, ku) -> np.ndarray:
+    """lhat(u, g)[t, kv, ku] for a volume that is zero except
+    u[ix, iz, iy] = values[k] at voxels[k] = (ix, iz, iy) (distinct voxels),
+    by the steps of lhat restricted to what those outputs need: F_u1D of the
+    occupied (x, y) columns, then for each sampled kv the F_u2D grid of that
+    plane gathered at its sampled points.  Equal to lhat up to rounding order;
+    its cost does not grow with n_theta, h or w, so it reaches full sizes."""
+    vox = np.asarray(voxels)
+    t, kv, ku = np.asarray(t), np.asarray(kv), np.asarray(ku)
+    cols, inv = np.unique(vox[:, [0, 2]], axis=0, return_inverse=True)
+    ucols = np.zeros((len(cols), g.n0))
+    np.add.at(ucols, (inv.ravel(), vox[:, 1]), np.asarray(values, dtype=np.float64))
+    u1c = usfft.usfft1d_type2(ucols, _xi_z(g), g.m, g.R, axis=-1)      # [columns, h]
+    xi_x, xi_y, _ = slice_frequency_points(g, t, kv, ku)
+    out = np.empty(len(t), dtype=np.complex128)
+    for k in np.unique(kv):
+        plane = np.zeros((g.n1, g.n2), dtype=np.complex128)
+        plane[cols[:, 0], cols[:, 1]] = u1c[:, k]
+        P = usfft.usfft2d_grid(plane, g.m, g.R)
+        sel = kv == k
+        out[sel] = usfft.usfft2d_gather(P, xi_x[sel], xi_y[sel], g.m, g.R)
+    return out
+
+
+def lhat_adj_sparse_points(t, kv, ku, values, g: Geometry, voxels, real: bool = True) -> np.ndarray:
+    """lhat_adj(r, g)[ix, iz, iy] at voxels[k] = (ix, iz, iy) for data that is
+    zero except r[t[i], kv[i], ku[i]] = values[i] (distinct points): F*_u2D of
+    each occupied kv plane from its non-zero points (zero points add nothing
+    to the spread), then F*_u1D of the sampled (x, y) columns."""
+    t, kv, ku = np.asarray(t), np.asarray(kv), np.asarray(ku)
+    values = np.asarray(values, dtype=np.complex128)
+    vox = np.asarray(voxels)
+    xi_x, xi_y, _ = slice_frequency_points(g, t, kv, ku)
+    col = np.zeros((len(vox), g.h), dtype=np.complex128)
+    for k in np.unique(kv):
+        sel = kv == k
+        a = usfft.usfft2d_type1(values[sel], xi_x[sel], xi_y[sel], g.n1, g.n2, g.m, g.R)
+        col[:, k] = a[vox[:, 0], vox[:, 2]]
+    v = usfft.usfft1d_type1(col, _xi_z(g), g.n0, g.m, g.R, axis=-1)    # [voxels, n0]
+    out = v[np.arange(len(vox)), vox[:, 1]]
+    return out.real if real else out
 
 
 def lam_forward_exact(u: np.ndarray, g: Geometry) -> np.ndarray:

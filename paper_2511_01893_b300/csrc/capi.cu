@@ -93,6 +93,7 @@ struct lam_plan {
     int njobs_pair;
     // launch shapes
     int TYf, TYa, RB, CB, TS, TG, nimg, nbatch;
+    int zthr = kFftThreads, pthr = kFftThreads;  // threads per z-stage / plane-FFT block
     double rmax;
     int pstride;
     int spread = kSpreadTiles;
@@ -300,13 +301,28 @@ template <typename T> lam_status build_tables(lam_plan* p, const double* theta) 
 // lines per block for an in-place FFT of length len: within the shared-memory
 // budget, within the FFT's register capacity (lines * len <= capacity * 512
 // threads), and dividing `divides` (the grid covers it exactly)
-static int pick_lines(int len, size_t celem, size_t budget, int divides, int cap, int maxb, size_t extra_per_line = 0) {
-    const long long capacity = (long long)fft_capacity(fft_code(len), maxb) * kFftThreads;
+static int pick_lines(int len, size_t celem, size_t budget, int divides, int cap, int maxb, size_t extra_per_line = 0,
+                      int threads = kFftThreads) {
+    const long long capacity = (long long)fft_capacity(fft_code(len), maxb) * threads;
     int l = cap;
     while (l > 1 && ((size_t)l * ((len + len / 16 + 1) * celem + extra_per_line) > budget ||
                      (long long)l * len > capacity || divides % l != 0))
         l >>= 1;
     return l;
+}
+
+// z stage: TY columns per block (column pairs share one complex line; E and
+// O halves are nz long each); plane FFTs: RB rows / CB columns per block.
+// Each within the FFT's capacity for the stage's block size.
+static void pick_fft_shapes(lam_plan* p) {
+    const size_t ce_ = p->celem();
+    const size_t budget = p->zthr <= 256 ? 100 * 1024 : 200 * 1024;
+    const size_t pbudget = p->pthr <= 256 ? 64 * 1024 : 128 * 1024;
+    const int maxb = p->prec == LAM_F32 ? 2 : 1;
+    p->TYf = std::max(2, pick_lines(p->nz, ce_, budget, p->n2, 16, maxb, 0, p->zthr));
+    p->TYa = std::max(2, pick_lines(p->nz, ce_, budget, p->n2, 16, maxb, (size_t)p->h * ce_, p->zthr));
+    p->RB = pick_lines(p->M2, ce_, pbudget, p->n1, 16, maxb, 0, p->pthr);
+    p->CB = pick_lines(p->M1, ce_, pbudget, p->M2, 16, maxb, 0, p->pthr);
 }
 
 template <typename T> Usfft1dArgs<T> args1d(const lam_plan* p, int TY, bool paired) {
@@ -319,6 +335,7 @@ template <typename T> Usfft1dArgs<T> args1d(const lam_plan* p, int TY, bool pair
     a.fcz = fft_code(p->nz, fft_max_radix<T>());
     a.m = p->m;
     a.TY = TY;
+    a.nthr = p->zthr;
     a.dz = (const T*)p->dz;
     a.j0z = p->j0z;
     a.wz = (const T*)p->wz;
@@ -353,6 +370,7 @@ template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p, bool paired) {
     a.tw2 = p->Nmax / p->M2;
     a.RB = p->RB;
     a.CB = p->CB;
+    a.fthr = p->pthr;
     a.TS = p->TS;
     a.TG = p->TG;
     a.nimg = p->nimg;
@@ -891,15 +909,8 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
         lam_plan_destroy(p);
         return st;
     }
+    pick_fft_shapes(p);
     const size_t ce_ = p->celem();
-    const size_t budget = 200 * 1024;
-    const int maxb = prec == LAM_F32 ? 2 : 1;
-    // z stage: TY columns per block
-    // (column pairs share one complex line; E and O halves are nz long each)
-    p->TYf = std::max(2, pick_lines(p->nz, ce_, budget, p->n2, 16, maxb));
-    p->TYa = std::max(2, pick_lines(p->nz, ce_, budget, p->n2, 16, maxb, (size_t)p->h * ce_));
-    p->RB = pick_lines(p->M2, ce_, 128 * 1024, p->n1, 16, maxb);
-    p->CB = pick_lines(p->M1, ce_, 128 * 1024, p->M2, 16, maxb);
     // plane tiles divide M1 = M2 = 2n (a multiple of 16): spread tiles 32 (the
     // tile spread's size) when possible; gather tiles up to 64, since larger
     // tiles amortise the per-block line tests over more points
@@ -971,6 +982,19 @@ lam_status lam_plan_set_option(lam_plan* p, int option, int value) {
             if (value != 1 && value != 2) return fail(LAM_EINVAL, "LSP form %d: 1 or 2", value);
             p->lsp_form = value;
             return LAM_OK;
+        case LAM_OPT_Z_THREADS:
+        case LAM_OPT_PLANE_FFT_THREADS: {
+            if (value != 256 && value != 512) return fail(LAM_EINVAL, "threads per block %d: 256 or 512", value);
+            (option == LAM_OPT_Z_THREADS ? p->zthr : p->pthr) = value;
+            pick_fft_shapes(p);  // batches built earlier keep their own shapes
+            std::lock_guard<std::mutex> lk(p->mu);
+            for (auto& kv : p->admm)
+                if (kv.second.graph) {
+                    cudaGraphExecDestroy(kv.second.graph);
+                    kv.second.graph = nullptr;
+                }
+            return LAM_OK;
+        }
         default:
             return fail(LAM_EINVAL, "unknown option %d", option);
     }
@@ -1354,6 +1378,21 @@ lam_status lam_plan_autotune(lam_plan* p, void* u, void* d_hat, void* ws, int re
     // divisibility and shared-memory rule the plan's own choice obeys
     double best = 0;
     err = measure(&best);
+    // threads per block first: each choice re-picks the lines per block
+    for (int which = 0; which < 2 && !err; ++which) {
+        int& thr = which ? p->pthr : p->zthr;
+        const int keep = thr;
+        thr = keep == 512 ? 256 : 512;
+        pick_fft_shapes(p);
+        double t = 0;
+        if ((err = measure(&t))) break;
+        if (t < best) {
+            best = t;
+        } else {
+            thr = keep;
+            pick_fft_shapes(p);
+        }
+    }
     struct Knob {
         int* v;
         std::vector<int> cand;
@@ -1620,7 +1659,8 @@ lam_status lamx_admm_graph_kernels(const lam_plan* p, void* state, size_t* count
 
 lam_status lamx_plan_info(const lam_plan* p, int* out, int count) {
     if (lam_status st = check_plan(p)) return st;
-    const int v[] = {p->TYf, p->TYa, p->RB, p->CB, p->TS, p->nimg, p->nbatch, p->jmin, p->jmax, p->njobs_pair, p->TG};
+    const int v[] = {p->TYf,  p->TYa,  p->RB,   p->CB,         p->TS, p->nimg, p->nbatch,
+                     p->jmin, p->jmax, p->njobs_pair, p->TG, p->zthr, p->pthr};
     const int nv = (int)(sizeof(v) / sizeof(v[0]));
     for (int i = 0; i < count && i < nv; ++i) out[i] = v[i];
     return LAM_OK;

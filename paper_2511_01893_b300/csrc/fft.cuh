@@ -378,4 +378,145 @@ __device__ __forceinline__ void fft_lines_ip(C<T>* buf, int nlines, int lstride,
     }
 }
 
+// ---------------------------------------------------------------------------
+// Compile-time length.  The same stages and arithmetic as fft_lines_ip (the
+// same stage sequence, butterflies, twiddles and operation order, so the
+// result is bitwise the same), with N, the stage radices, Ns and the line
+// stride fpad_len(N) known to the compiler: divisions become shifts and the
+// padded shared-memory offsets of a butterfly's R inputs and outputs become
+// constants from one base address.  For power-of-two N only.
+// ---------------------------------------------------------------------------
+
+__host__ __device__ constexpr int fft_code_pow2(int N, int maxr) {
+    int a = 0;
+    for (int m = N; m > 1; m >>= 1) ++a;
+    const int maxbits = maxr >= 16 ? 4 : 3;
+    const int nst = (a + maxbits - 1) / maxbits;
+    int code = 0, shift = 0;
+    for (int k = 0; k < nst; ++k) {
+        const int bits = (a + (nst - k) - 1) / (nst - k);
+        code |= (bits == 4 ? 6 : bits == 3 ? 3 : bits == 2 ? 2 : 1) << shift;
+        shift += 3;
+        a -= bits;
+    }
+    return code;
+}
+
+// padded offset of element e + r * step relative to fpad(e), when step is a
+// multiple of 16 (the pad count then grows by step / 16 per r)
+template <int STEP> __device__ __forceinline__ constexpr int fpad_step(int r) { return r * (STEP + STEP / 16); }
+
+template <int R, int DIR, int MAXB, typename T, int N, int NS>
+__device__ __forceinline__ void fft_stage_ct(C<T>* buf, int nlines, const C<T>* __restrict__ tw, int twstride, int tid,
+                                             int nthr) {
+    constexpr int nb = N / R;
+    constexpr int LS = N + N / 16 + 1;  // fpad_len(N)
+    const int total = nlines * nb;
+    const int twstep = (N / (NS * R)) * twstride;
+    C<T> v[MAXB][R];
+#pragma unroll
+    for (int bb = 0; bb < MAXB; ++bb) {
+        const int q = tid + bb * nthr;
+        if (q < total) {
+            const int line = q / nb, j = q % nb;
+            const C<T>* s = buf + line * LS;
+            if constexpr (nb % 16 == 0) {
+                const C<T>* s0 = s + fpad(j);
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[bb][r] = s0[fpad_step<nb>(r)];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[bb][r] = s[fpad(j + r * nb)];
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int bb = 0; bb < MAXB; ++bb) {
+        const int q = tid + bb * nthr;
+        if (q < total) {
+            const int line = q / nb, j = q % nb;
+            const int k = j & (NS - 1);
+            if constexpr (NS > 1) {
+                if constexpr (R == 16) {
+                    const int i1 = k * twstep;
+                    C<T> w1 = tw[i1], w2 = tw[2 * i1], w4 = tw[4 * i1], w8 = tw[8 * i1];
+                    if (DIR > 0) {
+                        w1.y = -w1.y;
+                        w2.y = -w2.y;
+                        w4.y = -w4.y;
+                        w8.y = -w8.y;
+                    }
+                    C<T> w = w1;
+#pragma unroll
+                    for (int r = 1; r < 8; ++r) {
+                        if (r == 2) w = w2;
+                        else if (r == 4) w = w4;
+                        else if (r > 1) w = cmul(w, w1);
+                        v[bb][r] = cmul(v[bb][r], w);
+                        v[bb][r + 8] = cmul(v[bb][r + 8], cmul(w, w8));
+                    }
+                    v[bb][8] = cmul(v[bb][8], w8);
+                } else {
+                    C<T> wv[R];
+                    twiddles<R, DIR, T>(wv, tw, k * twstep);
+#pragma unroll
+                    for (int r = 1; r < R; ++r) v[bb][r] = cmul(v[bb][r], wv[r]);
+                }
+            }
+            if constexpr (R == 16) dft16<DIR>(v[bb]);
+            else if constexpr (R == 8) dft8<DIR>(v[bb]);
+            else if constexpr (R == 4) dft4<DIR>(v[bb]);
+            else dft2<DIR>(v[bb]);
+            C<T>* d = buf + line * LS;
+            const int base = (j - k) * R + k;
+            if constexpr (NS % 16 == 0) {
+                C<T>* d0 = d + fpad(base);
+#pragma unroll
+                for (int r = 0; r < R; ++r) d0[fpad_step<NS>(r)] = v[bb][R == 16 ? dft16_out(r) : r];
+            } else if constexpr (NS == 1 && R == 16) {
+                C<T>* d0 = d + 17 * j;  // fpad(16 j + r) = 17 j + r
+#pragma unroll
+                for (int r = 0; r < R; ++r) d0[r] = v[bb][dft16_out(r)];
+            } else if constexpr (NS == 1 && R == 8) {
+                C<T>* d0 = d + 8 * j + (j >> 1);  // fpad(8 j + r) = 8 j + j / 2 + r for r < 8
+#pragma unroll
+                for (int r = 0; r < R; ++r) d0[r] = v[bb][r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) d[fpad(base + r * NS)] = v[bb][R == 16 ? dft16_out(r) : r];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <int DIR, int MAXB, typename T, int N, int CODE, int NS>
+__device__ __forceinline__ void fft_stages_ct(C<T>* buf, int nlines, const C<T>* __restrict__ tw, int twstride,
+                                              int tid, int nthr) {
+    if constexpr (CODE != 0) {
+        constexpr int R = fft_stage_radix(CODE & 7);
+        fft_stage_ct<R, DIR, fft_stage_maxb(R, MAXB), T, N, NS>(buf, nlines, tw, twstride, tid, nthr);
+        fft_stages_ct<DIR, MAXB, T, N, (CODE >> 3), NS * R>(buf, nlines, tw, twstride, tid, nthr);
+    }
+}
+
+// fft_lines_ip for a compile-time power-of-two length N (the stage code is
+// fft_code(N, fft_max_radix<T>())), lines at stride fpad_len(N).
+template <int DIR, int MAXB, typename T, int N>
+__device__ __forceinline__ void fft_lines_ct(C<T>* buf, int nlines, const C<T>* __restrict__ tw, int twstride) {
+    static_assert(N >= 16 && (N & (N - 1)) == 0, "power-of-two length");
+    constexpr int code = fft_code_pow2(N, fft_max_radix<T>());
+    fft_stages_ct<DIR, MAXB, T, N, code, 1>(buf, nlines, tw, twstride, threadIdx.x, blockDim.x);
+}
+
+// fft_lines_ct for NC > 0 (then N == NC and lstride == fpad_len(NC)), else
+// the runtime-length fft_lines_ip
+template <int DIR, typename T, bool MIXED, int NC>
+__device__ __forceinline__ void fft_lines(C<T>* buf, int nlines, int lstride, int N, int code,
+                                          const C<T>* __restrict__ tw, int twstride) {
+    if constexpr (NC > 0) fft_lines_ct<DIR, FftMaxB<T>::value, T, NC>(buf, nlines, tw, twstride);
+    else fft_lines_ip<DIR, FftMaxB<T>::value, T, MIXED>(buf, nlines, lstride, N, code, tw, twstride);
+}
+
 }  // namespace lam

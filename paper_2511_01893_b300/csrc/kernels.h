@@ -31,6 +31,7 @@ template <typename T> struct Usfft1dArgs {
     int M0, fcz;       // fcz: FFT stage code of length nz (fft_code)
     int m;             // half-width; 2m taps
     int TY;            // columns per block (divides n2)
+    int nthr;          // threads per block (256 or 512)
     const T* dz;       // [nz] deapodisation along z
     const int* j0z;    // [h] floor(M0 xi_z(kv))
     const T* wz;       // [h][2m] Gaussian weights of taps j0z - m + 1 + t
@@ -65,6 +66,7 @@ template <typename T> struct Usfft2dArgs {
     int tw1, tw2;                   // Nmax / M1, Nmax / M2
     int RB;                         // rows per block (row passes)
     int CB;                         // columns per block (column passes)
+    int fthr;                       // threads per row / column FFT block (256 or 512)
     int TS;                         // scatter tile side
     int TG;                         // gather tile side
     int nimg;                       // tile images +-1..nimg checked per line (unwrapped positions)

@@ -34,11 +34,11 @@ template <typename T> __device__ __forceinline__ C<T> pz_at(const C<T>* E, const
     return (jj & 1) ? O[fpad(jj >> 1)] : E[fpad(jj >> 1)];
 }
 
-template <typename T, bool MIXED>
+template <typename T, bool MIXED, int NC = 0>
 __device__ __forceinline__ void k_usfft1d_fwd_body(const T* __restrict__ u, C<T>* __restrict__ u1, const Usfft1dArgs<T>& a, int bx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);  // lines 2p (E) and 2p+1 (O), length nz
-    const int nz = a.nz, npair = a.TY / 2;
+    const int nz = NC ? NC : a.nz, npair = a.TY / 2, M0 = 2 * nz;  // NC: compile-time nz
     const int LS = fpad_len(nz);
     const int tiles = a.n2 / a.TY;
     const int x = bx / tiles;
@@ -63,12 +63,12 @@ __device__ __forceinline__ void k_usfft1d_fwd_body(const T* __restrict__ u, C<T>
         const T d = a.dz[z];
         const C<T> raw = buf[(2 * p) * LS + fpad(q)];
         const T va = raw.x * d, vb = raw.y * d;
-        const C<T> w = a.tw[wrap(xc, a.M0) * twM0];  // e^{-2 pi i xc / M0}
+        const C<T> w = a.tw[wrap(xc, M0) * twM0];  // e^{-2 pi i xc / M0}
         buf[(2 * p) * LS + fpad(q)] = cmake<T>(va, vb);
         buf[(2 * p + 1) * LS + fpad(q)] = cmake<T>(va * w.x - vb * w.y, va * w.y + vb * w.x);
     }
     __syncthreads();
-    fft_lines_ip<-1, FftMaxB<T>::value, T, MIXED>(buf, a.TY, LS, nz, a.fcz, a.tw, 2 * twM0);
+    fft_lines<-1, T, MIXED, NC>(buf, a.TY, LS, nz, a.fcz, a.tw, 2 * twM0);
     const int nt = 2 * a.m;
     C<T>* dst = u1 + (size_t)x * a.n2 + y0;
     const size_t plane = (size_t)a.n1 * a.n2;
@@ -80,8 +80,8 @@ __device__ __forceinline__ void k_usfft1d_fwd_body(const T* __restrict__ u, C<T>
         const T* wz = a.wz + kv * nt;
         T sar = 0, sai = 0, sbr = 0, sbi = 0;
         for (int t = 0; t < nt; ++t) {
-            const C<T> pp = pz_at(E, O, jb + t, a.M0);
-            const C<T> pm = pz_at(E, O, -(jb + t), a.M0);
+            const C<T> pp = pz_at(E, O, jb + t, M0);
+            const C<T> pm = pz_at(E, O, -(jb + t), M0);
             const T wt = wz[t];
             sar += wt * (pp.x + pm.x);
             sai += wt * (pp.y - pm.y);
@@ -96,10 +96,10 @@ __device__ __forceinline__ void k_usfft1d_fwd_body(const T* __restrict__ u, C<T>
     }
 }
 
-template <typename T, bool MIXED>
+template <typename T, bool MIXED, int NC = 0>
 __global__ void __launch_bounds__(kFftThreads) k_usfft1d_fwd(const T* __restrict__ u, C<T>* __restrict__ u1,
                                                              Usfft1dArgs<T> a) {
-    k_usfft1d_fwd_body<T, MIXED>(u, u1, a, (int)blockIdx.x);
+    k_usfft1d_fwd_body<T, MIXED, NC>(u, u1, a, (int)blockIdx.x);
 }
 
 // Transpose.  For real outputs only the Hermitian part of each spread column
@@ -125,10 +125,10 @@ __device__ __forceinline__ C<T> spread_at(const C<T>* vals, int j, const Usfft1d
     return cmake<T>(sr, si);
 }
 
-template <typename T, bool MIXED>
+template <typename T, bool MIXED, int NC = 0>
 __device__ __forceinline__ void k_usfft1d_adj_body(const C<T>* __restrict__ u1, T* __restrict__ u, const Usfft1dArgs<T>& a, int bx) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nz = a.nz, npair = a.TY / 2, M0 = a.M0;
+    const int nz = NC ? NC : a.nz, npair = a.TY / 2, M0 = 2 * nz;  // NC: compile-time nz
     const int LS = fpad_len(nz);
     C<T>* buf = reinterpret_cast<C<T>*>(smem_raw);  // TY lines of length nz (E, O per pair)
     C<T>* vals = buf + a.TY * LS;                  // [TY][h]
@@ -168,7 +168,7 @@ __device__ __forceinline__ void k_usfft1d_adj_body(const C<T>* __restrict__ u1, 
         if (jm != j) ((jm & 1) ? O : E)[fpad(jm >> 1)] = qm;
     }
     __syncthreads();
-    fft_lines_ip<+1, FftMaxB<T>::value, T, MIXED>(buf, a.TY, LS, nz, a.fcz, a.tw, 2 * a.twstride);
+    fft_lines<+1, T, MIXED, NC>(buf, a.TY, LS, nz, a.fcz, a.tw, 2 * a.twstride);
     T* dst = u + (size_t)x * nz * a.n2 + y0;
     for (int i = tid; i < nz * npair; i += nthr) {
         const int z = i >> ilog2_pow2(npair), p = i - z * npair;  // npair = TY / 2, a power of two
@@ -184,25 +184,47 @@ __device__ __forceinline__ void k_usfft1d_adj_body(const C<T>* __restrict__ u1, 
     }
 }
 
-template <typename T, bool MIXED>
+template <typename T, bool MIXED, int NC = 0>
 __global__ void __launch_bounds__(kFftThreads) k_usfft1d_adj(const C<T>* __restrict__ u1, T* __restrict__ u,
                                                              Usfft1dArgs<T> a) {
-    k_usfft1d_adj_body<T, MIXED>(u1, u, a, (int)blockIdx.x);
+    k_usfft1d_adj_body<T, MIXED, NC>(u1, u, a, (int)blockIdx.x);
 }
+
+// The FP32 z-stage kernels are also built for the power-of-two nz of the
+// large workloads, with nz a compile-time constant (bitwise the same
+// results); other lengths and FP64 take the runtime-length kernels.
+#define LAM_Z_NC(len, CALL)                  \
+    do {                                     \
+        if constexpr (sizeof(T) == 4) {      \
+            switch (len) {                   \
+                case 256: CALL(256); break;   \
+                case 512: CALL(512); break;   \
+                case 1024: CALL(1024); break; \
+                case 2048: CALL(2048); break; \
+                default: CALL(0); break;      \
+            }                                \
+        } else {                             \
+            CALL(0);                         \
+        }                                    \
+    } while (0)
 
 template <typename T>
 cudaError_t launch_usfft1d_fwd(const T* u, C<T>* u1, const Usfft1dArgs<T>& a, cudaStream_t s) {
     const size_t smem = (size_t)a.TY * fpad_len(a.nz) * sizeof(C<T>);
-    if (fft_mixed(a.fcz)) k_usfft1d_fwd<T, true><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u, u1, a);
-    else k_usfft1d_fwd<T, false><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u, u1, a);
+#define LAM_ZF(NC) k_usfft1d_fwd<T, false, NC><<<a.n1 * (a.n2 / a.TY), a.nthr, smem, s>>>(u, u1, a)
+    if (fft_mixed(a.fcz)) k_usfft1d_fwd<T, true><<<a.n1 * (a.n2 / a.TY), a.nthr, smem, s>>>(u, u1, a);
+    else LAM_Z_NC(a.nz, LAM_ZF);
+#undef LAM_ZF
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_usfft1d_adj(const C<T>* u1, T* u, const Usfft1dArgs<T>& a, cudaStream_t s) {
     const size_t smem = (size_t)(fpad_len(a.nz) + a.h) * a.TY * sizeof(C<T>);
-    if (fft_mixed(a.fcz)) k_usfft1d_adj<T, true><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u1, u, a);
-    else k_usfft1d_adj<T, false><<<a.n1 * (a.n2 / a.TY), kFftThreads, smem, s>>>(u1, u, a);
+#define LAM_ZA(NC) k_usfft1d_adj<T, false, NC><<<a.n1 * (a.n2 / a.TY), a.nthr, smem, s>>>(u1, u, a)
+    if (fft_mixed(a.fcz)) k_usfft1d_adj<T, true><<<a.n1 * (a.n2 / a.TY), a.nthr, smem, s>>>(u1, u, a);
+    else LAM_Z_NC(a.nz, LAM_ZA);
+#undef LAM_ZA
     return cudaGetLastError();
 }
 
@@ -213,6 +235,13 @@ template <typename T> cudaError_t configure_usfft1d() {
     if (!e) e = cudaFuncSetAttribute(k_usfft1d_adj<T, false>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_usfft1d_fwd<T, true>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_usfft1d_adj<T, true>, at, mx);
+    if constexpr (sizeof(T) == 4) {
+#define LAM_NCA(NC)                                                            \
+    if (!e) e = cudaFuncSetAttribute(k_usfft1d_fwd<T, false, NC>, at, mx); \
+    if (!e) e = cudaFuncSetAttribute(k_usfft1d_adj<T, false, NC>, at, mx);
+        LAM_NCA(256) LAM_NCA(512) LAM_NCA(1024) LAM_NCA(2048)
+#undef LAM_NCA
+    }
     return e;
 }
 

@@ -36,42 +36,43 @@ __device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(
 // row / column passes
 // --------------------------------------------------------------------------
 
-template <typename T, bool MIXED>
+template <typename T, bool MIXED, int NC = 0>
 __device__ __forceinline__ void k_rowfft_fwd_body(const C<T>* __restrict__ u1, C<T>* __restrict__ P, int j0, const Usfft2dArgs<T>& a, int bx, int by) {
+    const int n2 = NC ? NC / 2 : a.n2, M2 = NC ? NC : a.M2;  // the FFT axis (y)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
     const int b = by, kv = a.jobs[j0 + b].x;
     const int x0 = bx * a.RB;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int LS = fpad_len(a.M2);
+    const int LS = fpad_len(M2);
     for (int i = tid; i < a.RB * LS; i += nthr) bufa[i] = cmake<T>(0, 0);
     __syncthreads();
-    const C<T>* src = u1 + ((size_t)kv * a.n1 + x0) * a.n2;
-    for (int i = tid; i < a.RB * a.n2; i += nthr) {
-        const int r = udiv<!MIXED>(i, a.n2, ilog2_pow2(a.n2)), y = i - r * a.n2;
-        cp_async_elem<T>(bufa + r * LS + fpad(wrap(y - a.n2 / 2, a.M2)), src + i);
+    const C<T>* src = u1 + ((size_t)kv * a.n1 + x0) * n2;
+    for (int i = tid; i < a.RB * n2; i += nthr) {
+        const int r = udiv<!MIXED>(i, n2, ilog2_pow2(n2)), y = i - r * n2;
+        cp_async_elem<T>(bufa + r * LS + fpad(wrap(y - n2 / 2, M2)), src + i);
     }
     cp_async_commit();
     cp_async_wait_all();
     // each thread deapodises the elements it copied
-    for (int i = tid; i < a.RB * a.n2; i += nthr) {
-        const int r = udiv<!MIXED>(i, a.n2, ilog2_pow2(a.n2)), y = i - r * a.n2;
-        C<T>* e = bufa + r * LS + fpad(wrap(y - a.n2 / 2, a.M2));
+    for (int i = tid; i < a.RB * n2; i += nthr) {
+        const int r = udiv<!MIXED>(i, n2, ilog2_pow2(n2)), y = i - r * n2;
+        C<T>* e = bufa + r * LS + fpad(wrap(y - n2 / 2, M2));
         *e = cscale(*e, a.d1[x0 + r] * a.d2[y]);
     }
     __syncthreads();
-    fft_lines_ip<-1, FftMaxB<T>::value, T, MIXED>(bufa, a.RB, LS, a.M2, a.fcM2, a.tw, a.tw2);
-    C<T>* dst = P + (size_t)b * a.M1 * a.M2;
-    for (int i = tid; i < a.RB * a.M2; i += nthr) {
-        const int r = udiv<!MIXED>(i, a.M2, ilog2_pow2(a.M2)), j = i - r * a.M2;
-        dst[(size_t)wrap(x0 + r - a.n1 / 2, a.M1) * a.M2 + j] = bufa[r * LS + fpad(j)];
+    fft_lines<-1, T, MIXED, NC>(bufa, a.RB, LS, M2, a.fcM2, a.tw, a.tw2);
+    C<T>* dst = P + (size_t)b * a.M1 * M2;
+    for (int i = tid; i < a.RB * M2; i += nthr) {
+        const int r = udiv<!MIXED>(i, M2, ilog2_pow2(M2)), j = i - r * M2;
+        dst[(size_t)wrap(x0 + r - a.n1 / 2, a.M1) * M2 + j] = bufa[r * LS + fpad(j)];
     }
 }
 
-template <typename T, bool MIXED>
+template <typename T, bool MIXED, int NC = 0>
 __global__ void __launch_bounds__(kFftThreads) k_rowfft_fwd(const C<T>* __restrict__ u1, C<T>* __restrict__ P,
                                                     int j0, Usfft2dArgs<T> a) {
-    k_rowfft_fwd_body<T, MIXED>(u1, P, j0, a, (int)blockIdx.x, (int)blockIdx.y);
+    k_rowfft_fwd_body<T, MIXED, NC>(u1, P, j0, a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 template <typename T, bool MIXED>
@@ -99,11 +100,6 @@ __device__ __forceinline__ void k_colfft_fwd_body(C<T>* __restrict__ P, const Us
 }
 
 template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kFftThreads) k_colfft_fwd(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
-    k_colfft_fwd_body<T, MIXED>(P, a, (int)blockIdx.x, (int)blockIdx.y);
-}
-
-template <typename T, bool MIXED>
 __device__ __forceinline__ void k_colfft_adj_body(C<T>* __restrict__ P, const Usfft2dArgs<T>& a, int bx, int by) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
@@ -125,11 +121,6 @@ __device__ __forceinline__ void k_colfft_adj_body(C<T>* __restrict__ P, const Us
     }
 }
 
-template <typename T, bool MIXED>
-__global__ void __launch_bounds__(kFftThreads) k_colfft_adj(C<T>* __restrict__ P, Usfft2dArgs<T> a) {
-    k_colfft_adj_body<T, MIXED>(P, a, (int)blockIdx.x, (int)blockIdx.y);
-}
-
 // ---------------------------------------------------------------------------
 // Pipelined column passes: persistent blocks walk the (plane, column strip)
 // items with two shared-memory buffers; the next strip's loads (cp.async)
@@ -140,23 +131,24 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_adj(C<T>* __restrict__ P
 // forward: rows wrap(x - n1/2) (x < n1) hold data, the others are zero padding;
 // the FFT overwrites every row, so after the stores the padding rows are
 // zeroed again for the buffer's next strip
-template <typename T, bool MIXED>
+template <typename T, bool MIXED, int NC = 0>
 __global__ void __launch_bounds__(kFftThreads) k_colfft_fwd_pipe(C<T>* __restrict__ P, Usfft2dArgs<T> a, int nb) {
+    const int n1 = NC ? NC / 2 : a.n1, M1 = NC ? NC : a.M1;  // the FFT axis (x)
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int LS = fpad_len(a.M1);
+    const int LS = fpad_len(M1);
     C<T>* buf[2] = {reinterpret_cast<C<T>*>(smem_raw), reinterpret_cast<C<T>*>(smem_raw) + a.CB * LS};
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lcb = ilog2_pow2(a.CB);
     const int ncg = a.M2 / a.CB, total = ncg * nb;
-    const int half = a.n1 / 2, hi0 = a.M1 - half;  // data rows: [0, half) and [hi0, M1)
+    const int half = n1 / 2, hi0 = M1 - half;  // data rows: [0, half) and [hi0, M1)
     for (int i = tid; i < 2 * a.CB * LS; i += nthr) buf[0][i] = cmake<T>(0, 0);
     __syncthreads();
     auto issue = [&](int w, C<T>* bb) {
         const int b = w / ncg, c0 = (w - b * ncg) * a.CB;
-        const C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
-        for (int i = tid; i < a.n1 * a.CB; i += nthr) {
+        const C<T>* pl = P + (size_t)b * M1 * a.M2 + c0;
+        for (int i = tid; i < n1 * a.CB; i += nthr) {
             const int x = i >> lcb, c = i - (x << lcb);
-            const int row = wrap(x - half, a.M1);
+            const int row = wrap(x - half, M1);
             cp_async_elem<T>(bb + c * LS + fpad(row), pl + (size_t)row * a.M2 + c);
         }
         cp_async_commit();
@@ -170,10 +162,10 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_fwd_pipe(C<T>* __restric
         else cp_async_commit();  // an empty group keeps the wait count uniform
         cp_async_wait_prev();
         __syncthreads();
-        fft_lines_ip<-1, FftMaxB<T>::value, T, MIXED>(cur, a.CB, LS, a.M1, a.fcM1, a.tw, a.tw1);
+        fft_lines<-1, T, MIXED, NC>(cur, a.CB, LS, M1, a.fcM1, a.tw, a.tw1);
         const int b = w / ncg, c0 = (w - b * ncg) * a.CB;
-        C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
-        for (int i = tid; i < a.M1 * a.CB; i += nthr) {
+        C<T>* pl = P + (size_t)b * M1 * a.M2 + c0;
+        for (int i = tid; i < M1 * a.CB; i += nthr) {
             const int j = i >> lcb, c = i - (j << lcb);
             C<T>* e = cur + c * LS + fpad(j);
             pl[(size_t)j * a.M2 + c] = *e;
@@ -185,18 +177,19 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_fwd_pipe(C<T>* __restric
 }
 
 // transpose: every row is loaded; the n1 rows the crop keeps are stored
-template <typename T, bool MIXED>
+template <typename T, bool MIXED, int NC = 0>
 __global__ void __launch_bounds__(kFftThreads) k_colfft_adj_pipe(C<T>* __restrict__ P, Usfft2dArgs<T> a, int nb) {
+    const int n1 = NC ? NC / 2 : a.n1, M1 = NC ? NC : a.M1;  // the FFT axis (x)
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int LS = fpad_len(a.M1);
+    const int LS = fpad_len(M1);
     C<T>* buf[2] = {reinterpret_cast<C<T>*>(smem_raw), reinterpret_cast<C<T>*>(smem_raw) + a.CB * LS};
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lcb = ilog2_pow2(a.CB);
     const int ncg = a.M2 / a.CB, total = ncg * nb;
     auto issue = [&](int w, C<T>* bb) {
         const int b = w / ncg, c0 = (w - b * ncg) * a.CB;
-        const C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
-        for (int i = tid; i < a.M1 * a.CB; i += nthr) {
+        const C<T>* pl = P + (size_t)b * M1 * a.M2 + c0;
+        for (int i = tid; i < M1 * a.CB; i += nthr) {
             const int j = i >> lcb, c = i - (j << lcb);
             cp_async_elem<T>(bb + c * LS + fpad(j), pl + (size_t)j * a.M2 + c);
         }
@@ -211,12 +204,12 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_adj_pipe(C<T>* __restric
         else cp_async_commit();
         cp_async_wait_prev();
         __syncthreads();
-        fft_lines_ip<+1, FftMaxB<T>::value, T, MIXED>(cur, a.CB, LS, a.M1, a.fcM1, a.tw, a.tw1);
+        fft_lines<+1, T, MIXED, NC>(cur, a.CB, LS, M1, a.fcM1, a.tw, a.tw1);
         const int b = w / ncg, c0 = (w - b * ncg) * a.CB;
-        C<T>* pl = P + (size_t)b * a.M1 * a.M2 + c0;
-        for (int i = tid; i < a.n1 * a.CB; i += nthr) {
+        C<T>* pl = P + (size_t)b * M1 * a.M2 + c0;
+        for (int i = tid; i < n1 * a.CB; i += nthr) {
             const int x = i >> lcb, c = i - (x << lcb);
-            const int row = wrap(x - a.n1 / 2, a.M1);
+            const int row = wrap(x - n1 / 2, M1);
             pl[(size_t)row * a.M2 + c] = cur[c * LS + fpad(row)];
         }
         __syncthreads();
@@ -224,47 +217,53 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_adj_pipe(C<T>* __restric
     cp_async_wait_all();
 }
 
-// persistent grid of a pipelined column pass: one block per SM (the FFT
-// blocks use 512 threads at ~125 registers), at most one per item
-static int pipe_grid(int items) {
+// persistent grid of a pipelined column pass: as many blocks as fit on the
+// SMs by registers (the FFT blocks run at up to 128 registers a thread: one
+// 512-thread or two 256-thread blocks per SM), at most one per item
+static int pipe_grid(int items, int threads, size_t smem) {
     static int nsm = 0;
     if (!nsm) {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
             nsm = 148;
     }
-    return items < nsm ? items : nsm;
+    int per_sm = threads <= 256 ? 2 : 1;
+    // 228 KB of shared memory per SM, 1 KB of it reserved per block
+    while (per_sm > 1 && (size_t)per_sm * (smem + 1024) > 228 * 1024) --per_sm;
+    const int g = nsm * per_sm;
+    return items < g ? items : g;
 }
 
-template <typename T, bool MIXED>
+template <typename T, bool MIXED, int NC = 0>
 __device__ __forceinline__ void k_rowfft_adj_body(const C<T>* __restrict__ P, C<T>* __restrict__ u1, int j0, const Usfft2dArgs<T>& a, int bx, int by) {
+    const int n2 = NC ? NC / 2 : a.n2, M2 = NC ? NC : a.M2;  // the FFT axis (y)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
     const int b = by, kv = a.jobs[j0 + b].x;
     const int x0 = bx * a.RB;
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const C<T>* pl = P + (size_t)b * a.M1 * a.M2;
-    const int LS = fpad_len(a.M2);
-    for (int i = tid; i < a.RB * a.M2; i += nthr) {
-        const int r = udiv<!MIXED>(i, a.M2, ilog2_pow2(a.M2)), j = i - r * a.M2;
-        cp_async_elem<T>(bufa + r * LS + fpad(j), pl + (size_t)wrap(x0 + r - a.n1 / 2, a.M1) * a.M2 + j);
+    const C<T>* pl = P + (size_t)b * a.M1 * M2;
+    const int LS = fpad_len(M2);
+    for (int i = tid; i < a.RB * M2; i += nthr) {
+        const int r = udiv<!MIXED>(i, M2, ilog2_pow2(M2)), j = i - r * M2;
+        cp_async_elem<T>(bufa + r * LS + fpad(j), pl + (size_t)wrap(x0 + r - a.n1 / 2, a.M1) * M2 + j);
     }
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    fft_lines_ip<+1, FftMaxB<T>::value, T, MIXED>(bufa, a.RB, LS, a.M2, a.fcM2, a.tw, a.tw2);
-    C<T>* dst = u1 + ((size_t)kv * a.n1 + x0) * a.n2;
-    for (int i = tid; i < a.RB * a.n2; i += nthr) {
-        const int r = udiv<!MIXED>(i, a.n2, ilog2_pow2(a.n2)), y = i - r * a.n2;
+    fft_lines<+1, T, MIXED, NC>(bufa, a.RB, LS, M2, a.fcM2, a.tw, a.tw2);
+    C<T>* dst = u1 + ((size_t)kv * a.n1 + x0) * n2;
+    for (int i = tid; i < a.RB * n2; i += nthr) {
+        const int r = udiv<!MIXED>(i, n2, ilog2_pow2(n2)), y = i - r * n2;
         const T s = a.d1[x0 + r] * a.d2[y];
-        dst[i] = cscale(bufa[r * LS + fpad(wrap(y - a.n2 / 2, a.M2))], s);
+        dst[i] = cscale(bufa[r * LS + fpad(wrap(y - n2 / 2, M2))], s);
     }
 }
 
-template <typename T, bool MIXED>
+template <typename T, bool MIXED, int NC = 0>
 __global__ void __launch_bounds__(kFftThreads) k_rowfft_adj(const C<T>* __restrict__ P, C<T>* __restrict__ u1,
                                                     int j0, Usfft2dArgs<T> a) {
-    k_rowfft_adj_body<T, MIXED>(P, u1, j0, a, (int)blockIdx.x, (int)blockIdx.y);
+    k_rowfft_adj_body<T, MIXED, NC>(P, u1, j0, a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // --------------------------------------------------------------------------
@@ -1127,19 +1126,42 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
 // warps per tile-block in the gather and the scatter (16 measured slower)
 constexpr int kScatterWarps = 4;
 
+// The FP32 row / column FFT kernels are also built for the power-of-two plane
+// lengths 2n of the large workloads, with the length a compile-time constant
+// (bitwise the same results); other lengths and FP64 take the runtime-length
+// kernels.  CALL(NC) launches the NC instantiation.
+#define LAM_PLANE_NC(len, CALL)             \
+    do {                                    \
+        if constexpr (sizeof(T) == 4) {     \
+            switch (len) {                  \
+                case 512: CALL(512); break;   \
+                case 1024: CALL(1024); break; \
+                case 2048: CALL(2048); break; \
+                case 4096: CALL(4096); break; \
+                default: CALL(0); break;      \
+            }                               \
+        } else {                            \
+            CALL(0);                        \
+        }                                   \
+    } while (0)
+#define LAM_RF(NC) k_rowfft_fwd<T, false, NC><<<dim3(a.n1 / a.RB, nb), a.fthr, sr, s>>>(u1, P, kv0, a)
+#define LAM_CF(NC) k_colfft_fwd_pipe<T, false, NC><<<gp, a.fthr, 2 * sc, s>>>(P, a, nb)
+#define LAM_CA(NC) k_colfft_adj_pipe<T, false, NC><<<gp, a.fthr, 2 * sc, s>>>(P, a, nb)
+#define LAM_RA(NC) k_rowfft_adj<T, false, NC><<<dim3(a.n1 / a.RB, nb), a.fthr, sr, s>>>(P, u1, kv0, a)
+
 template <typename T>
 cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* sub, int j0, int nb,
                                const Usfft2dArgs<T>& a, cudaStream_t s) {
     const int kv0 = j0;
     const size_t sr = (size_t)a.RB * fpad_len(a.M2) * sizeof(C<T>);
     const size_t sc = (size_t)a.CB * fpad_len(a.M1) * sizeof(C<T>);
-    const int gp = pipe_grid((a.M2 / a.CB) * nb);
+    const int gp = pipe_grid((a.M2 / a.CB) * nb, a.fthr, 2 * sc);
     if (fft_mixed(a.fcM1) || fft_mixed(a.fcM2)) {
-        k_rowfft_fwd<T, true><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, kv0, a);
-        k_colfft_fwd_pipe<T, true><<<gp, kFftThreads, 2 * sc, s>>>(P, a, nb);
+        k_rowfft_fwd<T, true><<<dim3(a.n1 / a.RB, nb), a.fthr, sr, s>>>(u1, P, kv0, a);
+        k_colfft_fwd_pipe<T, true><<<gp, a.fthr, 2 * sc, s>>>(P, a, nb);
     } else {
-        k_rowfft_fwd<T, false><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, kv0, a);
-        k_colfft_fwd_pipe<T, false><<<gp, kFftThreads, 2 * sc, s>>>(P, a, nb);
+        LAM_PLANE_NC(a.M2, LAM_RF);
+        LAM_PLANE_NC(a.M1, LAM_CF);
     }
     constexpr int NW = kScatterWarps;
     const int ntiles = (a.M1 / a.TG) * (a.M2 / a.TG);
@@ -1160,13 +1182,14 @@ template <typename T>
 cudaError_t launch_usfft2d_planes(const C<T>* u1, C<T>* P, int j0, int nb, const Usfft2dArgs<T>& a, cudaStream_t s) {
     const size_t sr = (size_t)a.RB * fpad_len(a.M2) * sizeof(C<T>);
     const size_t sc = (size_t)a.CB * fpad_len(a.M1) * sizeof(C<T>);
-    const int gp = pipe_grid((a.M2 / a.CB) * nb);
+    const int gp = pipe_grid((a.M2 / a.CB) * nb, a.fthr, 2 * sc);
+    const int kv0 = j0;
     if (fft_mixed(a.fcM1) || fft_mixed(a.fcM2)) {
-        k_rowfft_fwd<T, true><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, j0, a);
-        k_colfft_fwd_pipe<T, true><<<gp, kFftThreads, 2 * sc, s>>>(P, a, nb);
+        k_rowfft_fwd<T, true><<<dim3(a.n1 / a.RB, nb), a.fthr, sr, s>>>(u1, P, kv0, a);
+        k_colfft_fwd_pipe<T, true><<<gp, a.fthr, 2 * sc, s>>>(P, a, nb);
     } else {
-        k_rowfft_fwd<T, false><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(u1, P, j0, a);
-        k_colfft_fwd_pipe<T, false><<<gp, kFftThreads, 2 * sc, s>>>(P, a, nb);
+        LAM_PLANE_NC(a.M2, LAM_RF);
+        LAM_PLANE_NC(a.M1, LAM_CF);
     }
     return cudaGetLastError();
 }
@@ -1237,13 +1260,13 @@ cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int j0, int nb
     else { LAM_SW(0) }
 #undef LAM_SW
 #undef LAM_S
-    const int gp = pipe_grid((a.M2 / a.CB) * nb);
+    const int gp = pipe_grid((a.M2 / a.CB) * nb, a.fthr, 2 * sc);
     if (fft_mixed(a.fcM1) || fft_mixed(a.fcM2)) {
-        k_colfft_adj_pipe<T, true><<<gp, kFftThreads, 2 * sc, s>>>(P, a, nb);
-        k_rowfft_adj<T, true><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(P, u1, kv0, a);
+        k_colfft_adj_pipe<T, true><<<gp, a.fthr, 2 * sc, s>>>(P, a, nb);
+        k_rowfft_adj<T, true><<<dim3(a.n1 / a.RB, nb), a.fthr, sr, s>>>(P, u1, kv0, a);
     } else {
-        k_colfft_adj_pipe<T, false><<<gp, kFftThreads, 2 * sc, s>>>(P, a, nb);
-        k_rowfft_adj<T, false><<<dim3(a.n1 / a.RB, nb), kFftThreads, sr, s>>>(P, u1, kv0, a);
+        LAM_PLANE_NC(a.M1, LAM_CA);
+        LAM_PLANE_NC(a.M2, LAM_RA);
     }
     return cudaGetLastError();
 }
@@ -1280,17 +1303,22 @@ template <typename T> cudaError_t configure_usfft2d() {
     cudaError_t e = cudaSuccess;
     const cudaFuncAttribute at = cudaFuncAttributeMaxDynamicSharedMemorySize;
     if (!e) e = cudaFuncSetAttribute(k_rowfft_fwd<T, false>, at, mx);
-    if (!e) e = cudaFuncSetAttribute(k_colfft_fwd<T, false>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_rowfft_adj<T, false>, at, mx);
-    if (!e) e = cudaFuncSetAttribute(k_colfft_adj<T, false>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_rowfft_fwd<T, true>, at, mx);
-    if (!e) e = cudaFuncSetAttribute(k_colfft_fwd<T, true>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_rowfft_adj<T, true>, at, mx);
-    if (!e) e = cudaFuncSetAttribute(k_colfft_adj<T, true>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_colfft_fwd_pipe<T, false>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_colfft_fwd_pipe<T, true>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_colfft_adj_pipe<T, false>, at, mx);
     if (!e) e = cudaFuncSetAttribute(k_colfft_adj_pipe<T, true>, at, mx);
+    if constexpr (sizeof(T) == 4) {
+#define LAM_NCA(NC)                                                                  \
+    if (!e) e = cudaFuncSetAttribute(k_rowfft_fwd<T, false, NC>, at, mx);      \
+    if (!e) e = cudaFuncSetAttribute(k_rowfft_adj<T, false, NC>, at, mx);      \
+    if (!e) e = cudaFuncSetAttribute(k_colfft_fwd_pipe<T, false, NC>, at, mx); \
+    if (!e) e = cudaFuncSetAttribute(k_colfft_adj_pipe<T, false, NC>, at, mx);
+        LAM_NCA(512) LAM_NCA(1024) LAM_NCA(2048) LAM_NCA(4096)
+#undef LAM_NCA
+    }
     // the tile kernels also hold static shared memory (the per-warp line lists)
     const int mt = kMaxDynSmem - 4096;
 #define LAM_A(MH)                                                                          \

@@ -307,6 +307,15 @@ class Plan:
                "lamx_plane_ffts")
         return P
 
+    def set_threads(self, z=None, fft=None):
+        """Threads per block (256 or 512) of the z-stage kernels and of the
+        plane row / column FFTs; the lines per block are picked again."""
+        if z is not None:
+            _check(lib().lam_plan_set_option(self._h, 4, int(z)), "lam_plan_set_option")
+        if fft is not None:
+            _check(lib().lam_plan_set_option(self._h, 5, int(fft)), "lam_plan_set_option")
+        return self
+
     def autotune(self, reps=2):
         """Pick launch shapes by timing L_hat + L_hat^H (scratch buffers are
         allocated here); returns the best pair time in seconds."""
@@ -318,10 +327,10 @@ class Plan:
         return t.value
 
     def info(self):
-        arr = (ctypes.c_int * 11)()
-        _check(lib().lamx_plan_info(self._h, arr, 11), "lamx_plan_info")
+        arr = (ctypes.c_int * 13)()
+        _check(lib().lamx_plan_info(self._h, arr, 13), "lamx_plan_info")
         keys = ["TY_fwd", "TY_adj", "rows_per_block", "cols_per_block", "tile", "images", "planes_per_batch",
-                "jmin", "jmax", "plane_jobs", "gather_tile"]
+                "jmin", "jmax", "plane_jobs", "gather_tile", "z_threads", "fft_threads"]
         return dict(zip(keys, list(arr)))
 
 

@@ -173,6 +173,25 @@ def test_autotune_keeps_results_bitwise(n):
     assert torch.equal(plan.adjoint(d), a0)
 
 
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_threads_per_block_keep_results_bitwise(prec):
+    # 256 or 512 threads per z-stage / plane-FFT block: the lines per block
+    # change, the arithmetic of every line does not
+    n = 256
+    plan, g = plan_and_geom(n, n // 4, n // 4, n, 8, 0.4, prec)
+    u = torch.from_numpy(rand_vol(n, n // 4, 23)).cuda().to(plan.rdtype)
+    d = torch.from_numpy(rand_data(8, n // 4, n, 24)).cuda().to(plan.cdtype)
+    f0, a0 = plan.forward(u), plan.adjoint(d)
+    for z, f in [(256, 512), (512, 256), (256, 256)]:
+        plan.set_threads(z=z, fft=f)
+        info = plan.info()
+        assert (info["z_threads"], info["fft_threads"]) == (z, f)
+        assert torch.equal(plan.forward(u), f0)
+        assert torch.equal(plan.adjoint(d), a0)
+    with pytest.raises(glam.LaminoError):
+        plan.set_threads(z=384)
+
+
 def test_hat_workspace_serves_the_hat_operators():
     n, nz, h, w, T = 32, 16, 32, 32, 12
     full, g = plan_and_geom(n, nz, h, w, T, 0.4, "f32")

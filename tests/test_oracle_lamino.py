@@ -133,3 +133,38 @@ def test_phi_zero_is_tomography():
 def test_accuracy_metric():
     a = np.array([3.0, 4.0])
     assert lamino.accuracy_error(a, a * 0.9) == pytest.approx(0.1)
+
+
+def _sparse_case(n1, n0, n2, h, w, T, K, S, seed):
+    rng = np.random.default_rng(seed)
+    g = _geom(n1, n0, n2, h, w, T, phi=0.52, seed=seed)
+    flat = rng.choice(n1 * n0 * n2, K, replace=False)
+    vox = np.stack(np.unravel_index(flat, (n1, n0, n2)), axis=1)
+    vals = rng.standard_normal(K)
+    u = np.zeros((n1, n0, n2))
+    u[vox[:, 0], vox[:, 1], vox[:, 2]] = vals
+    flat = rng.choice(T * h * w, S, replace=False)
+    t, kv, ku = np.unravel_index(flat, (T, h, w))
+    return g, vox, vals, u, t, kv, ku
+
+
+@pytest.mark.parametrize("dims", [(16, 12, 16, 10, 14, 9), (24, 16, 20, 16, 12, 7)])
+def test_point_sampled_forms_match_the_full_operators(dims):
+    # the point-sampled direct sum and the point-sampled USFFT steps against
+    # the full-array functions they restrict (lhat_exact pinned by the closed
+    # forms above, lhat by the direct sum)
+    g, vox, vals, u, t, kv, ku = _sparse_case(*dims, K=30, S=200, seed=11)
+    full = lamino.lhat(u, g)
+    assert _rel(lamino.lhat_sparse_points(vox, vals, g, t, kv, ku), full[t, kv, ku]) < 1e-12
+    assert _rel(lamino.lhat_exact_points(vox, vals, g, t, kv, ku), lamino.lhat_exact(u, g)[t, kv, ku]) < 1e-12
+    rng = np.random.default_rng(12)
+    rv = rng.standard_normal(len(t)) + 1j * rng.standard_normal(len(t))
+    r = np.zeros((g.n_theta, g.h, g.w), dtype=np.complex128)
+    r[t, kv, ku] = rv
+    adj = lamino.lhat_adj(r, g)
+    got = lamino.lhat_adj_sparse_points(t, kv, ku, rv, g, vox)
+    assert _rel(got, adj[vox[:, 0], vox[:, 1], vox[:, 2]]) < 1e-12
+    # the exact adjoint sum is the transpose of the exact forward sum
+    lhs = np.vdot(rv, lamino.lhat_exact_points(vox, vals, g, t, kv, ku)).real
+    rhs = np.dot(vals, lamino.lhat_adj_exact_points(t, kv, ku, rv, g, vox))
+    assert abs(lhs - rhs) < 1e-10 * np.linalg.norm(rv) * np.linalg.norm(vals) * len(t)
