@@ -85,6 +85,8 @@ struct lam_plan {
     // device tables
     void *dz, *d1, *d2, *wz, *tw, *ang;
     int *j0z, *kvlo, *kvhi;
+    void* wzc;  // z weights cell by cell ([jmax - jmin + 1][zcw])
+    int zcw;
     int jmin, jmax;
     // plane jobs: paired (for real volumes) and one job per plane
     int2* jobs_pair;
@@ -210,6 +212,16 @@ template <typename T> lam_status build_tables(lam_plan* p, const double* theta) 
     p->kvlo = (int*)upload(p, lo, &st);
     if (st) return st;
     p->kvhi = (int*)upload(p, hi, &st);
+    if (st) return st;
+    // the same weights cell by cell: wzc[e][kv - lo[e]] for kv in [lo[e], hi[e])
+    int cw = 1;
+    for (int e = 0; e < E; ++e) cw = std::max(cw, hi[e] - lo[e]);
+    std::vector<double> wzc((size_t)E * cw, 0.0);
+    for (int e = 0; e < E; ++e)
+        for (int kv = lo[e]; kv < hi[e]; ++kv)
+            wzc[(size_t)e * cw + (kv - lo[e])] = wz[(size_t)kv * nt + (jmin + e - (j0[kv] - m + 1))];
+    p->zcw = cw;
+    p->wzc = upload(p, cast_vec<T>(wzc), &st);
     if (st) return st;
     // Hermitian pairs: for a real volume, u1 at -kv is the conjugate of u1 at kv
     // when the z windows of -kv mirror those of kv (j0(-t) = -j0(t) - 1; the
@@ -341,6 +353,8 @@ template <typename T> Usfft1dArgs<T> args1d(const lam_plan* p, int TY, bool pair
     a.wz = (const T*)p->wz;
     a.kvlo = p->kvlo;
     a.kvhi = p->kvhi;
+    a.wzc = (const T*)p->wzc;
+    a.cw = p->zcw;
     a.jmin = p->jmin;
     a.jmax = p->jmax;
     a.tw = (const C<T>*)p->tw;

@@ -37,6 +37,8 @@ template <typename T> struct Usfft1dArgs {
     const T* wz;       // [h][2m] Gaussian weights of taps j0z - m + 1 + t
     const int* kvlo;   // [jmax - jmin + 1] first kv whose taps reach unwrapped cell e
     const int* kvhi;   // one past the last such kv
+    const T* wzc;      // [jmax - jmin + 1][cw]: weight of kv kvlo[e] + i on cell e at i
+    int cw;            // columns of wzc (most kv reaching one cell)
     int jmin, jmax;    // unwrapped cell range touched by any tap
     const C<T>* tw;    // twiddles exp(-2 pi i q / Nmax)
     int twstride;      // Nmax / M0

@@ -106,23 +106,32 @@ __global__ void __launch_bounds__(kFftThreads) k_usfft1d_fwd(const T* __restrict
 // matters, Re IDFT(Q) = IDFT((Q[j] + conj Q[-j]) / 2), so two columns pack as
 //   Q_c[j] = (Q_a[j] + conj Q_a[-j]) / 2 + i (Q_b[j] + conj Q_b[-j]) / 2,
 // whose inverse transform is Re f_a + i Re f_b.  One thread builds Q_c at the
-// mirror pair j, M0 - j from four gather-form spreads, then the even / odd
-// halves go through two inverse FFTs of length nz and recombine as
+// mirror pair j, M0 - j from the gather-form spreads of both columns at j and
+// at -j (one pass over each cell's kv range and weights serves both
+// columns), then the even / odd halves go through two inverse FFTs of length
+// nz and recombine as
 //   f[x] = E'[x mod nz] + e^{+2 pi i x / M0} O'[x mod nz].
 template <typename T>
-__device__ __forceinline__ C<T> spread_at(const C<T>* vals, int j, const Usfft1dArgs<T>& a, int nt) {
-    T sr = 0, si = 0;
-    int e = j + ((a.jmin - j + a.M0 - 1 + 64 * a.M0) / a.M0 - 64) * a.M0;  // smallest e >= jmin, e == j
-    for (; e <= a.jmax; e += a.M0) {
-        const int lo = a.kvlo[e - a.jmin], hi = a.kvhi[e - a.jmin];
+__device__ __forceinline__ void spread_pair_at(const C<T>* va, const C<T>* vb, int j, int M0, const Usfft1dArgs<T>& a,
+                                               C<T>& sa, C<T>& sb) {
+    // columns a and b of a pair share each cell's kv range and weights
+    T ar = 0, ai = 0, br = 0, bi = 0;
+    int e = j + ((a.jmin - j + M0 - 1 + 64 * M0) / M0 - 64) * M0;  // smallest e >= jmin, e == j
+    for (; e <= a.jmax; e += M0) {
+        const int c = e - a.jmin;
+        const int lo = a.kvlo[c], hi = a.kvhi[c];
+        const T* wt = a.wzc + (size_t)c * a.cw - lo;  // indexed by kv
         for (int kv = lo; kv < hi; ++kv) {
-            const T wt = a.wz[kv * nt + (e - (a.j0z[kv] - a.m + 1))];
-            const C<T> v = vals[kv];
-            sr += wt * v.x;
-            si += wt * v.y;
+            const T wk = wt[kv];
+            const C<T> x = va[kv], y = vb[kv];
+            ar += wk * x.x;
+            ai += wk * x.y;
+            br += wk * y.x;
+            bi += wk * y.y;
         }
     }
-    return cmake<T>(sr, si);
+    sa = cmake<T>(ar, ai);
+    sb = cmake<T>(br, bi);
 }
 
 template <typename T, bool MIXED, int NC = 0>
@@ -146,7 +155,6 @@ __device__ __forceinline__ void k_usfft1d_adj_body(const C<T>* __restrict__ u1, 
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
-    const int nt = 2 * a.m;
     const int half = M0 / 2;
     // i / (half + 1) through FP32: i < 2^24 and (i + 1/2) / (half + 1) stays at
     // least 1 / (2 half + 2) away from an integer, far above the rounding error
@@ -156,8 +164,9 @@ __device__ __forceinline__ void k_usfft1d_adj_body(const C<T>* __restrict__ u1, 
         const int jm = wrap(-j, M0);
         const C<T>* va = vals + (2 * p) * a.h;
         const C<T>* vb = va + a.h;
-        const C<T> ap = spread_at(va, j, a, nt), am = spread_at(va, jm, a, nt);
-        const C<T> bp = spread_at(vb, j, a, nt), bm = spread_at(vb, jm, a, nt);
+        C<T> ap, am, bp, bm;
+        spread_pair_at(va, vb, j, M0, a, ap, bp);
+        spread_pair_at(va, vb, jm, M0, a, am, bm);
         // Q_c[j] = (ap + conj am)/2 + i (bp + conj bm)/2
         const C<T> qj = cmake<T>((T)0.5 * ((ap.x + am.x) - (bp.y - bm.y)), (T)0.5 * ((ap.y - am.y) + (bp.x + bm.x)));
         // Q_c[-j] = (am + conj ap)/2 + i (bm + conj bp)/2
