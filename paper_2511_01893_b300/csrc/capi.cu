@@ -328,7 +328,8 @@ static int pick_lines(int len, size_t celem, size_t budget, int divides, int cap
 // Each within the FFT's capacity for the stage's block size.
 static void pick_fft_shapes(lam_plan* p) {
     const size_t ce_ = p->celem();
-    const size_t budget = p->zthr <= 256 ? 100 * 1024 : 200 * 1024;
+    // two blocks per SM: the compile-time-length z kernels run at ~60 registers
+    const size_t budget = p->zthr <= 256 ? 56 * 1024 : 110 * 1024;
     const size_t pbudget = p->pthr <= 256 ? 64 * 1024 : 128 * 1024;
     const int maxb = p->prec == LAM_F32 ? 2 : 1;
     p->TYf = std::max(2, pick_lines(p->nz, ce_, budget, p->n2, 16, maxb, 0, p->zthr));
