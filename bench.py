@@ -349,6 +349,7 @@ def run_op_pair(args):
     d = torch.empty(plan.data_shape, dtype=plan.cdtype, device=dev)
     v = torch.empty_like(u)
     s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream(dev))  # u was drawn on the current stream
     with torch.cuda.stream(s):
         for _ in range(args.warmup):
             plan.forward_hat(u, out=d)
@@ -476,6 +477,7 @@ def run_batch(args):
         datas.append(d)
     batch = glam.Batch(plans)
     s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream(dev))  # the data were made on the current stream
     res = {}
     with torch.cuda.stream(s):
         for mode in ("batched", "sequential"):
@@ -546,6 +548,7 @@ def run_ours(args):
     u_true = inputs.ellipsoid_circuit_phantom(n, nz, seed=1238, device=dev, dtype=torch.float32)
     plan = glam.Plan(n, nz, h, w, theta, phi, prec="f32", device=dev)
     stream = torch.cuda.Stream(device=dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))  # u_true was made on the current stream
     with torch.cuda.stream(stream):
         d = plan.forward(u_true)
         sigma = 0.01 * d.real.abs().max().item()

@@ -69,6 +69,70 @@ __device__ __forceinline__ void for_voxel_quads(const Vol& v, F body, G after_qu
 }
 
 // ---------------------------------------------------------------------------
+// quad access: four consecutive voxels (i0 a multiple of 4, so a 16-byte
+// aligned FP32 vector; two 16-byte halves in FP64).  Volume arrays start on a
+// 256-byte boundary and n2 is a multiple of 4, so the neighbouring quads at
+// +-n2 and +-nz n2 are aligned too.
+// ---------------------------------------------------------------------------
+
+template <typename T> struct Q4 {
+    T v[4];
+};
+__device__ __forceinline__ Q4<float> ld4(const float* __restrict__ p) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    return Q4<float>{{a.x, a.y, a.z, a.w}};
+}
+__device__ __forceinline__ Q4<double> ld4(const double* __restrict__ p) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    return Q4<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* __restrict__ p, const Q4<float>& q) {
+    *reinterpret_cast<float4*>(p) = make_float4(q.v[0], q.v[1], q.v[2], q.v[3]);
+}
+__device__ __forceinline__ void st4(double* __restrict__ p, const Q4<double>& q) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(q.v[0], q.v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(q.v[2], q.v[3]);
+}
+template <typename T> __device__ __forceinline__ Q4<T> zero4() { return Q4<T>{{(T)0, (T)0, (T)0, (T)0}}; }
+
+// Grid-stride walk over the quads: body(i0, x, z, y0) once per quad, then
+// after_quad().  The same traversal as for_voxel_quads.
+template <typename F, typename G>
+__device__ __forceinline__ void for_quads(const Vol& v, F body, G after_quad) {
+    const long long nq = v.N >> 2;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nq; q += (long long)gridDim.x * blockDim.x) {
+        const long long i0 = q << 2;
+        int x, z, y;
+        v.coords(i0, x, z, y);
+        body(i0, x, z, y);
+        after_quad();
+    }
+}
+
+// Forward differences of f for the four voxels of a quad along x, z, y, each
+// zero at the last index (fdiff, with the quad's loads shared).
+template <typename T> struct QuadDiff {
+    Q4<T> c, d[3];
+};
+template <typename T>
+__device__ __forceinline__ QuadDiff<T> quad_fdiff(const T* __restrict__ f, long long i0, int x, int z, int y0, const Vol& v) {
+    QuadDiff<T> q;
+    q.c = ld4(f + i0);
+    const long long X = (long long)v.nz * v.n2, Z = v.n2;
+    const Q4<T> fx = x + 1 < v.n1 ? ld4(f + i0 + X) : q.c;
+    const Q4<T> fz = z + 1 < v.nz ? ld4(f + i0 + Z) : q.c;
+    const T fy4 = y0 + 4 < v.n2 ? f[i0 + 4] : (T)0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        q.d[0].v[k] = x + 1 < v.n1 ? fx.v[k] - q.c.v[k] : (T)0;
+        q.d[1].v[k] = z + 1 < v.nz ? fz.v[k] - q.c.v[k] : (T)0;
+        const T nb = k < 3 ? q.c.v[k + 1] : fy4;
+        q.d[2].v[k] = y0 + k + 1 < v.n2 ? nb - q.c.v[k] : (T)0;
+    }
+    return q;
+}
+
+// ---------------------------------------------------------------------------
 // deterministic block + grid reduction of K doubles
 // ---------------------------------------------------------------------------
 
@@ -163,31 +227,60 @@ __global__ void __launch_bounds__(256) k_lsp_G(const T* __restrict__ Gd, const T
                                                T* __restrict__ G, int first, AdmmRed r, Vol v) {
     const double rho_d = r.sc[SC_RHO];
     const T rho = (T)rho_d, irho = (T)(1.0 / rho_d), ihw = (T)r.sc[SC_INVHW];
+    const long long N = v.N, X = (long long)v.nz * v.n2, Z = v.n2;
     double acc[3] = {0, 0, 0};
     T loc[3] = {0, 0, 0};
     int cnt = 0;
-    for_voxel_quads(v, [&](long long i, int x, int z, int y) {
-        auto q = [&](int a, long long j) -> T {
-            T d = 0;
-            if (!first) {
-                int xx = x, zz = z, yy = y;
-                if (j != i) {  // j = i - e_a
-                    if (a == 0) --xx;
-                    else if (a == 1) --zz;
-                    else --yy;
-                }
-                d = fdiff(du, j, xx, zz, yy, a, v);
-            }
-            return d + e[a * v.N + j] + lam[a * v.N + j] * irho;
-        };
-        const T g = Gd[i] * ihw - rho * div_at(q, i, x, z, y, v);
-        G[i] = g;
-        loc[0] += g * g;
+    for_quads(v, [&](long long i0, int x, int z, int y0) {
+        // du at the quad and its six neighbour quads / values (grad du at i and
+        // at i - e_a); e, lambda at the quad and at i - e_a
+        Q4<T> uc = zero4<T>(), uxp = zero4<T>(), uxm = zero4<T>(), uzp = zero4<T>(), uzm = zero4<T>();
+        T uym = 0, uyp = 0;
         if (!first) {
-            const T pi = p[i];
-            loc[1] += pi * g;
-            loc[2] += pi * Gprev[i];
+            uc = ld4(du + i0);
+            if (x + 1 < v.n1) uxp = ld4(du + i0 + X);
+            if (x >= 1) uxm = ld4(du + i0 - X);
+            if (z + 1 < v.nz) uzp = ld4(du + i0 + Z);
+            if (z >= 1) uzm = ld4(du + i0 - Z);
+            if (y0 >= 1) uym = du[i0 - 1];
+            if (y0 + 4 < v.n2) uyp = du[i0 + 4];
         }
+        const Q4<T> e0 = ld4(e + i0), e1 = ld4(e + N + i0), e2 = ld4(e + 2 * N + i0);
+        const Q4<T> l0 = ld4(lam + i0), l1 = ld4(lam + N + i0), l2 = ld4(lam + 2 * N + i0);
+        const Q4<T> e0m = x >= 1 ? ld4(e + i0 - X) : zero4<T>(), l0m = x >= 1 ? ld4(lam + i0 - X) : zero4<T>();
+        const Q4<T> e1m = z >= 1 ? ld4(e + N + i0 - Z) : zero4<T>(), l1m = z >= 1 ? ld4(lam + N + i0 - Z) : zero4<T>();
+        const T e2m = y0 >= 1 ? e[2 * N + i0 - 1] : (T)0, l2m = y0 >= 1 ? lam[2 * N + i0 - 1] : (T)0;
+        const Q4<T> gd = ld4(Gd + i0);
+        Q4<T> pq = zero4<T>(), gp = zero4<T>();
+        if (!first) {
+            pq = ld4(p + i0);
+            gp = ld4(Gprev + i0);
+        }
+        Q4<T> gout;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int y = y0 + k;
+            const T c = uc.v[k];
+            // q_a(j) = d_a du(j) + e_a(j) + lambda_a(j) / rho, as in div_at's order
+            T sdiv = 0;
+            if (x + 1 < v.n1) sdiv += (first ? (T)0 : uxp.v[k] - c) + e0.v[k] + l0.v[k] * irho;
+            if (x >= 1) sdiv -= (first ? (T)0 : c - uxm.v[k]) + e0m.v[k] + l0m.v[k] * irho;
+            if (z + 1 < v.nz) sdiv += (first ? (T)0 : uzp.v[k] - c) + e1.v[k] + l1.v[k] * irho;
+            if (z >= 1) sdiv -= (first ? (T)0 : c - uzm.v[k]) + e1m.v[k] + l1m.v[k] * irho;
+            const T ynext = k < 3 ? uc.v[k + 1] : uyp;
+            const T yprev = k > 0 ? uc.v[k - 1] : uym;
+            const T e2p = k > 0 ? e2.v[k - 1] : e2m, l2p = k > 0 ? l2.v[k - 1] : l2m;
+            if (y + 1 < v.n2) sdiv += (first ? (T)0 : ynext - c) + e2.v[k] + l2.v[k] * irho;
+            if (y >= 1) sdiv -= (first ? (T)0 : c - yprev) + e2p + l2p * irho;
+            const T g = gd.v[k] * ihw - rho * sdiv;
+            gout.v[k] = g;
+            loc[0] += g * g;
+            if (!first) {
+                loc[1] += pq.v[k] * g;
+                loc[2] += pq.v[k] * gp.v[k];
+            }
+        }
+        st4(G + i0, gout);
     }, [&]() {
         if (++cnt == 2) {  // FP32 partials of at most 8 terms
             for (int k = 0; k < 3; ++k) { acc[k] += (double)loc[k]; loc[k] = 0; }
@@ -228,11 +321,11 @@ __global__ void __launch_bounds__(256) k_gradnorm2(const T* __restrict__ f, Admm
     double acc[1] = {0};
     T loc = 0;
     int cnt = 0;
-    for_voxel_quads(v, [&](long long i, int x, int z, int y) {
-        for (int a = 0; a < 3; ++a) {
-            const T d = fdiff(f, i, x, z, y, a, v);
-            loc += d * d;
-        }
+    for_quads(v, [&](long long i0, int x, int z, int y0) {
+        const QuadDiff<T> q = quad_fdiff(f, i0, x, z, y0, v);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            for (int a = 0; a < 3; ++a) loc += q.d[a].v[k] * q.d[a].v[k];
     }, [&]() {
         if (++cnt == 2) { acc[0] += (double)loc; loc = 0; cnt = 0; }
     });
@@ -322,34 +415,51 @@ __global__ void __launch_bounds__(256) k_rsp(const T* __restrict__ u, const T* _
                                              T* __restrict__ lam, T* __restrict__ dpsi, AdmmRed r, Vol v) {
     const double rho_d = r.sc[SC_RHO];
     const T rho = (T)rho_d, irho = (T)(1.0 / rho_d), kappa = (T)(r.sc[SC_ALPHA] / rho_d);
+    const long long N = v.N;
     double acc[2] = {0, 0};
     T loc[2] = {0, 0};
     int cnt = 0;
-    for_voxel_quads(v, [&](long long i, int x, int z, int y) {
-        T gu[3], zz[3], lm[3];
-        T m2 = 0, g2 = 0;
+    for_quads(v, [&](long long i0, int x, int z, int y0) {
+        const QuadDiff<T> gq = quad_fdiff(u, i0, x, z, y0, v);
+        const QuadDiff<T> dq = quad_fdiff(du, i0, x, z, y0, v);
+        Q4<T> lq[3], eq[3], en4[3], ln4[3], dp4[3];
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
-            gu[a] = fdiff(u, i, x, z, y, a, v);
-            lm[a] = lam[a * v.N + i];
-            zz[a] = gu[a] + lm[a] * irho;
-            m2 += zz[a] * zz[a];
-            g2 += gu[a] * gu[a];
+            lq[a] = ld4(lam + a * N + i0);
+            eq[a] = ld4(e + a * N + i0);
         }
-        const T mag = sqrt(m2);
-        const bool active = mag > kappa;
-        const T kz = active ? kappa / mag : (T)0;
-        T e2 = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            T gu[3], zz[3], lm[3];
+            T m2 = 0, g2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                gu[a] = gq.d[a].v[k];
+                lm[a] = lq[a].v[k];
+                zz[a] = gu[a] + lm[a] * irho;
+                m2 += zz[a] * zz[a];
+                g2 += gu[a] * gu[a];
+            }
+            const T mag = sqrt(m2);
+            const bool active = mag > kappa;
+            const T kz = active ? kappa / mag : (T)0;
+            T e2 = 0;
+            for (int a = 0; a < 3; ++a) {
+                const T en = active ? kz * zz[a] - lm[a] * irho : gu[a];
+                const T ln = active ? rho * kz * zz[a] : lm[a] + rho * gu[a];
+                dp4[a].v[k] = dq.d[a].v[k] - (en - eq[a].v[k]);
+                en4[a].v[k] = en;
+                ln4[a].v[k] = ln;
+                e2 += en * en;
+            }
+            loc[0] += e2;
+            loc[1] += sqrt(g2);
+        }
+#pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const long long j = a * v.N + i;
-            const T en = active ? kz * zz[a] - lm[a] * irho : gu[a];
-            const T ln = active ? rho * kz * zz[a] : lm[a] + rho * gu[a];
-            dpsi[j] = fdiff(du, i, x, z, y, a, v) - (en - e[j]);
-            e[j] = en;
-            lam[j] = ln;
-            e2 += en * en;
+            st4(dpsi + a * N + i0, dp4[a]);
+            st4(e + a * N + i0, en4[a]);
+            st4(lam + a * N + i0, ln4[a]);
         }
-        loc[0] += e2;
-        loc[1] += sqrt(g2);
     }, [&]() {
         if (++cnt == 2) {
             acc[0] += (double)loc[0];

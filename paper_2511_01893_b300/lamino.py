@@ -388,6 +388,14 @@ class Admm:
         _check(lib().admm_state_bytes(plan._h, ctypes.byref(nb)), "admm_state_bytes")
         self.state = torch.empty(nb.value, dtype=torch.uint8, device=plan.device)
         self.iters = 0
+        self._ready = None  # event recorded after init, on the stream init ran on
+
+    def _order(self):
+        # later calls may come on another stream (a capture stream for graph
+        # replay): make it wait for the initialisation, which ran on the
+        # stream current at init()
+        if self._ready is not None:
+            torch.cuda.current_stream(self.plan.device).wait_event(self._ready)
 
     def init(self, d, alpha, rho, n_inner=4, adapt_rho=True, form=2):
         """form: the LSP form, 2 (Algorithm 2, default) or 1 (Algorithm 1)."""
@@ -396,13 +404,17 @@ class Admm:
         _check(lib().admm_init(self.plan._h, _ptr(self.state), _ptr(d), float(alpha), float(rho), int(n_inner),
                                int(bool(adapt_rho)), _ptr(self.plan.ws), _stream()), "admm_init")
         self.iters = 0
+        self._ready = torch.cuda.Event()
+        self._ready.record(torch.cuda.current_stream(self.plan.device))
         return self
 
     def step(self):
+        self._order()
         _check(lib().admm_step(self.plan._h, _ptr(self.state), _ptr(self.plan.ws), _stream()), "admm_step")
         self.iters += 1
 
     def run(self, iters, graph=False):
+        self._order()
         _check(lib().admm_run(self.plan._h, _ptr(self.state), _ptr(self.plan.ws), int(iters), int(bool(graph)),
                               _stream()), "admm_run")
         self.iters += iters
@@ -496,6 +508,8 @@ class Batch:
         """`iters` outer iterations of every Admm (one per plan, same order)."""
         if len(admms) != len(self.plans) or any(a.plan is not p for a, p in zip(admms, self.plans)):
             raise LaminoError("one Admm per plan of the batch, in order")
+        for a in admms:
+            a._order()
         _check(lib().admm_run_batched(self._h, _ptr_array([a.state for a in admms]), int(iters), int(bool(graph)),
                                       _stream()), "admm_run_batched")
         for a in admms:

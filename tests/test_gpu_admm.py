@@ -45,6 +45,7 @@ def _gpu_admm(case, prec, adapt, graph=False, fast_adjoint=False):
     a = glam.Admm(plan).init(torch.from_numpy(case["d"]), ALPHA, RHO, N_INNER, adapt_rho=adapt)
     if graph:
         s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
             a.run(N_OUTER, graph=True)
         s.synchronize()
@@ -145,6 +146,7 @@ def test_reconstruct_one_call_matches_state_api(case):
     d = torch.from_numpy(case["d"].real.astype(np.complex64))
     a = glam.Admm(plan).init(d, ALPHA, RHO, 4, adapt_rho=True)
     s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
     with torch.cuda.stream(s):
         a.run(3, graph=True)
     s.synchronize()

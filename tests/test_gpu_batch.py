@@ -75,6 +75,7 @@ def test_batched_admm_equals_single_plan_admm(graph):
     batched = [glam.Admm(p).init(d, 1e-3, 0.5, 3) for p, d in zip(plans, datas)]
     if graph:
         s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
             batch.admm_run(batched, 3, graph=True)
         s.synchronize()
