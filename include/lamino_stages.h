@@ -45,6 +45,25 @@ lam_status lamx_u2d_adj(const lam_plan* plan, const void* d_hat, void* u1, void*
  * wrong results: order them on one stream or synchronise between them. */
 lam_status lamx_u2d_fwd_static(const lam_plan* plan, const void* u1, void* d_hat, const void* sub, void* stream);
 
+/* The adjoint spread alone (the first kernel of F*_u2D, the type-1 Gaussian
+ * spread of Section 2's F_u2D transpose): the slice values of d_hat
+ * ([n_theta][h][w], plan precision) of the Hermitian plane jobs
+ * j0 .. j0 + nb - 1 are spread onto the padded planes of the workspace's
+ * plane batch, with the plan's spread variant.  Requires
+ * 0 <= j0, 1 <= nb, j0 + nb <= the number of plane jobs, and nb <= the
+ * planes per batch (LAM_EINVAL otherwise).  For timing the dominant kernel
+ * of L_hat^H on its own; the workspace planes are overwritten. */
+lam_status lamx_spread(const lam_plan* plan, const void* d_hat, void* ws, int j0, int nb, void* stream);
+
+/* Plane jobs per launch of the L_hat / L_hat^H plane stages (the batch size
+ * those calls use); 0 for a NULL plan. */
+int lamx_jobs_per_batch(const lam_plan* plan);
+
+/* Data planes (kv rows of d_hat) that plane jobs j0 .. j0 + nb - 1 cover: 2
+ * for a job with a conjugate-mirror plane, else 1; -1 for a NULL plan or a
+ * range outside the plan's jobs. */
+int lamx_job_planes(const lam_plan* plan, int j0, int nb);
+
 /* Launch shapes chosen by the plan, for diagnostics: out[0..count) receives
  * TY (z forward), TY (z transpose), rows per block, columns per block,
  * scatter tile side, tile images, planes per batch, jmin, jmax, the

@@ -90,6 +90,7 @@ struct lam_plan {
     int jmin, jmax;
     // plane jobs: paired (for real volumes) and one job per plane
     int2* jobs_pair;
+    std::vector<int2> jobs_pair_h;  // host copy of jobs_pair
     int2* jobs_all;
     int* skip;  // [h] 1 for the mirror plane of a paired job
     int njobs_pair;
@@ -259,6 +260,7 @@ template <typename T> lam_status build_tables(lam_plan* p, const double* theta) 
         std::stable_sort(jp.begin(), jp.end(),
                          [h](const int2& a, const int2& b) { return std::abs(a.x - h / 2) < std::abs(b.x - h / 2); });
         p->njobs_pair = (int)jp.size();
+        p->jobs_pair_h = jp;
         p->jobs_pair = (int2*)upload(p, jp, &st);
         if (st) return st;
         p->jobs_all = (int2*)upload(p, ja, &st);
@@ -653,6 +655,16 @@ template <typename T> lam_status u2d_fwd_t(const lam_plan* p, const void* u1, vo
                                  std::min(p->nbatch, p->h - j0), a, s));
     return LAM_OK;
 }
+template <typename T>
+lam_status spread_t(const lam_plan* p, const void* d_hat, void* ws, int j0, int nb, cudaStream_t s) {
+    char* w = (char*)ws;
+    Usfft2dArgs<T> a = args2d<T>(p, true);
+    a.halo = (C<T>*)(w + p->ws_halo);
+    if (lam_status st = prep_scatter<T>(p, (const C<T>*)d_hat, ws, s, a)) return st;
+    CK(launch_spread2d<T>((const C<T>*)d_hat, (C<T>*)(w + p->ws_planes), j0, nb, a, s));
+    return LAM_OK;
+}
+
 template <typename T> lam_status u2d_adj_t(const lam_plan* p, const void* in, void* u1, void* ws,
                                                   cudaStream_t s) {
     C<T>* P = (C<T>*)((char*)ws + p->ws_planes);
@@ -1340,6 +1352,25 @@ lam_status lamx_u2d_adj(const lam_plan* p, const void* d_hat, void* u1, void* ws
     if (lam_status st = check_plan(p)) return st;
     cudaStream_t s = (cudaStream_t)stream;
     return DISPATCH(p, u2d_adj_t<float>(p, d_hat, u1, ws, s), u2d_adj_t<double>(p, d_hat, u1, ws, s));
+}
+
+lam_status lamx_spread(const lam_plan* p, const void* d_hat, void* ws, int j0, int nb, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!d_hat || !ws) return fail(LAM_EINVAL, "NULL array argument");
+    if (j0 < 0 || nb < 1 || j0 + nb > p->njobs_pair)
+        return fail(LAM_EINVAL, "plane jobs [%d, %d) outside [0, %d)", j0, j0 + nb, p->njobs_pair);
+    if (nb > p->nbatch) return fail(LAM_EINVAL, "nb = %d: the workspace holds %d planes", nb, p->nbatch);
+    cudaStream_t s = (cudaStream_t)stream;
+    return DISPATCH(p, spread_t<float>(p, d_hat, ws, j0, nb, s), spread_t<double>(p, d_hat, ws, j0, nb, s));
+}
+
+int lamx_jobs_per_batch(const lam_plan* p) { return p ? even_batch(p, p->njobs_pair) : 0; }
+
+int lamx_job_planes(const lam_plan* p, int j0, int nb) {
+    if (!p || j0 < 0 || nb < 0 || j0 + nb > p->njobs_pair) return -1;
+    int planes = 0;
+    for (int j = j0; j < j0 + nb; ++j) planes += p->jobs_pair_h[j].y >= 0 ? 2 : 1;
+    return planes;
 }
 
 lam_status lamx_u2d_fwd_static(const lam_plan* p, const void* u1, void* d_hat, const void* sub, void* stream) {

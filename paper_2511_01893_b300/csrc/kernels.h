@@ -93,6 +93,8 @@ cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* s
 // a paired job spreads both planes (the mirror plane mirrored and conjugated)
 // into one grid and writes u1[jobs[j].x] = u1'(kv) + conj u1'(-kv)
 template <typename T>
+cudaError_t launch_spread2d(const C<T>* in, C<T>* P, int j0, int nb, const Usfft2dArgs<T>& a, cudaStream_t s);
+template <typename T>
 cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int kv0, int nb,
                                const Usfft2dArgs<T>& a, cudaStream_t s);
 

@@ -1214,14 +1214,13 @@ cudaError_t launch_fma_peak(float* sink, int blocks, int iters, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+// the adjoint spread alone: slice values of plane jobs j0 .. j0 + nb - 1 onto
+// their padded planes P[0 .. nb) (the spread variant a.spread selects)
 template <typename T>
-cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int j0, int nb, const Usfft2dArgs<T>& a,
-                               cudaStream_t s) {
+cudaError_t launch_spread2d(const C<T>* in, C<T>* P, int j0, int nb, const Usfft2dArgs<T>& a, cudaStream_t s) {
     const int kv0 = j0;
     constexpr int NW = kScatterWarps;
     const int ntiles = (a.M1 / a.TS) * (a.M2 / a.TS);
-    const size_t sr = (size_t)a.RB * fpad_len(a.M2) * sizeof(C<T>);
-    const size_t sc = (size_t)a.CB * fpad_len(a.M1) * sizeof(C<T>);
     // exact fixed-point accumulation (default) or plain atomic adds
     const size_t cells = (size_t)a.TS * a.TS;
     const dim3 grid1(ntiles, nb);
@@ -1260,6 +1259,17 @@ cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int j0, int nb
     else { LAM_SW(0) }
 #undef LAM_SW
 #undef LAM_S
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int j0, int nb, const Usfft2dArgs<T>& a,
+                               cudaStream_t s) {
+    const int kv0 = j0;
+    const size_t sr = (size_t)a.RB * fpad_len(a.M2) * sizeof(C<T>);
+    const size_t sc = (size_t)a.CB * fpad_len(a.M1) * sizeof(C<T>);
+    cudaError_t e = launch_spread2d<T>(in, P, j0, nb, a, s);
+    if (e != cudaSuccess) return e;
     const int gp = pipe_grid((a.M2 / a.CB) * nb, a.fthr, 2 * sc);
     if (fft_mixed(a.fcM1) || fft_mixed(a.fcM2)) {
         k_colfft_adj_pipe<T, true><<<gp, a.fthr, 2 * sc, s>>>(P, a, nb);
@@ -1497,6 +1507,9 @@ template cudaError_t launch_usfft2d_fwd<float>(const C<float>*, C<float>*, C<flo
                                                const Usfft2dArgs<float>&, cudaStream_t);
 template cudaError_t launch_usfft2d_fwd<double>(const C<double>*, C<double>*, C<double>*, const C<double>*, int,
                                                 int, const Usfft2dArgs<double>&, cudaStream_t);
+template cudaError_t launch_spread2d<float>(const C<float>*, C<float>*, int, int, const Usfft2dArgs<float>&, cudaStream_t);
+template cudaError_t launch_spread2d<double>(const C<double>*, C<double>*, int, int, const Usfft2dArgs<double>&,
+                                             cudaStream_t);
 template cudaError_t launch_usfft2d_planes<float>(const C<float>*, C<float>*, int, int, const Usfft2dArgs<float>&,
                                                   cudaStream_t);
 template cudaError_t launch_usfft2d_planes<double>(const C<double>*, C<double>*, int, int, const Usfft2dArgs<double>&,

@@ -74,6 +74,9 @@ def lib() -> ctypes.CDLL:
             "lam_adjoint_batched": [vp, vp, vp, vp],
             "admm_run_batched": [vp, vp, i, i, vp],
             "lamx_batch_info": [vp, ctypes.POINTER(i), i],
+            "lamx_spread": [vp, vp, vp, i, i, vp],
+            "lamx_jobs_per_batch": [vp],
+            "lamx_job_planes": [vp, i, i],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -306,6 +309,18 @@ class Plan:
         _check(lib().lamx_plane_ffts(self._h, _ptr(u1), _ptr(P), int(j0), int(P.shape[0]), _stream()),
                "lamx_plane_ffts")
         return P
+
+    def spread(self, d_hat, j0=0, nb=None):
+        """The adjoint spread alone for plane jobs j0 .. j0 + nb - 1 (default: one
+        operator batch) into the workspace planes; returns nb."""
+        nb = lib().lamx_jobs_per_batch(self._h) if nb is None else int(nb)
+        d_hat = self._inp(d_hat, self.cdtype, self.data_shape)
+        _check(lib().lamx_spread(self._h, _ptr(d_hat), _ptr(self.ws), int(j0), nb, _stream()), "lamx_spread")
+        return nb
+
+    def job_planes(self, j0, nb):
+        """Data planes (kv rows) plane jobs j0 .. j0 + nb - 1 cover."""
+        return lib().lamx_job_planes(self._h, int(j0), int(nb))
 
     def set_threads(self, z=None, fft=None):
         """Threads per block (256 or 512) of the z-stage kernels and of the

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import plan_and_geom, rand_data, rand_vol, rel, tol
+from gpu_helpers import TOL_F32_OP, plan_and_geom, rand_data, rand_vol, rel, tol
 from oracle import lamino as olam
 from oracle import tv as otv
 from paper_2511_01893_b300 import lamino as glam
@@ -190,6 +190,29 @@ def test_threads_per_block_keep_results_bitwise(prec):
         assert torch.equal(plan.adjoint(d), a0)
     with pytest.raises(glam.LaminoError):
         plan.set_threads(z=384)
+
+
+def test_spread_stage_entry_point(monkeypatch):
+    # the spread alone (timed by bench.py as the dominant kernel): one batch
+    # of plane jobs into the workspace planes, arguments checked on the host;
+    # 4 planes per batch, fewer than the 33 plane jobs
+    monkeypatch.setenv("LAMINO_PLANES_PER_BATCH", "4")
+    n, nz, h, w, T = 64, 16, 64, 64, 24
+    plan, g = plan_and_geom(n, nz, h, w, T, 0.4, "f32")
+    assert plan.info()["planes_per_batch"] == 4
+    d = torch.from_numpy(rand_data(T, h, w, 25)).cuda().to(torch.complex64)
+    nb = plan.spread(d)
+    assert 1 <= nb <= plan.info()["planes_per_batch"]
+    assert nb <= plan.job_planes(0, nb) <= 2 * nb
+    assert plan.job_planes(0, plan.info()["plane_jobs"]) == h
+    assert plan.job_planes(0, plan.info()["plane_jobs"] + 1) == -1
+    with pytest.raises(glam.LaminoError, match="outside"):
+        plan.spread(d, plan.info()["plane_jobs"], 1)
+    with pytest.raises(glam.LaminoError, match="workspace holds"):
+        plan.spread(d, 0, plan.info()["planes_per_batch"] + 1)
+    torch.cuda.synchronize()
+    # the full adjoint after the standalone spread is unchanged
+    assert rel(plan.adjoint_hat(d), olam.lhat_adj(rand_data(T, h, w, 25), g)) < TOL_F32_OP
 
 
 def test_hat_workspace_serves_the_hat_operators():
