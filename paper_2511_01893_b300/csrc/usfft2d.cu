@@ -1125,6 +1125,11 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
 
 // warps per tile-block in the gather and the scatter (16 measured slower)
 constexpr int kScatterWarps = 4;
+// warps per block of the tile spread (each with its private 32 x 32 tile):
+// 2 measured fastest (1024^3 L-hat^H: 145 ms against 153 with 3, 154 with 4
+// and 151 with 1); the warps of a tile split its slice lines, and fewer warps
+// per tile leave less of them idle at the tile's end
+constexpr int kSpreadWarps = 2;
 
 // The FP32 row / column FFT kernels are also built for the power-of-two plane
 // lengths 2n of the large workloads, with the length a compile-time constant
@@ -1248,9 +1253,9 @@ cudaError_t launch_spread2d(const C<T>* in, C<T>* P, int j0, int nb, const Usfft
         const long long hb = (ncells + 255) / 256;
         k_halo_sum<T><<<(int)(hb < 148 * 8 ? hb : 148 * 8), 256, 0, s>>>(a.halo, P, nb, kSpreadTS + 2 * a.m - 1, a);
     } else if ((a.spread == kSpreadTiles || a.spread == kSpreadHalo) && a.TS == kSpreadTS) {
-        const size_t st = spread_tiles_smem<T>(NW, a.m);
+        const size_t st = spread_tiles_smem<T>(kSpreadWarps, a.m);
         switch (a.m) {
-#define LAM_T(MH) case MH: k_spread2d_tiles<T, NW, MH><<<grid1, NW * 32, st, s>>>(in, P, kv0, a); break;
+#define LAM_T(MH) case MH: k_spread2d_tiles<T, kSpreadWarps, MH><<<grid1, kSpreadWarps * 32, st, s>>>(in, P, kv0, a); break;
             LAM_T(2) LAM_T(3) LAM_T(4) LAM_T(5) LAM_T(6) LAM_T(7) LAM_T(8)
 #undef LAM_T
             default: return cudaErrorInvalidValue;
@@ -1335,7 +1340,7 @@ template <typename T> cudaError_t configure_usfft2d() {
     if (!e) e = cudaFuncSetAttribute(k_gather2d_tiled<T, kScatterWarps, MH>, at, mt);       \
     if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 0>, at, mt);  \
     if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 3>, at, mt);    \
-    if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles<T, kScatterWarps, MH>, at, mt);    \
+    if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles<T, kSpreadWarps, MH>, at, mt);    \
     if (!e) e = cudaFuncSetAttribute(k_spread2d_halo<T, kScatterWarps, MH>, at, mt);
     LAM_A(2) LAM_A(3) LAM_A(4) LAM_A(5) LAM_A(6) LAM_A(7) LAM_A(8)
 #undef LAM_A
