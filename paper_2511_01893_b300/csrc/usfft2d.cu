@@ -1125,6 +1125,8 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
 
 // warps per tile-block in the gather and the scatter (16 measured slower)
 constexpr int kScatterWarps = 4;
+// warps per block of the tiled gather (they share the block's staged tile)
+constexpr int kGatherWarps = 4;
 // warps per block of the tile spread (each with its private 32 x 32 tile):
 // 2 measured fastest (1024^3 L-hat^H: 145 ms against 153 with 3, 154 with 4
 // and 151 with 1); the warps of a tile split its slice lines, and fewer warps
@@ -1168,7 +1170,7 @@ cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* s
         LAM_PLANE_NC(a.M2, LAM_RF);
         LAM_PLANE_NC(a.M1, LAM_CF);
     }
-    constexpr int NW = kScatterWarps;
+    constexpr int NW = kGatherWarps;
     const int ntiles = (a.M1 / a.TG) * (a.M2 / a.TG);
     const size_t sg = (size_t)(a.TG + 2 * a.m - 1) * (a.TG + 2 * a.m + 1) * sizeof(C<T>);
     const dim3 grid(ntiles, nb, 2);
@@ -1337,7 +1339,7 @@ template <typename T> cudaError_t configure_usfft2d() {
     // the tile kernels also hold static shared memory (the per-warp line lists)
     const int mt = kMaxDynSmem - 4096;
 #define LAM_A(MH)                                                                          \
-    if (!e) e = cudaFuncSetAttribute(k_gather2d_tiled<T, kScatterWarps, MH>, at, mt);       \
+    if (!e) e = cudaFuncSetAttribute(k_gather2d_tiled<T, kGatherWarps, MH>, at, mt);       \
     if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 0>, at, mt);  \
     if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 3>, at, mt);    \
     if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles<T, kSpreadWarps, MH>, at, mt);    \
