@@ -65,9 +65,11 @@ def workload_name(n):
 # ---------------------------------------------------------------------------
 
 def lhat_bytes(n, nz, h, w, T):
-    """L-hat: read u (4 B/voxel), write + read u1 (8 B per n^2 h point each),
-    write d_hat (8 B per T h w point).  L-hat^H moves the same bytes."""
-    return 4 * n * n * nz + 16 * n * n * h + 8 * T * h * w
+    """L-hat: read u (4 B/voxel), write + read u1 (8 B per (x, kv, y) point
+    each) for the h/2 + 1 kv planes a real volume needs (the others are the
+    conjugate mirrors), write d_hat (8 B per T h w point).  L-hat^H moves the
+    same bytes."""
+    return 4 * n * n * nz + 16 * n * n * (h // 2 + 1) + 8 * T * h * w
 
 
 # ---------------------------------------------------------------------------
