@@ -1448,7 +1448,6 @@ template <typename T> cudaError_t launch_batch_ptrs(BatchTable<T>* dev, const Ba
 
 // the kernel of a batched plane stage, as a void pointer for occupancy queries
 template <typename T> const void* batch_plane_kernel(int stage, bool mixed, int m) {
-    constexpr int NW = kScatterWarps;
 #define LAM_FFTK(ST) return mixed ? (const void*)kb_plane_fft<T, true, ST> : (const void*)kb_plane_fft<T, false, ST>;
     switch (stage) {
         case kBRowFwd: LAM_FFTK(kBRowFwd)
@@ -1458,7 +1457,7 @@ template <typename T> const void* batch_plane_kernel(int stage, bool mixed, int 
         default: break;
     }
 #undef LAM_FFTK
-#define LAM_MH(MH) case MH: return stage == kBGather ? (const void*)kb_gather<T, NW, MH> : (const void*)kb_spread<T, NW, MH>;
+#define LAM_MH(MH) case MH: return stage == kBGather ? (const void*)kb_gather<T, kGatherWarps, MH> : (const void*)kb_spread<T, kSpreadWarps, MH>;
     switch (m) {
         LAM_MH(2) LAM_MH(3) LAM_MH(4) LAM_MH(5) LAM_MH(6) LAM_MH(7) LAM_MH(8)
         default: return nullptr;
@@ -1466,19 +1465,25 @@ template <typename T> const void* batch_plane_kernel(int stage, bool mixed, int 
 #undef LAM_MH
 }
 
+// threads per block of a batched plane stage: the same block shapes as the
+// single-plan kernels, so both give bitwise the same results
+static int batch_plane_threads(int stage) {
+    return stage == kBGather ? kGatherWarps * 32 : stage == kBSpread ? kSpreadWarps * 32 : kFftThreads;
+}
+
 template <typename T>
 cudaError_t launch_batch_plane(const BatchTable<T>* dev, int stage, bool mixed, int m, const BatchLaunch& L,
                                cudaStream_t s) {
     const void* k = batch_plane_kernel<T>(stage, mixed, m);
     if (!k) return cudaErrorInvalidValue;
-    const int threads = (stage == kBGather || stage == kBSpread) ? kScatterWarps * 32 : kFftThreads;
+    const int threads = batch_plane_threads(stage);
     void* args[] = {(void*)&dev};
     return cudaLaunchKernel(k, dim3(L.grid), dim3(threads), args, L.smem, s);
 }
 
 template <typename T> int batch_occupancy(int stage, bool mixed, int m, size_t smem) {
     const void* k = batch_plane_kernel<T>(stage, mixed, m);
-    const int threads = (stage == kBGather || stage == kBSpread) ? kScatterWarps * 32 : kFftThreads;
+    const int threads = batch_plane_threads(stage);
     int nb = 0;
     if (!k || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, threads, smem) != cudaSuccess) return 0;
     return nb;
@@ -1496,7 +1501,7 @@ template <typename T> cudaError_t configure_batch_plane() {
     return e;
 }
 
-template <typename T> size_t spread_tiles_bytes(int m) { return spread_tiles_smem<T>(kScatterWarps, m); }
+template <typename T> size_t spread_tiles_bytes(int m) { return spread_tiles_smem<T>(kSpreadWarps, m); }
 template size_t spread_tiles_bytes<float>(int);
 template size_t spread_tiles_bytes<double>(int);
 
