@@ -77,17 +77,17 @@ def lhat_bytes(n, nz, h, w, T):
 # ---------------------------------------------------------------------------
 
 def source_hash():
-    """SHA-256 of the device-code sources (csrc/*.cu, *.cuh, *.h in name order,
-    without the host-side C ABI in capi.cu): ties a stored DRAM-traffic figure
-    to the kernels it was measured on."""
+    """SHA-256 of the sources the L-hat / L-hat^H stage kernels are built from
+    (csrc/common.cuh, fft.cuh, kernels.h, usfft1d.cu, usfft2d.cu, in that
+    order): ties a stored DRAM-traffic figure of those kernels to the code it
+    was measured on."""
     import hashlib
     d = os.path.join(ROOT, "paper_2511_01893_b300", "csrc")
     h = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")) and f != "capi.cu":
-            h.update(f.encode())
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(fh.read())
+    for f in ("common.cuh", "fft.cuh", "kernels.h", "usfft1d.cu", "usfft2d.cu"):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
     return h.hexdigest()
 
 

@@ -220,8 +220,11 @@ __global__ void k_div(const T* __restrict__ p, T* __restrict__ out, Vol v) {
 // G = Gd * inv_hw - rho * div(q),  q_a(j) = d_a du(j) + e_a(j) + lambda_a(j) / rho
 // (= d_a u - psi_a + lambda_a / rho; du = 0 on the first CG step).
 // Reduces ||G||^2, <p, G>, <p, G_prev> into sc[SC_GG..SC_GG+2].
+// three blocks per SM (<= 85 registers): the kernel is load-latency bound, and
+// 24 resident warps measured faster than 16 (at 98 registers) or 32 (at 64,
+// with spills)
 template <typename T>
-__global__ void __launch_bounds__(256) k_lsp_G(const T* __restrict__ Gd, const T* __restrict__ du,
+__global__ void __launch_bounds__(256, 3) k_lsp_G(const T* __restrict__ Gd, const T* __restrict__ du,
                                                const T* __restrict__ e, const T* __restrict__ lam,
                                                const T* __restrict__ p, const T* __restrict__ Gprev,
                                                T* __restrict__ G, int first, AdmmRed r, Vol v) {
