@@ -621,7 +621,9 @@ def run_ours(args):
         tj = json.load(open(prof))
         # only while the kernels are the ones the counters were taken on
         if tj.get("size") == n and tj.get("source_sha256") == source_hash():
-            traffic = tj.get("spread_launch_dram_bytes")
+            # per launch: only for a launch over the same plane jobs
+            if tj.get("spread_launch_jobs") == nbj:
+                traffic = tj.get("spread_launch_dram_bytes")
             pair_traffic = tj.get("lhat_pair_dram_bytes")
     # ---- the dominant kernel alone: the adjoint spread, one operator batch per
     # launch (plane jobs 0 .. nbj - 1), CUDA events on its stream ----------------
