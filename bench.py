@@ -615,16 +615,6 @@ def run_ours(args):
         peak, peak_src = json.load(open(peaks_path))["hbm_gbs"], "measured"
     else:
         peak, peak_src = 6400.0, "fallback"
-    traffic = pair_traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(prof):
-        tj = json.load(open(prof))
-        # only while the kernels are the ones the counters were taken on
-        if tj.get("size") == n and tj.get("source_sha256") == source_hash():
-            # per launch: only for a launch over the same plane jobs
-            if tj.get("spread_launch_jobs") == nbj:
-                traffic = tj.get("spread_launch_dram_bytes")
-            pair_traffic = tj.get("lhat_pair_dram_bytes")
     # ---- the dominant kernel alone: the adjoint spread, one operator batch per
     # launch (plane jobs 0 .. nbj - 1), CUDA events on its stream ----------------
     kreps = 5
@@ -643,6 +633,16 @@ def run_ours(args):
     # writes one padded plane (8 B per cell) per job
     spread_bytes = planes * T * w * 8 + nbj * M * M * 8
     spread_flops = planes * T * w * spread_point_flops()
+    traffic = pair_traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        tj = json.load(open(prof))
+        # only while the kernels are the ones the counters were taken on
+        if tj.get("size") == n and tj.get("source_sha256") == source_hash():
+            # per launch: only for a launch over the same plane jobs
+            if tj.get("spread_launch_jobs") == nbj:
+                traffic = tj.get("spread_launch_dram_bytes")
+            pair_traffic = tj.get("lhat_pair_dram_bytes")
     del p, out_c, out_r
     fma = glam.fma_peak(dev)
     op_flops = 2 * lhat_flops(n, nz, h, w, T)
