@@ -28,12 +28,18 @@ template <typename T> __host__ __device__ __forceinline__ C<T> cadd(C<T> a, C<T>
 template <typename T> __host__ __device__ __forceinline__ C<T> csub(C<T> a, C<T> b) {
     return cmake<T>(a.x - b.x, a.y - b.y);
 }
+// Products of complex numbers are written with explicit fused multiply-adds:
+// an expression a b - c d could otherwise be fused either way by the compiler,
+// depending on the surrounding code, so the same butterfly inlined into two
+// kernels could round differently.  With the fusion spelled out every kernel
+// variant (runtime or compile-time FFT length, pipelined or not, single-plan
+// or batched) computes bitwise the same values.
 template <typename T> __host__ __device__ __forceinline__ C<T> cmul(C<T> a, C<T> b) {
-    return cmake<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return cmake<T>(fma(a.x, b.x, -(a.y * b.y)), fma(a.x, b.y, a.y * b.x));
 }
 // a * conj(b)
 template <typename T> __host__ __device__ __forceinline__ C<T> cmulc(C<T> a, C<T> b) {
-    return cmake<T>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+    return cmake<T>(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -(a.x * b.y)));
 }
 template <typename T> __host__ __device__ __forceinline__ C<T> cscale(C<T> a, T s) {
     return cmake<T>(a.x * s, a.y * s);

@@ -72,7 +72,9 @@ template <int DIR, typename T> __device__ __forceinline__ void dft16(C<T>* v) {
         for (int k1 = 0; k1 < 4; ++k1) v[n2 + 4 * k1] = t[k1];  // a[n2][k1] at v[n2 + 4 k1]
     }
     // W16^e, e = n2 k1 in {1, 2, 3, 4, 6, 9}: multiply by cos + DIR i sin of 2 pi e / 16
-    auto tw = [&](C<T> x, T c, T sn) { return cmake<T>(x.x * c - DIR * x.y * sn, x.y * c + DIR * x.x * sn); };
+    auto tw = [&](C<T> x, T c, T sn) {
+        return cmake<T>(fma(x.x, c, (T)(-DIR) * (x.y * sn)), fma(x.y, c, (T)DIR * (x.x * sn)));
+    };
     v[1 + 4] = tw(v[1 + 4], c1, s1);      // n2 1, k1 1
     v[1 + 8] = tw(v[1 + 8], r2, r2);      // n2 1, k1 2
     v[2 + 4] = tw(v[2 + 4], r2, r2);      // n2 2, k1 1
@@ -92,7 +94,7 @@ template <int DIR, typename T> __device__ __forceinline__ void dft3(C<T>* v) {
     const T hs = (T)0.86602540378443864676;
     const C<T> b = cadd(v[1], v[2]);
     const C<T> d = csub(v[1], v[2]);
-    const C<T> t = cmake<T>(v[0].x - (T)0.5 * b.x, v[0].y - (T)0.5 * b.y);
+    const C<T> t = cmake<T>(fma((T)-0.5, b.x, v[0].x), fma((T)-0.5, b.y, v[0].y));
     const C<T> e = cmul_i<DIR>(cmake<T>(hs * d.x, hs * d.y));
     v[0] = cadd(v[0], b);
     v[1] = cadd(t, e);
@@ -108,10 +110,10 @@ template <int DIR, typename T> __device__ __forceinline__ void dft5(C<T>* v) {
     const T s1 = (T)0.95105651629515357212, s2 = (T)0.58778525229247312917;
     const C<T> b1 = cadd(v[1], v[4]), d1 = csub(v[1], v[4]);
     const C<T> b2 = cadd(v[2], v[3]), d2 = csub(v[2], v[3]);
-    const C<T> t1 = cmake<T>(v[0].x + c1 * b1.x + c2 * b2.x, v[0].y + c1 * b1.y + c2 * b2.y);
-    const C<T> t2 = cmake<T>(v[0].x + c2 * b1.x + c1 * b2.x, v[0].y + c2 * b1.y + c1 * b2.y);
-    const C<T> e1 = cmul_i<DIR>(cmake<T>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y));
-    const C<T> e2 = cmul_i<DIR>(cmake<T>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y));
+    const C<T> t1 = cmake<T>(fma(c2, b2.x, fma(c1, b1.x, v[0].x)), fma(c2, b2.y, fma(c1, b1.y, v[0].y)));
+    const C<T> t2 = cmake<T>(fma(c1, b2.x, fma(c2, b1.x, v[0].x)), fma(c1, b2.y, fma(c2, b1.y, v[0].y)));
+    const C<T> e1 = cmul_i<DIR>(cmake<T>(fma(s1, d1.x, s2 * d2.x), fma(s1, d1.y, s2 * d2.y)));
+    const C<T> e2 = cmul_i<DIR>(cmake<T>(fma(s2, d1.x, -(s1 * d2.x)), fma(s2, d1.y, -(s1 * d2.y))));
     v[0] = cadd(v[0], cadd(b1, b2));
     v[1] = cadd(t1, e1);
     v[4] = csub(t1, e1);

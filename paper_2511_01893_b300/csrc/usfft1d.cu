@@ -65,7 +65,7 @@ __device__ __forceinline__ void k_usfft1d_fwd_body(const T* __restrict__ u, C<T>
         const T va = raw.x * d, vb = raw.y * d;
         const C<T> w = a.tw[wrap(xc, M0) * twM0];  // e^{-2 pi i xc / M0}
         buf[(2 * p) * LS + fpad(q)] = cmake<T>(va, vb);
-        buf[(2 * p + 1) * LS + fpad(q)] = cmake<T>(va * w.x - vb * w.y, va * w.y + vb * w.x);
+        buf[(2 * p + 1) * LS + fpad(q)] = cmul(cmake<T>(va, vb), w);
     }
     __syncthreads();
     fft_lines<-1, T, MIXED, NC>(buf, a.TY, LS, nz, a.fcz, a.tw, 2 * twM0);
@@ -83,10 +83,10 @@ __device__ __forceinline__ void k_usfft1d_fwd_body(const T* __restrict__ u, C<T>
             const C<T> pp = pz_at(E, O, jb + t, M0);
             const C<T> pm = pz_at(E, O, -(jb + t), M0);
             const T wt = wz[t];
-            sar += wt * (pp.x + pm.x);
-            sai += wt * (pp.y - pm.y);
-            sbr += wt * (pp.x - pm.x);
-            sbi += wt * (pp.y + pm.y);
+            sar = fma(wt, pp.x + pm.x, sar);
+            sai = fma(wt, pp.y - pm.y, sai);
+            sbr = fma(wt, pp.x - pm.x, sbr);
+            sbi = fma(wt, pp.y + pm.y, sbi);
         }
         if (a.skip && a.skip[kv]) continue;
         // a = (sa) / 2, b = (sb) / (2i) = (sb.im, -sb.re) / 2
@@ -124,10 +124,10 @@ __device__ __forceinline__ void spread_pair_at(const C<T>* va, const C<T>* vb, i
         for (int kv = lo; kv < hi; ++kv) {
             const T wk = wt[kv];
             const C<T> x = va[kv], y = vb[kv];
-            ar += wk * x.x;
-            ai += wk * x.y;
-            br += wk * y.x;
-            bi += wk * y.y;
+            ar = fma(wk, x.x, ar);
+            ai = fma(wk, x.y, ai);
+            br = fma(wk, y.x, br);
+            bi = fma(wk, y.y, bi);
         }
     }
     sa = cmake<T>(ar, ai);
@@ -185,8 +185,9 @@ __device__ __forceinline__ void k_usfft1d_adj_body(const C<T>* __restrict__ u1, 
         const int q = wrap(xc, nz);
         const C<T> e = buf[(2 * p) * LS + fpad(q)], o = buf[(2 * p + 1) * LS + fpad(q)];
         C<T> w = a.tw[wrap(xc, M0) * a.twstride];  // e^{-2 pi i xc / M0}; use its conjugate
-        const T fr = e.x + (o.x * w.x + o.y * w.y);
-        const T fi = e.y + (o.y * w.x - o.x * w.y);
+        const C<T> ow = cmulc(o, w);  // o e^{+2 pi i xc / M0}
+        const T fr = e.x + ow.x;
+        const T fi = e.y + ow.y;
         const T d = a.dz[z];
         dst[(size_t)z * a.n2 + 2 * p] = fr * d;
         dst[(size_t)z * a.n2 + 2 * p + 1] = fi * d;

@@ -485,8 +485,8 @@ __device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P
 #pragma unroll
                     for (int t = 0; t < nt; ++t) {
                         const C<T> pv = rowp[t];
-                        rr += wy[t] * pv.x;
-                        ri += wy[t] * pv.y;
+                        rr = fma(wy[t], pv.x, rr);
+                        ri = fma(wy[t], pv.y, ri);
                     }
 #ifdef LAM_GATHER_KAHAN
                     {
@@ -498,8 +498,8 @@ __device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P
                         si = ti;
                     }
 #else
-                    sr += wx * rr;
-                    si += wx * ri;
+                    sr = fma(wx, rr, sr);
+                    si = fma(wx, ri, si);
 #endif
                 }
                 const size_t o = ((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2);

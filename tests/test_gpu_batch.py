@@ -29,6 +29,23 @@ def _plans(prec="f32", sizes=SIZES):
     return out
 
 
+def test_batched_equals_single_for_autotuned_power_of_two_among_mixed_radix():
+    # the batch runs every problem through the mixed-radix kernel variant when
+    # any problem needs it; a power-of-two problem's single-plan calls run the
+    # power-of-two variant (and, at 2n >= 512, the compile-time-length one),
+    # with launch shapes from the autotuner: the results must not depend on it
+    plans = _plans("f32", [96, 128, 160, 256])
+    for p in plans:
+        p.autotune(reps=1)
+    batch = glam.Batch(plans)
+    us = [torch.from_numpy(rand_vol(p.n, p.nz, 40 + i)).cuda().float() for i, p in enumerate(plans)]
+    ds = [torch.from_numpy(rand_data(p.T, p.h, p.w, 50 + i)).cuda().to(torch.complex64) for i, p in enumerate(plans)]
+    fb, ab = batch.forward_hat(us), batch.adjoint_hat(ds)
+    for k, p in enumerate(plans):
+        assert torch.equal(fb[k], p.forward_hat(us[k]))
+        assert torch.equal(ab[k], p.adjoint_hat(ds[k]))
+
+
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_batched_operators_equal_single_plan_calls(prec):
     plans = _plans(prec)
