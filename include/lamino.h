@@ -255,7 +255,8 @@ typedef struct lam_batch lam_batch;
 /* Binds up to 32 plans (same precision and half-width, plans on the current
  * device, n a multiple of 16) to their workspaces (ws[i] of
  * lam_workspace_bytes(plans[i]) bytes, holding all of the plan's plane jobs:
- * the default when the padded planes of the h/2 + 1 jobs need at most 8 GiB).  Allocates one small device
+ * the default when the padded planes of the h/2 + 1 jobs need at most 8 GiB in
+ * FP32, 1 GiB in FP64).  Allocates one small device
  * table; the batch does not own the plans or workspaces, which must outlive
  * it.  The batched adjoint always uses the tile spread (LAM_SPREAD_TILES). */
 lam_status lam_batch_create(lam_batch** out, const lam_plan* const* plans, void* const* ws, int count);

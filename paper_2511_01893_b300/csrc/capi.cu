@@ -957,10 +957,12 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     p->pstride = (int)std::ceil(std::sqrt(2.0) * p->w / (double)p->M1 - 1e-9);
     if (p->pstride < 1) p->pstride = 1;
     const size_t plane = (size_t)p->M1 * p->M2 * ce_;
-    // padded planes per batch: up to 8 GiB (fewer, larger launches: at 1024^3
-    // two batches of 257 planes ran the L-hat / L-hat^H pair 2.4 % faster than
-    // 17 batches of 31 under a 1 GiB budget)
-    p->nbatch = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->h, ((size_t)8 << 30) / plane));
+    // padded planes per batch: up to 8 GiB in FP32 (fewer, larger launches: at
+    // 1024^3 three batches of <= 171 plane jobs ran the L-hat / L-hat^H pair
+    // 2.4 % faster than 17 batches of <= 31 under 1 GiB); 1 GiB in FP64, whose
+    // ADMM state at 1024^3 (~180 GB) leaves no room for more
+    const size_t plane_budget = (size_t)(prec == LAM_F32 ? 8 : 1) << 30;
+    p->nbatch = (int)std::max<size_t>(1, std::min<size_t>((size_t)p->h, plane_budget / plane));
     // LAMINO_PLANES_PER_BATCH overrides the number of padded planes processed per
     // batch (workspace size follows); for tuning
     if (const char* env = std::getenv("LAMINO_PLANES_PER_BATCH")) {
