@@ -30,7 +30,7 @@ def _deps_mtime(src: str) -> float:
 
 def build(verbose: bool = False, extra_flags=()) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    objs = []
+    objs, jobs = [], []
     for f in sorted(os.listdir(CSRC)):
         if not f.endswith(".cu"):
             continue
@@ -39,10 +39,24 @@ def build(verbose: bool = False, extra_flags=()) -> str:
         objs.append(obj)
         if os.path.exists(obj) and os.path.getmtime(obj) >= _deps_mtime(src) and not extra_flags:
             continue
-        cmd = [NVCC, *FLAGS, *extra_flags, "-c", src, "-o", obj]
+        jobs.append([NVCC, *FLAGS, *extra_flags, "-c", src, "-o", obj])
+    # the translation units compile independently: run them side by side
+    # (capturing each one's output so that messages do not interleave)
+    procs = []
+    for cmd in jobs:
         if verbose:
             print(" ".join(cmd), flush=True)
-        subprocess.run(cmd, check=True)
+        procs.append(subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True))
+    failed = None
+    for cmd, p in zip(jobs, procs):
+        out, _ = p.communicate()
+        if out:
+            sys.stdout.write(out)
+            sys.stdout.flush()
+        if p.returncode != 0 and failed is None:
+            failed = subprocess.CalledProcessError(p.returncode, cmd)
+    if failed is not None:
+        raise failed
     if (not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
             or extra_flags):
         cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", LIB, *objs, "-lcudart"]
