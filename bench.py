@@ -91,6 +91,24 @@ def source_hash():
     return h.hexdigest()
 
 
+def admm_iteration_bytes(n, nz, h, w, T, n_inner=N_INNER):
+    """Algorithmic HBM bytes of one ADMM-TV outer iteration (Algorithm 2 form):
+    per CG step one L-hat^H and one L-hat (lhat_bytes each), the LSP gradient
+    (reads L-hat^H r, e, lambda, writes G: 32 B/voxel; from the second step
+    also du, p, G_prev: +12), the direction update (12 B/voxel), ||grad p||^2
+    (4), u / du update (8, +4 from the second step, +8 on the last step for u),
+    ||L-hat p||^2 (8 B per data point) and r += gamma L-hat p (24 B per data
+    point); then the RSP (reads u, du, e, lambda, writes e, lambda, dpsi: 68
+    B/voxel) and ||div dpsi||^2 (12).  Stencil neighbours count once."""
+    K, D = n * n * nz, T * h * w
+    vox = 0
+    for k in range(n_inner):
+        later = 12 if k > 0 else 0
+        vox += 32 + later + 12 + 4 + 8 + (4 if k > 0 else 0) + (8 if k == n_inner - 1 else 0)
+    vox += 68 + 12
+    return n_inner * 2 * lhat_bytes(n, nz, h, w, T) + K * vox + D * n_inner * (8 + 24)
+
+
 def spread_point_flops(m=4):
     """Algorithmic FP32 flops the adjoint spread spends per slice point: its
     (2m)^2 cells, each a complex accumulation of a real weight times the value
@@ -647,6 +665,7 @@ def run_ours(args):
     fma = glam.fma_peak(dev)
     op_flops = 2 * lhat_flops(n, nz, h, w, T)
     alu_achieved = op_flops / (t_fwd + t_adj)
+    it_bytes = admm_iteration_bytes(n, nz, h, w, T)
     comparator = plane_fft_comparator(plan, glam, dev, stream) if rank == 0 else None
 
     line = {
@@ -665,6 +684,9 @@ def run_ours(args):
                          "peak": fma / 1e12, "frac": spread_flops / t_spread / fma,
                          "peak_source": "measured FMA probe", "kernel": "k_spread2d_tiles",
                          "algorithmic_flops": spread_flops},
+        "iteration_hbm": {"bound": "hbm", "unit": "GB/s", "achieved": it_bytes / s_per_iter / 1e9, "peak": peak,
+                          "frac": it_bytes / s_per_iter / 1e9 / peak, "algorithmic_bytes": it_bytes,
+                          "note": "one whole outer iteration: 8 operator applications, CG elementwise passes, RSP"},
         "operator_pair": {"bound": "hbm", "unit": "GB/s", "achieved": achieved, "peak": peak,
                           "frac": achieved / peak, "traffic": pair_traffic, "algorithmic_bytes": op_bytes,
                           "t_lhat_s": t_fwd, "t_lhat_adj_s": t_adj,
