@@ -86,6 +86,7 @@ struct lam_plan {
     void *dz, *d1, *d2, *wz, *tw, *ang;
     int *j0z, *kvlo, *kvhi;
     void* wzc;  // z weights cell by cell ([jmax - jmin + 1][zcw])
+    int *kvplo, *kvphi;  // per cell: the kv range the paired transpose needs
     int zcw;
     int jmin, jmax;
     // plane jobs: paired (for real volumes) and one job per plane
@@ -267,6 +268,28 @@ template <typename T> lam_status build_tables(lam_plan* p, const double* theta) 
         if (st) return st;
         p->skip = (int*)upload(p, skip, &st);
         if (st) return st;
+        // the paired transpose's kv range per cell: the non-skipped kv of
+        // [lo, hi) when they are contiguous (skipped planes carry zeros), else
+        // the whole range
+        std::vector<int> plo(E), phi(E);
+        for (int e = 0; e < E; ++e) {
+            int a = hi[e], b = lo[e];
+            for (int kv = lo[e]; kv < hi[e]; ++kv)
+                if (!skip[kv]) {
+                    a = std::min(a, kv);
+                    b = std::max(b, kv + 1);
+                }
+            bool contiguous = true;
+            for (int kv = a; kv < b; ++kv)
+                if (skip[kv]) contiguous = false;
+            if (a >= b) a = b = lo[e];
+            plo[e] = contiguous ? a : lo[e];
+            phi[e] = contiguous ? b : hi[e];
+        }
+        p->kvplo = (int*)upload(p, plo, &st);
+        if (st) return st;
+        p->kvphi = (int*)upload(p, phi, &st);
+        if (st) return st;
     }
     // twiddles exp(-2 pi i q / Nmax)
     std::vector<T> tw(2 * (size_t)p->Nmax);
@@ -358,6 +381,8 @@ template <typename T> Usfft1dArgs<T> args1d(const lam_plan* p, int TY, bool pair
     a.kvhi = p->kvhi;
     a.wzc = (const T*)p->wzc;
     a.cw = p->zcw;
+    a.kvslo = paired ? p->kvplo : p->kvlo;
+    a.kvshi = paired ? p->kvphi : p->kvhi;
     a.jmin = p->jmin;
     a.jmax = p->jmax;
     a.tw = (const C<T>*)p->tw;

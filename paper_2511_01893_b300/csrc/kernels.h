@@ -39,6 +39,8 @@ template <typename T> struct Usfft1dArgs {
     const int* kvhi;   // one past the last such kv
     const T* wzc;      // [jmax - jmin + 1][cw]: weight of kv kvlo[e] + i on cell e at i
     int cw;            // columns of wzc (most kv reaching one cell)
+    const int* kvslo;  // kv range the transpose sums over per cell: kvlo / kvhi,
+    const int* kvshi;  // or without the skipped (mirror) planes when paired
     int jmin, jmax;    // unwrapped cell range touched by any tap
     const C<T>* tw;    // twiddles exp(-2 pi i q / Nmax)
     int twstride;      // Nmax / M0

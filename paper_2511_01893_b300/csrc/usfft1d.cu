@@ -74,6 +74,7 @@ __device__ __forceinline__ void k_usfft1d_fwd_body(const T* __restrict__ u, C<T>
     const size_t plane = (size_t)a.n1 * a.n2;
     for (int i = tid; i < a.h * npair; i += nthr) {
         const int kv = i >> ilog2_pow2(npair), p = i - kv * npair;
+        if (a.skip && a.skip[kv]) continue;  // a conjugate-mirror plane: not stored, not computed
         const C<T>* E = buf + (2 * p) * LS;
         const C<T>* O = E + LS;
         const int jb = a.j0z[kv] - a.m + 1;
@@ -88,7 +89,6 @@ __device__ __forceinline__ void k_usfft1d_fwd_body(const T* __restrict__ u, C<T>
             sbr = fma(wt, pp.x - pm.x, sbr);
             sbi = fma(wt, pp.y + pm.y, sbi);
         }
-        if (a.skip && a.skip[kv]) continue;
         // a = (sa) / 2, b = (sb) / (2i) = (sb.im, -sb.re) / 2
         C<T>* o = dst + kv * plane + 2 * p;
         o[0] = cmake<T>((T)0.5 * sar, (T)0.5 * sai);
@@ -119,8 +119,8 @@ __device__ __forceinline__ void spread_pair_at(const C<T>* va, const C<T>* vb, i
     int e = j + ((a.jmin - j + M0 - 1 + 64 * M0) / M0 - 64) * M0;  // smallest e >= jmin, e == j
     for (; e <= a.jmax; e += M0) {
         const int c = e - a.jmin;
-        const int lo = a.kvlo[c], hi = a.kvhi[c];
-        const T* wt = a.wzc + (size_t)c * a.cw - lo;  // indexed by kv
+        const int lo = a.kvslo[c], hi = a.kvshi[c];
+        const T* wt = a.wzc + (size_t)c * a.cw - a.kvlo[c];  // indexed by kv
         for (int kv = lo; kv < hi; ++kv) {
             const T wk = wt[kv];
             const C<T> x = va[kv], y = vb[kv];
