@@ -76,18 +76,27 @@ def lhat_bytes(n, nz, h, w, T):
 # multi-rank timing (replicas: no data-path collective; only the clock is reduced)
 # ---------------------------------------------------------------------------
 
+def _strip_comments(src: str) -> str:
+    """C/C++ source without // and /* */ comments (string literals in these
+    files hold no comment markers), whitespace runs collapsed to one space."""
+    import re
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return re.sub(r"\s+", " ", src).strip()
+
+
 def source_hash():
-    """SHA-256 of the sources the L-hat / L-hat^H stage kernels are built from
-    (csrc/common.cuh, fft.cuh, kernels.h, usfft1d.cu, usfft2d.cu, in that
-    order): ties a stored DRAM-traffic figure of those kernels to the code it
-    was measured on."""
+    """SHA-256 of the code (comments stripped) of the sources the L-hat /
+    L-hat^H stage kernels are built from (csrc/common.cuh, fft.cuh,
+    kernels.h, usfft1d.cu, usfft2d.cu, in that order): ties a stored
+    DRAM-traffic figure of those kernels to the code it was measured on."""
     import hashlib
     d = os.path.join(ROOT, "paper_2511_01893_b300", "csrc")
     h = hashlib.sha256()
     for f in ("common.cuh", "fft.cuh", "kernels.h", "usfft1d.cu", "usfft2d.cu"):
         h.update(f.encode())
-        with open(os.path.join(d, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(d, f), encoding="utf-8") as fh:
+            h.update(_strip_comments(fh.read()).encode())
     return h.hexdigest()
 
 

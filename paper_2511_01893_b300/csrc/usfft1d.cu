@@ -8,14 +8,16 @@
 //
 // One block owns TY adjacent y-columns of one x-slab: it reads u[x][:][y0:y0+TY]
 // (TY contiguous values per z row), transforms them in shared memory and
-// writes u1[kv][x][y0:y0+TY] for every kv.  u1 is
+// writes u1[kv][x][y0:y0+TY] for every kv the operator needs (in the paired
+// operators of a real volume the conjugate-mirror planes are skipped).  u1 is
 // stored plane-major ([h][n1][n2]) so the per-plane 2D stage reads contiguous
 // planes.
 //
 // The transpose spreads the h values of each column onto the padded line in
 // gather form: each padded cell sums, over the contiguous kv range whose taps
-// reach it (a plan table), weight * value.  This keeps the spread atomic-free
-// and deterministic and makes it the exact transpose of the gather.
+// reach it (plan tables; without the mirror planes when paired), weight *
+// value.  This keeps the spread atomic-free and deterministic and makes it the
+// exact transpose of the gather.
 #include "fft.cuh"
 #include "kernels.h"
 

@@ -4,24 +4,30 @@
 // it evaluates sum_{x,y} u1[x, kv, y] exp(-2 pi i (xi_x x + xi_y y)) at the
 // n_theta * w slice points (xi_x, xi_y)(theta, kv, ku).  Gaussian USFFT in 2D:
 // deapodise, zero-pad to M1 x M2 = 2 n1 x 2 n2, row FFTs (only the n1 non-zero
-// rows), column FFTs, then a separable 2m x 2m Gaussian gather.
+// rows), column FFTs, then a separable 2m x 2m Gaussian gather.  For a real
+// volume a plane job pairs plane kv with its conjugate mirror h - kv: one
+// padded FFT serves both.
 //
-// Forward (type 2) kernels, per batch of nb planes held in P[nb][M1][M2]:
-//   k_rowfft_fwd   u1 rows -> deapodised, padded, FFT along y -> P rows
-//   k_colfft_fwd   P columns (n1 non-zero entries) -> FFT along x, in place
-//   k_gather2d     one thread per slice point: 64 taps from P, optional fused
-//                  subtraction (out = value - sub, Section 4.2)
+// Forward (type 2) kernels, per batch of nb plane jobs held in P[nb][M1][M2]:
+//   k_rowfft_fwd       u1 rows -> deapodised, padded, FFT along y -> P rows
+//   k_colfft_fwd_pipe  P columns (n1 non-zero entries) -> FFT along x, in
+//                      place; persistent, the next column strip loading while
+//                      the current one is transformed
+//   k_gather2d_tiled   a 64 x 64 tile of P (+ halo) staged in shared memory,
+//                      one lane per slice point: 64 taps, optional fused
+//                      subtraction (out = value - sub, Section 4.2)
 // Transpose (type 1):
-//   k_scatter2d_atomic  tile-owned accumulation: a block owns a TS x TS tile of
-//                  the padded plane, finds the slice lines that cross it and,
-//                  per line, the ku range of points whose taps reach the tile,
-//                  and accumulates weight * value in shared memory with
-//                  shared-memory atomics; the tile is written once (no global
-//                  atomics).  Default cells are exact 64-bit fixed point, so
-//                  the result is the correctly rounded sum of the products and
-//                  does not depend on scheduling.
-//   k_colfft_adj   inverse FFT along x, keep the n1 rows the crop needs
-//   k_rowfft_adj   inverse FFT along y, crop, deapodise -> u1 rows
+//   k_spread2d_tiles   (default) a block owns a 32 x 32 tile of the padded
+//                      plane; each of its warps sums the slice points whose
+//                      windows meet the tile into a private tile, and the
+//                      warp tiles are added in a fixed order: no atomics,
+//                      bitwise reproducible
+//   k_spread2d_halo, k_scatter2d_atomic   options (owner tiles with a halo
+//                      pass; shared-memory atomics, plain or exact fixed point)
+//   k_colfft_adj_pipe  inverse FFT along x, keep the n1 rows the crop needs
+//   k_rowfft_adj       inverse FFT along y, crop, deapodise -> u1 rows
+// The FP32 row / column kernels are also built for the large power-of-two
+// lengths with the length a compile-time constant (LAM_PLANE_NC).
 #include "fft.cuh"
 #include "kernels.h"
 
