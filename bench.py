@@ -170,8 +170,11 @@ def plane_fft_comparator(plan, glam, dev, stream, reps=3):
 
 
 def job_seconds_per_iter(t_local, steps, world, device=None):
-    """Whole-job seconds per ADMM iteration over `world` independent replicas:
-    the slowest rank's time divided by the iterations all ranks completed."""
+    """Seconds per ADMM iteration of a job of `world` independent replicas,
+    each running `steps` iterations of its own problem: the slowest rank's
+    time over `steps` (a replica's iteration does not get shorter because
+    other GPUs run theirs).  Returns (s/iter, slowest time, aggregate
+    iterations per second over all replicas = world * steps / slowest time)."""
     import torch
     import torch.distributed as dist
     t = float(t_local)
@@ -179,7 +182,7 @@ def job_seconds_per_iter(t_local, steps, world, device=None):
         tt = torch.tensor([t], dtype=torch.float64, device=device)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t = tt.item()
-    return t / (steps * world), t
+    return t / steps, t, world * steps / t
 
 
 # ---------------------------------------------------------------------------
@@ -283,84 +286,189 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# oracle sample (cpu_baseline and --impl reference)
+# oracle on the host cores (cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
+#
+# The FP64 oracle runs as it stands, one NumPy thread per worker process and
+# one worker per host core (a spawn pool: no fork after CUDA).  The work of one
+# ADMM-TV iteration at n^3 splits into independent units (kv planes of the 2D
+# stage, x-slabs of the z stage, x-slabs of the elementwise TV steps), so a
+# sample of units timed on all cores at once, scaled by the units one
+# iteration needs, is that iteration's time on those cores.
 
-def oracle_sample(n, nz, h, w, T, n_planes=1, n_slabs=4):
-    """Time the FP64 oracle on a sample of the workload and scale to s/iter.
-
-    One ADMM iteration of the oracle's Algorithm 2 LSP applies L-hat twice
-    (forward pass on u, line search on p) and L-hat^H once per CG step, 4 CG
-    steps.  Timed: the 2D stage forward and transpose on n_planes kv planes,
-    the z stage forward and transpose on n_slabs x-slabs; scaled by h / n_planes
-    and n / n_slabs.  TV/elementwise terms are not included."""
+def _oracle_geom(n):
     from oracle import lamino as olam
-    from oracle import usfft
     from paper_2511_01893_b300 import inputs
-    theta = inputs.angles(T)
-    g = olam.Geometry(n1=n, n0=nz, n2=n, h=h, w=w, theta=theta, phi=np.deg2rad(PHI_DEG))
-    rng = np.random.default_rng(0)
-    xi_x, xi_y, xi_z = olam.slice_frequencies(g)
-    t2f = t2a = 0.0
-    for k in range(n_planes):
-        kv = (h // 2 + 7 * k) % h
+    return olam.Geometry(n1=n, n0=n, n2=n, h=n, w=n, theta=inputs.angles(n), phi=np.deg2rad(PHI_DEG))
+
+
+def _oracle_worker_init():
+    import threadpoolctl
+    threadpoolctl.threadpool_limits(1)
+
+
+def _oracle_unit(kind, n, idx):
+    """One unit of an n^3 ADMM-TV iteration's oracle work, timed in a worker
+    process; returns (kind, seconds of the forward part, seconds of the
+    transpose / rest).  kind: "plane" (F_u2D of one kv plane and its
+    transpose), "slab" (F_u1D of one x-slab and its transpose), "tv" (the
+    elementwise steps of one outer iteration, 4 CG steps + RSP, on one
+    x-slab)."""
+    from oracle import lamino as olam
+    from oracle import tv as otv
+    from oracle import usfft
+    g = _oracle_geom(n)
+    rng = np.random.default_rng(1000 + idx)
+    if kind == "plane":
+        kv = (n // 2 + 7 * idx) % n
+        t, ku = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+        xi_x, xi_y, _ = olam.slice_frequency_points(g, t.ravel(), np.full(t.size, kv), ku.ravel())
+        xi_x, xi_y = xi_x.reshape(n, n), xi_y.reshape(n, n)
         plane = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
-        vals = rng.standard_normal((T, w)) + 1j * rng.standard_normal((T, w))
+        vals = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
         t0 = time.perf_counter()
-        usfft.usfft2d_type2(plane, xi_x[:, kv, :], xi_y[:, kv, :])
+        usfft.usfft2d_type2(plane, xi_x, xi_y)
         t1 = time.perf_counter()
-        usfft.usfft2d_type1(vals, xi_x[:, kv, :], xi_y[:, kv, :], n, n)
-        t2 = time.perf_counter()
-        t2f += t1 - t0
-        t2a += t2 - t1
-    slab = rng.standard_normal((n_slabs, nz, n))
+        usfft.usfft2d_type1(vals, xi_x, xi_y, n, n)
+        return kind, t1 - t0, time.perf_counter() - t1
+    if kind == "slab":
+        _, _, xi_z = olam.slice_frequencies(olam.Geometry(n1=1, n0=n, n2=1, h=n, w=1, theta=np.zeros(1),
+                                                          phi=g.phi))
+        slab = rng.standard_normal((1, n, n))
+        t0 = time.perf_counter()
+        u1 = usfft.usfft1d_type2(slab, xi_z, axis=1)
+        t1 = time.perf_counter()
+        usfft.usfft1d_type1(u1, xi_z, n, axis=1)
+        return kind, t1 - t0, time.perf_counter() - t1
+    # elementwise TV / CG / RSP steps of one outer iteration on one x-slab,
+    # the oracle's primitives in admm.lsp / admm.admm order
+    u = rng.standard_normal((1, n, n))
+    psi = rng.standard_normal((3, 1, n, n))
+    lam = rng.standard_normal((3, 1, n, n))
+    rho = 0.5
     t0 = time.perf_counter()
-    u1 = usfft.usfft1d_type2(slab, xi_z, axis=1)
-    t1 = time.perf_counter()
-    usfft.usfft1d_type1(u1, xi_z, nz, axis=1)
-    t2 = time.perf_counter()
-    fwd = t2f / n_planes * h + (t1 - t0) / n_slabs * n
-    adj = t2a / n_planes * h + (t2 - t1) / n_slabs * n
-    s_per_iter = N_INNER * (2 * fwd + adj)
-    sample = (f"FP64 oracle: F_u2D and its transpose on {n_planes} of {h} kv planes and F_u1D and its "
-              f"transpose on {n_slabs} of {n} x-slabs of the {n}^3 problem, scaled to one ADMM iteration "
-              f"(4 CG steps x (2 L-hat + 1 L-hat^H)); TV/elementwise work not included")
-    return s_per_iter, sample, (t2f + t2a + (t2 - t0))
+    gg = psi - lam / rho
+    p = Gp = None
+    for i in range(N_INNER):
+        G = rng.standard_normal(u.shape) - rho * otv.div(otv.grad(u) - gg)  # data term stands in for L^H r
+        p = -G if i == 0 else -G + (np.vdot(G, G).real / np.vdot(p, G - Gp).real) * p
+        gp = otv.grad(p)
+        gamma = -np.vdot(G, p).real / (1.0 + rho * np.vdot(gp, gp).real)
+        u = u + gamma * p
+        Gp = G
+    gu = otv.grad(u)
+    psi_new = otv.shrink_iso(gu + lam / rho, 1e-3 / rho)
+    lam = lam + rho * (gu - psi_new)
+    np.linalg.norm((gu - psi_new).ravel())
+    np.linalg.norm(otv.div(psi_new - psi).ravel())
+    otv.tv(u)
+    return kind, time.perf_counter() - t0, 0.0
 
 
-def cores_used():
-    try:
-        import threadpoolctl
-        info = threadpoolctl.threadpool_info()
-        nt = max([i.get("num_threads", 1) for i in info] or [1])
-    except Exception:
-        nt = 1
-    return {"threads": int(nt), "host_cores": os.cpu_count()}
+def oracle_pool(workers=None):
+    import multiprocessing as mp
+    w = workers or len(os.sched_getaffinity(0))
+    return mp.get_context("spawn").Pool(w, initializer=_oracle_worker_init), w
 
 
-# ---------------------------------------------------------------------------
-# reference arm
-# ---------------------------------------------------------------------------
+def oracle_iteration_sample(pool, workers, n):
+    """Time one sample of an n^3 ADMM-TV iteration's oracle work on `workers`
+    processes: `workers` kv planes, `workers` x-slabs of the z stage and
+    `workers` x-slabs of the elementwise steps, each wave run concurrently.
+    One iteration = 4 CG steps x (2 L-hat + 1 L-hat^H) over h planes and n
+    x-slabs, plus the elementwise steps over n x-slabs; the sample's per-unit
+    times scale to it (units / workers concurrent).  Returns (s/iter on these
+    cores, wall seconds the sample took, description)."""
+    t_start = time.perf_counter()
+    res = {}
+    for kind in ("plane", "slab", "tv"):
+        out = pool.starmap(_oracle_unit, [(kind, n, i) for i in range(workers)])
+        res[kind] = (float(np.mean([o[1] for o in out])), float(np.mean([o[2] for o in out])))
+    waves = n / workers
+    pf, pa = res["plane"]
+    sf, sa = res["slab"]
+    s_iter = N_INNER * waves * ((2 * pf + pa) + (2 * sf + sa)) + waves * res["tv"][0]
+    wall = time.perf_counter() - t_start
+    desc = (f"FP64 oracle as it stands on {workers} host cores (one process, one thread each): per sample "
+            f"{workers} kv planes (F_u2D + transpose), {workers} x-slabs (F_u1D + transpose) and {workers} "
+            f"x-slabs of the elementwise TV/CG/RSP steps of the {n}^3 workload, timed concurrently and "
+            f"scaled to one ADMM-TV iteration (4 CG steps x (2 L-hat + 1 L-hat^H) over {n} planes and "
+            f"{n} x-slabs + the elementwise steps over {n} x-slabs): {workers}/{n} of the work")
+    return s_iter, wall, desc
+
+
+def oracle_full_runs(pool, workers, n=None, s_iter=None):
+    """Oracle runs done in full (not sampled), on the same cores: the plain
+    workload (64^3, 64 angles, 8 x 4 ADMM-TV iterations, one process: its
+    steps are too small to split) and one L-hat + L-hat^H at 512^3 (planes
+    and x-slabs spread over the workers)."""
+    out = {}
+    t0 = time.perf_counter()
+    r = pool.apply_async(_oracle_plain_admm)
+    n = 512
+    planes = pool.starmap(_oracle_unit, [("plane", n, i) for i in range(n)])
+    slabs = pool.starmap(_oracle_unit, [("slab", n, i) for i in range(n)])
+    out["lhat_pair_512_s"] = time.perf_counter() - t0
+    out["lhat_pair_512_note"] = (f"one L-hat + L-hat^H at 512^3 (512 kv planes and 512 x-slabs over "
+                                 f"{workers} processes), wall time; run in full")
+    out["plain_admm_64_s"] = r.get()
+    out["plain_admm_64_note"] = "plain workload 64^3, 8 outer x 4 CG ADMM-TV, one process, run in full"
+    if n and s_iter:
+        # one iteration = 4 x (2 L-hat + 1 L-hat^H) + elementwise: a pair is
+        # at most a quarter of it
+        out[f"lhat_pair_{n}"] = (f"not run in full ({n}^3): the sampled units put one iteration at "
+                                 f"{s_iter:.0f} s on these cores (a pair is under a quarter of it)")
+    del planes, slabs
+    return out
+
+
+def _oracle_plain_admm():
+    _oracle_worker_init()
+    from oracle import admm as oadmm
+    from oracle import lamino as olam
+    from paper_2511_01893_b300 import inputs
+    n = 64
+    g = _oracle_geom(n)
+    u = inputs.ellipsoid_phantom(n, n, 12, seed=1234).numpy()
+    clean = olam.lam_forward(u, g)
+    d = clean + 0.01 * np.abs(clean.real).max() * inputs.noise((n, n, n), seed=99).numpy()
+    t0 = time.perf_counter()
+    oadmm.admm(d, g, ALPHA, RHO, 8, N_INNER, adapt_rho=True)
+    return time.perf_counter() - t0
+
 
 def run_reference(args):
+    """The oracle arm: each step is one sample of the workload's ADMM-TV
+    iteration on all host cores (oracle_iteration_sample), scaled to s/iter;
+    ms_per_step is the wall time a step (a sample) took.  After the timed
+    steps, the plain workload and a 512^3 L-hat + L-hat^H run in full."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     n = args.size
-    vals = []
-    for i in range(args.warmup + args.steps):
-        v, sample, _ = oracle_sample(n, n, n, n, n, n_planes=1, n_slabs=2)
-        if i >= args.warmup:
-            vals.append(v)
+    pool, workers = oracle_pool()
+    try:
+        vals, walls = [], []
+        for i in range(args.warmup + args.steps):
+            v, wall, desc = oracle_iteration_sample(pool, workers, n)
+            if i >= args.warmup:
+                vals.append(v)
+                walls.append(wall)
+        full = oracle_full_runs(pool, workers, n, statistics.median(vals))
+    finally:
+        pool.close()
+        pool.join()
     value = statistics.median(vals)
-    c = cores_used()
     line = {
         "impl": "reference", "metric": "ADMM-TV seconds per iteration", "value": value, "unit": "s/iter",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": value * 1e3,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(walls) * 1e3,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": workload_name(n), "precision": "FP64 CPU oracle"},
-        "cpu_baseline": {"value": value, "unit": "s/iter", "cores": c["threads"], "kind": "oracle",
-                         "sample": sample},
+        "step": f"one sample ({workers}/{n} of an iteration's work) per step; value = the sample scaled to s/iter",
+        "cpu_baseline": {"value": value, "unit": "s/iter", "cores": workers, "kind": "oracle", "sample": desc,
+                         "host_cores": os.cpu_count()},
+        "full_runs": full,
         "e2e": {"value": value, "unit": "s/iter", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -613,7 +721,7 @@ def run_ours(args):
         stream.synchronize()
     torch.cuda.synchronize()
     barrier()
-    s_per_iter, t_admm = job_seconds_per_iter(ev0.elapsed_time(ev1) / 1e3, args.steps, world, dev)
+    s_per_iter, t_admm, agg_iters = job_seconds_per_iter(ev0.elapsed_time(ev1) / 1e3, args.steps, world, dev)
     status = admm.status()
     sc = admm.scalars()
 
@@ -702,6 +810,8 @@ def run_ours(args):
                           "alu_tflops": alu_achieved / 1e12, "alu_frac": alu_achieved / fma,
                           "algorithmic_flops": op_flops},
         "plane_fft_comparator": comparator,
+        "aggregate": {"value": agg_iters, "unit": "iterations/s", "replicas": world,
+                      "note": "every replica's iterations over the slowest replica's time"},
         "gpu_launches": launches_per_step * args.steps,
         "admm": {"status": status, "objective": sc["objective"], "rho": sc["rho"], "iters_done": sc["iter"]},
     }
@@ -720,7 +830,7 @@ def run_ours(args):
         torch.cuda.empty_cache()
         t0 = time.perf_counter()
         u_host = glam.reconstruct(d_host.numpy(), theta, phi, n, nz, args.steps, ALPHA, RHO)
-        e2e_value, _ = job_seconds_per_iter(time.perf_counter() - t0, args.steps, world, dev)
+        e2e_value, _, _ = job_seconds_per_iter(time.perf_counter() - t0, args.steps, world, dev)
         line["e2e"] = {"value": e2e_value, "unit": "s/iter",
                        "h2d_bytes_per_step": int(d_host.numel() * 4 // args.steps),
                        "d2h_bytes_per_step": int(u_host.size * 4 // args.steps),
@@ -729,10 +839,14 @@ def run_ours(args):
 
     # ---- oracle on the host cores (rank 0, N = 1) ----------------------------
     if not args.no_cpu and rank == 0 and world == 1:
-        v, sample, spent = oracle_sample(n, nz, h, w, T)
-        c = cores_used()
-        line["cpu_baseline"] = {"value": v, "unit": "s/iter", "cores": c["threads"], "kind": "oracle",
-                                "sample": sample, "host_cores": c["host_cores"], "sample_seconds": spent}
+        pool, workers = oracle_pool()
+        try:
+            v, spent, sample = oracle_iteration_sample(pool, workers, n)
+        finally:
+            pool.close()
+            pool.join()
+        line["cpu_baseline"] = {"value": v, "unit": "s/iter", "cores": workers, "kind": "oracle",
+                                "sample": sample, "host_cores": os.cpu_count(), "sample_seconds": spent}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -84,8 +84,10 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *                      bitwise reproducible run to run; the fastest.
  *   LAM_SPREAD_ATOMIC  floating-point shared-memory atomic adds; rounding
  *                      depends on scheduling (not reproducible bit for bit).
- *   LAM_SPREAD_EXACT   exact 64-bit fixed-point atomic adds: every cell is the
- *                      correctly rounded sum of its products; reproducible.
+ *   LAM_SPREAD_EXACT   64-bit fixed-point atomic adds: every cell is the exact
+ *                      sum of its products rounded to one fixed grid (step
+ *                      ~ 2^-61 x a bound on the cell sums, an absolute error
+ *                      per product); reproducible.
  *   LAM_SPREAD_HALO    per-warp tiles extended by a halo: each slice point is
  *                      visited once (by the tile of its window origin); the
  *                      halos are summed in a second pass; reproducible.
@@ -101,14 +103,25 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *   per block of the z-stage kernels and of the plane row / column FFT
  *   kernels.  The columns, rows or lines per block are picked again to fit;
  *   256 lets two blocks share an SM.  Results do not depend on either.
+ * LAM_OPT_RESIDUAL (default 0) is how ADMM states initialised afterwards keep
+ *   the Algorithm 2 residual r = L_hat u - d_hat, a combination of:
+ *   LAM_RESID_REFRESH      evaluate r afresh (one extra L_hat with the fused
+ *                          subtraction) at the start of every LSP instead of
+ *                          carrying it across LSPs by linearity;
+ *   LAM_RESID_COMPENSATED  carry the updates r += gamma L_hat p in a
+ *                          compensated (hi + lo) pair (needs no extra memory:
+ *                          the state always holds the lo part).
+ *   Batched ADMM accepts LAM_RESID_COMPENSATED only.
  * Setting an option invalidates ADMM graphs captured with the plan. */
 enum {
     LAM_OPT_FAST_ADJOINT = 1,
     LAM_OPT_ADJOINT_SPREAD = 2,
     LAM_OPT_LSP_FORM = 3,
     LAM_OPT_Z_THREADS = 4,
-    LAM_OPT_PLANE_FFT_THREADS = 5
+    LAM_OPT_PLANE_FFT_THREADS = 5,
+    LAM_OPT_RESIDUAL = 6
 };
+enum { LAM_RESID_REFRESH = 1, LAM_RESID_COMPENSATED = 2 };
 enum { LAM_SPREAD_TILES = 0, LAM_SPREAD_ATOMIC = 1, LAM_SPREAD_EXACT = 2, LAM_SPREAD_HALO = 3 };
 lam_status lam_plan_set_option(lam_plan* plan, int option, int value);
 

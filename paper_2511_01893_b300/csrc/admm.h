@@ -81,8 +81,9 @@ template <typename T> struct Admm {
     cudaError_t lsp_G(const T* Gd, const T* du, const T* e, const T* lam, const T* p, const T* Gprev, T* G,
                       int first, const AdmmRed& r, cudaStream_t s) const;
     cudaError_t lsp_p(const T* G, T* p, const AdmmRed& r, cudaStream_t s) const;
-    cudaError_t lsp_update(T* du, T* u, const T* p, int first, int last, C<T>* res, const C<T>* Lp, long long nd,
-                           const AdmmRed& r, cudaStream_t s) const;
+    // rlo != nullptr: the residual is carried as res + rlo (compensated)
+    cudaError_t lsp_update(T* du, T* u, const T* p, int first, int last, C<T>* res, C<T>* rlo, const C<T>* Lp,
+                           long long nd, const AdmmRed& r, cudaStream_t s) const;
     cudaError_t rsp(const T* u, const T* du, T* e, T* lam, T* dpsi, const AdmmRed& r, double* hist, int hist_cap,
                     cudaStream_t s) const;
     cudaError_t neg_copy(const C<T>* src, C<T>* dst, long long n, cudaStream_t s) const;

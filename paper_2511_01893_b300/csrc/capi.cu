@@ -60,6 +60,7 @@ namespace {
 struct AdmmHost {
     int n_inner = 4;
     int form = 2;  // LSP form: 2 (Algorithm 2, default) or 1 (Algorithm 1)
+    int resid = 0;  // residual handling (LAM_OPT_RESIDUAL bits)
     void* ws = nullptr;
     cudaGraphExec_t graph = nullptr;
     size_t graph_kernels = 0;  // kernel nodes in the captured outer iteration
@@ -102,6 +103,7 @@ struct lam_plan {
     int pstride;
     int spread = kSpreadTiles;
     int lsp_form = 2;  // LSP form new ADMM states take (LAM_OPT_LSP_FORM)
+    int resid = 0;     // residual handling new ADMM states take (LAM_OPT_RESIDUAL)
     // workspace layout
     size_t ws_u1, ws_planes, ws_halo, ws_tmp, ws_red, ws_bytes;
     mutable std::mutex mu;
@@ -509,7 +511,7 @@ template <typename T> lam_status fft2d(const lam_plan* p, const C<T>* in, C<T>* 
 // ---- ADMM state layout -------------------------------------------------------
 
 struct StateLayout {
-    size_t sc, hist, partials, counter, u, du, Gd, G0, G1, p, e, lam, dpsi, dhat, r, Lp, total;
+    size_t sc, hist, partials, counter, u, du, Gd, G0, G1, p, e, lam, dpsi, dhat, r, Lp, rlo, total;
 };
 
 StateLayout layout(const lam_plan* p) {
@@ -538,6 +540,7 @@ StateLayout layout(const lam_plan* p) {
     L.dhat = take(db);
     L.r = take(db);
     L.Lp = take(db);
+    L.rlo = take(db);  // low part of the compensated residual (LAM_RESID_COMPENSATED)
     L.total = o;
     return L;
 }
@@ -555,7 +558,7 @@ __global__ void k_init_scalars(double* sc, double rho, double alpha, double invh
 
 template <typename T> struct StatePtrs {
     T *u, *du, *Gd, *G0, *G1, *p, *e, *lam, *dpsi;
-    C<T>*dhat, *r, *Lp;
+    C<T>*dhat, *r, *Lp, *rlo;
     AdmmRed red;
     double* hist;
 };
@@ -576,6 +579,7 @@ template <typename T> StatePtrs<T> ptrs(const lam_plan* p, void* state) {
     s.dhat = (C<T>*)(b + L.dhat);
     s.r = (C<T>*)(b + L.r);
     s.Lp = (C<T>*)(b + L.Lp);
+    s.rlo = (C<T>*)(b + L.rlo);
     s.red.sc = (double*)(b + L.sc);
     s.red.partials = (double*)(b + L.partials);
     s.red.counter = (unsigned int*)(b + L.counter);
@@ -605,6 +609,7 @@ lam_status admm_init_t(const lam_plan* p, void* state, const void* d, double alp
     CK(cudaMemsetAsync(S.p, 0, vb, s));
     CK(cudaMemsetAsync(S.e, 0, 3 * vb, s));
     CK(cudaMemsetAsync(S.lam, 0, 3 * vb, s));
+    CK(cudaMemsetAsync(S.rlo, 0, (size_t)p->ndata() * p->celem(), s));
     (void)L;
     // Algorithm 2 works on d_hat = F_2D d with the Parseval weight 1/(hw);
     // Algorithm 1 keeps d in the data space (the slot holds d) with weight 1
@@ -624,7 +629,7 @@ lam_status admm_init_t(const lam_plan* p, void* state, const void* d, double alp
 }
 
 template <typename T>
-lam_status admm_step_t(const lam_plan* p, void* state, void* ws, int n_inner, int form, cudaStream_t s) {
+lam_status admm_step_t(const lam_plan* p, void* state, void* ws, int n_inner, int form, int resid, cudaStream_t s) {
     StatePtrs<T> S = ptrs<T>(p, state);
     const Admm<T> ops = admm_ops<T>(p);
     const long long nd = p->ndata();
@@ -651,6 +656,15 @@ lam_status admm_step_t(const lam_plan* p, void* state, void* ws, int n_inner, in
             if ((st = fft2d<T>(p, S.r, tmp, -1, sc, s))) return st;
             if ((st = adj_hat<T>(p, tmp, S.Gd, ws, s))) return st;
         } else {
+            // residual refresh: r = L_hat u - d_hat evaluated afresh (the
+            // subtraction fused into the gather) at the start of each LSP, so
+            // the rounding of the carried updates r += gamma L_hat p does not
+            // accumulate from one LSP to the next
+            if (i == 0 && (resid & LAM_RESID_REFRESH)) {
+                if ((st = fwd_hat<T>(p, S.u, S.r, S.dhat, ws, s))) return st;
+                if (resid & LAM_RESID_COMPENSATED)
+                    CK(cudaMemsetAsync(S.rlo, 0, (size_t)nd * sizeof(C<T>), s));
+            }
             // adjoint pass: G = Re L_hat^H r / (hw) - rho div(grad u - g)
             if ((st = adj_hat<T>(p, S.r, S.Gd, ws, s))) return st;
         }
@@ -660,7 +674,8 @@ lam_status admm_step_t(const lam_plan* p, void* state, void* ws, int n_inner, in
         if ((st = fwd_hat<T>(p, S.p, S.Lp, nullptr, ws, s))) return st;
         if (form == 1 && (st = fft2d<T>(p, S.Lp, S.Lp, +1, sc, s))) return st;
         // exact line search, increment and residual update (u += du on the last step)
-        CK(ops.lsp_update(S.du, S.u, S.p, i == 0, i == n_inner - 1, S.r, S.Lp, nd, S.red, s));
+        CK(ops.lsp_update(S.du, S.u, S.p, i == 0, i == n_inner - 1, S.r,
+                          form == 2 && (resid & LAM_RESID_COMPENSATED) ? S.rlo : nullptr, S.Lp, nd, S.red, s));
     }
     CK(ops.rsp(S.u, S.du, S.e, S.lam, S.dpsi, S.red, S.hist, kHistCap, s));
     return LAM_OK;
@@ -797,7 +812,8 @@ lam_status batch_adj_hat(const lam_batch* b, const void* const* in, void* const*
 // one ADMM outer iteration of every problem: the operators run batched, the
 // elementwise steps per problem (Section 2: LSP in the Algorithm 2 form, RSP,
 // multiplier and penalty updates), in the order admm_step uses
-template <typename T> lam_status batch_admm_step(const lam_batch* b, void* const* states, int n_inner, cudaStream_t s) {
+template <typename T>
+lam_status batch_admm_step(const lam_batch* b, void* const* states, const int* resid, int n_inner, cudaStream_t s) {
     std::vector<StatePtrs<T>> S;
     std::vector<Admm<T>> ops;
     for (int i = 0; i < b->count; ++i) {
@@ -822,7 +838,8 @@ template <typename T> lam_status batch_admm_step(const lam_batch* b, void* const
         }
         if (lam_status st = batch_fwd_hat<T>(b, in, out, s)) return st;
         for (int i = 0; i < b->count; ++i)
-            CK(ops[i].lsp_update(S[i].du, S[i].u, S[i].p, k == 0, k == n_inner - 1, S[i].r, S[i].Lp,
+            CK(ops[i].lsp_update(S[i].du, S[i].u, S[i].p, k == 0, k == n_inner - 1, S[i].r,
+                                 (resid[i] & LAM_RESID_COMPENSATED) ? S[i].rlo : nullptr, S[i].Lp,
                                  b->plans[i]->ndata(), S[i].red, s));
     }
     for (int i = 0; i < b->count; ++i)
@@ -870,6 +887,23 @@ lam_status static_planes(int dev, void** out) {
     return LAM_OK;
 }
 
+// an array argument must be device (or managed) memory of the plan's device:
+// a pointer into another GPU's memory or into pageable host memory would
+// otherwise reach the kernels
+lam_status check_device_ptr(const void* ptr, int dev, const char* name) {
+    if (!ptr) return LAM_OK;
+    cudaPointerAttributes at;
+    const cudaError_t e = cudaPointerGetAttributes(&at, ptr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // the failed query leaves a (non-sticky) error behind: clear it
+        return fail(LAM_EINVAL, "%s: not a CUDA pointer (%s)", name, cudaGetErrorString(e));
+    }
+    if (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)
+        return fail(LAM_EINVAL, "%s: not device memory", name);
+    if (at.device != dev) return fail(LAM_EINVAL, "%s lives on device %d, the plan on device %d", name, at.device, dev);
+    return LAM_OK;
+}
+
 template <typename T> lam_status u2d_fwd_static_t(const lam_plan* p, const void* u1, void* out, const void* sub,
                                                   cudaStream_t s) {
     const size_t plane = (size_t)p->M1 * p->M2 * sizeof(C<T>);
@@ -879,6 +913,9 @@ template <typename T> lam_status u2d_fwd_static_t(const lam_plan* p, const void*
     int dev = -1;
     CK(cudaGetDevice(&dev));
     if (dev != p->device) return fail(LAM_EINVAL, "current device %d is not the plan's device %d", dev, p->device);
+    if (lam_status st = check_device_ptr(u1, dev, "u1")) return st;
+    if (lam_status st = check_device_ptr(out, dev, "d_hat")) return st;
+    if (lam_status st = check_device_ptr(sub, dev, "sub")) return st;
     void* scratch = nullptr;
     if (lam_status st = static_planes(dev, &scratch)) return st;
     C<T>* P = (C<T>*)scratch;
@@ -1039,6 +1076,11 @@ lam_status lam_plan_set_option(lam_plan* p, int option, int value) {
             if (value != 1 && value != 2) return fail(LAM_EINVAL, "LSP form %d: 1 or 2", value);
             p->lsp_form = value;
             return LAM_OK;
+        case LAM_OPT_RESIDUAL:
+            if (value & ~(LAM_RESID_REFRESH | LAM_RESID_COMPENSATED))
+                return fail(LAM_EINVAL, "residual mode %d: a combination of LAM_RESID_REFRESH and LAM_RESID_COMPENSATED", value);
+            p->resid = value;
+            return LAM_OK;
         case LAM_OPT_Z_THREADS:
         case LAM_OPT_PLANE_FFT_THREADS: {
             if (value != 256 && value != 512) return fail(LAM_EINVAL, "threads per block %d: 256 or 512", value);
@@ -1192,6 +1234,7 @@ lam_status admm_init(const lam_plan* p, void* state, const void* d, double alpha
         h.n_inner = n_inner;
         h.ws = ws;
         h.form = p->lsp_form;
+        h.resid = p->resid;
     }
     return DISPATCH(p, admm_init_t<float>(p, state, d, alpha, rho, adapt_rho, p->lsp_form, s),
                     admm_init_t<double>(p, state, d, alpha, rho, adapt_rho, p->lsp_form, s));
@@ -1211,8 +1254,8 @@ lam_status admm_step(const lam_plan* p, void* state, void* ws, void* stream) {
     AdmmHost* h;
     if (lam_status st = lookup(p, state, &h)) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    return DISPATCH(p, admm_step_t<float>(p, state, ws, h->n_inner, h->form, s),
-                    admm_step_t<double>(p, state, ws, h->n_inner, h->form, s));
+    return DISPATCH(p, admm_step_t<float>(p, state, ws, h->n_inner, h->form, h->resid, s),
+                    admm_step_t<double>(p, state, ws, h->n_inner, h->form, h->resid, s));
 }
 
 lam_status admm_run(const lam_plan* p, void* state, void* ws, int iters, int use_graph, void* stream) {
@@ -1619,6 +1662,7 @@ lam_status admm_run_batched(lam_batch* b, void* const* states, int iters, int us
     if (!states) return fail(LAM_EINVAL, "states is NULL");
     if (iters < 0) return fail(LAM_EINVAL, "iters = %d", iters);
     int n_inner = -1;
+    int resid[kMaxBatch] = {};
     for (int i = 0; i < b->count; ++i) {
         if (!states[i]) return fail(LAM_EINVAL, "state %d is NULL", i);
         AdmmHost* h;
@@ -1626,12 +1670,15 @@ lam_status admm_run_batched(lam_batch* b, void* const* states, int iters, int us
         if (n_inner >= 0 && h->n_inner != n_inner)
             return fail(LAM_EINVAL, "state %d: every state of a batch needs the same number of CG steps", i);
         if (h->form != 2) return fail(LAM_EUNSUPPORTED, "state %d: batched ADMM runs the Algorithm 2 form", i);
+        if (h->resid & LAM_RESID_REFRESH)
+            return fail(LAM_EUNSUPPORTED, "state %d: batched ADMM carries the residual (no per-LSP refresh)", i);
+        resid[i] = h->resid;
         n_inner = h->n_inner;
     }
     cudaStream_t s = (cudaStream_t)stream;
     auto step = [&]() -> lam_status {
-        return b->prec == LAM_F32 ? batch_admm_step<float>(b, states, n_inner, s)
-                                  : batch_admm_step<double>(b, states, n_inner, s);
+        return b->prec == LAM_F32 ? batch_admm_step<float>(b, states, resid, n_inner, s)
+                                  : batch_admm_step<double>(b, states, resid, n_inner, s);
     };
     if (!use_graph) {
         for (int k = 0; k < iters; ++k)

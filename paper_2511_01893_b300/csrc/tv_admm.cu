@@ -406,6 +406,58 @@ __global__ void __launch_bounds__(256) k_axpy_r(C<T>* __restrict__ rr, const C<T
     reduce_store<1>(acc, r.partials, r.counter, r.sc, SC_R2);
 }
 
+// a + b as hi + lo exactly (Knuth's two-sum; no contraction, no reassociation)
+template <typename T> __device__ __forceinline__ T add_exact(T a, T b, T& err);
+template <> __device__ __forceinline__ float add_exact<float>(float a, float b, float& err) {
+    const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return s;
+}
+template <> __device__ __forceinline__ double add_exact<double>(double a, double b, double& err) {
+    const double s = __dadd_rn(a, b), bb = __dsub_rn(s, a);
+    err = __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb));
+    return s;
+}
+template <typename T> __device__ __forceinline__ T mul_rn(T a, T b);
+template <> __device__ __forceinline__ float mul_rn<float>(float a, float b) { return __fmul_rn(a, b); }
+template <> __device__ __forceinline__ double mul_rn<double>(double a, double b) { return __dmul_rn(a, b); }
+
+// one component of the compensated update (hi, lo) += g b: the product's
+// rounding error (an FMA gives it exactly) and the sum's two-sum error go to
+// lo, which is then folded back (fast two-sum), so hi is the nearest value to
+// hi + lo and the pair carries the residual to about twice the working precision
+template <typename T> __device__ __forceinline__ void comp_axpy(T& hi, T& lo, T g, T b) {
+    const T y = mul_rn(g, b);
+    const T ey = fma(g, b, -y);
+    T es;
+    const T s = add_exact(hi, y, es);
+    const T l = lo + (ey + es);
+    hi = s + l;
+    lo = l - (hi - s);
+}
+
+// (r, rlo) += gamma Lp with the residual carried as r + rlo; ||r + rlo||^2 into sc[SC_R2]
+template <typename T>
+__global__ void __launch_bounds__(256) k_axpy_r_comp(C<T>* __restrict__ rr, C<T>* __restrict__ rlo,
+                                                     const C<T>* __restrict__ Lp, long long n, AdmmRed r) {
+    const T g = (T)r.sc[SC_GAMMA];
+    double acc[1] = {0};
+    T loc = 0;
+    int cnt = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        C<T> a = rr[i], l = rlo[i];
+        const C<T> b = Lp[i];
+        comp_axpy(a.x, l.x, g, b.x);
+        comp_axpy(a.y, l.y, g, b.y);
+        rr[i] = a;
+        rlo[i] = l;
+        loc += a.x * a.x + a.y * a.y;
+        if (++cnt == 8) { acc[0] += (double)loc; loc = 0; cnt = 0; }
+    }
+    acc[0] += (double)loc;
+    reduce_store<1>(acc, r.partials, r.counter, r.sc, SC_R2);
+}
+
 // ---------------------------------------------------------------------------
 // RSP, multiplier, residuals
 // ---------------------------------------------------------------------------
@@ -602,12 +654,13 @@ cudaError_t Admm<T>::lsp_p(const T* G, T* p, const AdmmRed& r, cudaStream_t s) c
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t Admm<T>::lsp_update(T* du, T* u, const T* p, int first, int last, C<T>* res, const C<T>* Lp, long long nd,
-                                const AdmmRed& r, cudaStream_t s) const {
+cudaError_t Admm<T>::lsp_update(T* du, T* u, const T* p, int first, int last, C<T>* res, C<T>* rlo, const C<T>* Lp,
+                                long long nd, const AdmmRed& r, cudaStream_t s) const {
     k_cnorm2<T><<<egrid(nd), 256, 0, s>>>(Lp, nd, r, SC_LP2);
     k_gamma<<<1, 32, 0, s>>>(r.sc);
     k_axpy_u<T><<<egrid(v.N), 256, 0, s>>>(du, u, p, first, last, r.sc, v);
-    k_axpy_r<T><<<egrid(nd), 256, 0, s>>>(res, Lp, nd, r);
+    if (rlo) k_axpy_r_comp<T><<<egrid(nd), 256, 0, s>>>(res, rlo, Lp, nd, r);
+    else k_axpy_r<T><<<egrid(nd), 256, 0, s>>>(res, Lp, nd, r);
     return cudaGetLastError();
 }
 template <typename T>

@@ -558,9 +558,12 @@ template <typename T, int ACC> struct AtomAcc {  // ACC 0: plain FP32 / FP64 ato
 
 // Exact fixed-point cells: each product is scaled by a power of two (chosen
 // from a bound on every cell's magnitude, so no cell can overflow) and rounded
-// to a 64-bit integer; integer adds are exact and associative, so a cell ends
-// as the correctly rounded sum of its FP32 products, bitwise independent of the
-// order the lanes and warps add in.
+// to a 64-bit integer, i.e. to a fixed grid of step ~ bound_count * maxabs *
+// 2^-61.  Integer adds are exact and associative, so a cell is the exact sum
+// of its rounded products, bitwise independent of the order the lanes and
+// warps add in.  The per-product error is bounded in absolute terms (half a
+// grid step), not relative to the cell: cells far smaller than maxabs lose
+// relative precision, and in FP64 the grid step can exceed FP64 rounding.
 template <typename T> struct AtomAcc<T, 3> {
     unsigned long long* base;
     int ncell;

@@ -142,7 +142,12 @@ class Plan:
         fixed-point atomic adds); fast_adjoint=True is "atomic"."""
         if not torch.cuda.is_available():
             raise LaminoError("no CUDA device: the laminography operators run only on the GPU")
-        self.device = torch.device("cuda" if device is None else device)
+        # the plan's device with its index resolved (a bare "cuda" means the
+        # current device), so that arguments can be checked against it exactly
+        dev = torch.device("cuda" if device is None else device)
+        if dev.type != "cuda":
+            raise LaminoError(f"a plan lives on a CUDA device, not {dev}")
+        self.device = torch.device("cuda", torch.cuda.current_device() if dev.index is None else dev.index)
         theta = np.ascontiguousarray(np.asarray(theta, dtype=np.float64))
         self.n, self.nz, self.h, self.w, self.T = int(n), int(nz), int(h), int(w), len(theta)
         self.theta, self.phi, self.m = theta, float(phi), int(m)
@@ -290,8 +295,7 @@ class Plan:
                              (sub, self.cdtype, self.data_shape)):
             if t is None:
                 continue
-            dev_ok = t.device.type == self.device.type and self.device.index in (None, t.device.index)
-            if t.dtype != dt or not dev_ok or not t.is_contiguous() or tuple(t.shape) != shape:
+            if t.dtype != dt or t.device != self.device or not t.is_contiguous() or tuple(t.shape) != shape:
                 raise LaminoError(f"expected a contiguous {dt} tensor of shape {shape} on {self.device}")
         _check(lib().lamx_u2d_fwd_static(self._h, _ptr(u1), _ptr(out), _ptr(sub), _stream()),
                "lamx_u2d_fwd_static")
@@ -412,10 +416,18 @@ class Admm:
         if self._ready is not None:
             torch.cuda.current_stream(self.plan.device).wait_event(self._ready)
 
-    def init(self, d, alpha, rho, n_inner=4, adapt_rho=True, form=2):
-        """form: the LSP form, 2 (Algorithm 2, default) or 1 (Algorithm 1)."""
+    RESID = {"carry": 0, "refresh": 1, "compensated": 2, "refresh+compensated": 3}
+
+    def init(self, d, alpha, rho, n_inner=4, adapt_rho=True, form=2, resid="carry"):
+        """form: the LSP form, 2 (Algorithm 2, default) or 1 (Algorithm 1).
+        resid: how the Algorithm 2 residual is kept (LAM_OPT_RESIDUAL): "carry"
+        (by linearity across LSPs), "refresh" (evaluated afresh at each LSP
+        start), "compensated" (carried as a hi + lo pair) or both."""
         d = self.plan._inp(d, self.plan.cdtype, self.plan.data_shape)
+        if resid not in self.RESID:
+            raise LaminoError(f"resid must be one of {sorted(self.RESID)}")
         _check(lib().lam_plan_set_option(self.plan._h, 3, int(form)), "lam_plan_set_option")
+        _check(lib().lam_plan_set_option(self.plan._h, 6, self.RESID[resid]), "lam_plan_set_option")
         _check(lib().admm_init(self.plan._h, _ptr(self.state), _ptr(d), float(alpha), float(rho), int(n_inner),
                                int(bool(adapt_rho)), _ptr(self.plan.ws), _stream()), "admm_init")
         self.iters = 0

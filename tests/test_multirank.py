@@ -1,6 +1,8 @@
 """The bench's N > 1 path runs independent replicas and reduces only the clock:
-the whole-job value is the slowest rank's time over the iterations all ranks
-completed.  Checked with two gloo ranks on the CPU."""
+the job's seconds per iteration are the slowest rank's time over the
+iterations one replica ran (not divided by the number of replicas), and the
+aggregate throughput counts every replica's iterations.  Checked with two
+gloo ranks on the CPU."""
 import os
 import socket
 
@@ -22,8 +24,7 @@ def _rank(rank, world, port, out):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     t_local = [3.0, 5.0][rank]
-    value, t_max = bench.job_seconds_per_iter(t_local, steps=4, world=world)
-    out[rank] = (value, t_max)
+    out[rank] = bench.job_seconds_per_iter(t_local, steps=4, world=world)
     dist.destroy_process_group()
 
 
@@ -32,11 +33,11 @@ def test_replica_timing_takes_slowest_rank():
     out = mp.Manager().dict()
     mp.spawn(_rank, args=(world, port, out), nprocs=world, join=True)
     for rank in range(world):
-        value, t_max = out[rank]
+        value, t_max, agg = out[rank]
         assert t_max == pytest.approx(5.0)
-        assert value == pytest.approx(5.0 / (4 * 2))
+        assert value == pytest.approx(5.0 / 4)
+        assert agg == pytest.approx(2 * 4 / 5.0)
 
 
 def test_single_rank_needs_no_process_group():
-    value, t = bench.job_seconds_per_iter(2.0, steps=4, world=1)
-    assert (value, t) == (0.5, 2.0)
+    assert bench.job_seconds_per_iter(2.0, steps=4, world=1) == (0.5, 2.0, 2.0)
