@@ -59,7 +59,8 @@ typedef enum {
     LAM_ECUDA = -3,        /* a CUDA call or kernel launch failed */
     LAM_ETIMEOUT = -4,     /* reserved: a bounded device wait gave up */
     LAM_ENAN = -5,         /* non-finite value in an ADMM reduction */
-    LAM_EUNSUPPORTED = -6  /* size or option outside what the kernels support */
+    LAM_EUNSUPPORTED = -6, /* size or option outside what the kernels support */
+    LAM_EBOUNDS = -7       /* an index check of a LAM_BOUNDS_CHECK build failed */
 } lam_status;
 
 typedef enum { LAM_F32 = 0, LAM_F64 = 1 } lam_prec;
@@ -112,6 +113,14 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *                          compensated (hi + lo) pair (needs no extra memory:
  *                          the state always holds the lo part).
  *   Batched ADMM accepts LAM_RESID_COMPENSATED only.
+ * LAM_OPT_EXACT_CENTRE_JOBS (value >= 0) is the number of plane jobs nearest
+ *   the centre plane kv = h/2 (the paired adjoint treats planes kv and h - kv
+ *   as one job, centre first) whose tile spread (LAM_SPREAD_TILES) accumulates
+ *   in exact fixed point (as LAM_SPREAD_EXACT) instead of FP32.  Near the
+ *   centre every slice line passes close to the origin, so the cells there sum
+ *   thousands of nearly equal products, which FP32 running sums round
+ *   systematically; these few jobs carry most of the energy of L^H applied to
+ *   smooth data.  0 = none.
  * Setting an option invalidates ADMM graphs captured with the plan. */
 enum {
     LAM_OPT_FAST_ADJOINT = 1,
@@ -119,7 +128,8 @@ enum {
     LAM_OPT_LSP_FORM = 3,
     LAM_OPT_Z_THREADS = 4,
     LAM_OPT_PLANE_FFT_THREADS = 5,
-    LAM_OPT_RESIDUAL = 6
+    LAM_OPT_RESIDUAL = 6,
+    LAM_OPT_EXACT_CENTRE_JOBS = 7
 };
 enum { LAM_RESID_REFRESH = 1, LAM_RESID_COMPENSATED = 2 };
 enum { LAM_SPREAD_TILES = 0, LAM_SPREAD_ATOMIC = 1, LAM_SPREAD_EXACT = 2, LAM_SPREAD_HALO = 3 };
@@ -136,6 +146,19 @@ lam_status lam_plan_set_option(lam_plan* plan, int option, int value);
  * the plan are invalidated.  Batches read the shapes at lam_batch_create. */
 lam_status lam_plan_autotune(lam_plan* plan, void* u, void* d_hat, void* ws, int reps, double* seconds,
                              void* stream);
+
+/* Index checks.  A library built with LAM_BOUNDS_CHECK defined checks the
+ * table- and geometry-derived indices of the z-stage transpose (each cell's
+ * kv range against its weight row), the 2D gather (the tap window against the
+ * staged tile, the output index) and the 2D spread (the input index) before
+ * each access.  An index out of range skips that access and records the
+ * first failing site in the plan's device error word: nothing traps and
+ * nothing is accessed out of range.  Other builds compile the checks away.
+ * lam_plan_status reads the word (synchronises `stream`): LAM_OK, or
+ * LAM_EBOUNDS with the site named in lam_last_error(); it clears the word.
+ * lam_bounds_checked() is 1 in a LAM_BOUNDS_CHECK build, 0 otherwise. */
+lam_status lam_plan_status(const lam_plan* plan, void* stream);
+int lam_bounds_checked(void);
 
 /* Bytes of device scratch the operator calls need (ws argument).  The
  * workspace holds the z-transformed volume u1[h][n][n] (complex) and a batch

@@ -94,6 +94,21 @@ lam_status lamx_fma_peak(void* sink, int sink_floats, double* flops_per_s, void*
  * iteration); 0 before the first graph run. */
 lam_status lamx_admm_graph_kernels(const lam_plan* plan, void* state, size_t* count);
 
+/* Byte offsets of the pieces of an ADMM state buffer of this plan, in this
+ * order (up to `count` of them): FP64 scalars, history, reduction partials,
+ * reduction counter, u, du, G_lsp (L_hat^H r), G, G_prev, p, e = grad u - psi
+ * [3], lambda [3], dpsi [3], d_hat, r, L_hat p, r_lo, total bytes.  Volumes are
+ * real [n][nz][n] of the plan's precision, data arrays complex [T][h][w].
+ * For tools that inspect, convert or checkpoint a state; host only. */
+lam_status lamx_admm_layout(const lam_plan* plan, size_t* out, int count);
+
+/* Self-test of the index checks (LAM_BOUNDS_CHECK builds; LAM_EUNSUPPORTED
+ * otherwise): one checked device write of 1 into element `index` of the
+ * plan's 64-int self-test scratch.  An index outside [0, 64) is caught by the
+ * check itself (never written), and lam_plan_status then reports LAM_EBOUNDS
+ * at the self-test site.  Asynchronous on `stream`. */
+lam_status lamx_bounds_selftest(const lam_plan* plan, int index, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

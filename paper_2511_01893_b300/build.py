@@ -1,6 +1,6 @@
 """Build liblamino.so (the CUDA path) in-tree for sm_103a.
 
-    python -m paper_2511_01893_b300.build [--verbose]
+    python -m paper_2511_01893_b300.build [--verbose] [--checked]
 
 Compiles every ``csrc/*.cu`` with nvcc for ``arch=compute_103a,code=sm_103a``
 and links them into ``paper_2511_01893_b300/liblamino.so``.  Objects go to
@@ -17,6 +17,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "liblamino.so")
+# the same sources with LAM_BOUNDS_CHECK defined: index checks that record a
+# failing site in the plan's error word instead of accessing out of range
+LIB_CHECKED = os.path.join(HERE, "liblamino_checked.so")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
@@ -28,16 +31,23 @@ def _deps_mtime(src: str) -> float:
     return max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in headers])
 
 
-def build(verbose: bool = False, extra_flags=()) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
+    """Build liblamino.so, or with checked=True liblamino_checked.so (the
+    LAM_BOUNDS_CHECK variant, objects under _build/checked)."""
+    bdir = os.path.join(BUILD, "checked") if checked else BUILD
+    lib = LIB_CHECKED if checked else LIB
+    if checked:
+        extra_flags = ("-DLAM_BOUNDS_CHECK", *extra_flags)
+    os.makedirs(bdir, exist_ok=True)
     objs, jobs = [], []
     for f in sorted(os.listdir(CSRC)):
         if not f.endswith(".cu"):
             continue
         src = os.path.join(CSRC, f)
-        obj = os.path.join(BUILD, f[:-3] + ".o")
+        obj = os.path.join(bdir, f[:-3] + ".o")
         objs.append(obj)
-        if os.path.exists(obj) and os.path.getmtime(obj) >= _deps_mtime(src) and not extra_flags:
+        if os.path.exists(obj) and os.path.getmtime(obj) >= _deps_mtime(src) and list(extra_flags) in (
+                [], ["-DLAM_BOUNDS_CHECK"]):
             continue
         jobs.append([NVCC, *FLAGS, *extra_flags, "-c", src, "-o", obj])
     # the translation units compile independently: run them side by side
@@ -57,15 +67,15 @@ def build(verbose: bool = False, extra_flags=()) -> str:
             failed = subprocess.CalledProcessError(p.returncode, cmd)
     if failed is not None:
         raise failed
-    if (not os.path.exists(LIB) or any(os.path.getmtime(o) > os.path.getmtime(LIB) for o in objs)
-            or extra_flags):
-        cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", LIB, *objs, "-lcudart"]
+    if (not os.path.exists(lib) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs)
+            or jobs):
+        cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", lib, *objs, "-lcudart"]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
     extra = ["-Xptxas", "-v"] if "--ptxas" in sys.argv else []
-    print(build(verbose="--verbose" in sys.argv, extra_flags=extra))
+    print(build(verbose="--verbose" in sys.argv, extra_flags=extra, checked="--checked" in sys.argv))

@@ -95,6 +95,7 @@ struct lam_plan {
     std::vector<int2> jobs_pair_h;  // host copy of jobs_pair
     int2* jobs_all;
     int* skip;  // [h] 1 for the mirror plane of a paired job
+    int* err;   // error word of the index checks, then kSelftestCells ints of self-test scratch
     int njobs_pair;
     // launch shapes
     int TYf, TYa, RB, CB, TS, TG, nimg, nbatch;
@@ -102,6 +103,7 @@ struct lam_plan {
     double rmax;
     int pstride;
     int spread = kSpreadTiles;
+    int nacc = 0;  // leading plane jobs the tile spread accumulates exactly (LAM_OPT_EXACT_CENTRE_JOBS)
     int lsp_form = 2;  // LSP form new ADMM states take (LAM_OPT_LSP_FORM)
     int resid = 0;     // residual handling new ADMM states take (LAM_OPT_RESIDUAL)
     // workspace layout
@@ -270,6 +272,8 @@ template <typename T> lam_status build_tables(lam_plan* p, const double* theta) 
         if (st) return st;
         p->skip = (int*)upload(p, skip, &st);
         if (st) return st;
+        p->err = (int*)upload(p, std::vector<int>(1 + kSelftestCells, 0), &st);
+        if (st) return st;
         // the paired transpose's kv range per cell: the non-skipped kv of
         // [lo, hi) when they are contiguous (skipped planes carry zeros), else
         // the whole range
@@ -390,6 +394,7 @@ template <typename T> Usfft1dArgs<T> args1d(const lam_plan* p, int TY, bool pair
     a.tw = (const C<T>*)p->tw;
     a.twstride = p->Nmax / p->M0;
     a.skip = paired ? p->skip : nullptr;
+    a.err = p->err;
     return a;
 }
 
@@ -424,6 +429,8 @@ template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p, bool paired) {
     a.jobs = paired ? p->jobs_pair : p->jobs_all;
     a.maxabs = nullptr;
     a.halo = nullptr;
+    a.err = p->err;
+    a.nacc = paired ? p->nacc : 0;
     // points whose 2m x 2m window covers one cell: at most (2m / spacing + 2)^2 per
     // line neighbourhood, over all T lines and all periodic images; doubled for safety
     {
@@ -478,7 +485,8 @@ template <typename T> lam_status prep_scatter(const lam_plan* p, const C<T>* in,
                                               Usfft2dArgs<T>& a) {
     // the exact spread runs when chosen, and for the tile spread's small-plane
     // fallback (tiles narrower than 32)
-    const bool exact = p->spread == kSpreadExact || ((p->spread == kSpreadTiles || p->spread == kSpreadHalo) && p->TS != 32);
+    const bool exact = p->spread == kSpreadExact || ((p->spread == kSpreadTiles || p->spread == kSpreadHalo) && p->TS != 32) ||
+                       (p->spread == kSpreadTiles && a.nacc > 0);
     if (!exact) return LAM_OK;
     T* mx = (T*)((char*)ws + p->ws_red + align256(SC_COUNT * sizeof(double)) +
                  align256((size_t)kRedBlocks * 4 * sizeof(double)) + 256);
@@ -1076,6 +1084,19 @@ lam_status lam_plan_set_option(lam_plan* p, int option, int value) {
             if (value != 1 && value != 2) return fail(LAM_EINVAL, "LSP form %d: 1 or 2", value);
             p->lsp_form = value;
             return LAM_OK;
+        case LAM_OPT_EXACT_CENTRE_JOBS:
+            if (value < 0) return fail(LAM_EINVAL, "exact centre jobs %d < 0", value);
+            p->nacc = value;
+            {
+                // captured ADMM graphs hold the old launch sequence
+                std::lock_guard<std::mutex> lk(p->mu);
+                for (auto& kv : p->admm)
+                    if (kv.second.graph) {
+                        cudaGraphExecDestroy(kv.second.graph);
+                        kv.second.graph = nullptr;
+                    }
+            }
+            return LAM_OK;
         case LAM_OPT_RESIDUAL:
             if (value & ~(LAM_RESID_REFRESH | LAM_RESID_COMPENSATED))
                 return fail(LAM_EINVAL, "residual mode %d: a combination of LAM_RESID_REFRESH and LAM_RESID_COMPENSATED", value);
@@ -1209,6 +1230,45 @@ lam_status tv_smooth(const lam_plan* p, const void* u, double eps, void* grad, d
         CK(cudaStreamSynchronize(s));
     }
     return LAM_OK;
+}
+
+lam_status lam_plan_status(const lam_plan* p, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int word = 0;
+    CK(cudaMemcpyAsync(&word, p->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (word == 0) return LAM_OK;
+    CK(cudaMemsetAsync(p->err, 0, sizeof(int), s));
+    CK(cudaStreamSynchronize(s));
+    return fail(LAM_EBOUNDS, "index check failed at site %d (%s)", word,
+                word == kSiteZWeights      ? "z transpose weights"
+                : word == kSiteGatherWindow ? "2D gather window"
+                : word == kSiteGatherOut    ? "2D gather output"
+                : word == kSiteSpreadIn     ? "2D spread input"
+                : word == kSiteSelftest     ? "self-test"
+                                            : "unknown");
+}
+
+int lam_bounds_checked(void) {
+#ifdef LAM_BOUNDS_CHECK
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+lam_status lamx_bounds_selftest(const lam_plan* p, int index, void* stream) {
+#ifdef LAM_BOUNDS_CHECK
+    if (lam_status st = check_plan(p)) return st;
+    CK(launch_bounds_selftest(p->err + 1, index, p->err, (cudaStream_t)stream));
+    return LAM_OK;
+#else
+    (void)p;
+    (void)index;
+    (void)stream;
+    return fail(LAM_EUNSUPPORTED, "the self-test needs a LAM_BOUNDS_CHECK build");
+#endif
 }
 
 lam_status admm_state_bytes(const lam_plan* p, size_t* bytes) {
@@ -1777,6 +1837,16 @@ lam_status lamx_admm_graph_kernels(const lam_plan* p, void* state, size_t* count
     AdmmHost* h;
     if (lam_status st = lookup(p, state, &h)) return st;
     *count = h->graph ? h->graph_kernels : 0;
+    return LAM_OK;
+}
+
+lam_status lamx_admm_layout(const lam_plan* p, size_t* out, int count) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!out || count < 1) return fail(LAM_EINVAL, "out is NULL or count < 1");
+    const StateLayout L = layout(p);
+    const size_t v[18] = {L.sc, L.hist, L.partials, L.counter, L.u, L.du, L.Gd, L.G0, L.G1,
+                          L.p, L.e, L.lam, L.dpsi, L.dhat, L.r, L.Lp, L.rlo, L.total};
+    for (int i = 0; i < count && i < 18; ++i) out[i] = v[i];
     return LAM_OK;
 }
 

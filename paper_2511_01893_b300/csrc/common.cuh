@@ -116,6 +116,22 @@ __device__ __forceinline__ void grid_pos(int ku, int kv, double a, double s, int
     fr = p - fl;
 }
 
+// Index checks (LAM_BOUNDS_CHECK builds).  LAM_INB(i, n, err, site) is true
+// when 0 <= i < n; otherwise it records `site` in the plan's error word *err
+// (the first failing site wins) and is false, and the caller skips the access:
+// no trap, no out-of-range access.  In other builds it is the constant true.
+enum { kSiteZWeights = 1, kSiteGatherWindow = 2, kSiteGatherOut = 3, kSiteSpreadIn = 4, kSiteSelftest = 99 };
+#ifdef LAM_BOUNDS_CHECK
+__device__ __forceinline__ bool lam_in_bounds(long long i, long long n, int* err, int site) {
+    if (i >= 0 && i < n) return true;
+    if (err) atomicCAS(err, 0, site);
+    return false;
+}
+#define LAM_INB(i, n, err, site) ::lam::lam_in_bounds((long long)(i), (long long)(n), (err), (site))
+#else
+#define LAM_INB(i, n, err, site) true
+#endif
+
 // j mod M in [0, M) for any M >= 1 (a mask when M is a power of two)
 __host__ __device__ __forceinline__ int wrap(int j, int M) {
     if ((M & (M - 1)) == 0) return j & (M - 1);

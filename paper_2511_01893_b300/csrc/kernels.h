@@ -46,6 +46,7 @@ template <typename T> struct Usfft1dArgs {
     int twstride;      // Nmax / M0
     const int* skip;   // [h] or nullptr: planes that are mirrors of a paired plane
                        // (forward: not written; transpose: read as zero)
+    int* err;          // the plan's error word (index checks, LAM_BOUNDS_CHECK builds)
 };
 
 template <typename T>
@@ -81,6 +82,10 @@ template <typename T> struct Usfft2dArgs {
     const int2* jobs;               // plane jobs: .x plane computed, .y its conjugate mirror plane or -1
     const T* maxabs;                // device scalar: max |re|, |im| of the scatter input (fixed point)
     float bound_count;              // bound on the products summed into one padded cell
+    int nacc;                       // tile spread: leading plane jobs (the centre planes, which
+                                    // the paired job list puts first) spread with exact
+                                    // fixed-point accumulation instead
+    int* err;                       // the plan's error word (index checks, LAM_BOUNDS_CHECK builds)
 };
 
 // forward: plane jobs j0 .. j0 + nb - 1 of u1 ([h][n1][n2]) -> out ([T][h][w]),
@@ -104,6 +109,9 @@ cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int kv0, int n
 template <typename T>
 cudaError_t launch_usfft2d_planes(const C<T>* u1, C<T>* P, int j0, int nb, const Usfft2dArgs<T>& a, cudaStream_t s);
 cudaError_t launch_fma_peak(float* sink, int blocks, int iters, cudaStream_t s);
+// ints in the plan's self-test scratch (after its error word)
+constexpr int kSelftestCells = 64;
+cudaError_t launch_bounds_selftest(int* scratch, int index, int* err, cudaStream_t s);
 template <typename T> cudaError_t launch_absmax(const C<T>* in, long long n, T* out, cudaStream_t s);
 
 // ---- F_2D / F*_2D (centred, per angle) ----------------------------------------

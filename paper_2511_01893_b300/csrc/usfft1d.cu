@@ -122,6 +122,11 @@ __device__ __forceinline__ void spread_pair_at(const C<T>* va, const C<T>* vb, i
     for (; e <= a.jmax; e += M0) {
         const int c = e - a.jmin;
         const int lo = a.kvslo[c], hi = a.kvshi[c];
+        // a non-empty kv range must lie in the cell's row of cw weights
+        if (hi > lo && !(LAM_INB(lo - a.kvlo[c], a.cw, a.err, kSiteZWeights) &&
+                         LAM_INB(hi - 1 - a.kvlo[c], a.cw, a.err, kSiteZWeights) &&
+                         LAM_INB(hi - 1, a.h, a.err, kSiteZWeights)))
+            continue;
         const T* wt = a.wzc + (size_t)c * a.cw - a.kvlo[c];  // indexed by kv
         for (int kv = lo; kv < hi; ++kv) {
             const T wk = wt[kv];

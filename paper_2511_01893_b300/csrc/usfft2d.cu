@@ -28,6 +28,8 @@
 //   k_rowfft_adj       inverse FFT along y, crop, deapodise -> u1 rows
 // The FP32 row / column kernels are also built for the large power-of-two
 // lengths with the length a compile-time constant (LAM_PLANE_NC).
+#include <algorithm>
+
 #include "fft.cuh"
 #include "kernels.h"
 
@@ -472,6 +474,10 @@ __device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P
                 point_pos(g, kuc, kvc, jx, fx, jy, fy);
                 const int ox = jx - a.m + 1 - bx0, oy = jy - a.m + 1 - by0;
                 if (ox < 0 || ox >= TS || oy < 0 || oy >= TS) return;
+                // the window's last staged row and column
+                if (!(LAM_INB(ox + nt - 1, SH, a.err, kSiteGatherWindow) &&
+                      LAM_INB(oy + nt - 1, SH, a.err, kSiteGatherWindow)))
+                    return;
                 T wy[nt];
 #pragma unroll
                 for (int t = 0; t < nt; ++t) {
@@ -509,6 +515,8 @@ __device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P
 #endif
                 }
                 const size_t o = ((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2);
+                if (!(LAM_INB(kuc + a.w / 2, a.w, a.err, kSiteGatherOut) && LAM_INB(th, a.T_, a.err, kSiteGatherOut)))
+                    return;
                 C<T> v = cmake<T>(sr, mirror ? -si : si);
                 if (sub) v = csub(v, sub[o]);
                 out[o] = v;
@@ -820,6 +828,8 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
                     int ox = 0, oy = 0;
                     T fx = 0, fy = 0;
                     C<T> v = cmake<T>(0, 0);
+                    if (ok)
+                        ok = LAM_INB(kuc + a.w / 2, a.w, a.err, kSiteSpreadIn) && LAM_INB(th, a.T_, a.err, kSiteSpreadIn);
                     if (ok) {
                         const typename AngleT<T>::type g = a.ang[th];
                         int jx, jy;
@@ -989,6 +999,8 @@ __device__ __forceinline__ void k_spread2d_halo_body(const C<T>* __restrict__ in
                     int ox = 0, oy = 0;
                     T fx = 0, fy = 0;
                     C<T> v = cmake<T>(0, 0);
+                    if (ok)
+                        ok = LAM_INB(kuc + a.w / 2, a.w, a.err, kSiteSpreadIn) && LAM_INB(th, a.T_, a.err, kSiteSpreadIn);
                     if (ok) {
                         const typename AngleT<T>::type g = a.ang[th];
                         int jx, jy;
@@ -1230,6 +1242,19 @@ cudaError_t launch_fma_peak(float* sink, int blocks, int iters, cudaStream_t s) 
     return cudaGetLastError();
 }
 
+// Self-test of the index checks: one checked write of 1 at scratch[index],
+// scratch holding kSelftestCells ints.  An index outside the scratch is caught
+// by the check (the site is recorded, the write skipped), never performed.
+__global__ void k_bounds_selftest(int* scratch, int index, int* err) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (LAM_INB(index, kSelftestCells, err, kSiteSelftest)) scratch[index] = 1;
+}
+
+cudaError_t launch_bounds_selftest(int* scratch, int index, int* err, cudaStream_t s) {
+    k_bounds_selftest<<<1, 32, 0, s>>>(scratch, index, err);
+    return cudaGetLastError();
+}
+
 // the adjoint spread alone: slice values of plane jobs j0 .. j0 + nb - 1 onto
 // their padded planes P[0 .. nb) (the spread variant a.spread selects)
 template <typename T>
@@ -1264,12 +1289,34 @@ cudaError_t launch_spread2d(const C<T>* in, C<T>* P, int j0, int nb, const Usfft
         const long long hb = (ncells + 255) / 256;
         k_halo_sum<T><<<(int)(hb < 148 * 8 ? hb : 148 * 8), 256, 0, s>>>(a.halo, P, nb, kSpreadTS + 2 * a.m - 1, a);
     } else if ((a.spread == kSpreadTiles || a.spread == kSpreadHalo) && a.TS == kSpreadTS) {
-        const size_t st = spread_tiles_smem<T>(kSpreadWarps, a.m);
-        switch (a.m) {
-#define LAM_T(MH) case MH: k_spread2d_tiles<T, kSpreadWarps, MH><<<grid1, kSpreadWarps * 32, st, s>>>(in, P, kv0, a); break;
-            LAM_T(2) LAM_T(3) LAM_T(4) LAM_T(5) LAM_T(6) LAM_T(7) LAM_T(8)
+        // the first a.nacc plane jobs (the centre planes: every slice line
+        // passes close to the origin there, so the cells near it sum thousands
+        // of nearly equal products, where FP32 running sums round
+        // systematically) take the exact fixed-point accumulation; the others
+        // the tile spread
+        const int nx = a.maxabs ? std::max(0, std::min(nb, a.nacc - j0)) : 0;
+        if (nx > 0) {
+            const dim3 gx(ntiles, nx);
+#define LAM_X(MH)                                                                                                   \
+    case MH:                                                                                                        \
+        k_scatter2d_atomic<T, NW, MH, 3><<<gx, NW * 32, cells * atom_acc_bytes<T, 3>(), s>>>(in, P, kv0, a);        \
+        break;
+            switch (a.m) {
+                LAM_X(2) LAM_X(3) LAM_X(4) LAM_X(5) LAM_X(6) LAM_X(7) LAM_X(8)
+                default: return cudaErrorInvalidValue;
+            }
+#undef LAM_X
+        }
+        if (nb > nx) {
+            const size_t st = spread_tiles_smem<T>(kSpreadWarps, a.m);
+            const dim3 gt(ntiles, nb - nx);
+            C<T>* Pt = P + (size_t)nx * a.M1 * a.M2;
+            switch (a.m) {
+#define LAM_T(MH) case MH: k_spread2d_tiles<T, kSpreadWarps, MH><<<gt, kSpreadWarps * 32, st, s>>>(in, Pt, kv0 + nx, a); break;
+                LAM_T(2) LAM_T(3) LAM_T(4) LAM_T(5) LAM_T(6) LAM_T(7) LAM_T(8)
 #undef LAM_T
-            default: return cudaErrorInvalidValue;
+                default: return cudaErrorInvalidValue;
+            }
         }
     } else if (a.spread != kSpreadAtomic) { LAM_SW(3) }
     else { LAM_SW(0) }

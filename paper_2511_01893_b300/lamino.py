@@ -15,7 +15,9 @@ import numpy as np
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "liblamino.so")
+# LAMINO_LIB selects another build of the same ABI (liblamino_checked.so: the
+# LAM_BOUNDS_CHECK variant)
+LIB_PATH = os.environ.get("LAMINO_LIB") or os.path.join(_HERE, "liblamino.so")
 
 LAM_F32, LAM_F64 = 0, 1
 NSCALARS = 16
@@ -77,6 +79,10 @@ def lib() -> ctypes.CDLL:
             "lamx_spread": [vp, vp, vp, i, i, vp],
             "lamx_jobs_per_batch": [vp],
             "lamx_job_planes": [vp, i, i],
+            "lam_plan_status": [vp, vp],
+            "lamx_admm_layout": [vp, ctypes.POINTER(sz), i],
+            "lam_bounds_checked": [],
+            "lamx_bounds_selftest": [vp, i, vp],
         }
         for name, args in sig.items():
             fn = getattr(L, name)
@@ -326,6 +332,12 @@ class Plan:
         """Data planes (kv rows) plane jobs j0 .. j0 + nb - 1 cover."""
         return lib().lamx_job_planes(self._h, int(j0), int(nb))
 
+    def set_exact_centre_jobs(self, count):
+        """Plane jobs nearest the centre plane whose adjoint tile spread
+        accumulates in exact fixed point (LAM_OPT_EXACT_CENTRE_JOBS)."""
+        _check(lib().lam_plan_set_option(self._h, 7, int(count)), "lam_plan_set_option")
+        return self
+
     def set_threads(self, z=None, fft=None):
         """Threads per block (256 or 512) of the z-stage kernels and of the
         plane row / column FFTs; the lines per block are picked again."""
@@ -344,6 +356,11 @@ class Plan:
         _check(lib().lam_plan_autotune(self._h, _ptr(u), _ptr(d), _ptr(self.ws), int(reps), ctypes.byref(t),
                                        _stream()), "lam_plan_autotune")
         return t.value
+
+    def status(self) -> int:
+        """The plan's index-check status (lam_plan_status; synchronises):
+        0, or LAM_EBOUNDS (-7) once a LAM_BOUNDS_CHECK build caught an index."""
+        return lib().lam_plan_status(self._h, _stream())
 
     def info(self):
         arr = (ctypes.c_int * 13)()
@@ -466,6 +483,34 @@ class Admm:
         _check(lib().admm_read_history(self.plan._h, _ptr(self.state), count, arr, _stream()),
                "admm_read_history")
         return np.frombuffer(arr, dtype=np.float64)[: 4 * count].reshape(count, 4).copy()
+
+    LAYOUT = ["sc", "hist", "partials", "counter", "u", "du", "Gd", "G", "G_prev", "p", "e", "lam", "dpsi",
+              "d_hat", "r", "Lp", "r_lo", "total"]
+
+    def arrays(self) -> dict:
+        """Views (no copies) of the state's pieces by name: the FP64 scalars
+        and history, the volumes (u, du, Gd, G, G_prev, p; e, lam, dpsi with a
+        leading axis of 3) and the data arrays (d_hat, r, Lp, r_lo)."""
+        p = self.plan
+        arr = (ctypes.c_size_t * len(self.LAYOUT))()
+        _check(lib().lamx_admm_layout(p._h, arr, len(self.LAYOUT)), "lamx_admm_layout")
+        off = dict(zip(self.LAYOUT, list(arr)))
+        vol, dat = p.vol_shape, p.data_shape
+        rsz, csz = (4, 8) if p.prec == "f32" else (8, 16)
+        nv, nd = p.n * p.nz * p.n, p.T * p.h * p.w
+
+        def view(name, count, esz, dtype, shape):
+            o = off[name]
+            return self.state[o:o + count * esz].view(dtype).view(shape)
+        out = {"sc": view("sc", 64, 8, torch.float64, (64,)), "hist": view("hist", 4096 * 4, 8, torch.float64,
+                                                                           (4096, 4))}
+        for k in ("u", "du", "Gd", "G", "G_prev", "p"):
+            out[k] = view(k, nv, rsz, p.rdtype, vol)
+        for k in ("e", "lam", "dpsi"):
+            out[k] = view(k, 3 * nv, rsz, p.rdtype, (3,) + vol)
+        for k in ("d_hat", "r", "Lp", "r_lo"):
+            out[k] = view(k, nd, csz, p.cdtype, dat)
+        return out
 
     def graph_kernels(self) -> int:
         """Kernel launches per outer iteration in the captured graph (0 before a graph run)."""

@@ -42,6 +42,19 @@ def test_library_exports_every_declared_symbol(so):
     assert missing == []
 
 
+def test_checked_library_exports_every_declared_symbol():
+    path = build.build(checked=True)
+    lib = ctypes.CDLL(path)
+    assert [n for n in _declared() if not hasattr(lib, n)] == []
+    assert lib.lam_bounds_checked() == 1
+
+
+def test_plain_library_has_no_index_checks(so):
+    assert so.lam_bounds_checked() == 0
+    # the self-test refuses on the host before any launch
+    assert so.lamx_bounds_selftest(None, 70, None) == -6
+
+
 def test_binding_signatures_cover_exports(so):
     lib = lamino.lib()
     for n in _declared():
