@@ -34,6 +34,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 ALPHA, RHO, N_INNER, PHI_DEG = 1e-3, 0.5, 4, 30.0
+EXACT_CENTRE_JOBS = 3  # the library's FP32 default (LAM_OPT_EXACT_CENTRE_JOBS)
 
 
 def parse():
@@ -46,12 +47,20 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
-    ap.add_argument("--op", choices=["admm", "lhat_pair", "batch", "ablation"], default="admm",
+    ap.add_argument("--iters", type=int, default=32, help="--op precision: ADMM-TV iterations compared")
+    ap.add_argument("--taus", default="0.86,0.90,0.92,0.94,0.96", help="--op memo: thresholds")
+    ap.add_argument("--op", choices=["admm", "lhat_pair", "batch", "ablation", "precision", "fbp", "memo"],
+                    default="admm",
                     help="lhat_pair: time only L-hat + L-hat^H on the workload (no ADMM state); "
                          "a small footprint for profiling.  batch: the batching workload (16 "
                          "reconstructions of uneven sizes, batched operators, graph-captured ADMM).  "
                          "ablation: the plain LSP form (Algorithm 1) against the cancelled and fused "
-                         "form (Algorithm 2) on the workload")
+                         "form (Algorithm 2) on the workload.  precision: FP32 (graph) against the plain FP64 "
+                         "GPU path over --iters ADMM-TV iterations on the workload (relative L2 of u at "
+                         "iterations 1, 2, 4, ..., s/iter of both).  fbp: the FBP-style single pass "
+                         "(L^H of ramp-filtered data) on the workload: seconds per pass, voxels/s.  memo: "
+                         "ADMM-TV with F*_u2D memoized per plane job at each of --taus against the run "
+                         "without (accuracy error E of Section 6.1, reused jobs, s/iter)")
     return ap.parse_args()
 
 
@@ -83,6 +92,21 @@ def _strip_comments(src: str) -> str:
     src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
     src = re.sub(r"//[^\n]*", " ", src)
     return re.sub(r"\s+", " ", src).strip()
+
+
+def full_source_hash():
+    """SHA-256 of the code (comments stripped) of every CUDA source of the
+    library (csrc/*.cu, *.cuh, *.h, sorted): ties a stored FP32-vs-FP64
+    trajectory record to the code it was measured on."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2511_01893_b300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            h.update(f.encode())
+            with open(os.path.join(d, f), encoding="utf-8") as fh:
+                h.update(_strip_comments(fh.read()).encode())
+    return h.hexdigest()
 
 
 def source_hash():
@@ -587,6 +611,187 @@ def run_ablation(args):
     return 0
 
 
+def precision_data(glam, inputs, n, dev, stream):
+    """The workload's data at n^3: the ellipsoid + circuit phantom through the
+    FP64 GPU forward operator, 1 % Gaussian noise (seed 99), rounded to complex64
+    (FP32-representable, so both precisions start from the same data)."""
+    import torch
+    theta = inputs.angles(n)
+    phi = np.deg2rad(PHI_DEG)
+    p64 = glam.Plan(n, n, n, n, theta, phi, prec="f64", device=dev, workspace="hat")
+    with torch.cuda.stream(stream):
+        u = inputs.ellipsoid_circuit_phantom(n, n, seed=1238, device=dev, dtype=torch.float64)
+        d = p64.forward(u)
+        del u
+        sigma = 0.01 * d.real.abs().max().item()
+        gen = torch.Generator(device=dev).manual_seed(99)
+        for k in range(d.shape[0]):  # per angle: no second data-sized FP64 array
+            d[k].real.add_(torch.randn(d.shape[1:], generator=gen, device=dev, dtype=torch.float64), alpha=sigma)
+        d32 = d.to(torch.complex64)
+    stream.synchronize()
+    del d, p64
+    torch.cuda.empty_cache()
+    return theta, phi, d32
+
+
+PRECISION_SNAPS = (1, 2, 4, 8, 16, 32, 64, 128)
+
+
+def run_precision(args):
+    """FP32 ADMM-TV (the library's FP32 defaults, graph replay) against the
+    plain FP64 GPU path (eager, no graph) on the workload at --size, --iters
+    outer iterations each, from the same FP32-representable data: relative L2
+    of u at iterations 1, 2, 4, ... and s/iter of both.  Prints one JSON line."""
+    import torch
+
+    from paper_2511_01893_b300 import inputs
+    from paper_2511_01893_b300 import lamino as glam
+    n, iters = args.size, args.iters
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    s = torch.cuda.Stream(device=dev)
+    theta, phi, d32 = precision_data(glam, inputs, n, dev, s)
+    snaps = [k for k in PRECISION_SNAPS if k <= iters]
+    res = {}
+    for prec in ("f64", "f32"):
+        plan = glam.Plan(n, n, n, n, theta, phi, prec=prec, device=dev)
+        a = glam.Admm(plan)
+        with torch.cuda.stream(s):
+            a.init(d32, ALPHA, RHO, N_INNER, adapt_rho=True)
+        s.synchronize()
+        t, done, timed, us = 0.0, 0, 0, {}
+        for k in snaps:
+            with torch.cuda.stream(s):
+                if prec == "f32" and done == 0:
+                    a.run(1, graph=True)  # the capture stays outside the timed region
+                    done = 1
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                a.run(k - done, graph=(prec == "f32"))
+                e1.record(s)
+            s.synchronize()
+            t += e0.elapsed_time(e1) / 1e3
+            timed += k - done
+            done = k
+            # the FP64 snapshots wait in host memory while the FP32 run has the device
+            us[k] = a.u.to(torch.float64).cpu() if prec == "f64" else a.u.clone()
+        res[prec] = {"s_per_iter": t / max(timed, 1), "u": us, "rho": a.history(iters)[:, 1].tolist(),
+                     "status": a.status(), "objective": a.history(iters)[:, 0].tolist()}
+        del a, plan
+        torch.cuda.empty_cache()
+    rel = {}
+    for k in snaps:
+        ref = res["f64"]["u"][k].to(dev)
+        rel[k] = (torch.linalg.vector_norm(res["f32"]["u"][k].double() - ref) / torch.linalg.vector_norm(ref)).item()
+    obj = np.array(res["f32"]["objective"]) / np.array(res["f64"]["objective"]) - 1
+    print(json.dumps({
+        "op": "precision", "size": n, "iters": iters,
+        "workload": workload_name(n).replace("FP32, ", ""),
+        "f32_graph_s_per_iter": res["f32"]["s_per_iter"], "f64_plain_s_per_iter": res["f64"]["s_per_iter"],
+        "speedup": res["f64"]["s_per_iter"] / res["f32"]["s_per_iter"],
+        "rel_l2_u_f32_vs_f64": {str(k): v for k, v in rel.items()},
+        "max_rel_objective_diff": float(np.abs(obj).max()),
+        "rho_same": res["f32"]["rho"] == res["f64"]["rho"],
+        "status": max(res["f32"]["status"], res["f64"]["status"]),
+        "source_sha256": full_source_hash(),
+        "note": "FP32: exact spreads for the 3 centre plane jobs, compensated residual carry, graph replay; "
+                "FP64: plain eager path",
+    }), flush=True)
+    return 0
+
+
+def run_fbp(args):
+    """FBP-style single pass (lam_fbp: F_2D, ramp, L-hat^H) on the workload's
+    data at --size: seconds per pass over --steps passes after --warmup, and
+    the relative L2 distance of the result from the phantom (the missing cone
+    and the 1 % noise bound it; ADMM-TV is the method, FBP the one-pass
+    baseline).  Prints one JSON line."""
+    import torch
+
+    from paper_2511_01893_b300 import inputs
+    from paper_2511_01893_b300 import lamino as glam
+    n = args.size
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    plan = glam.Plan(n, n, n, n, inputs.angles(n), np.deg2rad(PHI_DEG), prec="f32", device=dev)
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        u_true = inputs.ellipsoid_circuit_phantom(n, n, seed=1238, device=dev, dtype=torch.float32)
+        d = plan.forward(u_true)
+        gen = torch.Generator(device=dev).manual_seed(99)
+        d.real.add_(torch.randn(d.shape, generator=gen, device=dev, dtype=torch.float32),
+                    alpha=0.01 * d.real.abs().max().item())
+        out = torch.empty_like(u_true)
+        for _ in range(args.warmup):
+            plan.fbp(d, out=out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            plan.fbp(d, out=out)
+        e1.record(s)
+    s.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / max(args.steps, 1)
+    err = (torch.linalg.vector_norm(out - u_true) / torch.linalg.vector_norm(u_true)).item()
+    print(json.dumps({"op": "fbp", "size": n, "s_per_pass": t, "voxels_per_s": n ** 3 / t,
+                      "rel_l2_vs_phantom": err, "steps": args.steps, "warmup": args.warmup,
+                      "note": "F_2D + ramp + L-hat^H, FP32; the phantom has content in the missing cone"}),
+          flush=True)
+    return 0
+
+
+def run_memo(args):
+    """Memoization of F*_u2D per plane job (LAM_OPT_MEMO_TAU) on the workload:
+    --steps ADMM-TV iterations (FP32, graph replay) without memoization, the
+    reference R_comp, then with each tau of --taus: the accuracy error
+    E = ||R_comp - R|| / ||R_comp|| (Section 6.1, Eq. 4), the fraction of
+    plane jobs served from the cache, s/iter.  Prints one JSON line."""
+    import torch
+
+    from paper_2511_01893_b300 import inputs
+    from paper_2511_01893_b300 import lamino as glam
+    n = args.size
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    s = torch.cuda.Stream(device=dev)
+    theta, phi = inputs.angles(n), np.deg2rad(PHI_DEG)
+    plan = glam.Plan(n, n, n, n, theta, phi, prec="f32", device=dev)
+    s.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(s):
+        u_true = inputs.ellipsoid_circuit_phantom(n, n, seed=1238, device=dev, dtype=torch.float32)
+        d = plan.forward(u_true)
+        gen = torch.Generator(device=dev).manual_seed(99)
+        d.real.add_(torch.randn(d.shape, generator=gen, device=dev, dtype=torch.float32),
+                    alpha=0.01 * d.real.abs().max().item())
+    s.synchronize()
+    res, ref = [], None
+    for tau in [0.0] + [float(t) for t in args.taus.split(",")]:
+        plan.set_memo(tau)
+        a = glam.Admm(plan)
+        with torch.cuda.stream(s):
+            a.init(d, ALPHA, RHO, N_INNER)
+            a.run(1, graph=True)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            a.run(args.steps - 1, graph=True)
+            e1.record(s)
+        s.synchronize()
+        sc = a.scalars()
+        u = a.u.clone()
+        if ref is None:
+            ref = u
+        err = (torch.linalg.vector_norm(u - ref) / torch.linalg.vector_norm(ref)).item()
+        res.append({"tau": tau, "s_per_iter": e0.elapsed_time(e1) / 1e3 / max(args.steps - 1, 1), "E": err,
+                    "one_minus_E": 1 - err, "reused_fraction": sc["memo_hits"] / max(sc["memo_lookups"], 1),
+                    "objective": sc["objective"], "status": a.status()})
+        del a
+        torch.cuda.empty_cache()
+    print(json.dumps({"op": "memo", "size": n, "iters": args.steps, "runs": res,
+                      "note": "tau = 0: no memoization (R_comp); E of each run against it (Section 6.1, Eq. 4)"}),
+          flush=True)
+    return 0
+
+
 BATCH_SIZES = [96, 128, 160, 192]
 
 
@@ -751,18 +956,21 @@ def run_ours(args):
     else:
         peak, peak_src = 6400.0, "fallback"
     # ---- the dominant kernel alone: the adjoint spread, one operator batch per
-    # launch (plane jobs 0 .. nbj - 1), CUDA events on its stream ----------------
+    # launch, CUDA events on its stream.  The launch covers the operator's plane
+    # jobs per batch, starting after the centre jobs that take the exact spread
+    # (LAM_OPT_EXACT_CENTRE_JOBS), so that it is the tile kernel alone ----------
     kreps = 5
+    j0s = EXACT_CENTRE_JOBS
     with torch.cuda.stream(stream):
-        nbj = plan.spread(out_c)
+        nbj = plan.spread(out_c, j0s)
         kev = [torch.cuda.Event(enable_timing=True) for _ in range(kreps + 1)]
         kev[0].record(stream)
         for r in range(kreps):
-            plan.spread(out_c, 0, nbj)
+            plan.spread(out_c, j0s, nbj)
             kev[r + 1].record(stream)
     stream.synchronize()
     t_spread = statistics.median([kev[r].elapsed_time(kev[r + 1]) / 1e3 for r in range(kreps)])
-    planes = plan.job_planes(0, nbj)
+    planes = plan.job_planes(j0s, nbj)
     M = 2 * n
     # reads the batch's slice values (8 B per (theta, ku) of each data plane),
     # writes one padded plane (8 B per cell) per job
@@ -816,14 +1024,12 @@ def run_ours(args):
         "admm": {"status": status, "objective": sc["objective"], "rho": sc["rho"], "iters_done": sc["iter"]},
     }
 
-    # ---- FP64 comparator at 256^3 (the precision workload) ------------------
-    if not args.no_f64 and rank == 0:
-        line["f64_comparison"] = f64_comparison(glam, inputs, dev, stream)
-
     # ---- end to end through the one-call API (host data in, host volume out) -
-    del admm
+    del admm, plan
     torch.cuda.empty_cache()
-    if not args.no_e2e:
+    if args.no_e2e:
+        del d
+    else:
         d_host = torch.empty(d.shape, dtype=torch.float32, pin_memory=True)
         d_host.copy_(d.real)
         del d
@@ -836,6 +1042,11 @@ def run_ours(args):
                        "d2h_bytes_per_step": int(u_host.size * 4 // args.steps),
                        "api": "reconstruct() one call, K iterations, host data/volume, includes plan + allocation"}
     line["clocks"] = clk.summary()
+
+    # ---- the chosen FP32 form against the plain FP64 GPU path at this size --
+    if not args.no_f64 and rank == 0:
+        torch.cuda.empty_cache()
+        line["f64_comparison"] = f64_comparison(glam, inputs, dev, stream, n)
 
     # ---- oracle on the host cores (rank 0, N = 1) ----------------------------
     if not args.no_cpu and rank == 0 and world == 1:
@@ -854,37 +1065,49 @@ def run_ours(args):
     return 0 if status == 0 else 1
 
 
-def f64_comparison(glam, inputs, dev, stream, n=256, iters=4):
-    """FP32 (graph) vs plain FP64 GPU path on the 256^3 precision workload."""
+def f64_comparison(glam, inputs, dev, stream, n, iters=2):
+    """The chosen form (FP32, graph replay, the library's FP32 defaults) against
+    the plain FP64 GPU path (eager) on the workload at n^3 from the same
+    FP32-representable data (precision_data): s/iter of both and the relative
+    L2 of u after `iters` iterations, measured here; the 32-iteration
+    comparison comes from the record bench.py --op precision wrote
+    (profiles/precision_<n>.json), attached only while its source hash matches
+    the current CUDA sources."""
     import torch
-    theta = inputs.angles(n)
-    phi = np.deg2rad(PHI_DEG)
-    u = inputs.ellipsoid_phantom(n, n, 12, seed=1235, device=dev, dtype=torch.float64)
-    out = {"workload": f"precision: {n}^3, {n} angles, detector {n}x{n}, phi=30deg, ellipsoid phantom, "
-                       f"1% noise, {iters} ADMM-TV iterations"}
-    p64 = glam.Plan(n, n, n, n, theta, phi, prec="f64", device=dev)
-    with torch.cuda.stream(stream):
-        d = p64.forward(u)
-        sigma = 0.01 * d.real.abs().max().item()
-        gen = torch.Generator(device=dev).manual_seed(7)
-        d.real.add_(torch.randn(d.shape, generator=gen, device=dev, dtype=torch.float64), alpha=sigma)
-    stream.synchronize()
+    theta, phi, d32 = precision_data(glam, inputs, n, dev, stream)
+    out = {"workload": f"{workload_name(n).replace('FP32, ', '')} (precision_data: FP64 forward, noise per angle)",
+           "iters": iters}
     res = {}
-    for prec, plan in (("f64", p64), ("f32", glam.Plan(n, n, n, n, theta, phi, prec="f32", device=dev))):
+    for prec in ("f64", "f32"):
+        plan = glam.Plan(n, n, n, n, theta, phi, prec=prec, device=dev)
         a = glam.Admm(plan)
         with torch.cuda.stream(stream):
-            a.init(d, ALPHA, RHO, N_INNER)
+            a.init(d32, ALPHA, RHO, N_INNER)
+            pre = 0
+            if prec == "f32":
+                a.run(1, graph=True)  # the capture stays outside the timed region
+                pre = 1
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            a.run(iters, graph=(prec == "f32"))
+            a.run(iters - pre, graph=(prec == "f32"))
             e1.record(stream)
         stream.synchronize()
-        res[prec] = (e0.elapsed_time(e1) / 1e3 / iters, a.u.double().clone())
-        del a
-    err = (torch.linalg.vector_norm(res["f32"][1] - res["f64"][1])
-           / torch.linalg.vector_norm(res["f64"][1])).item()
+        res[prec] = (e0.elapsed_time(e1) / 1e3 / max(iters - pre, 1), a.u.double().cpu(), a.status())
+        del a, plan
+        torch.cuda.empty_cache()
+    err = (torch.linalg.vector_norm(res["f32"][1] - res["f64"][1]) / torch.linalg.vector_norm(res["f64"][1])).item()
     out.update({"f32_graph_s_per_iter": res["f32"][0], "f64_plain_s_per_iter": res["f64"][0],
-                "speedup": res["f64"][0] / res["f32"][0], "rel_l2_f32_vs_f64": err})
+                "speedup": res["f64"][0] / res["f32"][0], f"rel_l2_f32_vs_f64_after_{iters}": err,
+                "status": max(res["f32"][2], res["f64"][2])})
+    rec = os.path.join(ROOT, "profiles", f"precision_{n}.json")
+    if os.path.exists(rec):
+        r = json.load(open(rec))
+        if r.get("source_sha256") == full_source_hash():
+            out["record_32_iterations"] = {k: r[k] for k in ("iters", "rel_l2_u_f32_vs_f64", "f32_graph_s_per_iter",
+                                                              "f64_plain_s_per_iter", "speedup", "rho_same")
+                                           if k in r}
+        else:
+            out["record_32_iterations"] = "stale (sources changed since the record was taken)"
     return out
 
 
@@ -898,6 +1121,12 @@ def main():
         return run_batch(args)
     if args.op == "ablation":
         return run_ablation(args)
+    if args.op == "precision":
+        return run_precision(args)
+    if args.op == "fbp":
+        return run_fbp(args)
+    if args.op == "memo":
+        return run_memo(args)
     return run_ours(args)
 
 

@@ -104,16 +104,18 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *   per block of the z-stage kernels and of the plane row / column FFT
  *   kernels.  The columns, rows or lines per block are picked again to fit;
  *   256 lets two blocks share an SM.  Results do not depend on either.
- * LAM_OPT_RESIDUAL (default 0) is how ADMM states initialised afterwards keep
- *   the Algorithm 2 residual r = L_hat u - d_hat, a combination of:
+ * LAM_OPT_RESIDUAL (default LAM_RESID_COMPENSATED for FP32 plans, 0 for FP64)
+ *   is how ADMM states initialised afterwards keep the Algorithm 2 residual
+ *   r = L_hat u - d_hat, a combination of:
  *   LAM_RESID_REFRESH      evaluate r afresh (one extra L_hat with the fused
  *                          subtraction) at the start of every LSP instead of
  *                          carrying it across LSPs by linearity;
  *   LAM_RESID_COMPENSATED  carry the updates r += gamma L_hat p in a
- *                          compensated (hi + lo) pair (needs no extra memory:
- *                          the state always holds the lo part).
+ *                          compensated (hi + lo) pair (FP32 states hold the lo
+ *                          part; FP64 states ignore this bit).
  *   Batched ADMM accepts LAM_RESID_COMPENSATED only.
- * LAM_OPT_EXACT_CENTRE_JOBS (value >= 0) is the number of plane jobs nearest
+ * LAM_OPT_EXACT_CENTRE_JOBS (value >= 0; default 3 for FP32 plans, the planes
+ *   with |kv - h/2| <= 2, and 0 for FP64) is the number of plane jobs nearest
  *   the centre plane kv = h/2 (the paired adjoint treats planes kv and h - kv
  *   as one job, centre first) whose tile spread (LAM_SPREAD_TILES) accumulates
  *   in exact fixed point (as LAM_SPREAD_EXACT) instead of FP32.  Near the
@@ -121,6 +123,17 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *   thousands of nearly equal products, which FP32 running sums round
  *   systematically; these few jobs carry most of the energy of L^H applied to
  *   smooth data.  0 = none.
+ * LAM_OPT_MEMO_TAU (default 0: off; else tau * 10000 in [1, 9999]) makes ADMM
+ *   states initialised afterwards (Algorithm 2 form; size them with
+ *   admm_state_bytes after setting it) memoize F*_u2D per plane job
+ *   (Sections 4.1, 4.4, 4.5): each job has a one-item cache of (key, value),
+ *   key = K = min(1024, T w) slice values per plane at fixed pseudo-random
+ *   positions, value = the job's u1 plane.  When the cosine similarity
+ *   (Eq. cs) of this call's key and the cached key exceeds tau, the job's
+ *   spread and inverse plane FFTs are skipped and its plane is the cached one
+ *   times <key, cached key> / |cached key|^2 (F*_u2D is linear); otherwise the
+ *   computed plane and its key replace the item.  An approximation: results
+ *   depend on tau.  Scalars LAM_SC_MEMO_HITS / LAM_SC_MEMO_LOOKUPS count jobs.
  * Setting an option invalidates ADMM graphs captured with the plan. */
 enum {
     LAM_OPT_FAST_ADJOINT = 1,
@@ -129,7 +142,8 @@ enum {
     LAM_OPT_Z_THREADS = 4,
     LAM_OPT_PLANE_FFT_THREADS = 5,
     LAM_OPT_RESIDUAL = 6,
-    LAM_OPT_EXACT_CENTRE_JOBS = 7
+    LAM_OPT_EXACT_CENTRE_JOBS = 7,
+    LAM_OPT_MEMO_TAU = 8
 };
 enum { LAM_RESID_REFRESH = 1, LAM_RESID_COMPENSATED = 2 };
 enum { LAM_SPREAD_TILES = 0, LAM_SPREAD_ATOMIC = 1, LAM_SPREAD_EXACT = 2, LAM_SPREAD_HALO = 3 };
@@ -191,6 +205,20 @@ lam_status lam_forward_hat(const lam_plan* plan, const void* u, void* d_hat, con
  * d_hat complex [T][h][w] (read); u real [n][nz][n] (written). */
 lam_status lam_adjoint_hat(const lam_plan* plan, const void* d_hat, void* u, void* ws, void* stream);
 
+/* FBP-style single-pass reconstruction: L^H of ramp-filtered data,
+ *   u = Re L_hat^H (W . F_2D d),  W(ku) = pi cos(phi) |ku| / (T w^2 h),
+ * with |ku| read as 1/4 at ku = 0.  W is the inverse density of the slice
+ * points in frequency space: in the plane xi_z = (kv/h) cos(phi) the T lines
+ * of plane kv lie tangent to the circle of radius |kv| sin(phi)/h, which makes
+ * the density T w h / (pi cos(phi) |ku|/w) per unit volume; so L_hat^H W L_hat
+ * approximates the identity on band-limited volumes outside the missing cone
+ * (frequencies within phi of the z axis, which no slice reaches).  Not part of
+ * the paper's method (which is iterative); a one-pass baseline.
+ * d: complex [T][h][w] (read); u: real [n][nz][n] (written); ws: the full
+ * workspace (lam_workspace_bytes: the filtered spectrum uses its data-space
+ * buffer). */
+lam_status lam_fbp(const lam_plan* plan, const void* d, void* u, void* ws, void* stream);
+
 /* Per-angle centred 2D DFT on the h x w grid (Section 4.2):
  *   inverse = 0: F_2D, out = sum in exp(-2 pi i (ku s/w + kv t/h))   (unnormalised)
  *   inverse = 1: F*_2D, out = 1/(h w) sum in exp(+2 pi i (...))
@@ -233,6 +261,8 @@ enum {
     LAM_SC_DATA2 = 6,      /* ||L u - d||^2 */
     LAM_SC_TV = 7,         /* TV(u) */
     LAM_SC_STATUS = 8,     /* 0, or LAM_ENAN once a reduction was non-finite */
+    LAM_SC_MEMO_HITS = 9,  /* plane jobs served from the memoization cache (LAM_OPT_MEMO_TAU) */
+    LAM_SC_MEMO_LOOKUPS = 10, /* plane jobs looked up */
     LAM_NSCALARS = 16
 };
 
@@ -294,7 +324,9 @@ typedef struct lam_batch lam_batch;
  * the default when the padded planes of the h/2 + 1 jobs need at most 8 GiB in
  * FP32, 1 GiB in FP64).  Allocates one small device
  * table; the batch does not own the plans or workspaces, which must outlive
- * it.  The batched adjoint always uses the tile spread (LAM_SPREAD_TILES). */
+ * it.  The batched adjoint always uses the tile spread (LAM_SPREAD_TILES),
+ * with each plan's LAM_OPT_EXACT_CENTRE_JOBS centre jobs spread exactly by
+ * launches of their own; the option is read at lam_batch_create. */
 lam_status lam_batch_create(lam_batch** out, const lam_plan* const* plans, void* const* ws, int count);
 lam_status lam_batch_destroy(lam_batch* batch);
 

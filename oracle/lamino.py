@@ -275,6 +275,33 @@ def lam_forward_exact(u: np.ndarray, g: Geometry) -> np.ndarray:
     return f_2d_inv(lhat_exact(u, g))
 
 
+# ----------------------------------------------------------------------------
+# FBP-style single pass (a one-pass baseline next to the iterative method)
+# ----------------------------------------------------------------------------
+
+def fbp_weights(g: Geometry) -> np.ndarray:
+    """Inverse density of the slice points per unit volume of frequency space,
+    as a function of ku alone: pi cos(phi) |ku| / (T w^2 h), |ku| read as 1/4 at
+    ku = 0 (the mean of |t| over the centre cell, t in units of 1/w).
+
+    Derivation (the paper gives no filter; this is the density compensation of
+    the geometry above).  Plane kv lies at xi_z = (kv/h) cos(phi); in it, the
+    T lines xi_xy(ku) = (ku/w)(cos th, sin th) + (kv/h) sin(phi) (sin th, -cos th)
+    are tangent to the circle of radius rho0 = |kv| sin(phi)/h and carry w
+    points per unit length.  At radius rho each line crosses the ring twice, so
+    the in-plane density is T w / (pi sqrt(rho^2 - rho0^2)), and
+    sqrt(rho^2 - rho0^2) = |ku|/w.  The planes are cos(phi)/h apart."""
+    ku = np.abs(centred(g.w))
+    ku[g.w // 2] = 0.25
+    return np.pi * np.cos(g.phi) * ku / (g.n_theta * g.w ** 2 * g.h)
+
+
+def fbp(d: np.ndarray, g: Geometry) -> np.ndarray:
+    """u = Re L_hat^H (W . F_2D d): since F_2D d = L_hat u for d = L u, this is
+    the quadrature of the inverse Fourier integral over the sampled slices."""
+    return lhat_adj(f_2d(d) * fbp_weights(g)[None, None, :], g)
+
+
 def accuracy_error(r_comp: np.ndarray, r: np.ndarray) -> float:
     """E of Section 6.1 (Eq. 4): ||R_comp - R||_F / ||R_comp||_F."""
     return float(np.linalg.norm((r_comp - r).ravel()) / np.linalg.norm(np.ravel(r_comp)))

@@ -69,7 +69,7 @@ def build(verbose: bool = False, extra_flags=(), checked: bool = False) -> str:
         raise failed
     if (not os.path.exists(lib) or any(os.path.getmtime(o) > os.path.getmtime(lib) for o in objs)
             or jobs):
-        cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", lib, *objs, "-lcudart"]
+        cmd = [NVCC, "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", lib, *objs, "-lcudart", "-ldl"]
         if verbose:
             print(" ".join(cmd), flush=True)
         subprocess.run(cmd, check=True)

@@ -18,6 +18,8 @@ enum {
     SC_DATA2 = 6,
     SC_TV = 7,
     SC_STATUS = 8,
+    SC_MEMO_HITS = 9,     // plane jobs of the adjoint served from the memoization cache (accumulated)
+    SC_MEMO_LOOKUPS = 10, // plane jobs looked up
     // internal
     SC_GG = 16,      // ||G||^2
     SC_PG = 17,      // <p_old, G>

@@ -7,6 +7,7 @@
 // caller's workspace; ADMM keeps all of its vectors and FP64 scalars in the
 // caller's state buffer.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -61,12 +62,26 @@ struct AdmmHost {
     int n_inner = 4;
     int form = 2;  // LSP form: 2 (Algorithm 2, default) or 1 (Algorithm 1)
     int resid = 0;  // residual handling (LAM_OPT_RESIDUAL bits)
+    double memo_tau = 0;  // memoization of F*_u2D (0: off)
     void* ws = nullptr;
     cudaGraphExec_t graph = nullptr;
     size_t graph_kernels = 0;  // kernel nodes in the captured outer iteration
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// NVTX range over a host scope: the stages show by name in a profiler's
+// timeline (free when no profiler is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// plane jobs nearest the centre plane that an FP32 plan spreads exactly by
+// default: kv = h/2 and the pairs h/2 +- 1, h/2 +- 2 (|kv - h/2| <= 2)
+constexpr int kDefaultExactCentreJobs = 3;
 
 static int ilog2(int v) {
     int l = 0;
@@ -106,6 +121,9 @@ struct lam_plan {
     int nacc = 0;  // leading plane jobs the tile spread accumulates exactly (LAM_OPT_EXACT_CENTRE_JOBS)
     int lsp_form = 2;  // LSP form new ADMM states take (LAM_OPT_LSP_FORM)
     int resid = 0;     // residual handling new ADMM states take (LAM_OPT_RESIDUAL)
+    double memo_tau = 0;  // memoization threshold new ADMM states take (LAM_OPT_MEMO_TAU; 0: off)
+    int* memo_samples = nullptr;  // [memo_K] key sample positions th * w + ku within a data plane
+    int memo_K = 0;
     // workspace layout
     size_t ws_u1, ws_planes, ws_halo, ws_tmp, ws_red, ws_bytes;
     mutable std::mutex mu;
@@ -274,6 +292,20 @@ template <typename T> lam_status build_tables(lam_plan* p, const double* theta) 
         if (st) return st;
         p->err = (int*)upload(p, std::vector<int>(1 + kSelftestCells, 0), &st);
         if (st) return st;
+        {
+            // memoization key samples: K slice points per data plane at fixed
+            // pseudo-random positions (a 64-bit LCG, seed fixed per plan shape)
+            const long long nplane = (long long)p->T * p->w;
+            p->memo_K = (int)std::min<long long>(1024, nplane);
+            std::vector<int> pos(p->memo_K);
+            unsigned long long x = 0x9E3779B97F4A7C15ull ^ (unsigned long long)nplane;
+            for (int k = 0; k < p->memo_K; ++k) {
+                x = x * 6364136223846793005ull + 1442695040888963407ull;
+                pos[k] = (int)((x >> 17) % (unsigned long long)nplane);
+            }
+            p->memo_samples = (int*)upload(p, pos, &st);
+            if (st) return st;
+        }
         // the paired transpose's kv range per cell: the non-skipped kv of
         // [lo, hi) when they are contiguous (skipped planes carry zeros), else
         // the whole range
@@ -431,6 +463,7 @@ template <typename T> Usfft2dArgs<T> args2d(const lam_plan* p, bool paired) {
     a.halo = nullptr;
     a.err = p->err;
     a.nacc = paired ? p->nacc : 0;
+    a.memo_hit = nullptr;
     // points whose 2m x 2m window covers one cell: at most (2m / spacing + 2)^2 per
     // line neighbourhood, over all T lines and all periodic images; doubled for safety
     {
@@ -466,6 +499,7 @@ int even_batch(const lam_plan* p, int njobs) {
 
 template <typename T>
 lam_status fwd_hat(const lam_plan* p, const T* u, C<T>* out, const C<T>* sub, void* ws, cudaStream_t s) {
+    NvtxRange range("lam: L_hat (F_u1D, F_u2D)");
     char* w = (char*)ws;
     C<T>* u1 = (C<T>*)(w + p->ws_u1);
     C<T>* P = (C<T>*)(w + p->ws_planes);
@@ -481,6 +515,13 @@ lam_status fwd_hat(const lam_plan* p, const T* u, C<T>* out, const C<T>* sub, vo
 
 // the fixed-point scatter needs a bound on its input: max(|re|, |im|) into the
 // workspace's scalar slot
+// device scalar slot for max(|re|, |im|) of a spread input, in the workspace's
+// reduction area
+template <typename T> T* maxabs_slot(const lam_plan* p, void* ws) {
+    return (T*)((char*)ws + p->ws_red + align256(SC_COUNT * sizeof(double)) +
+                align256((size_t)kRedBlocks * 4 * sizeof(double)) + 256);
+}
+
 template <typename T> lam_status prep_scatter(const lam_plan* p, const C<T>* in, void* ws, cudaStream_t s,
                                               Usfft2dArgs<T>& a) {
     // the exact spread runs when chosen, and for the tile spread's small-plane
@@ -488,41 +529,74 @@ template <typename T> lam_status prep_scatter(const lam_plan* p, const C<T>* in,
     const bool exact = p->spread == kSpreadExact || ((p->spread == kSpreadTiles || p->spread == kSpreadHalo) && p->TS != 32) ||
                        (p->spread == kSpreadTiles && a.nacc > 0);
     if (!exact) return LAM_OK;
-    T* mx = (T*)((char*)ws + p->ws_red + align256(SC_COUNT * sizeof(double)) +
-                 align256((size_t)kRedBlocks * 4 * sizeof(double)) + 256);
+    T* mx = maxabs_slot<T>(p, ws);
     CK(launch_absmax<T>(in, p->ndata(), mx, s));
     a.maxabs = mx;
     return LAM_OK;
 }
 
-template <typename T> lam_status adj_hat(const lam_plan* p, const C<T>* in, T* u, void* ws, cudaStream_t s) {
+// memoization of the plane stage inside ADMM (memo.cu): the state's slots and
+// the threshold
+template <typename T> struct MemoState {
+    T *key, *now;
+    C<T>* val;
+    MemoArgs m;
+};
+
+template <typename T>
+lam_status adj_hat(const lam_plan* p, const C<T>* in, T* u, void* ws, cudaStream_t s, const MemoState<T>* memo = nullptr) {
+    NvtxRange range("lam: L_hat^H (F*_u2D, F*_u1D)");
     char* w = (char*)ws;
     C<T>* u1 = (C<T>*)(w + p->ws_u1);
     C<T>* P = (C<T>*)(w + p->ws_planes);
     Usfft2dArgs<T> a = args2d<T>(p, true);
     a.halo = (C<T>*)(w + p->ws_halo);
     if (lam_status st = prep_scatter<T>(p, in, ws, s, a)) return st;
+    if (memo) {
+        // keys of this input; jobs whose key is close enough to their slot's are
+        // skipped by the spread and the inverse plane FFTs
+        CK(launch_memo_lookup<T>(in, memo->key, memo->now, memo->m, s));
+        a.memo_hit = memo->m.hit;
+    }
     const int per = even_batch(p, p->njobs_pair);
     for (int j0 = 0; j0 < p->njobs_pair; j0 += per) {
         const int nb = std::min(per, p->njobs_pair - j0);
         CK(launch_usfft2d_adj<T>(in, P, u1, j0, nb, a, s));
     }
+    if (memo) CK(launch_memo_update<T>(u1, memo->val, memo->key, memo->now, memo->m, s));
     CK(launch_usfft1d_adj<T>(u1, u, args1d<T>(p, p->TYa, true), s));
     return LAM_OK;
 }
+
+// FBP-style single pass: u = Re L_hat^H (W . F_2D d), W(ku) = pi cos(phi) |ku| / (T w^2 h)
+// (|ku| read as 1/4 at ku = 0): the density compensation of the slice points
+template <typename T> lam_status fbp_t(const lam_plan* p, const C<T>* d, T* u, void* ws, cudaStream_t s);
 
 template <typename T> lam_status fft2d(const lam_plan* p, const C<T>* in, C<T>* out, int dir, T scale, cudaStream_t s) {
     CK(launch_fft2d_angles<T>(in, out, dir, scale, argsfft<T>(p), s));
     return LAM_OK;
 }
 
+template <typename T> lam_status fbp_t(const lam_plan* p, const C<T>* d, T* u, void* ws, cudaStream_t s) {
+    NvtxRange range("lam: FBP single pass");
+    C<T>* tmp = (C<T>*)((char*)ws + p->ws_tmp);
+    if (lam_status st = fft2d<T>(p, d, tmp, -1, (T)1, s)) return st;
+    const double c0 = M_PI * std::cos(p->phi) / ((double)p->T * p->w * p->w * p->h);
+    CK(launch_ramp<T>(tmp, (long long)p->T * p->h, p->w, (T)c0, s));
+    return adj_hat<T>(p, tmp, u, ws, s);
+}
+
 // ---- ADMM state layout -------------------------------------------------------
 
 struct StateLayout {
-    size_t sc, hist, partials, counter, u, du, Gd, G0, G1, p, e, lam, dpsi, dhat, r, Lp, rlo, total;
+    size_t sc, hist, partials, counter, u, du, Gd, G0, G1, p, e, lam, dpsi, dhat, r, Lp, rlo;
+    // memoization pieces (at the end; empty when the state has no memoization)
+    size_t mkey, mnow, mval, mhit, mvalid, mscale, total;
 };
 
-StateLayout layout(const lam_plan* p) {
+// memo: the state memoizes F*_u2D (the pieces after rlo; nothing before them
+// depends on it)
+StateLayout layout(const lam_plan* p, bool memo = false) {
     StateLayout L;
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -548,7 +622,15 @@ StateLayout layout(const lam_plan* p) {
     L.dhat = take(db);
     L.r = take(db);
     L.Lp = take(db);
-    L.rlo = take(db);  // low part of the compensated residual (LAM_RESID_COMPENSATED)
+    L.rlo = take(p->prec == LAM_F32 ? db : 0);  // low part of the compensated residual (FP32 only)
+    const size_t nj = memo ? (size_t)p->njobs_pair : 0;
+    const size_t nk = (size_t)4 * p->memo_K;
+    L.mkey = take(nj * nk * p->elem());
+    L.mnow = take(nj * nk * p->elem());
+    L.mval = take(nj * p->n1 * p->n2 * p->celem());
+    L.mhit = take(nj * sizeof(int));
+    L.mvalid = take(nj * sizeof(int));
+    L.mscale = take(nj * sizeof(double));
     L.total = o;
     return L;
 }
@@ -569,10 +651,15 @@ template <typename T> struct StatePtrs {
     C<T>*dhat, *r, *Lp, *rlo;
     AdmmRed red;
     double* hist;
+    // memoization (null without it)
+    T *mkey, *mnow;
+    C<T>* mval;
+    int *mhit, *mvalid;
+    double* mscale;
 };
 
-template <typename T> StatePtrs<T> ptrs(const lam_plan* p, void* state) {
-    const StateLayout L = layout(p);
+template <typename T> StatePtrs<T> ptrs(const lam_plan* p, void* state, bool memo = false) {
+    const StateLayout L = layout(p, memo);
     char* b = (char*)state;
     StatePtrs<T> s;
     s.u = (T*)(b + L.u);
@@ -592,6 +679,12 @@ template <typename T> StatePtrs<T> ptrs(const lam_plan* p, void* state) {
     s.red.partials = (double*)(b + L.partials);
     s.red.counter = (unsigned int*)(b + L.counter);
     s.hist = (double*)(b + L.hist);
+    s.mkey = memo ? (T*)(b + L.mkey) : nullptr;
+    s.mnow = memo ? (T*)(b + L.mnow) : nullptr;
+    s.mval = memo ? (C<T>*)(b + L.mval) : nullptr;
+    s.mhit = memo ? (int*)(b + L.mhit) : nullptr;
+    s.mvalid = memo ? (int*)(b + L.mvalid) : nullptr;
+    s.mscale = memo ? (double*)(b + L.mscale) : nullptr;
     return s;
 }
 
@@ -609,15 +702,19 @@ template <typename T> Admm<T> admm_ops(const lam_plan* p) {
 
 template <typename T>
 lam_status admm_init_t(const lam_plan* p, void* state, const void* d, double alpha, double rho, int adapt,
-                       int form, cudaStream_t s) {
-    const StateLayout L = layout(p);
-    StatePtrs<T> S = ptrs<T>(p, state);
+                       int form, bool memo, cudaStream_t s) {
+    const StateLayout L = layout(p, memo);
+    StatePtrs<T> S = ptrs<T>(p, state, memo);
+    if (memo) {
+        CK(cudaMemsetAsync(S.mkey, 0, (size_t)p->njobs_pair * 4 * p->memo_K * sizeof(T), s));
+        CK(cudaMemsetAsync(S.mvalid, 0, (size_t)p->njobs_pair * sizeof(int), s));
+    }
     const size_t vb = (size_t)p->nvox() * p->elem();
     CK(cudaMemsetAsync(S.u, 0, vb, s));
     CK(cudaMemsetAsync(S.p, 0, vb, s));
     CK(cudaMemsetAsync(S.e, 0, 3 * vb, s));
     CK(cudaMemsetAsync(S.lam, 0, 3 * vb, s));
-    CK(cudaMemsetAsync(S.rlo, 0, (size_t)p->ndata() * p->celem(), s));
+    if (p->prec == LAM_F32) CK(cudaMemsetAsync(S.rlo, 0, (size_t)p->ndata() * p->celem(), s));
     (void)L;
     // Algorithm 2 works on d_hat = F_2D d with the Parseval weight 1/(hw);
     // Algorithm 1 keeps d in the data space (the slot holds d) with weight 1
@@ -637,8 +734,29 @@ lam_status admm_init_t(const lam_plan* p, void* state, const void* d, double alp
 }
 
 template <typename T>
-lam_status admm_step_t(const lam_plan* p, void* state, void* ws, int n_inner, int form, int resid, cudaStream_t s) {
-    StatePtrs<T> S = ptrs<T>(p, state);
+lam_status admm_step_t(const lam_plan* p, void* state, void* ws, int n_inner, int form, int resid, double memo_tau,
+                       cudaStream_t s) {
+    NvtxRange range("lam: ADMM outer iteration");
+    const bool memo = memo_tau > 0 && form == 2;
+    StatePtrs<T> S = ptrs<T>(p, state, memo);
+    MemoState<T> M{};
+    if (memo) {
+        M.key = S.mkey;
+        M.now = S.mnow;
+        M.val = S.mval;
+        M.m.njobs = p->njobs_pair;
+        M.m.K = p->memo_K;
+        M.m.jobs = p->jobs_pair;
+        M.m.samples = p->memo_samples;
+        M.m.h = p->h;
+        M.m.w = p->w;
+        M.m.plane = (long long)p->n1 * p->n2;
+        M.m.tau = memo_tau;
+        M.m.hit = S.mhit;
+        M.m.valid = S.mvalid;
+        M.m.scale = S.mscale;
+        M.m.stats = S.red.sc + SC_MEMO_HITS;
+    }
     const Admm<T> ops = admm_ops<T>(p);
     const long long nd = p->ndata();
     const T sc = (T)(1.0 / ((double)p->h * p->w));
@@ -674,7 +792,7 @@ lam_status admm_step_t(const lam_plan* p, void* state, void* ws, int n_inner, in
                     CK(cudaMemsetAsync(S.rlo, 0, (size_t)nd * sizeof(C<T>), s));
             }
             // adjoint pass: G = Re L_hat^H r / (hw) - rho div(grad u - g)
-            if ((st = adj_hat<T>(p, S.r, S.Gd, ws, s))) return st;
+            if ((st = adj_hat<T>(p, S.r, S.Gd, ws, s, memo ? &M : nullptr))) return st;
         }
         CK(ops.lsp_G(S.Gd, S.du, S.e, S.lam, S.p, Gp, Gc, i == 0, S.red, s));
         // CG direction and its forward pass
@@ -685,6 +803,7 @@ lam_status admm_step_t(const lam_plan* p, void* state, void* ws, int n_inner, in
         CK(ops.lsp_update(S.du, S.u, S.p, i == 0, i == n_inner - 1, S.r,
                           form == 2 && (resid & LAM_RESID_COMPENSATED) ? S.rlo : nullptr, S.Lp, nd, S.red, s));
     }
+    NvtxRange rsp("lam: RSP, multiplier, penalty");
     CK(ops.rsp(S.u, S.du, S.e, S.lam, S.dpsi, S.red, S.hist, kHistCap, s));
     return LAM_OK;
 }
@@ -752,7 +871,9 @@ template <typename T> lam_status batch_build(lam_batch* b) {
         const int gx[kBStages] = {q->n1 * (q->n2 / q->TYf),          q->n1 / q->RB, q->M2 / q->CB,
                                   (q->M1 / q->TG) * (q->M2 / q->TG), (q->M1 / q->TS) * (q->M2 / q->TS),
                                   q->M2 / q->CB,                     q->n1 / q->RB, q->n1 * (q->n2 / q->TYa)};
-        const int gy[kBStages] = {1, nj, nj, nj, nj, nj, nj, 1};
+        const int nacc = std::min(q->nacc, nj);  // centre jobs the exact spread takes (own launches)
+        H->a2[i].nacc = nacc;
+        const int gy[kBStages] = {1, nj, nj, nj, nj - nacc, nj, nj, 1};
         const int gz[kBStages] = {1, 1, 1, 2, 1, 1, 1, 1};
         const size_t sm[kBStages] = {(size_t)q->TYf * fpad_len(q->nz) * ce,
                                      (size_t)q->RB * fpad_len(q->M2) * ce,
@@ -811,6 +932,18 @@ lam_status batch_adj_hat(const lam_batch* b, const void* const* in, void* const*
     }
     BatchTable<T>* dev = (BatchTable<T>*)b->dev;
     CK(launch_batch_ptrs<T>(dev, ptrs, b->count, s));
+    // centre plane jobs with exact accumulation (LAM_OPT_EXACT_CENTRE_JOBS), per
+    // problem, as the single-plan adjoint does; the batched tile spread skips them
+    for (int i = 0; i < b->count; ++i) {
+        const lam_plan* q = b->plans[i];
+        const int nacc = std::min(q->nacc, q->njobs_pair);
+        if (nacc <= 0) continue;
+        Usfft2dArgs<T> a = args2d<T>(q, true);
+        a.spread = kSpreadTiles;  // the batch spreads with tiles whatever the plan's choice
+        a.maxabs = maxabs_slot<T>(q, b->ws[i]);
+        CK(launch_absmax<T>((const C<T>*)in[i], q->ndata(), (T*)a.maxabs, s));
+        CK(launch_spread2d<T>((const C<T>*)in[i], (C<T>*)((char*)b->ws[i] + q->ws_planes), 0, nacc, a, s));
+    }
     for (int st : {(int)kBSpread, (int)kBColAdj, (int)kBRowAdj})
         CK(launch_batch_plane<T>(dev, st, b->mixed, b->m, b->L[st], s));
     CK(launch_batch_z<T>(dev, false, b->mixed, b->L[kBZAdj], s));
@@ -973,6 +1106,11 @@ lam_status lam_plan_create(lam_plan** out, int n, int nz, int det_h, int det_w, 
     p->m = half_width;
     p->R = oversample;
     p->prec = prec;
+    // FP32 defaults (measured on the 512^3 workload, FP32 vs FP64 ADMM-TV):
+    // the centre plane jobs spread exactly and the LSP residual carried in a
+    // compensated pair.  FP64 sums need neither.
+    p->nacc = prec == LAM_F32 ? kDefaultExactCentreJobs : 0;
+    p->resid = prec == LAM_F32 ? LAM_RESID_COMPENSATED : 0;
     p->phi = phi;
     p->M0 = 2 * nz;
     p->M1 = 2 * n;
@@ -1084,6 +1222,10 @@ lam_status lam_plan_set_option(lam_plan* p, int option, int value) {
             if (value != 1 && value != 2) return fail(LAM_EINVAL, "LSP form %d: 1 or 2", value);
             p->lsp_form = value;
             return LAM_OK;
+        case LAM_OPT_MEMO_TAU:
+            if (value < 0 || value >= 10000) return fail(LAM_EINVAL, "memo threshold %d: 0 (off) or tau * 10000 in [1, 9999]", value);
+            p->memo_tau = value / 10000.0;
+            return LAM_OK;
         case LAM_OPT_EXACT_CENTRE_JOBS:
             if (value < 0) return fail(LAM_EINVAL, "exact centre jobs %d < 0", value);
             p->nacc = value;
@@ -1182,6 +1324,14 @@ lam_status lam_adjoint(const lam_plan* p, const void* d, void* u, void* ws, void
     return lam_adjoint_hat(p, tmp, u, ws, stream);
 }
 
+lam_status lam_fbp(const lam_plan* p, const void* d, void* u, void* ws, void* stream) {
+    if (lam_status st = check_plan(p)) return st;
+    if (!d || !u || !ws) return fail(LAM_EINVAL, "NULL array argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    return DISPATCH(p, fbp_t<float>(p, (const C<float>*)d, (float*)u, ws, s),
+                    fbp_t<double>(p, (const C<double>*)d, (double*)u, ws, s));
+}
+
 lam_status lam_fft2d(const lam_plan* p, const void* in, void* out, int inverse, void* stream) {
     if (lam_status st = check_plan(p)) return st;
     if (!in || !out) return fail(LAM_EINVAL, "NULL array argument");
@@ -1274,7 +1424,7 @@ lam_status lamx_bounds_selftest(const lam_plan* p, int index, void* stream) {
 lam_status admm_state_bytes(const lam_plan* p, size_t* bytes) {
     if (lam_status st = check_plan(p)) return st;
     if (!bytes) return fail(LAM_EINVAL, "bytes is NULL");
-    *bytes = layout(p).total;
+    *bytes = layout(p, p->lsp_form == 2 && p->memo_tau > 0).total;
     return LAM_OK;
 }
 
@@ -1294,10 +1444,12 @@ lam_status admm_init(const lam_plan* p, void* state, const void* d, double alpha
         h.n_inner = n_inner;
         h.ws = ws;
         h.form = p->lsp_form;
-        h.resid = p->resid;
+        h.resid = p->prec == LAM_F32 ? p->resid : (p->resid & LAM_RESID_REFRESH);  // no lo part in FP64
+        h.memo_tau = p->lsp_form == 2 ? p->memo_tau : 0.0;
     }
-    return DISPATCH(p, admm_init_t<float>(p, state, d, alpha, rho, adapt_rho, p->lsp_form, s),
-                    admm_init_t<double>(p, state, d, alpha, rho, adapt_rho, p->lsp_form, s));
+    const bool memo = p->lsp_form == 2 && p->memo_tau > 0;
+    return DISPATCH(p, admm_init_t<float>(p, state, d, alpha, rho, adapt_rho, p->lsp_form, memo, s),
+                    admm_init_t<double>(p, state, d, alpha, rho, adapt_rho, p->lsp_form, memo, s));
 }
 
 static lam_status lookup(const lam_plan* p, void* state, AdmmHost** h) {
@@ -1314,8 +1466,8 @@ lam_status admm_step(const lam_plan* p, void* state, void* ws, void* stream) {
     AdmmHost* h;
     if (lam_status st = lookup(p, state, &h)) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    return DISPATCH(p, admm_step_t<float>(p, state, ws, h->n_inner, h->form, h->resid, s),
-                    admm_step_t<double>(p, state, ws, h->n_inner, h->form, h->resid, s));
+    return DISPATCH(p, admm_step_t<float>(p, state, ws, h->n_inner, h->form, h->resid, h->memo_tau, s),
+                    admm_step_t<double>(p, state, ws, h->n_inner, h->form, h->resid, h->memo_tau, s));
 }
 
 lam_status admm_run(const lam_plan* p, void* state, void* ws, int iters, int use_graph, void* stream) {
@@ -1730,6 +1882,7 @@ lam_status admm_run_batched(lam_batch* b, void* const* states, int iters, int us
         if (n_inner >= 0 && h->n_inner != n_inner)
             return fail(LAM_EINVAL, "state %d: every state of a batch needs the same number of CG steps", i);
         if (h->form != 2) return fail(LAM_EUNSUPPORTED, "state %d: batched ADMM runs the Algorithm 2 form", i);
+        if (h->memo_tau > 0) return fail(LAM_EUNSUPPORTED, "state %d: batched ADMM does not memoize", i);
         if (h->resid & LAM_RESID_REFRESH)
             return fail(LAM_EUNSUPPORTED, "state %d: batched ADMM carries the residual (no per-LSP refresh)", i);
         resid[i] = h->resid;

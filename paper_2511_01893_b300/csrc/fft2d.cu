@@ -89,6 +89,28 @@ cudaError_t launch_fft2d_angles(const C<T>* in, C<T>* out, int dir, T scale, con
     return cudaGetLastError();
 }
 
+// FBP ramp: io[th][kv][iu] *= c0 * |iu - w/2| (c0 / 4 at iu = w/2), in place
+// on the centred spectrum F_2D d; n_rows = T h rows of w values
+template <typename T>
+__global__ void __launch_bounds__(256) k_ramp(C<T>* __restrict__ io, long long n_rows, int w, T c0) {
+    const long long n = n_rows * w;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int iu = (int)(i % w);
+        const int k = iu - w / 2;
+        const T r = k == 0 ? (T)0.25 : (T)(k < 0 ? -k : k);
+        io[i] = cscale(io[i], c0 * r);
+    }
+}
+
+template <typename T> cudaError_t launch_ramp(C<T>* io, long long n_rows, int w, T c0, cudaStream_t s) {
+    const long long n = n_rows * w;
+    const long long b = (n + 255) / 256;
+    k_ramp<T><<<(int)(b < 148 * 8 ? b : 148 * 8), 256, 0, s>>>(io, n_rows, w, c0);
+    return cudaGetLastError();
+}
+template cudaError_t launch_ramp<float>(C<float>*, long long, int, float, cudaStream_t);
+template cudaError_t launch_ramp<double>(C<double>*, long long, int, double, cudaStream_t);
+
 template <typename T> cudaError_t configure_fft2d() {
     const int mx = kMaxDynSmem;
     cudaError_t e = cudaSuccess;

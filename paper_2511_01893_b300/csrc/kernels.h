@@ -86,6 +86,8 @@ template <typename T> struct Usfft2dArgs {
                                     // the paired job list puts first) spread with exact
                                     // fixed-point accumulation instead
     int* err;                       // the plan's error word (index checks, LAM_BOUNDS_CHECK builds)
+    const int* memo_hit;            // adjoint with memoization: per plane job (absolute index), nonzero
+                                    // = served from the cache, so the spread and inverse FFTs skip it
 };
 
 // forward: plane jobs j0 .. j0 + nb - 1 of u1 ([h][n1][n2]) -> out ([T][h][w]),
@@ -104,6 +106,29 @@ cudaError_t launch_spread2d(const C<T>* in, C<T>* P, int j0, int nb, const Usfft
 template <typename T>
 cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int kv0, int nb,
                                const Usfft2dArgs<T>& a, cudaStream_t s);
+
+// ---- memoization of F*_u2D per plane job ------------------------------------------
+struct MemoArgs {
+    int njobs, K;          // plane jobs; key samples per plane
+    const int2* jobs;      // the paired job list
+    const int* samples;    // [K] sample positions th * w + ku within a plane
+    int h, w;
+    long long plane;       // n1 * n2 (values per u1 plane)
+    double tau;            // reuse when the cosine similarity of the keys exceeds tau
+    int* hit;              // [njobs] this call: 1 = served from the cache
+    int* valid;            // [njobs] the slot holds a value
+    double* scale;         // [njobs] least-squares factor <now, cached> / |cached|^2 of a hit
+    double* stats;         // [2]: hits, lookups (accumulated)
+};
+// keys of this call's input, gate against the cached keys: key[j] holds
+// 2 planes x K complex samples (the mirror plane's half is zero when unpaired)
+template <typename T>
+cudaError_t launch_memo_lookup(const C<T>* in, T* key_cached, T* key_now, const MemoArgs& m, cudaStream_t s);
+// after the plane stage: hits copy the cached plane (times the factor) into u1,
+// misses store the computed plane and their key in the slot
+template <typename T>
+cudaError_t launch_memo_update(C<T>* u1, C<T>* val, T* key_cached, const T* key_now, const MemoArgs& m,
+                               cudaStream_t s);
 
 // max(|re|, |im|) over n complex values into the device scalar *out
 template <typename T>
@@ -124,6 +149,9 @@ template <typename T> struct Fft2dArgs {
 template <typename T>
 cudaError_t launch_fft2d_angles(const C<T>* in, C<T>* out, int dir, T scale, const Fft2dArgs<T>& a,
                                 cudaStream_t s);
+// FBP ramp along the detector's u frequency, in place on [n_rows][w]:
+// value *= c0 |ku| with |ku| read as 1/4 at ku = 0 (ku = iu - w/2)
+template <typename T> cudaError_t launch_ramp(C<T>* io, long long n_rows, int w, T c0, cudaStream_t s);
 
 // ---- batched operators -------------------------------------------------------
 // A batch runs the plane-stage operators of up to kMaxBatch plans (of one

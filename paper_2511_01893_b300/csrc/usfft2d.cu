@@ -186,7 +186,8 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_fwd_pipe(C<T>* __restric
 
 // transpose: every row is loaded; the n1 rows the crop keeps are stored
 template <typename T, bool MIXED, int NC = 0>
-__global__ void __launch_bounds__(kFftThreads) k_colfft_adj_pipe(C<T>* __restrict__ P, Usfft2dArgs<T> a, int nb) {
+__global__ void __launch_bounds__(kFftThreads) k_colfft_adj_pipe(C<T>* __restrict__ P, Usfft2dArgs<T> a, int nb,
+                                                                int j0) {
     const int n1 = NC ? NC / 2 : a.n1, M1 = NC ? NC : a.M1;  // the FFT axis (x)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int LS = fpad_len(M1);
@@ -194,13 +195,16 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_adj_pipe(C<T>* __restric
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int lcb = ilog2_pow2(a.CB);
     const int ncg = a.M2 / a.CB, total = ncg * nb;
+    // plane jobs served from the memoization cache are not loaded or transformed
+    auto skipped = [&](int w) { return a.memo_hit && a.memo_hit[j0 + w / ncg]; };
     auto issue = [&](int w, C<T>* bb) {
         const int b = w / ncg, c0 = (w - b * ncg) * a.CB;
         const C<T>* pl = P + (size_t)b * M1 * a.M2 + c0;
-        for (int i = tid; i < M1 * a.CB; i += nthr) {
-            const int j = i >> lcb, c = i - (j << lcb);
-            cp_async_elem<T>(bb + c * LS + fpad(j), pl + (size_t)j * a.M2 + c);
-        }
+        if (!skipped(w))
+            for (int i = tid; i < M1 * a.CB; i += nthr) {
+                const int j = i >> lcb, c = i - (j << lcb);
+                cp_async_elem<T>(bb + c * LS + fpad(j), pl + (size_t)j * a.M2 + c);
+            }
         cp_async_commit();
     };
     int k = 0;
@@ -212,13 +216,15 @@ __global__ void __launch_bounds__(kFftThreads) k_colfft_adj_pipe(C<T>* __restric
         else cp_async_commit();
         cp_async_wait_prev();
         __syncthreads();
-        fft_lines<+1, T, MIXED, NC>(cur, a.CB, LS, M1, a.fcM1, a.tw, a.tw1);
-        const int b = w / ncg, c0 = (w - b * ncg) * a.CB;
-        C<T>* pl = P + (size_t)b * M1 * a.M2 + c0;
-        for (int i = tid; i < n1 * a.CB; i += nthr) {
-            const int x = i >> lcb, c = i - (x << lcb);
-            const int row = wrap(x - n1 / 2, M1);
-            pl[(size_t)row * a.M2 + c] = cur[c * LS + fpad(row)];
+        if (!skipped(w)) {  // block-uniform
+            fft_lines<+1, T, MIXED, NC>(cur, a.CB, LS, M1, a.fcM1, a.tw, a.tw1);
+            const int b = w / ncg, c0 = (w - b * ncg) * a.CB;
+            C<T>* pl = P + (size_t)b * M1 * a.M2 + c0;
+            for (int i = tid; i < n1 * a.CB; i += nthr) {
+                const int x = i >> lcb, c = i - (x << lcb);
+                const int row = wrap(x - n1 / 2, M1);
+                pl[(size_t)row * a.M2 + c] = cur[c * LS + fpad(row)];
+            }
         }
         __syncthreads();
     }
@@ -247,6 +253,7 @@ __device__ __forceinline__ void k_rowfft_adj_body(const C<T>* __restrict__ P, C<
     const int n2 = NC ? NC / 2 : a.n2, M2 = NC ? NC : a.M2;  // the FFT axis (y)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C<T>* bufa = reinterpret_cast<C<T>*>(smem_raw);
+    if (a.memo_hit && a.memo_hit[j0 + by]) return;  // the cached plane is copied into u1 instead
     const int b = by, kv = a.jobs[j0 + b].x;
     const int x0 = bx * a.RB;
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -624,6 +631,7 @@ __global__ void __launch_bounds__(TPB * 32, TPB >= 16 ? (sizeof(T) == 4 ? 2 : 1)
     const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, Usfft2dArgs<T> a) {
     constexpr int nt = 2 * MH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (a.memo_hit && a.memo_hit[j0 + blockIdx.y]) return;  // served from the memoization cache
     const int TS = a.TS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_y = a.M2 / TS;
@@ -788,6 +796,7 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
     C<T>* r_wyv = reinterpret_cast<C<T>*>(recb) + (size_t)warp * nt * kRecPitch;
     Rec* r_rec = reinterpret_cast<Rec*>(recb + (size_t)NW * nt * kRecPitch * sizeof(C<T>)) +
                  (size_t)warp * RPP * kRecPitch;
+    if (a.memo_hit && a.memo_hit[j0 + by]) return;  // served from the memoization cache (block-uniform)
     for (int i = lane; i < ncell; i += 32) mine[i] = cmake<T>(0, 0);
     __syncwarp();
     const int tiles_y = a.M2 / TS;
@@ -1174,7 +1183,7 @@ constexpr int kSpreadWarps = 2;
     } while (0)
 #define LAM_RF(NC) k_rowfft_fwd<T, false, NC><<<dim3(a.n1 / a.RB, nb), a.fthr, sr, s>>>(u1, P, kv0, a)
 #define LAM_CF(NC) k_colfft_fwd_pipe<T, false, NC><<<gp, a.fthr, 2 * sc, s>>>(P, a, nb)
-#define LAM_CA(NC) k_colfft_adj_pipe<T, false, NC><<<gp, a.fthr, 2 * sc, s>>>(P, a, nb)
+#define LAM_CA(NC) k_colfft_adj_pipe<T, false, NC><<<gp, a.fthr, 2 * sc, s>>>(P, a, nb, kv0)
 #define LAM_RA(NC) k_rowfft_adj<T, false, NC><<<dim3(a.n1 / a.RB, nb), a.fthr, sr, s>>>(P, u1, kv0, a)
 
 template <typename T>
@@ -1335,7 +1344,7 @@ cudaError_t launch_usfft2d_adj(const C<T>* in, C<T>* P, C<T>* u1, int j0, int nb
     if (e != cudaSuccess) return e;
     const int gp = pipe_grid((a.M2 / a.CB) * nb, a.fthr, 2 * sc);
     if (fft_mixed(a.fcM1) || fft_mixed(a.fcM2)) {
-        k_colfft_adj_pipe<T, true><<<gp, a.fthr, 2 * sc, s>>>(P, a, nb);
+        k_colfft_adj_pipe<T, true><<<gp, a.fthr, 2 * sc, s>>>(P, a, nb, kv0);
         k_rowfft_adj<T, true><<<dim3(a.n1 / a.RB, nb), a.fthr, sr, s>>>(P, u1, kv0, a);
     } else {
         LAM_PLANE_NC(a.M1, LAM_CA);
@@ -1492,7 +1501,9 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) kb_spread(con
             cur = p;
         }
         const int l = w - st[p], gx = bt->gx[kBSpread][p];
-        k_spread2d_tiles_body<T, NW, MH>((const C<T>*)bt->in[p], bt->P[p], 0, sa, l % gx, l / gx);
+        // the problem's first sa.nacc plane jobs were spread exactly by their own launches
+        k_spread2d_tiles_body<T, NW, MH>((const C<T>*)bt->in[p], bt->P[p] + (size_t)sa.nacc * sa.M1 * sa.M2, sa.nacc,
+                                         sa, l % gx, l / gx);
         __syncthreads();
     }
 }

@@ -21,7 +21,7 @@ LIB_PATH = os.environ.get("LAMINO_LIB") or os.path.join(_HERE, "liblamino.so")
 
 LAM_F32, LAM_F64 = 0, 1
 NSCALARS = 16
-SC = dict(rho=0, alpha=1, objective=2, r=3, s=4, iter=5, data2=6, tv=7, status=8)
+SC = dict(rho=0, alpha=1, objective=2, r=3, s=4, iter=5, data2=6, tv=7, status=8, memo_hits=9, memo_lookups=10)
 
 _lib = None
 
@@ -47,6 +47,7 @@ def lib() -> ctypes.CDLL:
             "lam_forward_hat": [vp, vp, vp, vp, vp, vp],
             "lam_adjoint_hat": [vp, vp, vp, vp, vp],
             "lam_fft2d": [vp, vp, vp, i, vp],
+            "lam_fbp": [vp, vp, vp, vp, vp],
             "tv_grad": [vp, vp, vp, vp],
             "tv_div": [vp, vp, vp, vp],
             "tv_smooth": [vp, vp, d, vp, ctypes.POINTER(d), vp, vp],
@@ -244,6 +245,14 @@ class Plan:
                "lam_adjoint_hat")
         return out
 
+    def fbp(self, d, out=None):
+        """FBP-style single pass: Re L_hat^H of the ramp-filtered F_2D d (lam_fbp)."""
+        self._need_full("fbp")
+        d = self._inp(d, self.cdtype, self.data_shape)
+        out = self._vol() if out is None else out
+        _check(lib().lam_fbp(self._h, _ptr(d), _ptr(out), _ptr(self.ws), _stream()), "lam_fbp")
+        return out
+
     def fft2d(self, x, inverse=False, out=None):
         x = self._inp(x, self.cdtype, self.data_shape)
         out = self._data() if out is None else out
@@ -331,6 +340,14 @@ class Plan:
     def job_planes(self, j0, nb):
         """Data planes (kv rows) plane jobs j0 .. j0 + nb - 1 cover."""
         return lib().lamx_job_planes(self._h, int(j0), int(nb))
+
+    def set_memo(self, tau):
+        """Memoization of F*_u2D per plane job in ADMM states created after this
+        call (LAM_OPT_MEMO_TAU): reuse a job's cached plane when the cosine
+        similarity of its keys exceeds tau; tau = 0 turns it off."""
+        v = int(round(float(tau) * 10000))
+        _check(lib().lam_plan_set_option(self._h, 8, v), "lam_plan_set_option")
+        return self
 
     def set_exact_centre_jobs(self, count):
         """Plane jobs nearest the centre plane whose adjoint tile spread
@@ -435,16 +452,18 @@ class Admm:
 
     RESID = {"carry": 0, "refresh": 1, "compensated": 2, "refresh+compensated": 3}
 
-    def init(self, d, alpha, rho, n_inner=4, adapt_rho=True, form=2, resid="carry"):
+    def init(self, d, alpha, rho, n_inner=4, adapt_rho=True, form=2, resid=None):
         """form: the LSP form, 2 (Algorithm 2, default) or 1 (Algorithm 1).
         resid: how the Algorithm 2 residual is kept (LAM_OPT_RESIDUAL): "carry"
         (by linearity across LSPs), "refresh" (evaluated afresh at each LSP
-        start), "compensated" (carried as a hi + lo pair) or both."""
+        start), "compensated" (carried as a hi + lo pair) or both; None keeps
+        the plan's setting (compensated for FP32, carry for FP64)."""
         d = self.plan._inp(d, self.plan.cdtype, self.plan.data_shape)
-        if resid not in self.RESID:
+        if resid is not None and resid not in self.RESID:
             raise LaminoError(f"resid must be one of {sorted(self.RESID)}")
         _check(lib().lam_plan_set_option(self.plan._h, 3, int(form)), "lam_plan_set_option")
-        _check(lib().lam_plan_set_option(self.plan._h, 6, self.RESID[resid]), "lam_plan_set_option")
+        if resid is not None:
+            _check(lib().lam_plan_set_option(self.plan._h, 6, self.RESID[resid]), "lam_plan_set_option")
         _check(lib().admm_init(self.plan._h, _ptr(self.state), _ptr(d), float(alpha), float(rho), int(n_inner),
                                int(bool(adapt_rho)), _ptr(self.plan.ws), _stream()), "admm_init")
         self.iters = 0
@@ -511,6 +530,17 @@ class Admm:
         for k in ("d_hat", "r", "Lp", "r_lo"):
             out[k] = view(k, nd, csz, p.cdtype, dat)
         return out
+
+    def log_jsonl(self, path, **extra) -> int:
+        """Append one JSON line per outer iteration done so far (iteration,
+        objective, rho used, primal and dual residuals, plus `extra` keys) to
+        `path`; returns the number of lines written (synchronises)."""
+        import json
+        h = self.history()
+        with open(path, "a", encoding="utf-8") as f:
+            for k, (obj, rho, r, s) in enumerate(h):
+                f.write(json.dumps({"iter": k + 1, "objective": obj, "rho": rho, "r": r, "s": s, **extra}) + "\n")
+        return len(h)
 
     def graph_kernels(self) -> int:
         """Kernel launches per outer iteration in the captured graph (0 before a graph run)."""

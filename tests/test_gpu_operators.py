@@ -227,3 +227,28 @@ def test_hat_workspace_serves_the_hat_operators():
     assert torch.equal(hat.forward(u), full.forward(u))
     with pytest.raises(glam.LaminoError, match="full workspace"):
         hat.adjoint(d)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
+@pytest.mark.parametrize("geom", [GEOMS[0], GEOMS[2], GEOMS[3], GEOMS[5]], ids=["cube16", "mixed64", "phi0", "radix3"])
+def test_fbp_single_pass(geom, prec):
+    # the one-pass baseline lam_fbp against the oracle's FBP on random data
+    n, nz, h, w, T, phi = geom
+    plan, g = plan_and_geom(n, nz, h, w, T, phi, prec)
+    d = rand_data(T, h, w, 7)
+    ref = olam.fbp(d, g)
+    got = plan.fbp(torch.from_numpy(d)).cpu().numpy()
+    assert rel(got, ref) < tol(prec)
+
+
+def test_fbp_of_the_forward_recovers_a_z_elongated_blob():
+    # GPU end to end: FP32 L then FBP at 32^3, phi = 30 deg (the oracle pin's case)
+    n, T = 32, 64
+    plan, g = plan_and_geom(n, n, n, n, T, np.deg2rad(30.0), "f32")
+    x = np.arange(n) - n // 2
+    X, Z, Y = np.meshgrid(x, x, x, indexing="ij")
+    u = np.exp(-((X - 1.3) ** 2 + (Y - 2.1) ** 2) / (2 * 2.5 ** 2) - (Z + 0.7) ** 2 / (2 * 8.0 ** 2))
+    r = plan.fbp(plan.forward(torch.from_numpy(u))).cpu().numpy()
+    ref = olam.fbp(olam.lam_forward(u, g), g)
+    assert rel(r, ref) < TOL_F32_OP
+    assert rel(r, u) < 0.09
