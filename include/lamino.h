@@ -92,6 +92,10 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *   LAM_SPREAD_HALO    per-warp tiles extended by a halo: each slice point is
  *                      visited once (by the tile of its window origin); the
  *                      halos are summed in a second pass; reproducible.
+ *   LAM_SPREAD_TILES_EXACT  the tile spread with 64-bit fixed-point cells
+ *                      (as LAM_SPREAD_EXACT, integer read-add-writes instead of
+ *                      atomics): exact sums of the rounded products,
+ *                      reproducible; the exact centre jobs use it too.
  * LAM_OPT_FAST_ADJOINT: value != 0 selects LAM_SPREAD_ATOMIC, 0 the default.
  * LAM_OPT_LSP_FORM (default 2) is the LSP form that ADMM states initialised
  *   afterwards use: 2 = Algorithm 2 (operation cancellation: the LSP works on
@@ -118,7 +122,7 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *   with |kv - h/2| <= 2, and 0 for FP64) is the number of plane jobs nearest
  *   the centre plane kv = h/2 (the paired adjoint treats planes kv and h - kv
  *   as one job, centre first) whose tile spread (LAM_SPREAD_TILES) accumulates
- *   in exact fixed point (as LAM_SPREAD_EXACT) instead of FP32.  Near the
+ *   in exact fixed point (as LAM_SPREAD_TILES_EXACT) instead of FP32.  Near the
  *   centre every slice line passes close to the origin, so the cells there sum
  *   thousands of nearly equal products, which FP32 running sums round
  *   systematically; these few jobs carry most of the energy of L^H applied to
@@ -146,7 +150,7 @@ enum {
     LAM_OPT_MEMO_TAU = 8
 };
 enum { LAM_RESID_REFRESH = 1, LAM_RESID_COMPENSATED = 2 };
-enum { LAM_SPREAD_TILES = 0, LAM_SPREAD_ATOMIC = 1, LAM_SPREAD_EXACT = 2, LAM_SPREAD_HALO = 3 };
+enum { LAM_SPREAD_TILES = 0, LAM_SPREAD_ATOMIC = 1, LAM_SPREAD_EXACT = 2, LAM_SPREAD_HALO = 3, LAM_SPREAD_TILES_EXACT = 4 };
 lam_status lam_plan_set_option(lam_plan* plan, int option, int value);
 
 /* Autotuner (a set-up call; synchronises `stream`, not under capture): times

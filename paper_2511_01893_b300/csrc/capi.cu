@@ -526,7 +526,8 @@ template <typename T> lam_status prep_scatter(const lam_plan* p, const C<T>* in,
                                               Usfft2dArgs<T>& a) {
     // the exact spread runs when chosen, and for the tile spread's small-plane
     // fallback (tiles narrower than 32)
-    const bool exact = p->spread == kSpreadExact || ((p->spread == kSpreadTiles || p->spread == kSpreadHalo) && p->TS != 32) ||
+    const bool exact = p->spread == kSpreadExact || p->spread == kSpreadTilesExact ||
+                       ((p->spread == kSpreadTiles || p->spread == kSpreadHalo) && p->TS != 32) ||
                        (p->spread == kSpreadTiles && a.nacc > 0);
     if (!exact) return LAM_OK;
     T* mx = maxabs_slot<T>(p, ws);
@@ -1207,6 +1208,7 @@ lam_status lam_plan_set_option(lam_plan* p, int option, int value) {
             else if (value == LAM_SPREAD_ATOMIC) p->spread = kSpreadAtomic;
             else if (value == LAM_SPREAD_EXACT) p->spread = kSpreadExact;
             else if (value == LAM_SPREAD_HALO) p->spread = kSpreadHalo;
+            else if (value == LAM_SPREAD_TILES_EXACT) p->spread = kSpreadTilesExact;
             else return fail(LAM_EINVAL, "unknown adjoint spread %d", value);
             {
                 // captured ADMM graphs hold the old kernel choice

@@ -758,9 +758,24 @@ template <typename T> size_t spread_rec_bytes(int mh) {
         default: return sizeof(SpreadRec<T, 8>);
     }
 }
-template <typename T> size_t spread_tiles_smem(int nw, int mh) {
-    return (size_t)nw * kSpreadTS * kSpreadTS * sizeof(C<T>) + (size_t)nw * (2 * mh) * kRecPitch * sizeof(C<T>) +
+// exact: the tile cells are 64-bit fixed-point pairs (16 bytes) instead of complex T
+template <typename T> size_t spread_tiles_smem(int nw, int mh, bool exact = false) {
+    const size_t cell = exact ? 16 : sizeof(C<T>);
+    return (size_t)nw * kSpreadTS * kSpreadTS * cell + (size_t)nw * (2 * mh) * kRecPitch * sizeof(C<T>) +
            (size_t)nw * spread_rpp(mh) * kRecPitch * spread_rec_bytes<T>(mh);
+}
+
+__device__ __forceinline__ void lds_ll2(unsigned ad, long long& a, long long& b) {
+    asm volatile("ld.shared.v2.s64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "r"(ad) : "memory");
+}
+__device__ __forceinline__ void sts_ll2(unsigned ad, long long a, long long b) {
+    asm volatile("st.shared.v2.s64 [%0], {%1, %2};" ::"r"(ad), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ long long fixed_ll(float x) { return __float2ll_rn(x); }
+__device__ __forceinline__ long long fixed_ll(double x) { return __double2ll_rn(x); }
+template <typename T> __device__ __forceinline__ T fixed_back(long long x) {
+    if constexpr (sizeof(T) == 4) return (T)__ll2float_rn(x);
+    else return (T)__ll2double_rn(x);
 }
 
 __device__ __forceinline__ void lds_c(unsigned ad, C<float>& v) {
@@ -777,19 +792,28 @@ __device__ __forceinline__ void sts_c(unsigned ad, const C<double>& v) {
 }
 
 
-template <typename T, int NW, int MH>
+// EXACT: the warp tiles hold 64-bit fixed-point cells (each product w v scaled
+// by a power of two from a bound on the cell sums and rounded to an integer,
+// as the atomic exact spread) and are added with integer read-add-writes: the
+// exact sum of the rounded products, independent of order, without atomics.
+// 16-byte cells need no swizzle: the 8 cells of a pass row span 128 bytes.
+template <typename T, int NW, int MH, bool EXACT = false>
 __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, const Usfft2dArgs<T>& a, int bx, int by) {
     constexpr int nt = 2 * MH;
     constexpr int RPP = 32 / nt;  // window rows per pass
     constexpr int NPASS = (nt + RPP - 1) / RPP;
     constexpr int TS = kSpreadTS;
     constexpr int ncell = TS * TS;
-    constexpr unsigned kCell = sizeof(C<T>);
+    constexpr unsigned kCell = EXACT ? 16u : (unsigned)sizeof(C<T>);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     C<T>* tiles = reinterpret_cast<C<T>*>(smem_raw);  // [NW][ncell]
     C<T>* mine = tiles + (size_t)warp * ncell;
-    unsigned char* recb = smem_raw + (size_t)NW * ncell * sizeof(C<T>);
+    long long* xtiles = reinterpret_cast<long long*>(smem_raw);  // EXACT: [NW][ncell][2]
+    long long* xmine = xtiles + (size_t)warp * ncell * 2;
+    unsigned char* recb = smem_raw + (size_t)NW * ncell * kCell;
+    T fscale = (T)1, finv = (T)1;
+    if constexpr (EXACT) fixed_scale<T>(*a.maxabs, a.bound_count, fscale, finv);
     // records: wyv[sy][pitch] (complex), then rec[rr][pitch] (x weights of the
     // lane row's passes + window origin)
     typedef SpreadRec<T, NPASS> Rec;
@@ -797,7 +821,11 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
     Rec* r_rec = reinterpret_cast<Rec*>(recb + (size_t)NW * nt * kRecPitch * sizeof(C<T>)) +
                  (size_t)warp * RPP * kRecPitch;
     if (a.memo_hit && a.memo_hit[j0 + by]) return;  // served from the memoization cache (block-uniform)
-    for (int i = lane; i < ncell; i += 32) mine[i] = cmake<T>(0, 0);
+    if constexpr (EXACT) {
+        for (int i = lane; i < 2 * ncell; i += 32) xmine[i] = 0;
+    } else {
+        for (int i = lane; i < ncell; i += 32) mine[i] = cmake<T>(0, 0);
+    }
     __syncwarp();
     const int tiles_y = a.M2 / TS;
     const int tile = bx;
@@ -809,7 +837,7 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
     const bool lane_on = rr < RPP;
     const int rrc = lane_on ? rr : 0;
     // lane-constant shared addresses of the record entries this lane reads
-    const unsigned tile_ad = (unsigned)__cvta_generic_to_shared(mine);
+    const unsigned tile_ad = EXACT ? (unsigned)__cvta_generic_to_shared(xmine) : (unsigned)__cvta_generic_to_shared(mine);
     const unsigned wyv_ad = (unsigned)__cvta_generic_to_shared(r_wyv + sy * kRecPitch);
     const Rec* rec_lane = r_rec + (size_t)rrc * kRecPitch;
     const unsigned lt = (1u << lane) - 1u;
@@ -892,21 +920,30 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
                         lds_c(wyv_ad + kn * kCell, nwv);
                         const int2 o = make_int2(rc.ox, rc.oy);
                         const int cx0 = o.x + rrc, ccy = o.y + sy;
-                        const int col = ccy ^ ((cx0 & 1) << 3);
+                        const int col = EXACT ? ccy : ccy ^ ((cx0 & 1) << 3);
                         const unsigned ad0 = tile_ad + (unsigned)(cx0 * TS + col) * kCell;
                         const bool yok = lane_on && (unsigned)ccy < (unsigned)TS;
 #pragma unroll
                         for (int q = 0; q < NPASS; ++q) {
                             const int row = cx0 + q * RPP;
                             // rows q * RPP apart: same swizzle when RPP is even
-                            const unsigned ad = ((q * RPP) & 1) ? tile_ad + (unsigned)(row * TS + (col ^ 8)) * kCell
-                                                                : ad0 + (unsigned)(q * RPP * TS) * kCell;
+                            const unsigned ad = (!EXACT && ((q * RPP) & 1))
+                                                    ? tile_ad + (unsigned)(row * TS + (col ^ 8)) * kCell
+                                                    : ad0 + (unsigned)(q * RPP * TS) * kCell;
                             if (yok && q * RPP + rr < nt && (unsigned)row < (unsigned)TS) {
-                                C<T> acc;
-                                lds_c(ad, acc);
-                                acc.x = fma(rc.wx[q], wv.x, acc.x);
-                                acc.y = fma(rc.wx[q], wv.y, acc.y);
-                                sts_c(ad, acc);
+                                if constexpr (EXACT) {
+                                    long long xr, xi;
+                                    lds_ll2(ad, xr, xi);
+                                    xr += fixed_ll(rc.wx[q] * wv.x * fscale);
+                                    xi += fixed_ll(rc.wx[q] * wv.y * fscale);
+                                    sts_ll2(ad, xr, xi);
+                                } else {
+                                    C<T> acc;
+                                    lds_c(ad, acc);
+                                    acc.x = fma(rc.wx[q], wv.x, acc.x);
+                                    acc.y = fma(rc.wx[q], wv.y, acc.y);
+                                    sts_c(ad, acc);
+                                }
                             }
                         }
                         __syncwarp();
@@ -921,13 +958,24 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
     C<T>* pl = P + (size_t)b * a.M1 * a.M2;
     for (int i = threadIdx.x; i < ncell; i += blockDim.x) {
         const int ccx = i / TS, ccy = i - ccx * TS;
-        const int si = ccx * TS + swz_row(ccx, ccy);
-        C<T> sum = tiles[si];
+        C<T> sum;
+        if constexpr (EXACT) {
+            long long sr = xtiles[2 * i], si = xtiles[2 * i + 1];
 #pragma unroll
-        for (int w = 1; w < NW; ++w) {
-            const C<T> t = tiles[(size_t)w * ncell + si];
-            sum.x += t.x;
-            sum.y += t.y;
+            for (int w = 1; w < NW; ++w) {
+                sr += xtiles[((size_t)w * ncell + i) * 2];
+                si += xtiles[((size_t)w * ncell + i) * 2 + 1];
+            }
+            sum = cmake<T>(fixed_back<T>(sr) * finv, fixed_back<T>(si) * finv);
+        } else {
+            const int si = ccx * TS + swz_row(ccx, ccy);
+            sum = tiles[si];
+#pragma unroll
+            for (int w = 1; w < NW; ++w) {
+                const C<T> t = tiles[(size_t)w * ncell + si];
+                sum.x += t.x;
+                sum.y += t.y;
+            }
         }
         pl[(size_t)(tx0 + ccx) * a.M2 + ty0 + ccy] = sum;
     }
@@ -1146,7 +1194,14 @@ __global__ void __launch_bounds__(256) k_halo_sum(const C<T>* __restrict__ H, C<
 template <typename T, int NW, int MH>
 __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_tiles(
     const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, Usfft2dArgs<T> a) {
-    k_spread2d_tiles_body<T, NW, MH>(in, P, j0, a, (int)blockIdx.x, (int)blockIdx.y);
+    k_spread2d_tiles_body<T, NW, MH, false>(in, P, j0, a, (int)blockIdx.x, (int)blockIdx.y);
+}
+
+// the exact (64-bit fixed-point) tile spread
+template <typename T, int NW, int MH>
+__global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_tiles_exact(
+    const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, Usfft2dArgs<T> a) {
+    k_spread2d_tiles_body<T, NW, MH, true>(in, P, j0, a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // --------------------------------------------------------------------------
@@ -1286,7 +1341,15 @@ cudaError_t launch_spread2d(const C<T>* in, C<T>* P, int j0, int nb, const Usfft
     }
     // the tile and halo spreads are built for 32 x 32 tiles; planes smaller
     // than that (n < 16) take the exact atomic spread
-    if (a.spread == kSpreadHalo && a.TS == kSpreadTS && a.halo) {
+    if (a.spread == kSpreadTilesExact && a.TS == kSpreadTS && a.maxabs) {
+        const size_t sx = spread_tiles_smem<T>(kSpreadWarps, a.m, true);
+        switch (a.m) {
+#define LAM_X(MH) case MH: k_spread2d_tiles_exact<T, kSpreadWarps, MH><<<grid1, kSpreadWarps * 32, sx, s>>>(in, P, kv0, a); break;
+            LAM_X(2) LAM_X(3) LAM_X(4) LAM_X(5) LAM_X(6) LAM_X(7) LAM_X(8)
+#undef LAM_X
+            default: return cudaErrorInvalidValue;
+        }
+    } else if (a.spread == kSpreadHalo && a.TS == kSpreadTS && a.halo) {
         const size_t st = spread_halo_smem<T>(NW, a.m);
         switch (a.m) {
 #define LAM_H(MH) case MH: k_spread2d_halo<T, NW, MH><<<grid1, NW * 32, st, s>>>(in, a.halo, kv0, a); break;
@@ -1306,15 +1369,13 @@ cudaError_t launch_spread2d(const C<T>* in, C<T>* P, int j0, int nb, const Usfft
         const int nx = a.maxabs ? std::max(0, std::min(nb, a.nacc - j0)) : 0;
         if (nx > 0) {
             const dim3 gx(ntiles, nx);
-#define LAM_X(MH)                                                                                                   \
-    case MH:                                                                                                        \
-        k_scatter2d_atomic<T, NW, MH, 3><<<gx, NW * 32, cells * atom_acc_bytes<T, 3>(), s>>>(in, P, kv0, a);        \
-        break;
+            const size_t sx = spread_tiles_smem<T>(kSpreadWarps, a.m, true);
             switch (a.m) {
+#define LAM_X(MH) case MH: k_spread2d_tiles_exact<T, kSpreadWarps, MH><<<gx, kSpreadWarps * 32, sx, s>>>(in, P, kv0, a); break;
                 LAM_X(2) LAM_X(3) LAM_X(4) LAM_X(5) LAM_X(6) LAM_X(7) LAM_X(8)
+#undef LAM_X
                 default: return cudaErrorInvalidValue;
             }
-#undef LAM_X
         }
         if (nb > nx) {
             const size_t st = spread_tiles_smem<T>(kSpreadWarps, a.m);
@@ -1408,6 +1469,7 @@ template <typename T> cudaError_t configure_usfft2d() {
     if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 0>, at, mt);  \
     if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 3>, at, mt);    \
     if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles<T, kSpreadWarps, MH>, at, mt);    \
+    if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles_exact<T, kSpreadWarps, MH>, at, mt); \
     if (!e) e = cudaFuncSetAttribute(k_spread2d_halo<T, kScatterWarps, MH>, at, mt);
     LAM_A(2) LAM_A(3) LAM_A(4) LAM_A(5) LAM_A(6) LAM_A(7) LAM_A(8)
 #undef LAM_A

@@ -59,8 +59,9 @@ def test_memo_that_always_hits_serves_every_later_call(data):
     got, sc, njobs = _run(theta, d, 0.0001, 2)
     assert sc["memo_lookups"] == 2 * 4 * njobs
     # the first call fills every item; later calls hit unless a key turned
-    # against its item (cosine similarity below 1e-4)
-    assert sc["memo_lookups"] - njobs - 2 <= sc["memo_hits"] <= sc["memo_lookups"] - njobs
+    # against its item (cosine similarity below 1e-4: early residual planes can
+    # flip sign), and such a miss refills the item
+    assert 0.9 * (sc["memo_lookups"] - njobs) <= sc["memo_hits"] <= sc["memo_lookups"] - njobs
     assert torch.isfinite(got).all()
 
 

@@ -44,7 +44,7 @@ def test_u1d_forward_and_adjoint(geom, prec):
     assert rel(got, ref) < tol(prec)
 
 
-@pytest.mark.parametrize("spread", ["tiles", "halo", "atomic", "exact"])
+@pytest.mark.parametrize("spread", ["tiles", "halo", "atomic", "exact", "tiles_exact"])
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("geom", GEOMS, ids=IDS)
 def test_u2d_forward_and_adjoint(geom, prec, spread):
@@ -133,7 +133,7 @@ def test_adjoint_spread_variants_other_widths(m):
     plan, g = plan_and_geom(n, nz, h, w, T, 0.5, "f32", m=m)
     d = rand_data(T, h, w, 18)
     ref = olam.f_u2d_adj(d, g)
-    for spread in ("tiles", "halo", "atomic", "exact"):
+    for spread in ("tiles", "halo", "atomic", "exact", "tiles_exact"):
         p = glam.Plan(n, nz, h, w, plan.theta, 0.5, m=m, prec="f32", spread=spread)
         got = p.u2d_adj(torch.from_numpy(d)).cpu().numpy().transpose(1, 0, 2)
         assert rel(got, ref) < tol("f32"), spread
@@ -150,6 +150,11 @@ def test_adjoint_spreads_are_bitwise_reproducible():
     exact = glam.Plan(n, nz, h, w, plan.theta, 0.5, prec="f32", spread="exact")
     e1, e2 = exact.adjoint(d), exact.adjoint(d)
     assert torch.equal(e1, e2)
+    tx = glam.Plan(n, nz, h, w, plan.theta, 0.5, prec="f32", spread="tiles_exact")
+    t1, t2 = tx.adjoint(d), tx.adjoint(d)
+    assert torch.equal(t1, t2)
+    # the same products formed in another order (wx (wy v) against wy (wx v)): ~1 ulp apart
+    assert rel(t1, e1) < 3e-7
     fast = glam.Plan(n, nz, h, w, plan.theta, 0.5, prec="f32", fast_adjoint=True)
     assert rel(fast.adjoint(d), e1) < 2e-6
     assert rel(a, e1) < 2e-6
