@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--iters", type=int, default=32, help="--op precision: ADMM-TV iterations compared")
+    ap.add_argument("--spread", default=None, help="adjoint spread variant of the FP32 plans (library default if unset)")
     ap.add_argument("--taus", default="0.86,0.90,0.92,0.94,0.96", help="--op memo: thresholds")
     ap.add_argument("--op", choices=["admm", "lhat_pair", "batch", "ablation", "precision", "fbp", "memo"],
                     default="admm",
@@ -512,7 +513,8 @@ def run_op_pair(args):
     from paper_2511_01893_b300 import lamino as glam
     n = args.size
     dev = torch.device("cuda", 0)
-    plan = glam.Plan(n, n, n, n, inputs.angles(n), np.deg2rad(PHI_DEG), prec="f32", device=dev, workspace="hat")
+    plan = glam.Plan(n, n, n, n, inputs.angles(n), np.deg2rad(PHI_DEG), prec="f32", device=dev, workspace="hat",
+                     spread=args.spread)
     u = torch.rand((n, n, n), device=dev, dtype=torch.float32)
     d = torch.empty(plan.data_shape, dtype=plan.cdtype, device=dev)
     v = torch.empty_like(u)
@@ -895,7 +897,7 @@ def run_ours(args):
 
     # ---- inputs (synthetic, resident in HBM) --------------------------------
     u_true = inputs.ellipsoid_circuit_phantom(n, nz, seed=1238, device=dev, dtype=torch.float32)
-    plan = glam.Plan(n, nz, h, w, theta, phi, prec="f32", device=dev)
+    plan = glam.Plan(n, nz, h, w, theta, phi, prec="f32", device=dev, spread=args.spread)
     stream = torch.cuda.Stream(device=dev)
     stream.wait_stream(torch.cuda.current_stream(dev))  # u_true was made on the current stream
     with torch.cuda.stream(stream):
@@ -980,12 +982,17 @@ def run_ours(args):
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(prof):
         tj = json.load(open(prof))
-        # only while the kernels are the ones the counters were taken on
-        if tj.get("size") == n and tj.get("source_sha256") == source_hash():
-            # per launch: only for a launch over the same plane jobs
-            if tj.get("spread_launch_jobs") == nbj:
-                traffic = tj.get("spread_launch_dram_bytes")
-            pair_traffic = tj.get("lhat_pair_dram_bytes")
+        # only while the kernels are the ones the counters were taken on.  The
+        # counters come from a small capture (capture_size^3, a few GB on the
+        # device) and scale to this size by the units processed: a spread job's
+        # traffic (its two planes' slice values and its padded plane) grows as
+        # n^2 for T = w = h = n, the operator pair's as n^3
+        if tj.get("source_sha256") == source_hash() and tj.get("capture_size"):
+            f = n / tj["capture_size"]
+            if tj.get("spread_bytes_per_job"):
+                traffic = tj["spread_bytes_per_job"] * f ** 2 * nbj
+            if tj.get("lhat_pair_dram_bytes"):
+                pair_traffic = tj["lhat_pair_dram_bytes"] * f ** 3
     del p, out_c, out_r
     fma = glam.fma_peak(dev)
     op_flops = 2 * lhat_flops(n, nz, h, w, T)
@@ -1002,7 +1009,9 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (state ~80 GB)"},
         "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": spread_bytes / t_spread / 1e9, "peak": peak,
                      "frac": spread_bytes / t_spread / 1e9 / peak, "traffic": traffic, "peak_source": peak_src,
-                     "kernel": f"k_spread2d_tiles (adjoint spread; one launch = {nbj} plane jobs, {planes} kv planes)",
+                     "kernel": f"k_spread2d_tiles (adjoint spread; one launch = plane jobs {j0s}..{j0s + nbj - 1}, "
+                               f"{planes} kv planes)",
+                     "traffic_note": "dram bytes per job from a 512^3 capture, scaled by (n/512)^2 per job",
                      "algorithmic_bytes": spread_bytes, "t_launch_s": t_spread,
                      "note": "bound by the L1/shared pipe (ncu: 80 % of its peak), not by HBM"},
         "roofline_alu": {"bound": "alu", "unit": "TFLOP/s", "achieved": spread_flops / t_spread / 1e12,

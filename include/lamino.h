@@ -96,6 +96,9 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *                      (as LAM_SPREAD_EXACT, integer read-add-writes instead of
  *                      atomics): exact sums of the rounded products,
  *                      reproducible; the exact centre jobs use it too.
+ *   LAM_SPREAD_TILES2  the tile spread with one slice point per half-warp,
+ *                      each half-warp summing into a tile of its own (two
+ *                      tiles per warp, added in a fixed order): reproducible.
  * LAM_OPT_FAST_ADJOINT: value != 0 selects LAM_SPREAD_ATOMIC, 0 the default.
  * LAM_OPT_LSP_FORM (default 2) is the LSP form that ADMM states initialised
  *   afterwards use: 2 = Algorithm 2 (operation cancellation: the LSP works on
@@ -150,7 +153,14 @@ enum {
     LAM_OPT_MEMO_TAU = 8
 };
 enum { LAM_RESID_REFRESH = 1, LAM_RESID_COMPENSATED = 2 };
-enum { LAM_SPREAD_TILES = 0, LAM_SPREAD_ATOMIC = 1, LAM_SPREAD_EXACT = 2, LAM_SPREAD_HALO = 3, LAM_SPREAD_TILES_EXACT = 4 };
+enum {
+    LAM_SPREAD_TILES = 0,
+    LAM_SPREAD_ATOMIC = 1,
+    LAM_SPREAD_EXACT = 2,
+    LAM_SPREAD_HALO = 3,
+    LAM_SPREAD_TILES_EXACT = 4,
+    LAM_SPREAD_TILES2 = 5
+};
 lam_status lam_plan_set_option(lam_plan* plan, int option, int value);
 
 /* Autotuner (a set-up call; synchronises `stream`, not under capture): times

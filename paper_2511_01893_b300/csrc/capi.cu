@@ -527,8 +527,9 @@ template <typename T> lam_status prep_scatter(const lam_plan* p, const C<T>* in,
     // the exact spread runs when chosen, and for the tile spread's small-plane
     // fallback (tiles narrower than 32)
     const bool exact = p->spread == kSpreadExact || p->spread == kSpreadTilesExact ||
-                       ((p->spread == kSpreadTiles || p->spread == kSpreadHalo) && p->TS != 32) ||
-                       (p->spread == kSpreadTiles && a.nacc > 0);
+                       ((p->spread == kSpreadTiles || p->spread == kSpreadTiles2 || p->spread == kSpreadHalo) &&
+                        p->TS != 32) ||
+                       ((p->spread == kSpreadTiles || p->spread == kSpreadTiles2) && a.nacc > 0);
     if (!exact) return LAM_OK;
     T* mx = maxabs_slot<T>(p, ws);
     CK(launch_absmax<T>(in, p->ndata(), mx, s));
@@ -1209,6 +1210,7 @@ lam_status lam_plan_set_option(lam_plan* p, int option, int value) {
             else if (value == LAM_SPREAD_EXACT) p->spread = kSpreadExact;
             else if (value == LAM_SPREAD_HALO) p->spread = kSpreadHalo;
             else if (value == LAM_SPREAD_TILES_EXACT) p->spread = kSpreadTilesExact;
+            else if (value == LAM_SPREAD_TILES2) p->spread = kSpreadTiles2;
             else return fail(LAM_EINVAL, "unknown adjoint spread %d", value);
             {
                 // captured ADMM graphs hold the old kernel choice

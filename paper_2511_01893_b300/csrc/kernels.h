@@ -21,6 +21,7 @@ constexpr int kSpreadAtomic = 1;
 constexpr int kSpreadExact = 3;
 constexpr int kSpreadHalo = 4;  // owner-tile spread with halos (one visit per point)
 constexpr int kSpreadTilesExact = 5;  // per-warp tiles of 64-bit fixed-point cells (exact, no atomics)
+constexpr int kSpreadTiles2 = 6;      // the tile spread with one point per half-warp (two tiles per warp)
 
 template <typename T> cudaError_t configure_usfft1d();
 template <typename T> cudaError_t configure_usfft2d();

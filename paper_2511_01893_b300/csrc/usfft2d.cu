@@ -745,24 +745,29 @@ template <typename T, int NPASS> struct alignas(sizeof(T) * NPASS + 8 == 16 ? 16
     T wx[NPASS];
     int ox, oy;
 };
-__host__ __device__ constexpr int spread_rpp(int mh) { return 32 / (2 * mh); }
-__host__ __device__ constexpr int spread_npass(int mh) { return (2 * mh + spread_rpp(mh) - 1) / spread_rpp(mh); }
-template <typename T> size_t spread_rec_bytes(int mh) {
-    switch (spread_npass(mh)) {
+// split: points a warp spreads at once (1: all 32 lanes cover one point's
+// window; 2: each half-warp covers its own point in its own tile)
+__host__ __device__ constexpr int spread_rpp(int mh, int split = 1) { return 32 / split / (2 * mh); }
+__host__ __device__ constexpr int spread_npass(int mh, int split = 1) {
+    return (2 * mh + spread_rpp(mh, split) - 1) / spread_rpp(mh, split);
+}
+template <typename T> size_t spread_rec_bytes(int mh, int split = 1) {
+    switch (spread_npass(mh, split)) {
         case 1: return sizeof(SpreadRec<T, 1>);
         case 2: return sizeof(SpreadRec<T, 2>);
         case 3: return sizeof(SpreadRec<T, 3>);
         case 4: return sizeof(SpreadRec<T, 4>);
         case 6: return sizeof(SpreadRec<T, 6>);
         case 7: return sizeof(SpreadRec<T, 7>);
-        default: return sizeof(SpreadRec<T, 8>);
+        case 8: return sizeof(SpreadRec<T, 8>);
+        default: return sizeof(SpreadRec<T, 16>);
     }
 }
 // exact: the tile cells are 64-bit fixed-point pairs (16 bytes) instead of complex T
-template <typename T> size_t spread_tiles_smem(int nw, int mh, bool exact = false) {
+template <typename T> size_t spread_tiles_smem(int nw, int mh, bool exact = false, int split = 1) {
     const size_t cell = exact ? 16 : sizeof(C<T>);
-    return (size_t)nw * kSpreadTS * kSpreadTS * cell + (size_t)nw * (2 * mh) * kRecPitch * sizeof(C<T>) +
-           (size_t)nw * spread_rpp(mh) * kRecPitch * spread_rec_bytes<T>(mh);
+    return (size_t)nw * split * kSpreadTS * kSpreadTS * cell + (size_t)nw * (2 * mh) * kRecPitch * sizeof(C<T>) +
+           (size_t)nw * spread_rpp(mh, split) * kRecPitch * spread_rec_bytes<T>(mh, split);
 }
 
 __device__ __forceinline__ void lds_ll2(unsigned ad, long long& a, long long& b) {
@@ -797,21 +802,27 @@ __device__ __forceinline__ void sts_c(unsigned ad, const C<double>& v) {
 // as the atomic exact spread) and are added with integer read-add-writes: the
 // exact sum of the rounded products, independent of order, without atomics.
 // 16-byte cells need no swizzle: the 8 cells of a pass row span 128 bytes.
-template <typename T, int NW, int MH, bool EXACT = false>
+// SPLIT = 2: each half-warp takes every other record into a tile of its own
+// (2 rows x 8 columns per pass for m = 4): the same shared-memory bytes per
+// point with half the instructions; the two tiles per warp are summed at the end.
+template <typename T, int NW, int MH, bool EXACT = false, int SPLIT = 1>
 __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, const Usfft2dArgs<T>& a, int bx, int by) {
+    static_assert(SPLIT == 1 || !EXACT, "the exact tiles take one point per warp");
     constexpr int nt = 2 * MH;
-    constexpr int RPP = 32 / nt;  // window rows per pass
+    constexpr int LP = 32 / SPLIT;  // lanes per point
+    constexpr int RPP = LP / nt;    // window rows per pass
     constexpr int NPASS = (nt + RPP - 1) / RPP;
     constexpr int TS = kSpreadTS;
     constexpr int ncell = TS * TS;
     constexpr unsigned kCell = EXACT ? 16u : (unsigned)sizeof(C<T>);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    C<T>* tiles = reinterpret_cast<C<T>*>(smem_raw);  // [NW][ncell]
-    C<T>* mine = tiles + (size_t)warp * ncell;
+    const int hw = lane / LP, lp = lane - hw * LP;  // sub-warp and lane within it
+    C<T>* tiles = reinterpret_cast<C<T>*>(smem_raw);  // [NW * SPLIT][ncell]
+    C<T>* mine = tiles + (size_t)(warp * SPLIT + hw) * ncell;
     long long* xtiles = reinterpret_cast<long long*>(smem_raw);  // EXACT: [NW][ncell][2]
     long long* xmine = xtiles + (size_t)warp * ncell * 2;
-    unsigned char* recb = smem_raw + (size_t)NW * ncell * kCell;
+    unsigned char* recb = smem_raw + (size_t)NW * SPLIT * ncell * kCell;
     T fscale = (T)1, finv = (T)1;
     if constexpr (EXACT) fixed_scale<T>(*a.maxabs, a.bound_count, fscale, finv);
     // records: wyv[sy][pitch] (complex), then rec[rr][pitch] (x weights of the
@@ -824,7 +835,8 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
     if constexpr (EXACT) {
         for (int i = lane; i < 2 * ncell; i += 32) xmine[i] = 0;
     } else {
-        for (int i = lane; i < ncell; i += 32) mine[i] = cmake<T>(0, 0);
+        C<T>* wt = tiles + (size_t)warp * SPLIT * ncell;  // the warp's SPLIT tiles
+        for (int i = lane; i < SPLIT * ncell; i += 32) wt[i] = cmake<T>(0, 0);
     }
     __syncwarp();
     const int tiles_y = a.M2 / TS;
@@ -833,7 +845,7 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
     const int b = by;
     const int2 job = a.jobs[j0 + b];
     const T hb = (T)(TS + 2 * a.m) * (T)0.5;
-    const int rr = lane / nt, sy = lane - rr * nt;
+    const int rr = lp / nt, sy = lp - rr * nt;
     const bool lane_on = rr < RPP;
     const int rrc = lane_on ? rr : 0;
     // lane-constant shared addresses of the record entries this lane reads
@@ -909,15 +921,21 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
                     }
                     __syncwarp();
                     const int cnt = __popc(mask);
-                    Rec rc = rec_lane[0];
+                    // sub-warp hw takes records hw, hw + SPLIT, ...; the value
+                    // records are complex T whatever the tile cells are
+                    constexpr unsigned kRecCell = sizeof(C<T>);
+                    const int k0 = hw < cnt ? hw : cnt - 1;
+                    Rec rc = rec_lane[k0];
                     C<T> wv;
-                    lds_c(wyv_ad, wv);
-                    for (int k = 0; k < cnt; ++k) {
+                    lds_c(wyv_ad + k0 * kRecCell, wv);
+                    for (int kk = 0; kk < cnt; kk += SPLIT) {
+                        const int k = kk + hw;
+                        const bool kon = SPLIT == 1 || k < cnt;
                         // read the next record first (its latency overlaps the update)
-                        const int kn = k + 1 < cnt ? k + 1 : k;
+                        const int kn = k + SPLIT < cnt ? k + SPLIT : (kon ? k : cnt - 1);
                         const Rec nrc = rec_lane[kn];
                         C<T> nwv;
-                        lds_c(wyv_ad + kn * kCell, nwv);
+                        lds_c(wyv_ad + kn * kRecCell, nwv);
                         const int2 o = make_int2(rc.ox, rc.oy);
                         const int cx0 = o.x + rrc, ccy = o.y + sy;
                         const int col = EXACT ? ccy : ccy ^ ((cx0 & 1) << 3);
@@ -930,7 +948,7 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
                             const unsigned ad = (!EXACT && ((q * RPP) & 1))
                                                     ? tile_ad + (unsigned)(row * TS + (col ^ 8)) * kCell
                                                     : ad0 + (unsigned)(q * RPP * TS) * kCell;
-                            if (yok && q * RPP + rr < nt && (unsigned)row < (unsigned)TS) {
+                            if (kon && yok && q * RPP + rr < nt && (unsigned)row < (unsigned)TS) {
                                 if constexpr (EXACT) {
                                     long long xr, xi;
                                     lds_ll2(ad, xr, xi);
@@ -971,7 +989,7 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
             const int si = ccx * TS + swz_row(ccx, ccy);
             sum = tiles[si];
 #pragma unroll
-            for (int w = 1; w < NW; ++w) {
+            for (int w = 1; w < NW * SPLIT; ++w) {
                 const C<T> t = tiles[(size_t)w * ncell + si];
                 sum.x += t.x;
                 sum.y += t.y;
@@ -1197,6 +1215,13 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
     k_spread2d_tiles_body<T, NW, MH, false>(in, P, j0, a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
+// the tile spread with one point per half-warp
+template <typename T, int NW, int MH>
+__global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_tiles2(
+    const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, Usfft2dArgs<T> a) {
+    k_spread2d_tiles_body<T, NW, MH, false, 2>(in, P, j0, a, (int)blockIdx.x, (int)blockIdx.y);
+}
+
 // the exact (64-bit fixed-point) tile spread
 template <typename T, int NW, int MH>
 __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_tiles_exact(
@@ -1360,7 +1385,7 @@ cudaError_t launch_spread2d(const C<T>* in, C<T>* P, int j0, int nb, const Usfft
         const long long ncells = (long long)nb * a.M1 * a.M2;
         const long long hb = (ncells + 255) / 256;
         k_halo_sum<T><<<(int)(hb < 148 * 8 ? hb : 148 * 8), 256, 0, s>>>(a.halo, P, nb, kSpreadTS + 2 * a.m - 1, a);
-    } else if ((a.spread == kSpreadTiles || a.spread == kSpreadHalo) && a.TS == kSpreadTS) {
+    } else if ((a.spread == kSpreadTiles || a.spread == kSpreadTiles2 || a.spread == kSpreadHalo) && a.TS == kSpreadTS) {
         // the first a.nacc plane jobs (the centre planes: every slice line
         // passes close to the origin there, so the cells near it sum thousands
         // of nearly equal products, where FP32 running sums round
@@ -1378,14 +1403,24 @@ cudaError_t launch_spread2d(const C<T>* in, C<T>* P, int j0, int nb, const Usfft
             }
         }
         if (nb > nx) {
-            const size_t st = spread_tiles_smem<T>(kSpreadWarps, a.m);
             const dim3 gt(ntiles, nb - nx);
             C<T>* Pt = P + (size_t)nx * a.M1 * a.M2;
-            switch (a.m) {
-#define LAM_T(MH) case MH: k_spread2d_tiles<T, kSpreadWarps, MH><<<gt, kSpreadWarps * 32, st, s>>>(in, Pt, kv0 + nx, a); break;
-                LAM_T(2) LAM_T(3) LAM_T(4) LAM_T(5) LAM_T(6) LAM_T(7) LAM_T(8)
+            if (a.spread == kSpreadTiles2) {
+                const size_t st = spread_tiles_smem<T>(kSpreadWarps, a.m, false, 2);
+                switch (a.m) {
+#define LAM_T(MH) case MH: k_spread2d_tiles2<T, kSpreadWarps, MH><<<gt, kSpreadWarps * 32, st, s>>>(in, Pt, kv0 + nx, a); break;
+                    LAM_T(2) LAM_T(3) LAM_T(4) LAM_T(5) LAM_T(6) LAM_T(7) LAM_T(8)
 #undef LAM_T
-                default: return cudaErrorInvalidValue;
+                    default: return cudaErrorInvalidValue;
+                }
+            } else {
+                const size_t st = spread_tiles_smem<T>(kSpreadWarps, a.m);
+                switch (a.m) {
+#define LAM_T(MH) case MH: k_spread2d_tiles<T, kSpreadWarps, MH><<<gt, kSpreadWarps * 32, st, s>>>(in, Pt, kv0 + nx, a); break;
+                    LAM_T(2) LAM_T(3) LAM_T(4) LAM_T(5) LAM_T(6) LAM_T(7) LAM_T(8)
+#undef LAM_T
+                    default: return cudaErrorInvalidValue;
+                }
             }
         }
     } else if (a.spread != kSpreadAtomic) { LAM_SW(3) }
@@ -1470,6 +1505,7 @@ template <typename T> cudaError_t configure_usfft2d() {
     if (!e) e = cudaFuncSetAttribute(k_scatter2d_atomic<T, kScatterWarps, MH, 3>, at, mt);    \
     if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles<T, kSpreadWarps, MH>, at, mt);    \
     if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles_exact<T, kSpreadWarps, MH>, at, mt); \
+    if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles2<T, kSpreadWarps, MH>, at, mt); \
     if (!e) e = cudaFuncSetAttribute(k_spread2d_halo<T, kScatterWarps, MH>, at, mt);
     LAM_A(2) LAM_A(3) LAM_A(4) LAM_A(5) LAM_A(6) LAM_A(7) LAM_A(8)
 #undef LAM_A

@@ -140,7 +140,7 @@ class Geometry:
 class Plan:
     """A plan for one geometry and precision ('f32' or 'f64') on the current device."""
 
-    SPREADS = {"tiles": 0, "atomic": 1, "exact": 2, "halo": 3, "tiles_exact": 4}
+    SPREADS = {"tiles": 0, "atomic": 1, "exact": 2, "halo": 3, "tiles_exact": 4, "tiles2": 5}
 
     def __init__(self, n, nz, h, w, theta, phi, m=4, prec="f32", device=None, fast_adjoint=False, spread=None,
                  workspace="full"):

@@ -44,7 +44,7 @@ def test_u1d_forward_and_adjoint(geom, prec):
     assert rel(got, ref) < tol(prec)
 
 
-@pytest.mark.parametrize("spread", ["tiles", "halo", "atomic", "exact", "tiles_exact"])
+@pytest.mark.parametrize("spread", ["tiles", "halo", "atomic", "exact", "tiles_exact", "tiles2"])
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("geom", GEOMS, ids=IDS)
 def test_u2d_forward_and_adjoint(geom, prec, spread):
@@ -133,7 +133,7 @@ def test_adjoint_spread_variants_other_widths(m):
     plan, g = plan_and_geom(n, nz, h, w, T, 0.5, "f32", m=m)
     d = rand_data(T, h, w, 18)
     ref = olam.f_u2d_adj(d, g)
-    for spread in ("tiles", "halo", "atomic", "exact", "tiles_exact"):
+    for spread in ("tiles", "halo", "atomic", "exact", "tiles_exact", "tiles2"):
         p = glam.Plan(n, nz, h, w, plan.theta, 0.5, m=m, prec="f32", spread=spread)
         got = p.u2d_adj(torch.from_numpy(d)).cpu().numpy().transpose(1, 0, 2)
         assert rel(got, ref) < tol("f32"), spread
@@ -153,6 +153,10 @@ def test_adjoint_spreads_are_bitwise_reproducible():
     tx = glam.Plan(n, nz, h, w, plan.theta, 0.5, prec="f32", spread="tiles_exact")
     t1, t2 = tx.adjoint(d), tx.adjoint(d)
     assert torch.equal(t1, t2)
+    h2 = glam.Plan(n, nz, h, w, plan.theta, 0.5, prec="f32", spread="tiles2")
+    s1, s2 = h2.adjoint(d), h2.adjoint(d)
+    assert torch.equal(s1, s2)
+    assert rel(s1, e1) < 2e-6
     # the same products formed in another order (wx (wy v) against wy (wx v)): ~1 ulp apart
     assert rel(t1, e1) < 3e-7
     fast = glam.Plan(n, nz, h, w, plan.theta, 0.5, prec="f32", fast_adjoint=True)
