@@ -205,3 +205,25 @@ def test_fbp_missing_cone_is_not_recovered():
     u = _blob(n, 2.5, 2.5)
     r = olam.fbp(olam.lam_forward(u, g), g)
     assert np.vdot(r, u).real / np.vdot(u, u).real < 0.95
+
+
+def test_tap_rule_on_grid_nodes_matches_direct_nudft():
+    # theta at multiples of pi/2 and phi = 30 deg put every in-plane slice point
+    # exactly on a node of the padded grid (M xi = (2 ku, -kv) up to sign and
+    # order): the tap window's switch point (2^-17 below each node) decides
+    # which 2m nodes serve it.  At m = 12 the USFFT is exact to ~1e-12, so a
+    # window shifted by one node, or taps read from the wrong side, shows here.
+    n, nz, T = 16, 8, 4
+    g = Geometry(n1=n, n0=nz, n2=n, h=n, w=n, theta=np.arange(T) * np.pi / 2, phi=np.pi / 6, m=12)
+    xi_x, xi_y, _ = lamino.slice_frequencies(g)
+    M = 2 * n
+    for a in (M * xi_x, M * xi_y):
+        assert np.abs(a - np.round(a)).max() < 1e-12
+    rng = np.random.default_rng(3)
+    u = rng.standard_normal((n, nz, n))
+    assert _rel(lamino.lhat(u, g), lamino.lhat_exact(u, g)) < 1e-10
+    r = rng.standard_normal((T, n, n)) + 1j * rng.standard_normal((T, n, n))
+    # the transpose at the same nodes, against the transpose of the direct sum
+    lhs = np.vdot(lamino.lhat_exact(u, g), r).real
+    rhs = np.vdot(u, lamino.lhat_adj(r, g)).real
+    assert abs(lhs - rhs) / (np.linalg.norm(u) * np.linalg.norm(r)) < 1e-10
