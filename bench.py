@@ -143,6 +143,12 @@ def admm_iteration_bytes(n, nz, h, w, T, n_inner=N_INNER):
     return n_inner * 2 * lhat_bytes(n, nz, h, w, T) + K * vox + D * n_inner * (8 + 24)
 
 
+# the kernel each adjoint spread variant launches for the non-centre plane jobs
+SPREAD_KERNELS = {"tiles": "k_spread2d_tiles", "sweep": "k_spread2d_sweep", "tiles2": "k_spread2d_tiles2",
+                  "tiles_exact": "k_spread2d_tiles_exact", "halo": "k_spread2d_halo", "atomic": "k_scatter2d_atomic",
+                  "exact": "k_scatter2d_atomic"}
+
+
 def spread_point_flops(m=4):
     """Algorithmic FP32 flops the adjoint spread spends per slice point: its
     (2m)^2 cells, each a complex accumulation of a real weight times the value
@@ -809,14 +815,20 @@ def run_memo(args):
 BATCH_SIZES = [96, 128, 160, 192]
 
 
+BATCH_STREAMS = (2, 4, 16)  # other side-stream counts tried by the concurrent batch mode
+DEFAULT_BATCH_STREAMS = 8  # the library's default for 16 problems
+
+
 def run_batch(args):
     """Batching workload: 16 FP32 reconstructions, n in {96, 128, 160, 192}
     (four each), nz = n / 2, n angles, detector n x n, tilt 20 + 20 i / 15 deg,
     ellipsoid phantoms + 1 % noise, launch shapes from the autotuner.  A step
-    is one ADMM-TV outer iteration (4 CG steps) of all 16 problems, with every
-    operator stage one persistent launch over the batch, captured as a CUDA
-    graph.  Also timed: the same 16 problems one after another (one graph per
-    problem).  Prints one JSON line."""
+    is one ADMM-TV outer iteration (4 CG steps) of all 16 problems in the
+    library's default batch mode: every problem's own iteration on side
+    stream i mod 8, forked and joined inside one CUDA graph.  Also timed: the
+    persistent mode (every operator stage one launch over the batch), the same
+    16 problems one after another (one graph per problem) and other stream
+    counts.  Prints one JSON line."""
     import torch
 
     from paper_2511_01893_b300 import inputs
@@ -842,16 +854,23 @@ def run_batch(args):
     s = torch.cuda.Stream(device=dev)
     s.wait_stream(torch.cuda.current_stream(dev))  # the data were made on the current stream
     res = {}
+    # "batched": the library's default (concurrent, 8 side streams); then the
+    # persistent batched stages, the problems one after another, other stream counts
+    modes = ["batched", "persistent", "sequential"] + [f"concurrent{k}" for k in BATCH_STREAMS]
     with torch.cuda.stream(s):
-        for mode in ("batched", "sequential"):
+        for mode in modes:
             admms = [glam.Admm(p).init(d, ALPHA, RHO, N_INNER) for p, d in zip(plans, datas)]
+            if mode.startswith("concurrent"):
+                batch.set_streams(int(mode[len("concurrent"):]))
+            elif mode == "persistent":
+                batch.set_streams(0)
 
             def step(k):
-                if mode == "batched":
-                    batch.admm_run(admms, k, graph=True)
-                else:
+                if mode == "sequential":
                     for a in admms:
                         a.run(k, graph=True)
+                else:
+                    batch.admm_run(admms, k, graph=True)
             step(args.warmup)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             s.synchronize()
@@ -862,9 +881,13 @@ def run_batch(args):
             res[mode] = e0.elapsed_time(e1) / 1e3 / max(args.steps, 1)
             res[mode + "_u"] = [a.u.clone() for a in admms]
             res[mode + "_status"] = max(a.status() for a in admms)
-    same = all(torch.equal(a, b) for a, b in zip(res["batched_u"], res["sequential_u"]))
+            if mode == "persistent":
+                info = batch.info()  # persistent-mode stage grids and graph kernels
+    same = all(all(torch.equal(a, b) for a, b in zip(res[m + "_u"], res["sequential_u"])) for m in modes)
+    conc = {k: res[f"concurrent{k}"] for k in BATCH_STREAMS}
+    conc[DEFAULT_BATCH_STREAMS] = res["batched"]
+    best_k = min(conc, key=conc.get)
     vox = sum(p.n * p.nz * p.n for p in plans)
-    info = batch.info()
     line = {
         "metric": "batched ADMM-TV seconds per iteration (16 problems)", "value": res["batched"], "unit": "s/iter",
         "higher_is_better": False, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
@@ -873,8 +896,13 @@ def run_batch(args):
                                "detector n x n, phi 20-40 deg, FP32, 4 CG steps/iter, graph-captured",
                    "sizes": [p.n for p in plans]},
         "sequential_s_per_iter": res["sequential"], "speedup_vs_sequential": res["sequential"] / res["batched"],
+        "mode": f"concurrent: each problem's outer iteration on side stream i mod {DEFAULT_BATCH_STREAMS}, one graph",
+        "persistent_s_per_iter": res["persistent"],
+        "persistent_speedup_vs_sequential": res["sequential"] / res["persistent"],
+        "concurrent_s_per_iter": dict(sorted(conc.items())), "concurrent_best": {"streams": best_k, "s_per_iter": conc[best_k],
+                                                           "speedup_vs_sequential": res["sequential"] / conc[best_k]},
         "voxel_updates_per_s": vox / res["batched"], "batched_equals_sequential_bitwise": same,
-        "status": max(res["batched_status"], res["sequential_status"]), "autotune_s": tune,
+        "status": max(res[m + "_status"] for m in modes), "autotune_s": tune,
         "launches_per_iter": info["graph_kernels"],
         "stage_grids": {k: v for k, v in info.items() if k != "graph_kernels"},
         "plans": [p.info() for p in plans[:4]],
@@ -984,6 +1012,7 @@ def run_ours(args):
             kev[r + 1].record(stream)
     stream.synchronize()
     t_spread = statistics.median([kev[r].elapsed_time(kev[r + 1]) / 1e3 for r in range(kreps)])
+    spread_kernel = SPREAD_KERNELS[plan.info()["spread"]]
     planes = plan.job_planes(j0s, nbj)
     M = 2 * n
     # reads the batch's slice values (8 B per (theta, ku) of each data plane),
@@ -1021,14 +1050,14 @@ def run_ours(args):
                    "l2": "inputs larger than L2 (state ~80 GB)"},
         "roofline": {"bound": "hbm", "unit": "GB/s", "achieved": spread_bytes / t_spread / 1e9, "peak": peak,
                      "frac": spread_bytes / t_spread / 1e9 / peak, "traffic": traffic, "peak_source": peak_src,
-                     "kernel": f"k_spread2d_tiles (adjoint spread; one launch = plane jobs {j0s}..{j0s + nbj - 1}, "
+                     "kernel": f"{spread_kernel} (adjoint spread; one launch = plane jobs {j0s}..{j0s + nbj - 1}, "
                                f"{planes} kv planes)",
                      "traffic_note": "dram bytes per job from a 512^3 capture, scaled by (n/512)^2 per job",
                      "algorithmic_bytes": spread_bytes, "t_launch_s": t_spread,
                      "note": "bound by the L1/shared pipe (ncu: 80 % of its peak), not by HBM"},
         "roofline_alu": {"bound": "alu", "unit": "TFLOP/s", "achieved": spread_flops / t_spread / 1e12,
                          "peak": fma / 1e12, "frac": spread_flops / t_spread / fma,
-                         "peak_source": "measured FMA probe", "kernel": "k_spread2d_tiles",
+                         "peak_source": "measured FMA probe", "kernel": spread_kernel,
                          "algorithmic_flops": spread_flops},
         "iteration_hbm": {"bound": "hbm", "unit": "GB/s", "achieved": it_bytes / s_per_iter / 1e9, "peak": peak,
                           "frac": it_bytes / s_per_iter / 1e9 / peak, "algorithmic_bytes": it_bytes,

@@ -99,6 +99,11 @@ lam_status lam_plan_destroy(lam_plan* plan);
  *   LAM_SPREAD_TILES2  the tile spread with one slice point per half-warp,
  *                      each half-warp summing into a tile of its own (two
  *                      tiles per warp, added in a fixed order): reproducible.
+ *   LAM_SPREAD_SWEEP   row sweep: a warp sorts its slice points by the x
+ *                      origin of their windows and sweeps a 64 x 8 band of the
+ *                      plane with the window rows held in registers (no
+ *                      shared-memory read-add-write per tap); the order of
+ *                      every sum follows from the input: reproducible.
  * LAM_OPT_FAST_ADJOINT: value != 0 selects LAM_SPREAD_ATOMIC, 0 the default.
  * LAM_OPT_LSP_FORM (default 2) is the LSP form that ADMM states initialised
  *   afterwards use: 2 = Algorithm 2 (operation cancellation: the LSP works on
@@ -159,7 +164,8 @@ enum {
     LAM_SPREAD_EXACT = 2,
     LAM_SPREAD_HALO = 3,
     LAM_SPREAD_TILES_EXACT = 4,
-    LAM_SPREAD_TILES2 = 5
+    LAM_SPREAD_TILES2 = 5,
+    LAM_SPREAD_SWEEP = 6
 };
 lam_status lam_plan_set_option(lam_plan* plan, int option, int value);
 
@@ -354,12 +360,28 @@ lam_status lam_forward_batched(const lam_batch* batch, const void* const* u, voi
 lam_status lam_adjoint_batched(const lam_batch* batch, const void* const* d, void* const* u, void* stream);
 
 /* `iters` ADMM outer iterations of every problem: states[i] initialised with
- * admm_init on plan i (all with the same n_inner).  The operators run
- * batched; the elementwise steps run per problem in admm_step's order, so
- * each state evolves bitwise as under admm_step.  use_graph != 0 captures
+ * admm_init on plan i.  By default the problems run concurrently on side
+ * streams (lam_batch_set_streams).  In the persistent mode (streams = 0, all
+ * states with the same n_inner, Algorithm 2 form, no memoization or residual
+ * refresh) the operators run batched and the elementwise steps per problem
+ * in admm_step's order.  Either way each state evolves bitwise as under
+ * admm_step.  use_graph != 0 captures
  * one outer iteration of the whole batch as a CUDA graph (re-captured when
  * the states change) and replays it; it needs a non-default stream. */
 lam_status admm_run_batched(lam_batch* batch, void* const* states, int iters, int use_graph, void* stream);
+
+/* Concurrent mode of admm_run_batched.  streams = 0: the persistent batched
+ * stages above.  streams >= 1 (lam_batch_create sets min(count, 8) unless two
+ * problems share a workspace): every problem runs its own
+ * outer iteration (admm_step's kernels and options: either LSP form,
+ * memoization, residual options) with problem i on the batch's side stream
+ * i mod streams; the side streams fork from and join to the caller's stream
+ * (one graph with use_graph), so small problems overlap on the GPU.  Each
+ * state evolves bitwise as under admm_step.  Creates the side streams and
+ * events (released by lam_batch_destroy or the next call); drops a captured
+ * graph.  LAM_EINVAL if two problems share a workspace or the current device
+ * is not the batch's. */
+lam_status lam_batch_set_streams(lam_batch* batch, int streams);
 
 /* Thread-local message for the last non-OK status returned on this thread. */
 const char* lam_last_error(void);

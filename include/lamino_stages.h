@@ -68,8 +68,9 @@ int lamx_job_planes(const lam_plan* plan, int j0, int nb);
  * TY (z forward), TY (z transpose), rows per block, columns per block,
  * scatter tile side, tile images, planes per batch, jmin, jmax, the
  * number of plane jobs the full operators run (h/2 + 1 when every plane
- * pairs with its conjugate mirror), the gather tile side, and the threads
- * per block of the z stage and of the plane FFTs. */
+ * pairs with its conjugate mirror), the gather tile side, the threads per
+ * block of the z stage and of the plane FFTs, and the adjoint spread (its
+ * LAM_SPREAD_* value). */
 lam_status lamx_plan_info(const lam_plan* plan, int* out, int count);
 
 /* Batch diagnostics: out[2 s], out[2 s + 1] = work items and persistent grid

@@ -136,6 +136,10 @@ struct lam_plan {
 };
 
 // a batch of plans run together by the batched operators (lam_batch_create)
+// side streams of a new batch's concurrent ADMM mode (8 and 16 measured alike
+// on 16 problems of n = 96 .. 192)
+constexpr int kDefaultBatchStreams = 8;
+
 struct lam_batch {
     int count = 0;
     int prec = LAM_F32;
@@ -151,6 +155,11 @@ struct lam_batch {
     std::vector<void*> graph_states;
     cudaGraphExec_t graph = nullptr;
     size_t graph_kernels = 0;
+    // concurrent mode (lam_batch_set_streams): side streams and fork / join events
+    int nstreams = 0;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
 };
 
 namespace {
@@ -527,9 +536,11 @@ template <typename T> lam_status prep_scatter(const lam_plan* p, const C<T>* in,
     // the exact spread runs when chosen, and for the tile spread's small-plane
     // fallback (tiles narrower than 32)
     const bool exact = p->spread == kSpreadExact || p->spread == kSpreadTilesExact ||
-                       ((p->spread == kSpreadTiles || p->spread == kSpreadTiles2 || p->spread == kSpreadHalo) &&
+                       ((p->spread == kSpreadTiles || p->spread == kSpreadTiles2 || p->spread == kSpreadHalo ||
+                         p->spread == kSpreadSweep) &&
                         p->TS != 32) ||
-                       ((p->spread == kSpreadTiles || p->spread == kSpreadTiles2) && a.nacc > 0);
+                       ((p->spread == kSpreadTiles || p->spread == kSpreadTiles2 || p->spread == kSpreadSweep) &&
+                        a.nacc > 0);
     if (!exact) return LAM_OK;
     T* mx = maxabs_slot<T>(p, ws);
     CK(launch_absmax<T>(in, p->ndata(), mx, s));
@@ -1211,6 +1222,7 @@ lam_status lam_plan_set_option(lam_plan* p, int option, int value) {
             else if (value == LAM_SPREAD_HALO) p->spread = kSpreadHalo;
             else if (value == LAM_SPREAD_TILES_EXACT) p->spread = kSpreadTilesExact;
             else if (value == LAM_SPREAD_TILES2) p->spread = kSpreadTiles2;
+            else if (value == LAM_SPREAD_SWEEP) p->spread = kSpreadSweep;
             else return fail(LAM_EINVAL, "unknown adjoint spread %d", value);
             {
                 // captured ADMM graphs hold the old kernel choice
@@ -1806,6 +1818,12 @@ lam_status lam_batch_create(lam_batch** out, const lam_plan* const* plans, void*
     if (!ce) ce = b->prec == LAM_F32 ? configure_batch_z<float>() : configure_batch_z<double>();
     lam_status st = ce ? fail(LAM_ECUDA, "batched kernel configuration failed: %s", cudaGetErrorString(ce)) : LAM_OK;
     if (!st) st = b->prec == LAM_F32 ? batch_build<float>(b) : batch_build<double>(b);
+    // ADMM runs concurrently by default (lam_batch_set_streams), unless two
+    // problems share a workspace
+    bool shared = false;
+    for (int i = 0; i < count; ++i)
+        for (int j = 0; j < i; ++j) shared = shared || ws[i] == ws[j];
+    if (!st && !shared) st = lam_batch_set_streams(b, std::min(count, kDefaultBatchStreams));
     if (st) {
         lam_batch_destroy(b);
         return st;
@@ -1814,11 +1832,51 @@ lam_status lam_batch_create(lam_batch** out, const lam_plan* const* plans, void*
     return LAM_OK;
 }
 
+static void release_streams(lam_batch* b) {
+    for (cudaStream_t x : b->side) cudaStreamDestroy(x);
+    for (cudaEvent_t e : b->join) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    b->side.clear();
+    b->join.clear();
+    b->fork = nullptr;
+}
+
 lam_status lam_batch_destroy(lam_batch* b) {
     if (!b) return LAM_OK;
     if (b->graph) cudaGraphExecDestroy(b->graph);
+    release_streams(b);
     if (b->dev) cudaFree(b->dev);
     delete b;
+    return LAM_OK;
+}
+
+lam_status lam_batch_set_streams(lam_batch* b, int streams) {
+    if (!b) return fail(LAM_EINVAL, "batch is NULL");
+    if (streams < 0 || streams > kMaxBatch) return fail(LAM_EINVAL, "streams = %d (0 .. %d)", streams, kMaxBatch);
+    if (streams > 0) {
+        // problems on different streams must not share a workspace
+        for (int i = 0; i < b->count; ++i)
+            for (int j = 0; j < i; ++j)
+                if (b->ws[i] == b->ws[j])
+                    return fail(LAM_EINVAL, "problems %d and %d share a workspace: they cannot run concurrently", j, i);
+    }
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != b->device) return fail(LAM_EINVAL, "current device %d is not the batch's device %d", dev, b->device);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    b->graph = nullptr;
+    b->graph_states.clear();
+    release_streams(b);
+    b->nstreams = streams;
+    for (int k = 0; k < streams; ++k) {
+        cudaStream_t x = nullptr;
+        cudaEvent_t e = nullptr;
+        CK(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        b->side.push_back(x);
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->join.push_back(e);
+    }
+    if (streams > 0) CK(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
     return LAM_OK;
 }
 
@@ -1879,10 +1937,16 @@ lam_status admm_run_batched(lam_batch* b, void* const* states, int iters, int us
     if (iters < 0) return fail(LAM_EINVAL, "iters = %d", iters);
     int n_inner = -1;
     int resid[kMaxBatch] = {};
+    AdmmHost* hosts[kMaxBatch] = {};
+    const bool conc = b->nstreams > 0;
     for (int i = 0; i < b->count; ++i) {
         if (!states[i]) return fail(LAM_EINVAL, "state %d is NULL", i);
         AdmmHost* h;
         if (lam_status st = lookup(b->plans[i], states[i], &h)) return st;
+        hosts[i] = h;
+        for (int j = 0; j < i; ++j)
+            if (states[j] == states[i]) return fail(LAM_EINVAL, "states %d and %d are the same state", j, i);
+        if (conc) continue;  // each problem runs its own admm_step: any form and options
         if (n_inner >= 0 && h->n_inner != n_inner)
             return fail(LAM_EINVAL, "state %d: every state of a batch needs the same number of CG steps", i);
         if (h->form != 2) return fail(LAM_EUNSUPPORTED, "state %d: batched ADMM runs the Algorithm 2 form", i);
@@ -1893,7 +1957,29 @@ lam_status admm_run_batched(lam_batch* b, void* const* states, int iters, int us
         n_inner = h->n_inner;
     }
     cudaStream_t s = (cudaStream_t)stream;
+    // concurrent mode: problem i's own outer iteration (the single-plan
+    // kernels, as admm_step) on side stream i mod nstreams, forked from and
+    // joined to s; problems on different streams overlap on the GPU
+    auto conc_step = [&]() -> lam_status {
+        CK(cudaEventRecord(b->fork, s));
+        for (int j = 0; j < b->nstreams; ++j) CK(cudaStreamWaitEvent(b->side[j], b->fork, 0));
+        for (int i = 0; i < b->count; ++i) {
+            const lam_plan* p = b->plans[i];
+            const AdmmHost* h = hosts[i];
+            cudaStream_t x = b->side[i % b->nstreams];
+            if (lam_status st = DISPATCH(
+                    p, admm_step_t<float>(p, states[i], b->ws[i], h->n_inner, h->form, h->resid, h->memo_tau, x),
+                    admm_step_t<double>(p, states[i], b->ws[i], h->n_inner, h->form, h->resid, h->memo_tau, x)))
+                return st;
+        }
+        for (int j = 0; j < b->nstreams; ++j) {
+            CK(cudaEventRecord(b->join[j], b->side[j]));
+            CK(cudaStreamWaitEvent(s, b->join[j], 0));
+        }
+        return LAM_OK;
+    };
     auto step = [&]() -> lam_status {
+        if (conc) return conc_step();
         return b->prec == LAM_F32 ? batch_admm_step<float>(b, states, resid, n_inner, s)
                                   : batch_admm_step<double>(b, states, resid, n_inner, s);
     };
@@ -2009,8 +2095,19 @@ lam_status lamx_admm_layout(const lam_plan* p, size_t* out, int count) {
 
 lam_status lamx_plan_info(const lam_plan* p, int* out, int count) {
     if (lam_status st = check_plan(p)) return st;
+    // the adjoint spread as its LAM_SPREAD_* value
+    int spread = LAM_SPREAD_TILES;
+    switch (p->spread) {
+        case kSpreadAtomic: spread = LAM_SPREAD_ATOMIC; break;
+        case kSpreadExact: spread = LAM_SPREAD_EXACT; break;
+        case kSpreadHalo: spread = LAM_SPREAD_HALO; break;
+        case kSpreadTilesExact: spread = LAM_SPREAD_TILES_EXACT; break;
+        case kSpreadTiles2: spread = LAM_SPREAD_TILES2; break;
+        case kSpreadSweep: spread = LAM_SPREAD_SWEEP; break;
+        default: break;
+    }
     const int v[] = {p->TYf,  p->TYa,  p->RB,   p->CB,         p->TS, p->nimg, p->nbatch,
-                     p->jmin, p->jmax, p->njobs_pair, p->TG, p->zthr, p->pthr};
+                     p->jmin, p->jmax, p->njobs_pair, p->TG, p->zthr, p->pthr, spread};
     const int nv = (int)(sizeof(v) / sizeof(v[0]));
     for (int i = 0; i < count && i < nv; ++i) out[i] = v[i];
     return LAM_OK;

@@ -22,6 +22,7 @@ constexpr int kSpreadExact = 3;
 constexpr int kSpreadHalo = 4;  // owner-tile spread with halos (one visit per point)
 constexpr int kSpreadTilesExact = 5;  // per-warp tiles of 64-bit fixed-point cells (exact, no atomics)
 constexpr int kSpreadTiles2 = 6;      // the tile spread with one point per half-warp (two tiles per warp)
+constexpr int kSpreadSweep = 7;       // row sweep: window rows in registers, records sorted by window row
 
 template <typename T> cudaError_t configure_usfft1d();
 template <typename T> cudaError_t configure_usfft2d();

@@ -334,6 +334,43 @@ __device__ __forceinline__ void clip_line(T A, T Cc, T bmin, T bmax, int& lo, in
     hi = min(hi, h);
 }
 
+// Hands out the points of the warp's up to 32 lines (lane i: line th_i with
+// the centred ku interval [lo_i, hi_i]; th_i = -1 or lo_i > hi_i for none)
+// 32 at a time, one per lane, in lane order and ku order within a line:
+// fn(th, kuc) is called by all lanes together, with th = -1 for idle lanes.
+template <typename F>
+__device__ __forceinline__ void walk_line_points(int th, int lo, int hi, F&& fn) {
+    const int lane = threadIdx.x & 31;
+    const int cnt = th >= 0 && hi >= lo ? hi - lo + 1 : 0;
+    // inclusive scan of cnt over the warp
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    const int excl = incl - cnt;
+    for (int p0 = 0; p0 < total; p0 += 32) {
+        const int p = p0 + lane;
+        // owner lane: the last lane whose exclusive prefix is <= p (with cnt > 0)
+        int owner = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const int cand = owner + step;
+            const int ex = __shfl_sync(0xffffffffu, excl, cand);
+            if (ex <= p) owner = cand;
+        }
+        const int ocnt = __shfl_sync(0xffffffffu, cnt, owner);
+        const int oex = __shfl_sync(0xffffffffu, excl, owner);
+        const int olo = __shfl_sync(0xffffffffu, lo, owner);
+        const int oth = __shfl_sync(0xffffffffu, th, owner);
+        const bool valid = p < total && ocnt > 0 && p - oex < ocnt;
+        const int kuc = olo + (p - oex);
+        fn(valid ? oth : -1, kuc);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Warp-level enumeration of the slice points that may touch one tile image.
 // The warp tests 32 lines at a time against the tile's position box (lane
@@ -367,34 +404,7 @@ __device__ __forceinline__ void for_tile_points(const Usfft2dArgs<T>& a, int kvc
             clip_line<T>(Ax, Cx, bxmin, bxmax, lo, hi);
             clip_line<T>(Ay, Cy, bymin, bymax, lo, hi);
         }
-        const int cnt = hi >= lo ? hi - lo + 1 : 0;
-        // inclusive scan of cnt over the warp
-        int incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += v;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        const int excl = incl - cnt;
-        for (int p0 = 0; p0 < total; p0 += 32) {
-            const int p = p0 + lane;
-            // owner lane: the last lane whose exclusive prefix is <= p (with cnt > 0)
-            int owner = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const int cand = owner + step;
-                const int ex = __shfl_sync(0xffffffffu, excl, cand);
-                if (ex <= p) owner = cand;
-            }
-            const int ocnt = __shfl_sync(0xffffffffu, cnt, owner);
-            const int oex = __shfl_sync(0xffffffffu, excl, owner);
-            const int olo = __shfl_sync(0xffffffffu, lo, owner);
-            const int oth = __shfl_sync(0xffffffffu, th, owner);
-            const bool valid = p < total && ocnt > 0 && p - oex < ocnt;
-            const int kuc = olo + (p - oex);
-            fn(valid ? oth : -1, kuc);
-        }
+        walk_line_points(th, lo, hi, fn);
     };
     int nlist = 0;  // warp-uniform
     for (int base = 0; base * NW < a.T_; base += 32) {
@@ -1229,6 +1239,363 @@ __global__ void __launch_bounds__(NW * 32, sizeof(T) == 4 ? 4 : 2) k_spread2d_ti
     k_spread2d_tiles_body<T, NW, MH, true>(in, P, j0, a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
+// ---------------------------------------------------------------------------
+// Row-sweep spread (LAM_SPREAD_SWEEP): the window sums stay in registers; no
+// shared-memory read-add-write per tap.
+//
+// One block of kSweepWarps = 4 warps per kSweepX x kSweepY tile (x rows by y
+// cells; y is the contiguous axis of the padded plane) of one plane job; warp
+// w owns the band of y cells [8w, 8w + 8).  For every pass (plane, mirror
+// plane) and periodic image the block lists the slice lines that cross the
+// tile's box (warp w tests the angles th = w mod 4, in order); each warp then
+// clips the listed lines against its band's box and walks their points,
+// writing one record per point whose window meets the band: the value, the
+// y fraction, the nt x weights and the window's origin.  A record's key is
+// its window's x origin; its rank within the key (match-any groups, in
+// walking order) makes the bucketing a stable counting sort.  When the
+// warp's records fill its buffer (and at the end) it sorts them by key and
+// sweeps the rows: lane 8q + l owns y cell 8w + l and holds the nt window
+// rows of its current origin as nt complex registers; quarter q takes the
+// q-th quarter of the sorted records, so the four quarters cover disjoint,
+// increasing origin ranges.  Moving on to a larger origin, a quarter adds
+// the rows it leaves into the shared tile (no other quarter touches those
+// rows during the sweep); the rows each quarter holds at the end are added
+// quarter by quarter.  The order of every sum follows from the input alone,
+// so the result is bitwise reproducible.
+// ---------------------------------------------------------------------------
+#ifndef LAM_SWEEP_CAP
+#define LAM_SWEEP_CAP 128  // FP32 records per warp buffer (FP64: half)
+#endif
+#ifndef LAM_SWEEP_MINB
+#define LAM_SWEEP_MINB 4  // FP32 blocks per SM the registers are sized for
+#endif
+constexpr int kSweepX = 64, kSweepY = 32, kSweepWarps = kSweepY / 8, kSweepCap = LAM_SWEEP_CAP;
+template <typename T> __host__ __device__ constexpr int sweep_cap() { return sizeof(T) == 4 ? kSweepCap : kSweepCap / 2; }
+// bucket counters per warp: window x origins -(nt - 1) .. kSweepX - 1, padded to a multiple of 32
+__host__ __device__ constexpr int sweep_keys(int mh) { return (kSweepX + 2 * mh - 1 + 31) / 32 * 32; }
+__host__ __device__ constexpr int sweep_line_pitch(int nang) {
+    return ((nang + kSweepWarps - 1) / kSweepWarps + 31) / 32 * 32;
+}
+
+// a point record: value, y fraction, pk = key | (y origin in the band + 16) << 8 | rank << 16, x weights
+template <typename T, int NT> struct alignas(16) SweepRec {
+    T vx, vy, fy;
+    int pk;
+    T wx[NT];
+};
+template <typename T> size_t sweep_rec_bytes(int mh) {
+    switch (mh) {
+        case 2: return sizeof(SweepRec<T, 4>);
+        case 3: return sizeof(SweepRec<T, 6>);
+        case 4: return sizeof(SweepRec<T, 8>);
+        case 5: return sizeof(SweepRec<T, 10>);
+        case 6: return sizeof(SweepRec<T, 12>);
+        case 7: return sizeof(SweepRec<T, 14>);
+        default: return sizeof(SweepRec<T, 16>);
+    }
+}
+template <typename T> size_t spread_sweep_smem(int mh, int nang) {
+    return (size_t)kSweepX * kSweepY * sizeof(C<T>) +
+           (size_t)kSweepWarps * sweep_cap<T>() * (sweep_rec_bytes<T>(mh) + sizeof(unsigned short)) +
+           (size_t)kSweepWarps * sweep_keys(mh) * sizeof(int) + (size_t)kSweepWarps * sweep_line_pitch(nang) * sizeof(int);
+}
+
+template <int NT>
+__device__ __forceinline__ void sweep_load(const SweepRec<float, NT>* r, float& vx, float& vy, float& fy, int& pk,
+                                           float (&w)[NT]) {
+    const float4 h = *reinterpret_cast<const float4*>(r);
+    vx = h.x;
+    vy = h.y;
+    fy = h.z;
+    pk = __float_as_int(h.w);
+    if constexpr (NT % 4 == 0) {
+#pragma unroll
+        for (int k = 0; k < NT / 4; ++k) {
+            const float4 t = reinterpret_cast<const float4*>(r->wx)[k];
+            w[4 * k] = t.x;
+            w[4 * k + 1] = t.y;
+            w[4 * k + 2] = t.z;
+            w[4 * k + 3] = t.w;
+        }
+    } else {
+#pragma unroll
+        for (int t = 0; t < NT; ++t) w[t] = r->wx[t];
+    }
+}
+template <int NT>
+__device__ __forceinline__ void sweep_load(const SweepRec<double, NT>* r, double& vx, double& vy, double& fy, int& pk,
+                                           double (&w)[NT]) {
+    const double2 h = *reinterpret_cast<const double2*>(r);
+    vx = h.x;
+    vy = h.y;
+    fy = r->fy;
+    pk = r->pk;
+#pragma unroll
+    for (int k = 0; k < NT / 2; ++k) {
+        const double2 t = reinterpret_cast<const double2*>(r->wx)[k];
+        w[2 * k] = t.x;
+        w[2 * k + 1] = t.y;
+    }
+}
+
+template <typename T, int MH>
+__global__ void __launch_bounds__(kSweepWarps * 32, sizeof(T) == 4 ? LAM_SWEEP_MINB : 1) k_spread2d_sweep(
+    const C<T>* __restrict__ in, C<T>* __restrict__ P, int j0, Usfft2dArgs<T> a) {
+    constexpr int NT = 2 * MH, SX = kSweepX, SY = kSweepY, CAP = sweep_cap<T>(), NKP = sweep_keys(MH);
+    static_assert(NT <= 16 && SX + NT - 1 < 256, "key and y origin fields of the record");
+    typedef SweepRec<T, NT> Rec;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ int s_nl[kSweepWarps];
+    if (a.memo_hit && a.memo_hit[j0 + blockIdx.y]) return;  // served from the memoization cache (block-uniform)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = lane >> 3, l8 = lane & 7;
+    const unsigned lt = (1u << lane) - 1u;
+    const int lp = sweep_line_pitch(a.T_);
+    C<T>* tile = reinterpret_cast<C<T>*>(smem_raw);  // [SX][SY]
+    unsigned char* sp = smem_raw + (size_t)SX * SY * sizeof(C<T>);
+    Rec* recs = reinterpret_cast<Rec*>(sp) + (size_t)warp * CAP;
+    sp += (size_t)kSweepWarps * CAP * sizeof(Rec);
+    unsigned short* ent = reinterpret_cast<unsigned short*>(sp) + (size_t)warp * CAP;
+    sp += (size_t)kSweepWarps * CAP * sizeof(unsigned short);
+    int* cnt = reinterpret_cast<int*>(sp) + (size_t)warp * NKP;
+    sp += (size_t)kSweepWarps * NKP * sizeof(int);
+    int* lines = reinterpret_cast<int*>(sp);  // [kSweepWarps][lp]
+    for (int i = threadIdx.x; i < SX * SY; i += blockDim.x) tile[i] = cmake<T>(0, 0);
+    for (int i = lane; i < NKP; i += 32) cnt[i] = 0;
+    __syncthreads();
+    // edge tiles may reach past the plane (sides not multiples of the tile):
+    // their outside cells are summed like the others and not written
+    const int tiles_y = (a.M2 + SY - 1) / SY;
+    const int tx0 = ((int)blockIdx.x / tiles_y) * SX, ty0 = ((int)blockIdx.x % tiles_y) * SY;
+    const int2 job = a.jobs[j0 + blockIdx.y];
+    const int ycell = warp * 8 + l8;
+    int nrec = 0;  // warp-uniform
+
+    // adds a held window row (key row = x origin + nt - 1) into the tile if it lies inside
+    auto put = [&](int row, T x, T y) {
+        const int xr = row - (NT - 1);
+        if ((unsigned)xr < (unsigned)SX) {
+            C<T>& c = tile[xr * SY + ycell];
+            c.x += x;
+            c.y += y;
+        }
+    };
+    // sort the warp's records by key and sweep them into the tile
+    auto process = [&]() {
+        constexpr int PER = NKP / 32;
+        int cv[PER], s = 0;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            cv[k] = cnt[lane * PER + k];
+            s += cv[k];
+        }
+        int incl = s;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int run = incl - s;
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            cnt[lane * PER + k] = run;
+            run += cv[k];
+        }
+        __syncwarp();
+        for (int i = lane; i < nrec; i += 32) {
+            const int pk = recs[i].pk;
+            ent[cnt[pk & 0xff] + (pk >> 16)] = (unsigned short)i;
+        }
+        __syncwarp();
+        const int e0 = (nrec * q) >> 2, e1 = (nrec * (q + 1)) >> 2;
+        const int iters = (nrec + 3) >> 2;
+        T ax[NT], ay[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) ax[t] = ay[t] = (T)0;
+        int cur = e0 < e1 ? (recs[ent[e0]].pk & 0xff) : 0;
+        // the quarter's current record; the next one is read while it is applied
+        T vx = 0, vy = 0, fy = 0, w[NT];
+        int pk = 0;
+        if (e0 < e1) sweep_load<NT>(recs + ent[e0], vx, vy, fy, pk, w);
+        for (int it = 0; it < iters; ++it) {
+            const int e = e0 + it;
+            if (e < e1) {
+                T nvx, nvy, nfy, nw[NT];
+                int npk;
+                sweep_load<NT>(recs + ent[e + 1 < e1 ? e + 1 : e], nvx, nvy, nfy, npk, nw);
+                const int key = pk & 0xff;
+                while (cur < key) {
+                    if (key - cur >= NT) {
+#pragma unroll
+                        for (int t = 0; t < NT; ++t) {
+                            put(cur + t, ax[t], ay[t]);
+                            ax[t] = ay[t] = (T)0;
+                        }
+                        cur = key;
+                    } else {
+                        put(cur, ax[0], ay[0]);
+#pragma unroll
+                        for (int t = 0; t < NT - 1; ++t) {
+                            ax[t] = ax[t + 1];
+                            ay[t] = ay[t + 1];
+                        }
+                        ax[NT - 1] = ay[NT - 1] = (T)0;
+                        ++cur;
+                    }
+                }
+                const int dyl = l8 - (((pk >> 8) & 0xff) - 16);
+                T wy = (T)0;
+                if ((unsigned)dyl < (unsigned)NT) {
+                    const T d = fy + (T)(MH - 1 - dyl);
+                    wy = gexp(-d * d * a.inv4beta);
+                }
+                const T px = wy * vx, py = wy * vy;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) {
+                    ax[t] = fma(px, w[t], ax[t]);
+                    ay[t] = fma(py, w[t], ay[t]);
+                }
+                vx = nvx;
+                vy = nvy;
+                fy = nfy;
+                pk = npk;
+#pragma unroll
+                for (int t = 0; t < NT; ++t) w[t] = nw[t];
+            }
+        }
+        __syncwarp();
+        for (int qq = 0; qq < 4; ++qq) {
+            if (q == qq && e0 < e1) {
+#pragma unroll
+                for (int t = 0; t < NT; ++t) put(cur + t, ax[t], ay[t]);
+            }
+            __syncwarp();
+        }
+        for (int i = lane; i < NKP; i += 32) cnt[i] = 0;
+        __syncwarp();
+        nrec = 0;
+    };
+
+    const int kmin = -a.w / 2, kmax = a.w / 2 - 1;
+    const T hx = (T)(SX + 2 * a.m) * (T)0.5, hy = (T)(SY + 2 * a.m) * (T)0.5;
+    // pass 0: the job's own plane; pass 1: its mirror plane (conjugate values
+    // spread around the negated positions)
+    for (int pass = 0; pass < 2; ++pass) {
+        const int kv = pass ? job.y : job.x;
+        if (kv < 0) break;
+        const int kvc = kv - a.h / 2;
+        const T sg = pass ? (T)-1 : (T)1;
+        for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
+            const int bx0 = tx0 + ix * a.M1;
+            for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
+                const int by0 = ty0 + iy * a.M2;
+                const T cx = (T)bx0 + (T)(SX - 1) * (T)0.5, cy = (T)by0 + (T)(SY - 1) * (T)0.5;
+                if (sqrt(cx * cx + cy * cy) > a.rmax + hx + hy) continue;  // block-uniform
+                // list the lines crossing the tile's box (distance test against its support)
+                int n = 0;  // warp-uniform
+                for (int base = 0; base * kSweepWarps < a.T_; base += 32) {
+                    const int th = (base + lane) * kSweepWarps + warp;
+                    bool cross = false;
+                    if (th < a.T_) {
+                        const typename AngleT<T>::type g = a.ang[th];
+                        T Ax, Cx, Ay, Cy;
+                        line_coef(g, kvc, Ax, Cx, Ay, Cy);
+                        const T nrm = sqrt(Ax * Ax + Ay * Ay);
+                        const T nx = -Ay / nrm, ny = Ax / nrm;
+                        const T dist = fabs((sg * cx - Cx) * nx + (sg * cy - Cy) * ny);
+                        cross = dist <= hx * fabs(nx) + hy * fabs(ny) + (T)1;
+                    }
+                    const unsigned mk = __ballot_sync(0xffffffffu, cross);
+                    if (cross) lines[warp * lp + n + __popc(mk & lt)] = th;
+                    n += __popc(mk);
+                }
+                if (lane == 0) s_nl[warp] = n;
+                __syncthreads();
+                // the warp's band box in this pass's positions
+                T bxl = (T)(bx0 - a.m), bxh = (T)(bx0 + SX + a.m - 1);
+                T byl = (T)(by0 + 8 * warp - a.m), byh = (T)(by0 + 8 * warp + 8 + a.m - 1);
+                if (pass) {
+                    const T t0 = -bxh, t1 = -bxl + (T)1, t2 = -byh, t3 = -byl + (T)1;
+                    bxl = t0; bxh = t1; byl = t2; byh = t3;
+                }
+                for (int lw = 0; lw < kSweepWarps; ++lw) {
+                    const int nl = s_nl[lw];
+                    for (int c0 = 0; c0 < nl; c0 += 32) {
+                        const int th = c0 + lane < nl ? lines[lw * lp + c0 + lane] : -1;
+                        int lo = 1, hi = 0;
+                        if (th >= 0) {
+                            const typename AngleT<T>::type g = a.ang[th];
+                            T Ax, Cx, Ay, Cy;
+                            line_coef(g, kvc, Ax, Cx, Ay, Cy);
+                            lo = kmin;
+                            hi = kmax;
+                            clip_line<T>(Ax, Cx, bxl, bxh, lo, hi);
+                            clip_line<T>(Ay, Cy, byl, byh, lo, hi);
+                        }
+                        walk_line_points(th, lo, hi, [&](int tp, int kuc) {
+                            bool ok = tp >= 0;
+                            int ox = 0, oyb = 0;
+                            T fx = 0, fy = 0;
+                            C<T> v = cmake<T>(0, 0);
+                            if (ok)
+                                ok = LAM_INB(kuc + a.w / 2, a.w, a.err, kSiteSpreadIn) && LAM_INB(tp, a.T_, a.err, kSiteSpreadIn);
+                            if (ok) {
+                                const typename AngleT<T>::type g = a.ang[tp];
+                                int jx, jy;
+                                point_pos(g, kuc, kvc, jx, fx, jy, fy);
+                                v = in[((size_t)tp * a.h + kv) * a.w + (kuc + a.w / 2)];
+                                if (pass) {
+                                    jx = -jx - 1;
+                                    jy = -jy - 1;
+                                    fx = (T)1 - fx;
+                                    fy = (T)1 - fy;
+                                    v.y = -v.y;
+                                }
+                                ox = jx - MH + 1 - bx0;
+                                oyb = jy - MH + 1 - by0 - 8 * warp;
+                                ok = ox > -NT && ox < SX && oyb > -NT && oyb < 8;
+                            }
+                            const unsigned mk = __ballot_sync(0xffffffffu, ok);
+                            if (!mk) return;
+                            const int c = __popc(mk);
+                            if (nrec + c > CAP) process();
+                            const int key = ox + NT - 1;
+                            const unsigned peers = __match_any_sync(0xffffffffu, ok ? key : -1);
+                            int rank = 0;
+                            if (ok) rank = cnt[key] + __popc(peers & lt);
+                            __syncwarp();
+                            // the group's lowest lane moves the key's count past the group
+                            if (ok && !(peers & lt)) cnt[key] = rank + __popc(peers);
+                            if (ok) {
+                                Rec* r = recs + nrec + __popc(mk & lt);
+                                r->vx = v.x;
+                                r->vy = v.y;
+                                r->fy = fy;
+                                r->pk = key | ((oyb + 16) << 8) | (rank << 16);
+#pragma unroll
+                                for (int t = 0; t < NT; ++t) {
+                                    const T d = fx + (T)(MH - 1 - t);
+                                    r->wx[t] = gexp(-d * d * a.inv4beta);
+                                }
+                            }
+                            nrec += c;
+                            __syncwarp();
+                        });
+                    }
+                }
+                __syncthreads();  // the line lists are rewritten for the next image
+            }
+        }
+    }
+    if (nrec > 0) process();
+    __syncthreads();
+    C<T>* pl = P + (size_t)blockIdx.y * a.M1 * a.M2;
+    for (int i = threadIdx.x; i < SX * SY; i += blockDim.x) {
+        const int x = i / SY, y = i - x * SY;
+        if (tx0 + x < a.M1 && ty0 + y < a.M2) pl[(size_t)(tx0 + x) * a.M2 + ty0 + y] = tile[i];
+    }
+}
+
 // --------------------------------------------------------------------------
 // launchers
 // --------------------------------------------------------------------------
@@ -1385,7 +1752,8 @@ cudaError_t launch_spread2d(const C<T>* in, C<T>* P, int j0, int nb, const Usfft
         const long long ncells = (long long)nb * a.M1 * a.M2;
         const long long hb = (ncells + 255) / 256;
         k_halo_sum<T><<<(int)(hb < 148 * 8 ? hb : 148 * 8), 256, 0, s>>>(a.halo, P, nb, kSpreadTS + 2 * a.m - 1, a);
-    } else if ((a.spread == kSpreadTiles || a.spread == kSpreadTiles2 || a.spread == kSpreadHalo) && a.TS == kSpreadTS) {
+    } else if ((a.spread == kSpreadTiles || a.spread == kSpreadTiles2 || a.spread == kSpreadHalo ||
+                a.spread == kSpreadSweep) && a.TS == kSpreadTS) {
         // the first a.nacc plane jobs (the centre planes: every slice line
         // passes close to the origin there, so the cells near it sum thousands
         // of nearly equal products, where FP32 running sums round
@@ -1405,7 +1773,16 @@ cudaError_t launch_spread2d(const C<T>* in, C<T>* P, int j0, int nb, const Usfft
         if (nb > nx) {
             const dim3 gt(ntiles, nb - nx);
             C<T>* Pt = P + (size_t)nx * a.M1 * a.M2;
-            if (a.spread == kSpreadTiles2) {
+            const size_t sw = spread_sweep_smem<T>(a.m, a.T_);
+            if (a.spread == kSpreadSweep && sw <= (size_t)kMaxDynSmem - 1024) {
+                const dim3 gw(((a.M1 + kSweepX - 1) / kSweepX) * ((a.M2 + kSweepY - 1) / kSweepY), nb - nx);
+                switch (a.m) {
+#define LAM_W(MH) case MH: k_spread2d_sweep<T, MH><<<gw, kSweepWarps * 32, sw, s>>>(in, Pt, kv0 + nx, a); break;
+                    LAM_W(2) LAM_W(3) LAM_W(4) LAM_W(5) LAM_W(6) LAM_W(7) LAM_W(8)
+#undef LAM_W
+                    default: return cudaErrorInvalidValue;
+                }
+            } else if (a.spread == kSpreadTiles2) {
                 const size_t st = spread_tiles_smem<T>(kSpreadWarps, a.m, false, 2);
                 switch (a.m) {
 #define LAM_T(MH) case MH: k_spread2d_tiles2<T, kSpreadWarps, MH><<<gt, kSpreadWarps * 32, st, s>>>(in, Pt, kv0 + nx, a); break;
@@ -1506,7 +1883,8 @@ template <typename T> cudaError_t configure_usfft2d() {
     if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles<T, kSpreadWarps, MH>, at, mt);    \
     if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles_exact<T, kSpreadWarps, MH>, at, mt); \
     if (!e) e = cudaFuncSetAttribute(k_spread2d_tiles2<T, kSpreadWarps, MH>, at, mt); \
-    if (!e) e = cudaFuncSetAttribute(k_spread2d_halo<T, kScatterWarps, MH>, at, mt);
+    if (!e) e = cudaFuncSetAttribute(k_spread2d_halo<T, kScatterWarps, MH>, at, mt); \
+    if (!e) e = cudaFuncSetAttribute(k_spread2d_sweep<T, MH>, at, kMaxDynSmem - 1024);
     LAM_A(2) LAM_A(3) LAM_A(4) LAM_A(5) LAM_A(6) LAM_A(7) LAM_A(8)
 #undef LAM_A
     return e;

@@ -76,6 +76,7 @@ def lib() -> ctypes.CDLL:
             "lam_forward_batched": [vp, vp, vp, vp],
             "lam_adjoint_batched": [vp, vp, vp, vp],
             "admm_run_batched": [vp, vp, i, i, vp],
+            "lam_batch_set_streams": [vp, i],
             "lamx_batch_info": [vp, ctypes.POINTER(i), i],
             "lamx_spread": [vp, vp, vp, i, i, vp],
             "lamx_jobs_per_batch": [vp],
@@ -140,7 +141,7 @@ class Geometry:
 class Plan:
     """A plan for one geometry and precision ('f32' or 'f64') on the current device."""
 
-    SPREADS = {"tiles": 0, "atomic": 1, "exact": 2, "halo": 3, "tiles_exact": 4, "tiles2": 5}
+    SPREADS = {"tiles": 0, "atomic": 1, "exact": 2, "halo": 3, "tiles_exact": 4, "tiles2": 5, "sweep": 6}
 
     def __init__(self, n, nz, h, w, theta, phi, m=4, prec="f32", device=None, fast_adjoint=False, spread=None,
                  workspace="full"):
@@ -380,11 +381,13 @@ class Plan:
         return lib().lam_plan_status(self._h, _stream())
 
     def info(self):
-        arr = (ctypes.c_int * 13)()
-        _check(lib().lamx_plan_info(self._h, arr, 13), "lamx_plan_info")
+        arr = (ctypes.c_int * 14)()
+        _check(lib().lamx_plan_info(self._h, arr, 14), "lamx_plan_info")
         keys = ["TY_fwd", "TY_adj", "rows_per_block", "cols_per_block", "tile", "images", "planes_per_batch",
-                "jmin", "jmax", "plane_jobs", "gather_tile", "z_threads", "fft_threads"]
-        return dict(zip(keys, list(arr)))
+                "jmin", "jmax", "plane_jobs", "gather_tile", "z_threads", "fft_threads", "spread"]
+        out = dict(zip(keys, list(arr)))
+        out["spread"] = {v: k for k, v in self.SPREADS.items()}[out["spread"]]
+        return out
 
 
 class LamOp(torch.autograd.Function):
@@ -569,8 +572,10 @@ def _ptr_array(items):
 
 
 class Batch:
-    """Several plans run together: every plane-stage step of L_hat / L_hat^H is
-    one persistent launch over all problems (lam_batch_create)."""
+    """Several plans run together (lam_batch_create): every plane-stage step of
+    the batched L_hat / L_hat^H is one persistent launch over all problems;
+    admm_run runs the problems concurrently on side streams by default
+    (set_streams)."""
 
     STAGES = ["z_fwd", "row_fwd", "col_fwd", "gather", "spread", "col_adj", "row_adj", "z_adj"]
 
@@ -616,6 +621,13 @@ class Batch:
                                       _stream()), "admm_run_batched")
         for a in admms:
             a.iters += iters
+
+    def set_streams(self, streams):
+        """Concurrent mode of admm_run (lam_batch_set_streams): 0 = persistent
+        batched stages; k >= 1 = each problem's own outer iteration, problem i
+        on side stream i mod k."""
+        _check(lib().lam_batch_set_streams(self._h, int(streams)), "lam_batch_set_streams")
+        return self
 
     def info(self):
         arr = (ctypes.c_int * 17)()

@@ -90,6 +90,7 @@ def test_batched_admm_equals_single_plan_admm(graph):
     for a in single:
         a.run(3)
     batched = [glam.Admm(p).init(d, 1e-3, 0.5, 3) for p, d in zip(plans, datas)]
+    batch.set_streams(0)  # the persistent batched stages (the default is concurrent)
     if graph:
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
@@ -103,6 +104,61 @@ def test_batched_admm_equals_single_plan_admm(graph):
         assert b.status() == 0
         assert torch.equal(a.u, b.u)
         assert np.array_equal(a.history(), b.history())
+
+
+@pytest.mark.parametrize("streams,graph,prec", [(2, False, "f32"), (4, True, "f32"), (3, True, "f64")],
+                         ids=["2eager", "4graph", "3graph-f64"])
+def test_concurrent_batch_admm_equals_single_plan_admm(streams, graph, prec):
+    # concurrent mode: each problem's own outer iteration on side stream i mod
+    # streams, forked from and joined to the caller's stream; the states must
+    # evolve bitwise as under single-plan runs, whatever the interleaving
+    plans = _plans(prec)
+    batch = glam.Batch(plans).set_streams(streams)
+    datas = []
+    for i, p in enumerate(plans):
+        u = inputs.ellipsoid_phantom(p.n, p.nz, 8, seed=90 + i, device="cuda").to(p.rdtype)
+        datas.append(p.forward(u))
+    single = [glam.Admm(p).init(d, 1e-3, 0.5, 3) for p, d in zip(plans, datas)]
+    for a in single:
+        a.run(3)
+    conc = [glam.Admm(p).init(d, 1e-3, 0.5, 3) for p, d in zip(plans, datas)]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        batch.admm_run(conc, 2, graph=graph)
+        batch.admm_run(conc, 1, graph=graph)
+    s.synchronize()
+    for a, b in zip(single, conc):
+        assert b.status() == 0
+        assert torch.equal(a.u, b.u)
+        assert np.array_equal(a.history(), b.history())
+
+
+def test_concurrent_batch_runs_memoized_and_plain_states_together():
+    # the concurrent mode runs admm_step per problem, so options the
+    # persistent batch refuses (memoization) work, bitwise as single runs
+    plans = _plans("f32", [32, 48])
+    plans[1].set_memo(0.92)
+    datas = [p.forward(inputs.ellipsoid_phantom(p.n, p.nz, 8, seed=95 + i, device="cuda"))
+             for i, p in enumerate(plans)]
+    single = [glam.Admm(p).init(d, 1e-3, 0.5, 2) for p, d in zip(plans, datas)]
+    for a in single:
+        a.run(3)
+    batch = glam.Batch(plans).set_streams(0)
+    conc = [glam.Admm(p).init(d, 1e-3, 0.5, 2) for p, d in zip(plans, datas)]
+    with pytest.raises(glam.LaminoError, match="memoize"):
+        batch.admm_run(conc, 1)
+    conc = [glam.Admm(p).init(d, 1e-3, 0.5, 2) for p, d in zip(plans, datas)]
+    batch.set_streams(2).admm_run(conc, 3)
+    torch.cuda.synchronize()
+    for a, b in zip(single, conc):
+        assert torch.equal(a.u, b.u)
+
+
+def test_concurrent_batch_refuses_a_shared_workspace():
+    p = _plans("f32", [32])[0]
+    with pytest.raises(glam.LaminoError, match="share a workspace"):
+        glam.Batch([p, p]).set_streams(2)
 
 
 def test_batch_rejects_mixed_precision_and_bad_counts():

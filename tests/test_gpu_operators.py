@@ -8,9 +8,10 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import TOL_F32_OP, plan_and_geom, rand_data, rand_vol, rel, tol
+from gpu_helpers import TOL_F32_OP, TOL_F64_OP, plan_and_geom, rand_data, rand_vol, rel, tol
 from oracle import lamino as olam
 from oracle import tv as otv
+from oracle import usfft as ousfft
 from paper_2511_01893_b300 import lamino as glam
 
 pytestmark = pytest.mark.gpu
@@ -44,7 +45,7 @@ def test_u1d_forward_and_adjoint(geom, prec):
     assert rel(got, ref) < tol(prec)
 
 
-@pytest.mark.parametrize("spread", ["tiles", "halo", "atomic", "exact", "tiles_exact", "tiles2"])
+@pytest.mark.parametrize("spread", ["tiles", "halo", "atomic", "exact", "tiles_exact", "tiles2", "sweep"])
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 @pytest.mark.parametrize("geom", GEOMS, ids=IDS)
 def test_u2d_forward_and_adjoint(geom, prec, spread):
@@ -133,7 +134,7 @@ def test_adjoint_spread_variants_other_widths(m):
     plan, g = plan_and_geom(n, nz, h, w, T, 0.5, "f32", m=m)
     d = rand_data(T, h, w, 18)
     ref = olam.f_u2d_adj(d, g)
-    for spread in ("tiles", "halo", "atomic", "exact", "tiles_exact", "tiles2"):
+    for spread in ("tiles", "halo", "atomic", "exact", "tiles_exact", "tiles2", "sweep"):
         p = glam.Plan(n, nz, h, w, plan.theta, 0.5, m=m, prec="f32", spread=spread)
         got = p.u2d_adj(torch.from_numpy(d)).cpu().numpy().transpose(1, 0, 2)
         assert rel(got, ref) < tol("f32"), spread
@@ -157,6 +158,10 @@ def test_adjoint_spreads_are_bitwise_reproducible():
     s1, s2 = h2.adjoint(d), h2.adjoint(d)
     assert torch.equal(s1, s2)
     assert rel(s1, e1) < 2e-6
+    sw = glam.Plan(n, nz, h, w, plan.theta, 0.5, prec="f32", spread="sweep")
+    w1, w2 = sw.adjoint(d), sw.adjoint(d)
+    assert torch.equal(w1, w2)
+    assert rel(w1, e1) < 2e-6
     # the same products formed in another order (wx (wy v) against wy (wx v)): ~1 ulp apart
     assert rel(t1, e1) < 3e-7
     fast = glam.Plan(n, nz, h, w, plan.theta, 0.5, prec="f32", fast_adjoint=True)
@@ -165,6 +170,30 @@ def test_adjoint_spreads_are_bitwise_reproducible():
     ref = olam.lam_adjoint(d.cpu().numpy(), g)
     assert rel(a, ref) < 1e-5
     assert rel(e1, ref) < 1e-5
+
+
+@pytest.mark.parametrize("prec,m", [("f32", 4), ("f32", 8), ("f64", 4), ("f64", 8)])
+def test_sweep_spread_on_dense_planes_matches_exact_sums(prec, m):
+    # 360 lines through the middle of the centre planes: thousands of records
+    # per warp band there, so the row sweep fills and sorts its record buffer
+    # many times; the exact centre jobs are off, so every plane job sweeps.
+    # Reference (oracle-pinned in the tests above): in FP32 the tile spread
+    # with exact fixed-point sums; in FP64 the plain tile spread, since the
+    # fixed-point grid (step ~ 2^-61 x a bound on the cell sums, per product,
+    # growing with the window) is coarser than FP64 rounding for small cells.
+    n, nz, h, w, T = 128, 32, 128, 128, 360
+    plan, g = plan_and_geom(n, nz, h, w, T, 0.5, prec, m=m)
+    d = torch.from_numpy(rand_data(T, h, w, 21)).cuda()
+    ex = glam.Plan(n, nz, h, w, plan.theta, 0.5, m=m, prec=prec, spread="tiles_exact" if prec == "f32" else "tiles")
+    sw = glam.Plan(n, nz, h, w, plan.theta, 0.5, m=m, prec=prec, spread="sweep").set_exact_centre_jobs(0)
+    a, b = sw.u2d_adj(d), ex.u2d_adj(d)
+    assert torch.equal(a, sw.u2d_adj(d))
+    assert rel(a, b) < (2e-6 if prec == "f32" else TOL_F64_OP)
+    # the centre plane alone (every line passes its origin) against the oracle
+    xi_x, xi_y, _ = olam.slice_frequencies(g)
+    c = h // 2
+    ref = ousfft.usfft2d_type1(d.cpu().numpy()[:, c, :], xi_x[:, c, :], xi_y[:, c, :], n, n, g.m, g.R)
+    assert rel(a[c].cpu().numpy(), ref) < tol(prec)
 
 
 @pytest.mark.parametrize("n", [48, 64])
