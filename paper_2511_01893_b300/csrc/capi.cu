@@ -887,11 +887,11 @@ template <typename T> lam_status batch_build(lam_batch* b) {
         const int nacc = std::min(q->nacc, nj);  // centre jobs the exact spread takes (own launches)
         H->a2[i].nacc = nacc;
         const int gy[kBStages] = {1, nj, nj, nj, nj - nacc, nj, nj, 1};
-        const int gz[kBStages] = {1, 1, 1, 2, 1, 1, 1, 1};
+        const int gz[kBStages] = {1, 1, 1, 1, 1, 1, 1, 1};
         const size_t sm[kBStages] = {(size_t)q->TYf * fpad_len(q->nz) * ce,
                                      (size_t)q->RB * fpad_len(q->M2) * ce,
                                      (size_t)q->CB * fpad_len(q->M1) * ce,
-                                     (size_t)(q->TG + 2 * q->m - 1) * (q->TG + 2 * q->m + 1) * ce,
+                                     gather_smem_bytes<T>(q->TG, q->m),
                                      spread_tiles_bytes<T>(q->m),
                                      (size_t)q->CB * fpad_len(q->M1) * ce,
                                      (size_t)q->RB * fpad_len(q->M2) * ce,

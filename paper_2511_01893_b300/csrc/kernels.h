@@ -98,6 +98,12 @@ template <typename T> struct Usfft2dArgs {
 // jobs[j].x and, if jobs[j].y >= 0, its mirror plane from the same padded FFT
 // (P_mirror[j] = conj P[-j]).  If sub != nullptr the output is the value minus
 // sub (same layout as out).
+// shared memory of one tiled-gather block: the tile of window origins plus
+// the (2m - 1) halo and one more row and column below (the shifted windows of
+// mirror points next to grid nodes), rows padded to an odd stride
+template <typename T> constexpr size_t gather_smem_bytes(int tg, int m) {
+    return (size_t)(tg + 2 * m) * (size_t)(tg + 2 * m + 1) * sizeof(C<T>);
+}
 template <typename T>
 cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* sub, int kv0, int nb,
                                const Usfft2dArgs<T>& a, cudaStream_t s);

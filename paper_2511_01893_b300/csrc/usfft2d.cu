@@ -15,13 +15,16 @@
 //                      the current one is transformed
 //   k_gather2d_tiled   a 64 x 64 tile of P (+ halo) staged in shared memory,
 //                      one lane per slice point: 64 taps, optional fused
-//                      subtraction (out = value - sub, Section 4.2)
+//                      subtraction (out = value - sub, Section 4.2); a paired
+//                      job's mirror-plane point is the conjugate of its
+//                      partner's sum, so each pair is summed once
 // Transpose (type 1):
 //   k_spread2d_tiles   (default) a block owns a 32 x 32 tile of the padded
 //                      plane; each of its warps sums the slice points whose
 //                      windows meet the tile into a private tile, and the
 //                      warp tiles are added in a fixed order: no atomics,
-//                      bitwise reproducible
+//                      bitwise reproducible; a paired job's two planes share
+//                      one record per pair of mirror points
 //   k_spread2d_halo, k_scatter2d_atomic   options (owner tiles with a halo
 //                      pass; shared-memory atomics, plain or exact fixed point)
 //   k_colfft_adj_pipe  inverse FFT along x, keep the n1 rows the crop needs
@@ -385,12 +388,14 @@ __device__ __forceinline__ void walk_line_points(int th, int lo, int hi, F&& fn)
 // ---------------------------------------------------------------------------
 template <typename T, int NW, typename F>
 __device__ __forceinline__ void for_tile_points(const Usfft2dArgs<T>& a, int kvc, T cx, T cy, T hbox,
-                                                T bxmin, T bxmax, T bymin, T bymax, int w, F&& fn) {
+                                                T bxmin, T bxmax, T bymin, T bymax, int w, int kext, F&& fn) {
     __shared__ int s_lines[NW][64];
     int* list = s_lines[w];
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
-    const int kmin = -a.w / 2, kmax = a.w / 2 - 1;
+    // kext = 1 adds the point ku = w/2 past each line's end (the partner of
+    // the mirror plane's ku = -w/2 point in the paired operators)
+    const int kmin = -a.w / 2, kmax = a.w / 2 - 1 + kext;
     // clip up to 32 listed lines (lane i takes list[i]) and enumerate their points
     auto flush = [&](int count) {
         const int th = lane < count ? list[lane] : -1;
@@ -440,17 +445,31 @@ __device__ __forceinline__ void for_tile_points(const Usfft2dArgs<T>& a, int kvc
 
 // Tiled gather: one block per TS x TS tile of tap-window origins.  The block
 // stages its tile plus a (2m - 1) halo of the padded plane in shared memory
-// and evaluates exactly the points whose window origin (j0 - m + 1 in both
-// axes, unwrapped) falls in the tile or one of its periodic images, one point
-// per lane, with the slice lines dealt to the warps and each warp's point
-// list flattened across lines.  Each point is
-// owned by exactly one (tile, image), so every output is written once.
+// (and one more row and column on the low side, below) and evaluates exactly
+// the points whose window origin (j0 - m + 1 in both axes, unwrapped) falls in
+// the tile or one of its periodic images, one point per lane, with the slice
+// lines dealt to the warps and each warp's point list flattened across lines.
+// Each point is owned by exactly one (tile, image), so every output is
+// written once.
+//
+// Paired jobs (real volumes): the mirror plane -kv is the conjugate mirror of
+// this plane's padded FFT, P_mirror[j] = conj P[-j], and its slice point
+// (theta, -ku, -kv) sits at exactly the negated position of this plane's point
+// (theta, ku, kv).  Where the two tap windows mirror (j0' = -j0 - 1 on both
+// axes) the mirror point's value is conj of this point's sum, so each pair is
+// summed once.  Where a position lies within the tap shift of a grid node the
+// mirror point's window is this one shifted down by one cell; it is summed
+// separately over the staged cells one row / column below, which is what the
+// extra low row and column are for.  The mirror point ku = -w/2 has no partner
+// among this plane's points: its partner is the point ku = w/2 one step past
+// the line's end, which the enumeration adds for paired jobs (it has no output
+// of its own).
 template <typename T, int TPB, int MH>
-__device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P, C<T>* __restrict__ out, const C<T>* __restrict__ sub, int j0, const Usfft2dArgs<T>& a, int bx, int by, int bz) {
+__device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P, C<T>* __restrict__ out, const C<T>* __restrict__ sub, int j0, const Usfft2dArgs<T>& a, int bx, int by) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int nt = 2 * MH;
     const int TS = a.TG;
-    const int SH = TS + nt - 1;  // staged rows
+    const int SH = TS + nt;      // staged rows: window origins tx0 - 1 .. tx0 + TS - 1
     const int SW = TS + nt + 1;  // staged row stride (odd: lanes two rows apart hit different banks)
     const int warp = threadIdx.x >> 5;
     const int tiles_y = a.M2 / TS;
@@ -459,21 +478,57 @@ __device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P
     const int tx0 = (tile / tiles_y) * TS, ty0 = (tile % tiles_y) * TS;
     const int b = by;
     const int2 job = a.jobs[j0 + b];
-    const bool mirror = bz == 1;  // the conjugate-mirror plane of this job
-    if (mirror && job.y < 0) return;
-    const int kv = mirror ? job.y : job.x, kvc = kv - a.h / 2;
+    const bool paired = job.y >= 0;
+    const int kv = job.x, kvc = kv - a.h / 2;
     const C<T>* pl = P + (size_t)b * a.M1 * a.M2;
-    // P_mirror[j] = conj P[-j]: the mirror plane stages P[-j] and conjugates
-    // the result (the weights are real, so sum w conj P = conj sum w P,
-    // bitwise)
     for (int i = threadIdx.x; i < SH * SH; i += blockDim.x) {
         const int r = i / SH, c = i - r * SH;
-        const int gx = mirror ? -(tx0 + r) : tx0 + r, gy = mirror ? -(ty0 + c) : ty0 + c;
-        cp_async_elem<T>(st + r * SW + c, pl + (size_t)wrap(gx, a.M1) * a.M2 + wrap(gy, a.M2));
+        cp_async_elem<T>(st + r * SW + c, pl + (size_t)wrap(tx0 - 1 + r, a.M1) * a.M2 + wrap(ty0 - 1 + c, a.M2));
     }
     cp_async_commit();
     cp_async_wait_all();
     __syncthreads();
+    // sum of the (2m)^2 taps whose window starts at staged row sx0, column sy0
+    // (tile-relative origin + 1), at fractions fx, fy
+    auto window_sum = [&](int sx0, int sy0, T fx, T fy) {
+        T wy[nt];
+#pragma unroll
+        for (int t = 0; t < nt; ++t) {
+            const T d = fy + (T)(MH - 1 - t);
+            wy[t] = gexp(-d * d * a.inv4beta);
+        }
+        T sr = 0, si = 0;
+#ifdef LAM_GATHER_KAHAN
+        T csr = 0, csi = 0;
+#endif
+#pragma unroll
+        for (int sx = 0; sx < nt; ++sx) {
+            const T d = fx + (T)(MH - 1 - sx);
+            const T wx = gexp(-d * d * a.inv4beta);
+            const C<T>* rowp = st + (sx0 + sx) * SW + sy0;
+            T rr = 0, ri = 0;
+#pragma unroll
+            for (int t = 0; t < nt; ++t) {
+                const C<T> pv = rowp[t];
+                rr = fma(wy[t], pv.x, rr);
+                ri = fma(wy[t], pv.y, ri);
+            }
+#ifdef LAM_GATHER_KAHAN
+            {
+                const T yr = wx * rr - csr, yi = wx * ri - csi;
+                const T tr = add_rn(sr, yr), ti = add_rn(si, yi);
+                csr = sub_rn(sub_rn(tr, sr), yr);
+                csi = sub_rn(sub_rn(ti, si), yi);
+                sr = tr;
+                si = ti;
+            }
+#else
+            sr = fma(wx, rr, sr);
+            si = fma(wx, ri, si);
+#endif
+        }
+        return cmake<T>(sr, si);
+    };
     const T hb = (T)TS * (T)0.5 + (T)1;
     for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
         const int bx0 = tx0 + ix * a.M1;
@@ -483,7 +538,7 @@ __device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P
             const T cx = (T)(bx0 + a.m - 1) + (T)TS * (T)0.5, cy = (T)(by0 + a.m - 1) + (T)TS * (T)0.5;
             if (sqrt(cx * cx + cy * cy) > a.rmax + hb * (T)1.5) continue;
             for_tile_points<T, TPB>(a, kvc, cx, cy, hb, (T)(bx0 + a.m - 1), (T)(bx0 + TS + a.m - 1),
-                               (T)(by0 + a.m - 1), (T)(by0 + TS + a.m - 1), warp, [&](int th, int kuc) {
+                               (T)(by0 + a.m - 1), (T)(by0 + TS + a.m - 1), warp, paired ? 1 : 0, [&](int th, int kuc) {
                 if (th < 0) return;
                 const typename AngleT<T>::type g = a.ang[th];
                 int jx, jy;
@@ -492,51 +547,43 @@ __device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P
                 const int ox = jx - a.m + 1 - bx0, oy = jy - a.m + 1 - by0;
                 if (ox < 0 || ox >= TS || oy < 0 || oy >= TS) return;
                 // the window's last staged row and column
-                if (!(LAM_INB(ox + nt - 1, SH, a.err, kSiteGatherWindow) &&
-                      LAM_INB(oy + nt - 1, SH, a.err, kSiteGatherWindow)))
+                if (!(LAM_INB(ox + nt, SH, a.err, kSiteGatherWindow) &&
+                      LAM_INB(oy + nt, SH, a.err, kSiteGatherWindow)))
                     return;
-                T wy[nt];
-#pragma unroll
-                for (int t = 0; t < nt; ++t) {
-                    const T d = fy + (T)(MH - 1 - t);
-                    wy[t] = gexp(-d * d * a.inv4beta);
+                if (!(LAM_INB(th, a.T_, a.err, kSiteGatherOut))) return;
+                const bool has_p = kuc < a.w / 2;              // a point of this plane (not the one past the end)
+                const bool has_q = paired && kuc > -a.w / 2;   // its partner (theta, -ku) in the mirror plane
+                int jxq = 0, jyq = 0;
+                T fxq = 0, fyq = 0;
+                bool mir = true;
+                if (has_q) {
+                    point_pos(g, -kuc, -kvc, jxq, fxq, jyq, fyq);
+                    mir = jxq == -jx - 1 && jyq == -jy - 1;
                 }
-                T sr = 0, si = 0;
-#ifdef LAM_GATHER_KAHAN
-                T csr = 0, csi = 0;
-#endif
-#pragma unroll
-                for (int sx = 0; sx < nt; ++sx) {
-                    const T d = fx + (T)(MH - 1 - sx);
-                    const T wx = gexp(-d * d * a.inv4beta);
-                    const C<T>* rowp = st + (ox + sx) * SW + oy;
-                    T rr = 0, ri = 0;
-#pragma unroll
-                    for (int t = 0; t < nt; ++t) {
-                        const C<T> pv = rowp[t];
-                        rr = fma(wy[t], pv.x, rr);
-                        ri = fma(wy[t], pv.y, ri);
-                    }
-#ifdef LAM_GATHER_KAHAN
-                    {
-                        const T yr = wx * rr - csr, yi = wx * ri - csi;
-                        const T tr = add_rn(sr, yr), ti = add_rn(si, yi);
-                        csr = sub_rn(sub_rn(tr, sr), yr);
-                        csi = sub_rn(sub_rn(ti, si), yi);
-                        sr = tr;
-                        si = ti;
-                    }
-#else
-                    sr = fma(wx, rr, sr);
-                    si = fma(wx, ri, si);
-#endif
+                C<T> vp = cmake<T>(0, 0);
+                if (has_p || (has_q && mir)) vp = window_sum(ox + 1, oy + 1, fx, fy);
+                if (has_p) {
+                    const size_t o = ((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2);
+                    C<T> v = vp;
+                    if (sub) v = csub(v, sub[o]);
+                    out[o] = v;
                 }
-                const size_t o = ((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2);
-                if (!(LAM_INB(kuc + a.w / 2, a.w, a.err, kSiteGatherOut) && LAM_INB(th, a.T_, a.err, kSiteGatherOut)))
-                    return;
-                C<T> v = cmake<T>(sr, mirror ? -si : si);
-                if (sub) v = csub(v, sub[o]);
-                out[o] = v;
+                if (has_q) {
+                    if (!mir) {
+                        // the mirror window in this plane's grid: origin -j0' - m,
+                        // fraction 1 - fr' (one cell below this point's window)
+                        const int sxq = (-jxq - 1) - a.m + 1 - bx0 + 1, syq = (-jyq - 1) - a.m + 1 - by0 + 1;
+                        if (!(LAM_INB(sxq, TS + 1, a.err, kSiteGatherWindow) &&
+                              LAM_INB(syq, TS + 1, a.err, kSiteGatherWindow)))
+                            return;
+                        if ((unsigned)sxq > (unsigned)TS || (unsigned)syq > (unsigned)TS) return;
+                        vp = window_sum(sxq, syq, (T)1 - fxq, (T)1 - fyq);
+                    }
+                    const size_t o = ((size_t)th * a.h + job.y) * a.w + (a.w / 2 - kuc);
+                    C<T> v = cconj(vp);
+                    if (sub) v = csub(v, sub[o]);
+                    out[o] = v;
+                }
             });
         }
     }
@@ -545,7 +592,7 @@ __device__ __forceinline__ void k_gather2d_tiled_body(const C<T>* __restrict__ P
 template <typename T, int TPB, int MH>
 __global__ void __launch_bounds__(TPB * 32) k_gather2d_tiled(const C<T>* __restrict__ P, C<T>* __restrict__ out,
                                                              const C<T>* __restrict__ sub, int j0, Usfft2dArgs<T> a) {
-    k_gather2d_tiled_body<T, TPB, MH>(P, out, sub, j0, a, (int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z);
+    k_gather2d_tiled_body<T, TPB, MH>(P, out, sub, j0, a, (int)blockIdx.x, (int)blockIdx.y);
 }
 
 // Cells are stored planar (real parts, then imaginary parts) with the column
@@ -679,7 +726,7 @@ __global__ void __launch_bounds__(TPB * 32, TPB >= 16 ? (sizeof(T) == 4 ? 2 : 1)
                     const T t0 = -bxh, t1 = -bxl + (T)1, t2 = -byh, t3 = -byl + (T)1;
                     bxl = t0; bxh = t1; byl = t2; byh = t3;
                 }
-                for_tile_points<T, TPB>(a, kvc, sg * cx, sg * cy, hb, bxl, bxh, byl, byh, warp, [&](int th, int kuc) {
+                for_tile_points<T, TPB>(a, kvc, sg * cx, sg * cy, hb, bxl, bxh, byl, byh, warp, 0, [&](int th, int kuc) {
                     if (th < 0) return;
                     const typename AngleT<T>::type g = a.ang[th];
                     int jx, jy;
@@ -863,123 +910,143 @@ __device__ __forceinline__ void k_spread2d_tiles_body(const C<T>* __restrict__ i
     const unsigned wyv_ad = (unsigned)__cvta_generic_to_shared(r_wyv + sy * kRecPitch);
     const Rec* rec_lane = r_rec + (size_t)rrc * kRecPitch;
     const unsigned lt = (1u << lane) - 1u;
-    // pass 0: the job's own plane; pass 1: its mirror plane (conjugate values
-    // spread around the negated positions, as in the atomic kernel)
-    for (int pass = 0; pass < 2; ++pass) {
-        const int kv = pass ? job.y : job.x;
-        if (kv < 0) break;
-        const int kvc = kv - a.h / 2;
-        const T sg = pass ? (T)-1 : (T)1;
-        for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
-            const int bx0 = tx0 + ix * a.M1;
-            for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
-                const int by0 = ty0 + iy * a.M2;
-                const T cx = (T)bx0 + (T)(TS - 1) * (T)0.5, cy = (T)by0 + (T)(TS - 1) * (T)0.5;
-                if (sqrt(cx * cx + cy * cy) > a.rmax + hb * (T)1.5) continue;
-                T bxl = (T)(bx0 - a.m), bxh = (T)(bx0 + TS + a.m - 1);
-                T byl = (T)(by0 - a.m), byh = (T)(by0 + TS + a.m - 1);
-                if (pass) {
-                    const T t0 = -bxh, t1 = -bxl + (T)1, t2 = -byh, t3 = -byl + (T)1;
-                    bxl = t0; bxh = t1; byl = t2; byh = t3;
-                }
-                for_tile_points<T, NW>(a, kvc, sg * cx, sg * cy, hb, bxl, bxh, byl, byh, warp, [&](int th, int kuc) {
-                    bool ok = th >= 0;
-                    int ox = 0, oy = 0;
-                    T fx = 0, fy = 0;
-                    C<T> v = cmake<T>(0, 0);
-                    if (ok)
-                        ok = LAM_INB(kuc + a.w / 2, a.w, a.err, kSiteSpreadIn) && LAM_INB(th, a.T_, a.err, kSiteSpreadIn);
-                    if (ok) {
-                        const typename AngleT<T>::type g = a.ang[th];
-                        int jx, jy;
-                        point_pos(g, kuc, kvc, jx, fx, jy, fy);
-                        v = in[((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2)];
-                        if (pass) {
-                            jx = -jx - 1;
-                            jy = -jy - 1;
-                            fx = (T)1 - fx;
-                            fy = (T)1 - fy;
-                            v.y = -v.y;
-                        }
-                        ox = jx - MH + 1 - bx0;
-                        oy = jy - MH + 1 - by0;
-                        ok = !(ox <= -nt || ox >= TS || oy <= -nt || oy >= TS);
-                    }
-                    const unsigned mask = __ballot_sync(0xffffffffu, ok);
-                    if (!mask) return;
-                    if (ok) {
-                        const int k = __popc(mask & lt);  // compacted record index
+    // One pass over this plane's points.  For a paired job the mirror plane's
+    // point (theta, -ku, -kv) sits at exactly the negated position of this
+    // plane's point (theta, ku, kv), and the mirror plane lands in this grid
+    // conjugated around -position: where the two tap windows mirror
+    // (j0' = -j0 - 1 on both axes) its conj(value) joins this point's value in
+    // one record.  Where a position lies within the tap shift of a grid node the
+    // mirror window is this one shifted down by a cell; those mirror points get
+    // records of their own (origin -j0' - m, fraction 1 - fr').  The point
+    // ku = w/2 past each line's end (no value of its own) carries the mirror
+    // plane's ku = -w/2 point.
+    const bool paired = job.y >= 0;
+    const int kv = job.x, kvc = kv - a.h / 2;
+    // writes one record per lane with ok set (compacted in lane order) and adds
+    // the records' windows into the warp's tile(s)
+    auto emit = [&](bool ok, int ox, int oy, T fx, T fy, C<T> v) {
+        const unsigned mask = __ballot_sync(0xffffffffu, ok);
+        if (!mask) return;
+        if (ok) {
+            const int k = __popc(mask & lt);  // compacted record index
 #pragma unroll
-                        for (int t = 0; t < nt; ++t) {
-                            const T dy = fy + (T)(MH - 1 - t);
-                            const T wy = gexp(-dy * dy * a.inv4beta);
-                            r_wyv[t * kRecPitch + k] = cmake<T>(wy * v.x, wy * v.y);
-                        }
-#pragma unroll
-                        for (int r = 0; r < RPP; ++r) {
-                            Rec rc;
-#pragma unroll
-                            for (int q = 0; q < NPASS; ++q) {
-                                const int t = q * RPP + r;
-                                const T dx = fx + (T)(MH - 1 - t);
-                                rc.wx[q] = t < nt ? gexp(-dx * dx * a.inv4beta) : (T)0;
-                            }
-                            rc.ox = ox;
-                            rc.oy = oy;
-                            r_rec[r * kRecPitch + k] = rc;
-                        }
-                    }
-                    __syncwarp();
-                    const int cnt = __popc(mask);
-                    // sub-warp hw takes records hw, hw + SPLIT, ...; the value
-                    // records are complex T whatever the tile cells are
-                    constexpr unsigned kRecCell = sizeof(C<T>);
-                    const int k0 = hw < cnt ? hw : cnt - 1;
-                    Rec rc = rec_lane[k0];
-                    C<T> wv;
-                    lds_c(wyv_ad + k0 * kRecCell, wv);
-                    for (int kk = 0; kk < cnt; kk += SPLIT) {
-                        const int k = kk + hw;
-                        const bool kon = SPLIT == 1 || k < cnt;
-                        // read the next record first (its latency overlaps the update)
-                        const int kn = k + SPLIT < cnt ? k + SPLIT : (kon ? k : cnt - 1);
-                        const Rec nrc = rec_lane[kn];
-                        C<T> nwv;
-                        lds_c(wyv_ad + kn * kRecCell, nwv);
-                        const int2 o = make_int2(rc.ox, rc.oy);
-                        const int cx0 = o.x + rrc, ccy = o.y + sy;
-                        const int col = EXACT ? ccy : ccy ^ ((cx0 & 1) << 3);
-                        const unsigned ad0 = tile_ad + (unsigned)(cx0 * TS + col) * kCell;
-                        const bool yok = lane_on && (unsigned)ccy < (unsigned)TS;
-#pragma unroll
-                        for (int q = 0; q < NPASS; ++q) {
-                            const int row = cx0 + q * RPP;
-                            // rows q * RPP apart: same swizzle when RPP is even
-                            const unsigned ad = (!EXACT && ((q * RPP) & 1))
-                                                    ? tile_ad + (unsigned)(row * TS + (col ^ 8)) * kCell
-                                                    : ad0 + (unsigned)(q * RPP * TS) * kCell;
-                            if (kon && yok && q * RPP + rr < nt && (unsigned)row < (unsigned)TS) {
-                                if constexpr (EXACT) {
-                                    long long xr, xi;
-                                    lds_ll2(ad, xr, xi);
-                                    xr += fixed_ll(rc.wx[q] * wv.x * fscale);
-                                    xi += fixed_ll(rc.wx[q] * wv.y * fscale);
-                                    sts_ll2(ad, xr, xi);
-                                } else {
-                                    C<T> acc;
-                                    lds_c(ad, acc);
-                                    acc.x = fma(rc.wx[q], wv.x, acc.x);
-                                    acc.y = fma(rc.wx[q], wv.y, acc.y);
-                                    sts_c(ad, acc);
-                                }
-                            }
-                        }
-                        __syncwarp();
-                        rc = nrc;
-                        wv = nwv;
-                    }
-                });
+            for (int t = 0; t < nt; ++t) {
+                const T dy = fy + (T)(MH - 1 - t);
+                const T wy = gexp(-dy * dy * a.inv4beta);
+                r_wyv[t * kRecPitch + k] = cmake<T>(wy * v.x, wy * v.y);
             }
+#pragma unroll
+            for (int r = 0; r < RPP; ++r) {
+                Rec rc;
+#pragma unroll
+                for (int q = 0; q < NPASS; ++q) {
+                    const int t = q * RPP + r;
+                    const T dx = fx + (T)(MH - 1 - t);
+                    rc.wx[q] = t < nt ? gexp(-dx * dx * a.inv4beta) : (T)0;
+                }
+                rc.ox = ox;
+                rc.oy = oy;
+                r_rec[r * kRecPitch + k] = rc;
+            }
+        }
+        __syncwarp();
+        const int cnt = __popc(mask);
+        // sub-warp hw takes records hw, hw + SPLIT, ...; the value
+        // records are complex T whatever the tile cells are
+        constexpr unsigned kRecCell = sizeof(C<T>);
+        const int k0 = hw < cnt ? hw : cnt - 1;
+        Rec rc = rec_lane[k0];
+        C<T> wv;
+        lds_c(wyv_ad + k0 * kRecCell, wv);
+        for (int kk = 0; kk < cnt; kk += SPLIT) {
+            const int k = kk + hw;
+            const bool kon = SPLIT == 1 || k < cnt;
+            // read the next record first (its latency overlaps the update)
+            const int kn = k + SPLIT < cnt ? k + SPLIT : (kon ? k : cnt - 1);
+            const Rec nrc = rec_lane[kn];
+            C<T> nwv;
+            lds_c(wyv_ad + kn * kRecCell, nwv);
+            const int2 o = make_int2(rc.ox, rc.oy);
+            const int cx0 = o.x + rrc, ccy = o.y + sy;
+            const int col = EXACT ? ccy : ccy ^ ((cx0 & 1) << 3);
+            const unsigned ad0 = tile_ad + (unsigned)(cx0 * TS + col) * kCell;
+            const bool yok = lane_on && (unsigned)ccy < (unsigned)TS;
+#pragma unroll
+            for (int q = 0; q < NPASS; ++q) {
+                const int row = cx0 + q * RPP;
+                // rows q * RPP apart: same swizzle when RPP is even
+                const unsigned ad = (!EXACT && ((q * RPP) & 1))
+                                        ? tile_ad + (unsigned)(row * TS + (col ^ 8)) * kCell
+                                        : ad0 + (unsigned)(q * RPP * TS) * kCell;
+                if (kon && yok && q * RPP + rr < nt && (unsigned)row < (unsigned)TS) {
+                    if constexpr (EXACT) {
+                        long long xr, xi;
+                        lds_ll2(ad, xr, xi);
+                        xr += fixed_ll(rc.wx[q] * wv.x * fscale);
+                        xi += fixed_ll(rc.wx[q] * wv.y * fscale);
+                        sts_ll2(ad, xr, xi);
+                    } else {
+                        C<T> acc;
+                        lds_c(ad, acc);
+                        acc.x = fma(rc.wx[q], wv.x, acc.x);
+                        acc.y = fma(rc.wx[q], wv.y, acc.y);
+                        sts_c(ad, acc);
+                    }
+                }
+            }
+            __syncwarp();
+            rc = nrc;
+            wv = nwv;
+        }
+    };
+    for (int ix = -a.nimg; ix <= a.nimg; ++ix) {
+        const int bx0 = tx0 + ix * a.M1;
+        for (int iy = -a.nimg; iy <= a.nimg; ++iy) {
+            const int by0 = ty0 + iy * a.M2;
+            const T cx = (T)bx0 + (T)(TS - 1) * (T)0.5, cy = (T)by0 + (T)(TS - 1) * (T)0.5;
+            if (sqrt(cx * cx + cy * cy) > a.rmax + hb * (T)1.5) continue;
+            // positions whose window (or, paired, the mirror window one cell
+            // below it) reaches the tile image
+            const T bxl = (T)(bx0 - a.m), bxh = (T)(bx0 + TS + a.m - 1 + (paired ? 1 : 0));
+            const T byl = (T)(by0 - a.m), byh = (T)(by0 + TS + a.m - 1 + (paired ? 1 : 0));
+            for_tile_points<T, NW>(a, kvc, cx, cy, hb, bxl, bxh, byl, byh, warp, paired ? 1 : 0, [&](int th, int kuc) {
+                bool ok = th >= 0;
+                if (ok) ok = LAM_INB(th, a.T_, a.err, kSiteSpreadIn);
+                const bool has_p = ok && kuc < a.w / 2;
+                const bool has_q = ok && paired && kuc > -a.w / 2;
+                int ox = 0, oy = 0, oxq = 0, oyq = 0;
+                T fx = 0, fy = 0, fxq = 0, fyq = 0;
+                C<T> v = cmake<T>(0, 0), vq = cmake<T>(0, 0);
+                bool mir = true;
+                if (ok) {
+                    const typename AngleT<T>::type g = a.ang[th];
+                    int jx, jy;
+                    point_pos(g, kuc, kvc, jx, fx, jy, fy);
+                    ox = jx - MH + 1 - bx0;
+                    oy = jy - MH + 1 - by0;
+                    if (has_p && LAM_INB(kuc + a.w / 2, a.w, a.err, kSiteSpreadIn))
+                        v = in[((size_t)th * a.h + kv) * a.w + (kuc + a.w / 2)];
+                    if (has_q && LAM_INB(a.w / 2 - kuc, a.w, a.err, kSiteSpreadIn)) {
+                        int jxq, jyq;
+                        point_pos(g, -kuc, -kvc, jxq, fxq, jyq, fyq);
+                        mir = jxq == -jx - 1 && jyq == -jy - 1;
+                        vq = in[((size_t)th * a.h + job.y) * a.w + (a.w / 2 - kuc)];
+                        vq.y = -vq.y;
+                        oxq = (-jxq - 1) - MH + 1 - bx0;
+                        oyq = (-jyq - 1) - MH + 1 - by0;
+                        fxq = (T)1 - fxq;
+                        fyq = (T)1 - fyq;
+                        if (mir) {
+                            v.x += vq.x;
+                            v.y += vq.y;
+                        }
+                    }
+                }
+                const bool ok_a = (has_p || (has_q && mir)) && !(ox <= -nt || ox >= TS || oy <= -nt || oy >= TS);
+                emit(ok_a, ox, oy, fx, fy, v);
+                const bool ok_b = has_q && !mir && !(oxq <= -nt || oxq >= TS || oyq <= -nt || oyq >= TS);
+                if (__any_sync(0xffffffffu, ok_b)) emit(ok_b, oxq, oyq, fxq, fyq, vq);
+            });
         }
     }
     __syncthreads();
@@ -1079,7 +1146,7 @@ __device__ __forceinline__ void k_spread2d_halo_body(const C<T>* __restrict__ in
                     const T t0 = -bxh, t1 = -bxl + (T)1, t2 = -byh, t3 = -byl + (T)1;
                     bxl = t0; bxh = t1; byl = t2; byh = t3;
                 }
-                for_tile_points<T, NW>(a, kvc, sg * cx, sg * cy, hb, bxl, bxh, byl, byh, warp, [&](int th, int kuc) {
+                for_tile_points<T, NW>(a, kvc, sg * cx, sg * cy, hb, bxl, bxh, byl, byh, warp, 0, [&](int th, int kuc) {
                     bool ok = th >= 0;
                     int ox = 0, oy = 0;
                     T fx = 0, fy = 0;
@@ -1649,8 +1716,8 @@ cudaError_t launch_usfft2d_fwd(const C<T>* u1, C<T>* P, C<T>* out, const C<T>* s
     }
     constexpr int NW = kGatherWarps;
     const int ntiles = (a.M1 / a.TG) * (a.M2 / a.TG);
-    const size_t sg = (size_t)(a.TG + 2 * a.m - 1) * (a.TG + 2 * a.m + 1) * sizeof(C<T>);
-    const dim3 grid(ntiles, nb, 2);
+    const size_t sg = gather_smem_bytes<T>(a.TG, a.m);
+    const dim3 grid(ntiles, nb);
     switch (a.m) {
 #define LAM_G(MH) case MH: k_gather2d_tiled<T, NW, MH><<<grid, NW * 32, sg, s>>>(P, out, sub, kv0, a); break;
         LAM_G(2) LAM_G(3) LAM_G(4) LAM_G(5) LAM_G(6) LAM_G(7) LAM_G(8)
@@ -1956,9 +2023,9 @@ __global__ void __launch_bounds__(NW * 32) kb_gather(const BatchTable<T>* __rest
             __syncthreads();
             cur = p;
         }
-        const int l = w - st[p], gx = bt->gx[kBGather][p], gy = bt->gy[kBGather][p];
+        const int l = w - st[p], gx = bt->gx[kBGather][p];
         const int t = l / gx;
-        k_gather2d_tiled_body<T, NW, MH>(bt->P[p], (C<T>*)bt->out[p], nullptr, 0, sa, l - t * gx, t % gy, t / gy);
+        k_gather2d_tiled_body<T, NW, MH>(bt->P[p], (C<T>*)bt->out[p], nullptr, 0, sa, l - t * gx, t);
         __syncthreads();
     }
 }
