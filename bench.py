@@ -1054,7 +1054,7 @@ def run_ours(args):
                                f"{planes} kv planes)",
                      "traffic_note": "dram bytes per job from a 512^3 capture, scaled by (n/512)^2 per job",
                      "algorithmic_bytes": spread_bytes, "t_launch_s": t_spread,
-                     "note": "bound by the L1/shared pipe (ncu: 80 % of its peak), not by HBM"},
+                     "note": "bound by the L1/shared pipe (ncu: 74 % of its peak) and instruction issue, not by HBM"},
         "roofline_alu": {"bound": "alu", "unit": "TFLOP/s", "achieved": spread_flops / t_spread / 1e12,
                          "peak": fma / 1e12, "frac": spread_flops / t_spread / fma,
                          "peak_source": "measured FMA probe", "kernel": spread_kernel,
