@@ -77,6 +77,34 @@ def test_lam_forward_adjoint(geom, prec):
 
 
 @pytest.mark.parametrize("prec", ["f32", "f64"])
+def test_forward_hermitian_pairs(prec):
+    """For a real volume the paired gather sums each pair of mirror slice
+    points (theta, ku, kv) / (theta, -ku, -kv) once: where the z, x and y tap
+    windows mirror, L-hat u at the mirror point is bitwise the conjugate of its
+    partner's value.  Where a position lies within the tap shift of a grid
+    node the mirror window is a cell lower and the value is summed on its own,
+    so it differs, as the oracle's does (test_oracle_lamino P5); both kinds
+    match the oracle (test_lam_forward_adjoint)."""
+    n, T = 32, 24
+    plan, g = plan_and_geom(n, n, n, n, T, np.deg2rad(30.0), prec)
+    L = plan.forward_hat(torch.from_numpy(rand_vol(n, n, 8))).cpu().numpy()
+    xi_x, xi_y, xi_z = olam.slice_frequencies(g)
+    kv = np.arange(1, n // 2)[None, :, None]   # the paired planes and their mirrors h - kv
+    ku = np.arange(1, n)[None, None, :]        # partner column w - ku
+    t = np.arange(T)[:, None, None]
+
+    def mirrors(x):
+        return np.floor(-x + ousfft.TAP_SHIFT) == -np.floor(x + ousfft.TAP_SHIFT) - 1
+
+    mir = (mirrors(2 * n * xi_x[t, kv, ku]) & mirrors(2 * n * xi_y[t, kv, ku])
+           & mirrors(2 * n * xi_z[kv[0, :, 0]])[None, :, None])
+    p, q = L[t, kv, ku], L[t, n - kv, n - ku]
+    assert 0.5 < mir.mean() < 1.0
+    assert np.array_equal(q[mir].real, p[mir].real) and np.array_equal(q[mir].imag, -p[mir].imag)
+    assert np.abs(q[~mir] - np.conj(p[~mir])).max() > 1e-9 * np.abs(L).max()
+
+
+@pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_fused_subtraction(prec):
     n, nz, h, w, T, phi = 32, 32, 32, 32, 16, np.deg2rad(30.0)
     plan, g = plan_and_geom(n, nz, h, w, T, phi, prec)

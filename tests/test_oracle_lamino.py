@@ -16,6 +16,7 @@ import pytest
 from oracle import lamino
 from oracle.lamino import Geometry, centred
 from oracle import lamino as olam
+from oracle import usfft
 from paper_2511_01893_b300 import inputs
 
 
@@ -227,3 +228,39 @@ def test_tap_rule_on_grid_nodes_matches_direct_nudft():
     lhs = np.vdot(lamino.lhat_exact(u, g), r).real
     rhs = np.vdot(u, lamino.lhat_adj(r, g)).real
     assert abs(lhs - rhs) / (np.linalg.norm(u) * np.linalg.norm(r)) < 1e-10
+
+
+def test_hermitian_pairs_of_slice_points():
+    """P5: for a real volume the slice point (theta, -ku, -kv) sits at the
+    negated position of (theta, ku, kv), so where all three tap windows mirror
+    (j0(-t) = -j0(t) - 1 for the z, x and y grid positions t) the value there
+    is the conjugate of its partner's value, to rounding.  Where a position
+    lies within the tap shift of a grid node (whole lines at theta in
+    (pi/2)Z; at phi = 30 deg also x at theta = pi/2) the windows differ by a
+    cell, and so do the two values, by no more than the truncation error.
+    The oracle computes every plane from its own padded FFT, so this checks
+    the identity the paired GPU gather and spread are built on."""
+    n, T = 16, 16
+    g = Geometry(n1=n, n0=n, n2=n, h=n, w=n, theta=2 * np.pi * np.arange(T) / T, phi=np.deg2rad(30.0))
+    u = np.random.default_rng(21).standard_normal((n, n, n))
+    L = lamino.lhat(u, g)
+    xi_x, xi_y, xi_z = lamino.slice_frequencies(g)
+    kv = np.arange(1, g.h)[None, :, None]  # partner row h - kv: centred -kv
+    ku = np.arange(1, g.w)[None, None, :]  # partner column w - ku: centred -ku
+    t_idx = np.arange(T)[:, None, None]
+    p, q = L[t_idx, kv, ku], L[t_idx, g.h - kv, g.w - ku]
+    # the partner positions are the exact negatives
+    assert np.array_equal(xi_x[t_idx, g.h - kv, g.w - ku], -xi_x[t_idx, kv, ku])
+    assert np.array_equal(xi_y[t_idx, g.h - kv, g.w - ku], -xi_y[t_idx, kv, ku])
+    assert np.array_equal(xi_z[g.h - kv[0, :, 0]], -xi_z[kv[0, :, 0]])
+
+    def mirrors(t):
+        return np.floor(-t + usfft.TAP_SHIFT) == -np.floor(t + usfft.TAP_SHIFT) - 1
+
+    mir = (mirrors(2 * g.n1 * xi_x[t_idx, kv, ku]) & mirrors(2 * g.n2 * xi_y[t_idx, kv, ku])
+           & mirrors(2 * g.n0 * xi_z[kv[0, :, 0]])[None, :, None])
+    scale = np.abs(L).max()
+    d = np.abs(q - np.conj(p))
+    assert 0.5 < mir.mean() < 1.0
+    assert d[mir].max() < 1e-12 * scale
+    assert 1e-9 * scale < d[~mir].max() < 1e-2 * scale
