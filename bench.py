@@ -449,9 +449,9 @@ def oracle_full_runs(pool, workers, n=None, s_iter=None):
     out = {}
     t0 = time.perf_counter()
     r = pool.apply_async(_oracle_plain_admm)
-    n = 512
-    planes = pool.starmap_async(_oracle_unit, [("plane", n, i) for i in range(n)]).get(timeout=1800)
-    slabs = pool.starmap_async(_oracle_unit, [("slab", n, i) for i in range(n)]).get(timeout=1800)
+    nf = 512  # the size run in full (n is the workload's)
+    planes = pool.starmap_async(_oracle_unit, [("plane", nf, i) for i in range(nf)]).get(timeout=1800)
+    slabs = pool.starmap_async(_oracle_unit, [("slab", nf, i) for i in range(nf)]).get(timeout=1800)
     out["lhat_pair_512_s"] = time.perf_counter() - t0
     out["lhat_pair_512_note"] = (f"one L-hat + L-hat^H at 512^3 (512 kv planes and 512 x-slabs over "
                                  f"{workers} processes), wall time; run in full")
